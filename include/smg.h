@@ -1,0 +1,170 @@
+/*
+ * smg.h -- C ABI of libsmg, a GB300 (sm_103a) staggered multigrid solver.
+ *
+ * The library solves M x = b for the staggered operator M = m + D
+ * (arXiv:2212.12559, Sec. 2.2; naive or HISQ-shaped with Naik links) with
+ * flexible GCR preconditioned by the Kahler-Dirac multigrid K-cycle of
+ * Sec. 2.1 and 2.3 (Table 1), to a relative residual of the full (non-Schur)
+ * operator (Sec. 3.2).
+ *
+ * Conventions shared by every call:
+ *  - A lattice has extents dims = {Lx, Ly, Lz, Lt}, each even and >= 4
+ *    (Kahler-Dirac hypercubes, Sec. 2.2), periodic boundaries.  Site index
+ *    x + Lx*(y + Ly*(z + Lz*t)).
+ *  - A colour field is V x 3 complex numbers, FP64, real/imaginary
+ *    interleaved ([V][3][2] doubles).  A link field is [4][V][3][3] complex
+ *    FP64 (row-major 3x3; entry [mu][x][a][b] links x to x+mu).
+ *  - `where` says where a caller buffer lives: SMG_HOST (pageable or pinned
+ *    host memory) or SMG_DEVICE (device memory on the context's GPU).
+ *  - The caller owns every buffer it passes; the library copies what it
+ *    keeps and never retains a caller pointer after a call returns.
+ *  - Every call returns an smg_status.  On failure smg_last_error() gives a
+ *    one-line reason.  No call aborts the process or traps the GPU.
+ *  - All device work is ordered on the context's stream (smg_set_stream);
+ *    calls return after that work has completed unless stated otherwise.
+ */
+#ifndef SMG_H
+#define SMG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SMG_API __attribute__((visibility("default")))
+#else
+#define SMG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smg_ctx smg_ctx;
+
+typedef enum {
+  SMG_OK = 0,
+  SMG_ERR_ARG = -1,            /* invalid argument or size */
+  SMG_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  SMG_ERR_OOM = -3,            /* device allocation failed */
+  SMG_ERR_STATE = -4,          /* call out of order (e.g. solve before mg_setup) */
+  SMG_ERR_NOT_CONVERGED = -5,  /* iteration cap reached; x holds the best iterate */
+  SMG_ERR_BREAKDOWN = -6,      /* NaN/Inf or zero norm met inside a solver */
+  SMG_ERR_TIMEOUT = -7         /* a bounded device wait gave up */
+} smg_status;
+
+enum { SMG_HOST = 0, SMG_DEVICE = 1 };
+
+/* Precision of the preconditioner (the outer GCR and its residuals are always FP64). */
+enum {
+  SMG_PREC_DOUBLE = 0,   /* FP64 vectors, FP64 links / blocks / stencils */
+  SMG_PREC_SINGLE = 1,   /* FP32 vectors and storage */
+  SMG_PREC_HALF = 2      /* FP32 vectors and arithmetic, FP16 storage with FP32 scales */
+};
+
+#define SMG_MAX_COARSE 3
+
+/* Multigrid parameters; Table 1 of the paper gives the defaults in the comments. */
+typedef struct smg_mg_params {
+  int n_coarse;                    /* coarsenings: 1 = fine+KD+1 coarse level, 2 = one more */
+  int agg[SMG_MAX_COARSE][4];      /* aggregate extents of each coarsening (4^4, then 2^4) */
+  int nvec[SMG_MAX_COARSE];        /* near-null vectors per coarsening; coarse dof = 2*nvec */
+  double setup_tol;                /* CGNE relative residual for near-null vectors: 1e-6 */
+  int setup_maxiter;               /* CGNE iteration cap: 2000 (0 = use phi0 as given) */
+  double inner_tol;                /* inner GCR tolerance on levels >= 1: 0.25 */
+  int inner_maxiter;               /* inner GCR iteration cap: 8 */
+  int smoother_s;                  /* CA-GCR(s) post-smoother length: 8 */
+  int dense_max;                   /* coarsest level solved exactly when its dof <= dense_max */
+  int nkrylov;                     /* outer GCR restart length: 16 */
+  int max_outer;                   /* outer GCR iteration cap */
+  int precision;                   /* SMG_PREC_* of the preconditioner */
+  int use_graph;                   /* 1: replay the K-cycle from a captured CUDA graph */
+} smg_mg_params;
+
+/* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */
+SMG_API void smg_default_params(smg_mg_params* p);
+
+typedef struct smg_solve_info {
+  int converged;          /* 1 when the recomputed residual meets tol */
+  int iterations;         /* outer GCR iterations */
+  int restarts;           /* outer GCR restarts (true-residual recomputations) */
+  double true_residual;   /* ||b - M x|| / ||b|| recomputed in FP64 at exit */
+  double seconds;         /* wall time of the call */
+} smg_solve_info;
+
+/* ---------------------------------------------------------------- lifetime */
+/* Creates a context for one lattice on the current CUDA device. */
+SMG_API int smg_create(const int dims[4], smg_ctx** out);
+SMG_API int smg_destroy(smg_ctx* ctx);
+SMG_API const char* smg_last_error(const smg_ctx* ctx);
+/* Orders all further work on `stream` (a cudaStream_t; NULL = the context's own stream). */
+SMG_API int smg_set_stream(smg_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------------------ problem */
+/* Sec. 2.2 / 3.1: fat links (distance 1) and optional Naik links (distance 3,
+ * NULL for the naive operator) with coefficient c_naik.  Copies the links;
+ * invalidates the KD blocks and the multigrid setup. */
+SMG_API int smg_set_gauge(smg_ctx* ctx, const void* fat, const void* naik, double c_naik, int where);
+/* M = m + D with the given real mass.  Rebuilds the KD blocks (B+m)^{-1}
+ * (Sec. 3.1); keeps the near-null vectors and the coarse operators, which
+ * stay those of the mass they were built with (Sec. 3.2: operators from the
+ * lightest mass are reused for the others). */
+SMG_API int smg_set_mass(smg_ctx* ctx, double mass);
+
+/* Sec. 2.1 / 2.3 / Table 1: builds the hierarchy for the current gauge field
+ * and mass.  phi0[l] is the random start of the near-null CGNE of
+ * coarsening l: nvec[l] fields of the level's size (V*3 complex on the fine
+ * level, V_l*2*nvec[l-1] complex on coarse level l), FP64 interleaved,
+ * [nvec][sites][dof], in `where` memory.  With setup_maxiter = 0 the starts
+ * are used as the near-null vectors unchanged. */
+SMG_API int smg_mg_setup(smg_ctx* ctx, const smg_mg_params* params, const void* const* phi0, int where);
+
+/* Sec. 3.2: solves M x = b to ||b - M x|| <= tol ||b|| (recomputed in FP64).
+ * b, x: V*3 complex FP64.  x is output only (zero initial guess).
+ * Returns SMG_ERR_NOT_CONVERGED (with x the last iterate) at max_outer. */
+SMG_API int smg_solve(smg_ctx* ctx, const void* b, void* x, double tol, int where, smg_solve_info* info);
+
+/* Sec. 3.3: nrhs sources times nshift masses solved together as one batch.
+ * b: [nrhs][V][3]; x: [nshift][nrhs][V][3]; info: nshift*nrhs entries (may be
+ * NULL).  The near-null vectors and coarse operators of the current setup
+ * serve every mass; M and (B+m)^{-1} use each system's own mass. */
+SMG_API int smg_multi_solve(smg_ctx* ctx, int nrhs, const void* b, int nshift, const double* masses, void* x,
+                    double tol, int where, smg_solve_info* info);
+
+/* ------------------------------------------------------ test / bench hooks */
+/* Operators applied to nsys FP64 fields (in/out [nsys][V][3]) in precision
+ * `prec` (SMG_PREC_*; inputs are rounded to it, outputs widened to FP64). */
+enum {
+  SMG_OP_M = 0,      /* m + D                     (Sec. 2.2)          */
+  SMG_OP_MDAG = 1,   /* m - D = M^dag                                  */
+  SMG_OP_KD = 2,     /* (B+m)^{-1}                (Eq. 2, Sec. 3.1)   */
+  SMG_OP_KDDAG = 3,  /* (B+m)^{-dag}                                   */
+  SMG_OP_A = 4,      /* (B+m)^{-1} M              (Eq. 2)             */
+  SMG_OP_ADAG = 5    /* M^dag (B+m)^{-dag}                             */
+};
+SMG_API int smg_apply_fine(smg_ctx* ctx, int op, int prec, int nsys, const void* in, void* out, int where);
+/* Maps (Sec. 2.2): parity, hypercube index, position in hypercube, aggregate
+ * index and position in aggregate for aggregates agg[4]; five int32 arrays of V. */
+SMG_API int smg_get_maps(smg_ctx* ctx, const int agg[4], int* parity, int* kd_block, int* kd_pos, int* agg_idx,
+                 int* agg_pos, int where);
+/* (B+m)^{-1} for the current mass: [V/16][48][48] complex FP64 row-major. */
+SMG_API int smg_get_kd_inverse(smg_ctx* ctx, void* out, int where);
+/* Block-orthonormal near-null vectors of coarsening l: [nvec][sites][dof] FP64. */
+SMG_API int smg_get_null_vectors(smg_ctx* ctx, int l, void* out, int where);
+/* Coarse operator produced by coarsening l: [Vc][N][9][N] FP64 (Sec. 2.1). */
+SMG_API int smg_get_coarse_op(smg_ctx* ctx, int l, void* out, int where);
+/* Restriction / prolongation of coarsening l and the coarse operator of
+ * level l in precision `prec`, on nsys FP64 fields. */
+SMG_API int smg_restrict(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where);
+SMG_API int smg_prolong(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where);
+SMG_API int smg_coarse_apply(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where);
+/* Fermion-force outer product: F_mu(x) = -c eta_mu(x) [Y(x) X(x+k mu)^dag - X(x) Y(x+k mu)^dag]
+ * with k = 1, c = 1 (which = 0, fat links) or k = 3, c = c_naik (which = 1, Naik links).
+ * X, Y: V*3 complex FP64; F: [4][V][3][3] complex FP64. */
+SMG_API int smg_force(smg_ctx* ctx, const void* X, const void* Y, int which, void* F, int where);
+/* Iterations used by the near-null CGNE of coarsening l (max over vectors). */
+SMG_API int smg_setup_iterations(smg_ctx* ctx, int l, int* iters);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMG_H */

@@ -1,0 +1,318 @@
+"""Python binding of libsmg's C ABI (argument marshalling only).
+
+Every numeric step runs inside the CUDA library; this module converts
+numpy arrays (host memory) or torch CUDA tensors (device memory) into
+pointers and back.  There is no fallback: if libsmg.so cannot be loaded the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsmg.so")
+
+SMG_HOST, SMG_DEVICE = 0, 1
+PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
+OP_M, OP_MDAG, OP_KD, OP_KDDAG, OP_A, OP_ADAG = range(6)
+MAX_COARSE = 3
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_STATE",
+          -5: "ERR_NOT_CONVERGED", -6: "ERR_BREAKDOWN", -7: "ERR_TIMEOUT"}
+
+EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", "smg_set_stream",
+           "smg_set_gauge", "smg_set_mass", "smg_mg_setup", "smg_solve", "smg_multi_solve",
+           "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
+           "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
+           "smg_setup_iterations"]
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [
+        ("n_coarse", ctypes.c_int),
+        ("agg", (ctypes.c_int * 4) * MAX_COARSE),
+        ("nvec", ctypes.c_int * MAX_COARSE),
+        ("setup_tol", ctypes.c_double),
+        ("setup_maxiter", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("inner_maxiter", ctypes.c_int),
+        ("smoother_s", ctypes.c_int),
+        ("dense_max", ctypes.c_int),
+        ("nkrylov", ctypes.c_int),
+        ("max_outer", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class SmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsmg.so not found at {path}; build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "smg_default_params": (None, [ctypes.POINTER(MGParams)]),
+        "smg_create": (i, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp)]),
+        "smg_destroy": (i, [vp]),
+        "smg_last_error": (ctypes.c_char_p, [vp]),
+        "smg_set_stream": (i, [vp, vp]),
+        "smg_set_gauge": (i, [vp, vp, vp, d, i]),
+        "smg_set_mass": (i, [vp, d]),
+        "smg_mg_setup": (i, [vp, ctypes.POINTER(MGParams), ctypes.POINTER(vp), i]),
+        "smg_solve": (i, [vp, vp, vp, d, i, ctypes.POINTER(SolveInfo)]),
+        "smg_multi_solve": (i, [vp, i, vp, i, ctypes.POINTER(d), vp, d, i, ctypes.POINTER(SolveInfo)]),
+        "smg_apply_fine": (i, [vp, i, i, i, vp, vp, i]),
+        "smg_get_maps": (i, [vp, ip, ip, ip, ip, ip, ip, i]),
+        "smg_get_kd_inverse": (i, [vp, vp, i]),
+        "smg_get_null_vectors": (i, [vp, i, vp, i]),
+        "smg_get_coarse_op": (i, [vp, i, vp, i]),
+        "smg_restrict": (i, [vp, i, i, i, vp, vp, i]),
+        "smg_prolong": (i, [vp, i, i, i, vp, vp, i]),
+        "smg_coarse_apply": (i, [vp, i, i, i, vp, vp, i]),
+        "smg_force": (i, [vp, vp, vp, i, vp, i]),
+        "smg_setup_iterations": (i, [vp, i, ip]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_params(**kw) -> MGParams:
+    p = MGParams()
+    load().smg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "agg":
+            for l, a in enumerate(v):
+                for mu in range(4):
+                    p.agg[l][mu] = int(a[mu])
+        elif k == "nvec":
+            for l, n in enumerate(v):
+                p.nvec[l] = int(n)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    """(pointer, where) for a complex128 numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if a.is_cuda:
+                return ctypes.c_void_p(a.data_ptr()), SMG_DEVICE
+            return ctypes.c_void_p(a.data_ptr()), SMG_HOST
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous numpy array or a torch tensor")
+    return ctypes.c_void_p(a.ctypes.data), SMG_HOST
+
+
+class Solver:
+    """One lattice context of libsmg."""
+
+    def __init__(self, dims):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.ctx = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        rc = self.lib.smg_create(arr, ctypes.byref(self.ctx))
+        if rc != 0:
+            raise SmgError(rc, f"smg_create failed for {self.dims}")
+        self.params = None
+
+    def close(self):
+        if self.ctx:
+            self.lib.smg_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != 0 and rc not in allow:
+            raise SmgError(rc, self.lib.smg_last_error(self.ctx).decode())
+        return rc
+
+    # -- problem ---------------------------------------------------------------
+    def set_gauge(self, fat, naik=None, c_naik=0.0):
+        fat = _prep(fat)
+        pf, where = _ptr(fat)
+        if naik is not None:
+            naik = _prep(naik)
+            pn, _ = _ptr(naik)
+        else:
+            pn = None
+        self._check(self.lib.smg_set_gauge(self.ctx, pf, pn, float(c_naik), where))
+
+    def set_mass(self, m):
+        self._check(self.lib.smg_set_mass(self.ctx, float(m)))
+
+    def set_stream(self, stream_handle):
+        self._check(self.lib.smg_set_stream(self.ctx, ctypes.c_void_p(stream_handle)))
+
+    def mg_setup(self, params: MGParams, phi0):
+        arrs = [_prep(a) for a in phi0]
+        ptrs = [_ptr(a) for a in arrs]
+        where = ptrs[0][1]
+        arr = (ctypes.c_void_p * len(arrs))(*[p for p, _ in ptrs])
+        self._check(self.lib.smg_mg_setup(self.ctx, ctypes.byref(params), arr, where))
+        self.params = params
+        self._keep = arrs
+
+    def solve(self, b, tol=1e-10, x=None):
+        b = _prep(b)
+        x = _like(b) if x is None else x
+        pb, where = _ptr(b)
+        px, _ = _ptr(x)
+        info = SolveInfo()
+        self._check(self.lib.smg_solve(self.ctx, pb, px, float(tol), where, ctypes.byref(info)), allow=(-5,))
+        return x, info
+
+    def multi_solve(self, b, masses, tol=1e-10, x=None):
+        """b: (nrhs, V, 3); returns x: (nshift, nrhs, V, 3) and a list of infos."""
+        b = _prep(b)
+        nrhs = b.shape[0]
+        masses = np.ascontiguousarray(masses, dtype=np.float64)
+        nshift = masses.size
+        if x is None:
+            x = _like(b, (nshift,) + tuple(b.shape))
+        pb, where = _ptr(b)
+        px, _ = _ptr(x)
+        infos = (SolveInfo * (nrhs * nshift))()
+        mp = masses.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(self.lib.smg_multi_solve(self.ctx, nrhs, pb, nshift, mp, px, float(tol), where, infos),
+                    allow=(-5,))
+        return x, list(infos)
+
+    # -- hooks -------------------------------------------------------------------
+    def apply(self, op, v, prec=PREC_DOUBLE):
+        v = _prep(v)
+        nsys = v.shape[0] if v.ndim == 3 else 1
+        out = _like(v)
+        pi, where = _ptr(v)
+        po, _ = _ptr(out)
+        self._check(self.lib.smg_apply_fine(self.ctx, op, prec, nsys, pi, po, where))
+        return out
+
+    def maps(self, agg):
+        outs = [np.empty(self.V, dtype=np.int32) for _ in range(5)]
+        a = (ctypes.c_int * 4)(*agg)
+        ptrs = [o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for o in outs]
+        self._check(self.lib.smg_get_maps(self.ctx, a, *ptrs, SMG_HOST))
+        return outs
+
+    def kd_inverse(self):
+        out = np.empty((self.V // 16, 48, 48), dtype=np.complex128)
+        self._check(self.lib.smg_get_kd_inverse(self.ctx, ctypes.c_void_p(out.ctypes.data), SMG_HOST))
+        return out
+
+    def _level_shape(self, l):
+        p = self.params
+        dims = self.dims
+        ndof = 3
+        for k in range(l):
+            dims = tuple(d // a for d, a in zip(dims, p.agg[k]))
+            ndof = 2 * p.nvec[k]
+        cdims = tuple(d // a for d, a in zip(dims, p.agg[l]))
+        return int(np.prod(dims)), ndof, int(np.prod(cdims)), 2 * p.nvec[l]
+
+    def null_vectors(self, l):
+        Vf, ndof, _, _ = self._level_shape(l)
+        out = np.empty((self.params.nvec[l], Vf, ndof), dtype=np.complex128)
+        self._check(self.lib.smg_get_null_vectors(self.ctx, l, ctypes.c_void_p(out.ctypes.data), SMG_HOST))
+        return out
+
+    def coarse_op(self, l):
+        _, _, Vc, N = self._level_shape(l)
+        out = np.empty((Vc, N, 9, N), dtype=np.complex128)
+        self._check(self.lib.smg_get_coarse_op(self.ctx, l, ctypes.c_void_p(out.ctypes.data), SMG_HOST))
+        return out
+
+    def _xfer(self, fn, l, v, prec, out_shape):
+        v = _prep(v)
+        nsys = v.shape[0]
+        out = _like(v, (nsys,) + out_shape)
+        pi, where = _ptr(v)
+        po, _ = _ptr(out)
+        self._check(fn(self.ctx, l, prec, nsys, pi, po, where))
+        return out
+
+    def restrict(self, l, v, prec=PREC_DOUBLE):
+        _, _, Vc, N = self._level_shape(l)
+        return self._xfer(self.lib.smg_restrict, l, v, prec, (Vc, N))
+
+    def prolong(self, l, v, prec=PREC_DOUBLE):
+        Vf, ndof, _, _ = self._level_shape(l)
+        return self._xfer(self.lib.smg_prolong, l, v, prec, (Vf, ndof))
+
+    def coarse_apply(self, l, v, prec=PREC_DOUBLE):
+        _, _, Vc, N = self._level_shape(l)
+        return self._xfer(self.lib.smg_coarse_apply, l, v, prec, (Vc, N))
+
+    def force(self, X, Y, which=0):
+        X, Y = _prep(X), _prep(Y)
+        F = _like(X, (4, self.V, 3, 3))
+        px, where = _ptr(X)
+        py, _ = _ptr(Y)
+        pf, _ = _ptr(F)
+        self._check(self.lib.smg_force(self.ctx, px, py, int(which), pf, where))
+        return F
+
+    def setup_iterations(self, l):
+        v = ctypes.c_int()
+        self._check(self.lib.smg_setup_iterations(self.ctx, l, ctypes.byref(v)))
+        return v.value
+
+
+def _prep(a):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.complex128:
+                raise ValueError("tensors must be complex128")
+            return a.contiguous()
+    except ImportError:
+        pass
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _like(a, shape=None):
+    shape = tuple(a.shape) if shape is None else tuple(shape)
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return torch.empty(shape, dtype=torch.complex128, device=a.device)
+    except ImportError:
+        pass
+    return np.empty(shape, dtype=np.complex128)

@@ -1,0 +1,269 @@
+// The C ABI of libsmg (declared in include/smg.h): argument checks, error
+// translation and host/device staging around the solver in solver.cu.
+#include <cmath>
+#include <cstring>
+
+#include "solver.cuh"
+
+struct smg_ctx {
+  smg::Context c;
+};
+
+namespace {
+
+template <class F>
+int guarded(smg_ctx* ctx, F&& f) {
+  if (ctx == nullptr) return SMG_ERR_ARG;
+  try {
+    ctx->c.err.clear();
+    return f(ctx->c);
+  } catch (const smg::ArgError& e) {
+    ctx->c.err = e.what;
+    return SMG_ERR_ARG;
+  } catch (const smg::OomError& e) {
+    ctx->c.err = e.what;
+    return SMG_ERR_OOM;
+  } catch (const smg::StateError& e) {
+    ctx->c.err = e.what;
+    return e.what.rfind("breakdown", 0) == 0 ? SMG_ERR_BREAKDOWN : SMG_ERR_STATE;
+  } catch (const smg::CudaError& e) {
+    ctx->c.err = e.what;
+    return SMG_ERR_CUDA;
+  } catch (const std::exception& e) {
+    ctx->c.err = e.what();
+    return SMG_ERR_CUDA;
+  }
+}
+
+bool valid_where(int w) { return w == SMG_HOST || w == SMG_DEVICE; }
+
+}  // namespace
+
+extern "C" {
+
+void smg_default_params(smg_mg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n_coarse = 1;
+  for (int l = 0; l < SMG_MAX_COARSE; ++l) {
+    for (int mu = 0; mu < 4; ++mu) p->agg[l][mu] = (l == 0) ? 4 : 2;
+    p->nvec[l] = (l == 0) ? 24 : 32;
+  }
+  p->setup_tol = 1e-6;
+  p->setup_maxiter = 2000;
+  p->inner_tol = 0.25;
+  p->inner_maxiter = 8;
+  p->smoother_s = 8;
+  p->dense_max = 4096;
+  p->nkrylov = 16;
+  p->max_outer = 500;
+  p->precision = SMG_PREC_DOUBLE;
+  p->use_graph = 0;
+}
+
+int smg_create(const int dims[4], smg_ctx** out) {
+  if (dims == nullptr || out == nullptr) return SMG_ERR_ARG;
+  *out = nullptr;
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (dims[mu] < 4 || dims[mu] % 2 != 0) return SMG_ERR_ARG;
+    V *= dims[mu];
+  }
+  if (V > (1LL << 30)) return SMG_ERR_ARG;
+  smg_ctx* ctx = new (std::nothrow) smg_ctx();
+  if (!ctx) return SMG_ERR_OOM;
+  for (int mu = 0; mu < 4; ++mu) ctx->c.g.L[mu] = dims[mu];
+  ctx->c.g.V = (int)V;
+  if (cudaStreamCreateWithFlags(&ctx->c.own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return SMG_ERR_CUDA;
+  }
+  ctx->c.stream = ctx->c.own_stream;
+  *out = ctx;
+  return SMG_OK;
+}
+
+int smg_destroy(smg_ctx* ctx) {
+  if (!ctx) return SMG_ERR_ARG;
+  cudaStreamSynchronize(ctx->c.stream);
+  delete ctx;
+  return SMG_OK;
+}
+
+const char* smg_last_error(const smg_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->c.err.c_str();
+}
+
+int smg_set_stream(smg_ctx* ctx, void* stream) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    c.stream = stream ? (cudaStream_t)stream : c.own_stream;
+    c.engine.reset();
+    return SMG_OK;
+  });
+}
+
+int smg_set_gauge(smg_ctx* ctx, const void* fat, const void* naik, double c_naik, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(fat != nullptr && valid_where(where), "set_gauge: null links or bad `where`");
+    SMG_REQUIRE(std::isfinite(c_naik), "set_gauge: c_naik must be finite");
+    smg::ctx_set_gauge(c, fat, naik, c_naik, where);
+    return SMG_OK;
+  });
+}
+
+int smg_set_mass(smg_ctx* ctx, double mass) {
+  return guarded(ctx, [&](smg::Context& c) {
+    smg::ctx_set_mass(c, mass);
+    return SMG_OK;
+  });
+}
+
+int smg_mg_setup(smg_ctx* ctx, const smg_mg_params* params, const void* const* phi0, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(params != nullptr && valid_where(where), "mg_setup: null params or bad `where`");
+    if (!c.gauge_set || !c.mass_set) throw smg::StateError("mg_setup needs set_gauge and set_mass first");
+    smg::ctx_mg_setup(c, *params, phi0, where);
+    return SMG_OK;
+  });
+}
+
+int smg_solve(smg_ctx* ctx, const void* b, void* x, double tol, int where, smg_solve_info* info) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(b != nullptr && x != nullptr && valid_where(where), "solve: null buffer or bad `where`");
+    if (!c.setup_done) throw smg::StateError("solve needs mg_setup first");
+    return smg::ctx_solve(c, 1, b, 1, nullptr, x, tol, where, info);
+  });
+}
+
+int smg_multi_solve(smg_ctx* ctx, int nrhs, const void* b, int nshift, const double* masses, void* x, double tol,
+                    int where, smg_solve_info* info) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(b != nullptr && x != nullptr && masses != nullptr && valid_where(where),
+                "multi_solve: null buffer or bad `where`");
+    if (!c.setup_done) throw smg::StateError("multi_solve needs mg_setup first");
+    return smg::ctx_solve(c, nrhs, b, nshift, masses, x, tol, where, info);
+  });
+}
+
+int smg_apply_fine(smg_ctx* ctx, int op, int prec, int nsys, const void* in, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(in != nullptr && out != nullptr && valid_where(where), "apply_fine: null buffer or bad `where`");
+    if (!c.gauge_set || !c.mass_set) throw smg::StateError("apply_fine needs set_gauge and set_mass first");
+    smg::ctx_apply_fine(c, op, prec, nsys, in, out, where);
+    return SMG_OK;
+  });
+}
+
+int smg_get_maps(smg_ctx* ctx, const int agg[4], int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_pos,
+                 int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(agg && parity && kd_block && kd_pos && agg_idx && agg_pos && valid_where(where),
+                "get_maps: null argument");
+    for (int mu = 0; mu < 4; ++mu)
+      SMG_REQUIRE(agg[mu] >= 1 && c.g.L[mu] % agg[mu] == 0, "get_maps: aggregate must divide the lattice");
+    smg::DevBuf buf;
+    const size_t V = c.g.V;
+    buf.alloc(sizeof(int) * V * 5);
+    int* d = buf.as<int>();
+    smg::site_maps(d, d + V, d + 2 * V, d + 3 * V, d + 4 * V, c.g, agg, c.stream);
+    int* outs[5] = {parity, kd_block, kd_pos, agg_idx, agg_pos};
+    for (int i = 0; i < 5; ++i) smg::download(outs[i], d + i * V, sizeof(int) * V, where, c.stream);
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    return SMG_OK;
+  });
+}
+
+int smg_get_kd_inverse(smg_ctx* ctx, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(out != nullptr && valid_where(where), "get_kd_inverse: null buffer");
+    if (!c.gauge_set || !c.mass_set) throw smg::StateError("get_kd_inverse needs set_gauge and set_mass");
+    if (!c.kd_valid) smg::ctx_build_kd(c);
+    smg::download(out, c.kd_row64.p, c.kd_row64.bytes, where, c.stream);
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    return SMG_OK;
+  });
+}
+
+int smg_get_null_vectors(smg_ctx* ctx, int l, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(out != nullptr && valid_where(where), "get_null_vectors: null buffer");
+    if (!c.setup_done) throw smg::StateError("get_null_vectors needs mg_setup");
+    SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "get_null_vectors: bad level");
+    smg::download(out, c.coarse[l].raw64.p, c.coarse[l].raw64.bytes, where, c.stream);
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    return SMG_OK;
+  });
+}
+
+int smg_get_coarse_op(smg_ctx* ctx, int l, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(out != nullptr && valid_where(where), "get_coarse_op: null buffer");
+    if (!c.setup_done) throw smg::StateError("get_coarse_op needs mg_setup");
+    SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "get_coarse_op: bad level");
+    smg::download(out, c.coarse[l].S64.p, c.coarse[l].S64.bytes, where, c.stream);
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    return SMG_OK;
+  });
+}
+
+int smg_restrict(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(in && out && valid_where(where), "restrict: null buffer");
+    if (!c.setup_done) throw smg::StateError("restrict needs mg_setup");
+    smg::ctx_transfer(c, 0, l, prec, nsys, in, out, where);
+    return SMG_OK;
+  });
+}
+
+int smg_prolong(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(in && out && valid_where(where), "prolong: null buffer");
+    if (!c.setup_done) throw smg::StateError("prolong needs mg_setup");
+    smg::ctx_transfer(c, 1, l, prec, nsys, in, out, where);
+    return SMG_OK;
+  });
+}
+
+int smg_coarse_apply(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(in && out && valid_where(where), "coarse_apply: null buffer");
+    if (!c.setup_done) throw smg::StateError("coarse_apply needs mg_setup");
+    smg::ctx_transfer(c, 2, l, prec, nsys, in, out, where);
+    return SMG_OK;
+  });
+}
+
+int smg_force(smg_ctx* ctx, const void* X, const void* Y, int which, void* F, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(X && Y && F && valid_where(where) && (which == 0 || which == 1), "force: bad argument");
+    if (!c.gauge_set) throw smg::StateError("force needs set_gauge");
+    SMG_REQUIRE(which == 0 || c.has_naik, "force: no Naik links were set");
+    const size_t nv = (size_t)c.g.V * 3 * sizeof(double2);
+    const size_t nf = (size_t)c.g.V * 36 * sizeof(double2);
+    smg::DevBuf buf;
+    buf.alloc(2 * nv + nf);
+    char* b = (char*)buf.p;
+    smg::upload(b, X, nv, where, c.stream);
+    smg::upload(b + nv, Y, nv, where, c.stream);
+    smg::force_outer((double2*)(b + 2 * nv), (const double2*)b, (const double2*)(b + nv), c.g, which ? 3 : 1,
+                     which ? c.c_naik : 1.0, c.stream);
+    smg::download(F, b + 2 * nv, nf, where, c.stream);
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    return SMG_OK;
+  });
+}
+
+int smg_setup_iterations(smg_ctx* ctx, int l, int* iters) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(iters != nullptr, "setup_iterations: null output");
+    if (!c.setup_done) throw smg::StateError("setup_iterations needs mg_setup");
+    SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "setup_iterations: bad level");
+    *iters = c.coarse[l].setup_iters;
+    return SMG_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,348 @@
+// The Galerkin coarse operator A_hat = R A P as a 9-point stencil
+// (Sec. 2.1, 3.1): (A_hat v)(X) = X v(X) + sum_mu Y_{+mu} v(X+mu) + Y_{-mu} v(X-mu).
+//
+// Stencil layout [Vc][N rows][9 dirs][N cols] (dir 0 self, 1+2mu forward,
+// 2+2mu backward): for one output row the nine N-long rows are one
+// contiguous "super-row" of 9N complex numbers, which a warp streams with
+// consecutive lanes on consecutive entries while the nine neighbour vectors
+// sit in shared memory.  FP16 storage keeps one FP32 scale per (site, row),
+// the 16-bit analogue of the paper's fixed-point coarse links with a norm.
+#include "ops.cuh"
+
+namespace smg {
+namespace {
+
+__device__ __forceinline__ int nbr(const Geom& g, const int c[4], int dir) {
+  if (dir == 0) return g.index(c);
+  const int mu = (dir - 1) >> 1;
+  const int k = ((dir - 1) & 1) ? -1 : 1;
+  return g.shift(c, mu, k);
+}
+
+// Whether direction `dir` contributes to operator part `part` at coarse coords c.
+__device__ __forceinline__ bool dir_in_part(int dir, int part, const int c[4], const int agg[4]) {
+  if (part < 0) return true;
+  if (dir == 0) return part == 0;
+  const int mu = (dir - 1) >> 1;
+  const int r = c[mu] % agg[mu];
+  const bool cross = ((dir - 1) & 1) ? (r - 1 < 0) : (r + 1 >= agg[mu]);
+  return part == 0 ? !cross : (part == dir && cross);
+}
+
+template <typename R, typename SL>
+__global__ void __launch_bounds__(256) coarse_apply_kernel(typename cplx<R>::T* __restrict__ out,
+                                                           const typename cplx<R>::T* __restrict__ in,
+                                                           const SL* __restrict__ S, const float* __restrict__ rs,
+                                                           Geom g, int N, int part, int4 agg4, const int* run) {
+  using C = typename cplx<R>::T;
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ unsigned char smem_raw[];
+  C* vin = (C*)smem_raw;   // [9][N]
+  const int X = blockIdx.x, s = blockIdx.y;
+  const int agg[4] = {agg4.x, agg4.y, agg4.z, agg4.w};
+  int c[4];
+  g.coords(X, c);
+  const long long n = (long long)g.V * N;
+  for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
+    const int dir = e / N, j = e % N;
+    C v = C{0, 0};
+    if (dir_in_part(dir, part, c, agg)) v = in[(size_t)s * n + (size_t)nbr(g, c, dir) * N + j];
+    vin[e] = v;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = w; i < N; i += nw) {
+    const SL* row = S + ((size_t)X * N + i) * 9 * N;
+    C acc = C{0, 0};
+    for (int e = lane; e < 9 * N; e += 32) cfma(acc, ld<R>(row, e), vin[e]);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) {
+      if (rs != nullptr) acc = cscale(acc, (R)rs[(size_t)X * N + i]);
+      out[(size_t)s * n + (size_t)X * N + i] = acc;
+    }
+  }
+}
+
+template <typename SL>
+__global__ void coarse_pack_kernel(SL* __restrict__ dst, float* __restrict__ rs, const double2* __restrict__ S,
+                                   long long rows, int N) {
+  const long long row = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const double2* src = S + (size_t)row * 9 * N;
+  float sc = 1.0f;
+  if (rs != nullptr) {
+    double mx = 0.0;
+    for (int e = lane; e < 9 * N; e += 32) mx = fmax(mx, fmax(fabs(src[e].x), fabs(src[e].y)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    sc = mx > 0 ? (float)mx : 1.0f;
+    if (lane == 0) rs[row] = sc;
+  }
+  const double isc = 1.0 / sc;
+  for (int e = lane; e < 9 * N; e += 32) {
+    const double2 v = src[e];
+    SL* o = dst + (size_t)row * 9 * N + e;
+    if constexpr (sizeof(SL) == 16) *o = SL{v.x, v.y};
+    else if constexpr (sizeof(SL) == 8) *o = SL{(float)v.x, (float)v.y};
+    else *o = __floats2half2_rn((float)(v.x * isc), (float)(v.y * isc));
+  }
+}
+
+__global__ void coarse_dagger_kernel(double2* __restrict__ dst, const double2* __restrict__ src, Geom g, int N) {
+  const long long total = (long long)g.V * N * 9 * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % N);
+    long long q = e / N;
+    const int dir = (int)(q % 9);
+    q /= 9;
+    const int i = (int)(q % N);
+    const int X = (int)(q / N);
+    int c[4];
+    g.coords(X, c);
+    int Xs = X, sdir = 0;
+    if (dir > 0) {
+      const int mu = (dir - 1) >> 1;
+      const bool fwd = ((dir - 1) & 1) == 0;
+      Xs = g.shift(c, mu, fwd ? 1 : -1);
+      sdir = fwd ? dir + 1 : dir - 1;
+    }
+    const double2 v = src[(((size_t)Xs * N + j) * 9 + sdir) * N + i];
+    dst[e] = make_double2(v.x, -v.y);
+  }
+}
+
+__global__ void galerkin_scatter_kernel(double2* __restrict__ S, const double2* __restrict__ Cm, long long Vc,
+                                        int N, int dir, int j0, int ncol) {
+  const long long total = (long long)ncol * Vc * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % N);
+    const long long q = e / N;
+    const long long X = q % Vc;
+    const int s = (int)(q / Vc);
+    S[(((size_t)X * N + i) * 9 + dir) * N + j0 + s] = Cm[e];
+  }
+}
+
+__global__ void unit_probes_kernel(double2* __restrict__ E, long long Vc, int N, int j0, int ncol) {
+  const long long total = (long long)ncol * Vc * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % N);
+    const int s = (int)(e / ((long long)Vc * N));
+    E[e] = make_double2(i == j0 + s ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// ------------------------------------------------------------ dense coarsest
+__global__ void dense_from_stencil_kernel(double2* __restrict__ D, const double2* __restrict__ S, Geom g, int N) {
+  const long long n = (long long)g.V * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / n, col = e % n;
+    const int X = (int)(row / N), i = (int)(row % N);
+    const int Xp = (int)(col / N), j = (int)(col % N);
+    int c[4];
+    g.coords(X, c);
+    double2 acc = make_double2(0, 0);
+    for (int dir = 0; dir < 9; ++dir)
+      if (nbr(g, c, dir) == Xp) acc = cadd(acc, S[(((size_t)X * N + i) * 9 + dir) * N + j]);
+    D[e] = acc;
+  }
+}
+
+// pivot search, row swap and pivot-row scaling for column k (one CTA)
+__global__ void __launch_bounds__(1024) gj_pivot_kernel(double2* __restrict__ A, int n, int k,
+                                                        double2* __restrict__ fac, int* __restrict__ perm) {
+  __shared__ double bm[32];
+  __shared__ int bi[32];
+  __shared__ int prow;
+  const int t = threadIdx.x;
+  double best = -1.0;
+  int idx = k;
+  for (int i = k + t; i < n; i += blockDim.x) {
+    const double2 v = A[(size_t)i * n + k];
+    const double m2 = v.x * v.x + v.y * v.y;
+    if (m2 > best) { best = m2; idx = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, o);
+    if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+  }
+  if ((t & 31) == 0) { bm[t >> 5] = best; bi[t >> 5] = idx; }
+  __syncthreads();
+  if (t == 0) {
+    double b = -1.0; int p = k;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (bm[w] > b || (bm[w] == b && bi[w] < p)) { b = bm[w]; p = bi[w]; }
+    prow = p;
+    perm[k] = p;
+    if (!(b > 0.0)) perm[n] = 1;   // singular flag
+  }
+  __syncthreads();
+  const int p = prow;
+  if (p != k)
+    for (int j = t; j < n; j += blockDim.x) {
+      const double2 tmp = A[(size_t)k * n + j];
+      A[(size_t)k * n + j] = A[(size_t)p * n + j];
+      A[(size_t)p * n + j] = tmp;
+    }
+  __syncthreads();
+  const double2 pv = A[(size_t)k * n + k];
+  const double d = pv.x * pv.x + pv.y * pv.y;
+  const double2 ip = d > 0 ? make_double2(pv.x / d, -pv.y / d) : make_double2(0, 0);
+  __syncthreads();
+  for (int j = t; j < n; j += blockDim.x) {
+    const double2 v = (j == k) ? make_double2(1, 0) : A[(size_t)k * n + j];
+    A[(size_t)k * n + j] = cmul(v, ip);
+  }
+  for (int i = t; i < n; i += blockDim.x) fac[i] = (i == k) ? make_double2(0, 0) : A[(size_t)i * n + k];
+}
+
+__global__ void gj_eliminate_kernel(double2* __restrict__ A, int n, int k, const double2* __restrict__ fac) {
+  const long long total = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i == k) continue;
+    const double2 f = fac[i];
+    double2 v = (j == k) ? make_double2(0, 0) : A[e];
+    const double2 w = A[(size_t)k * n + j];
+    v.x -= f.x * w.x - f.y * w.y;
+    v.y -= f.x * w.y + f.y * w.x;
+    A[e] = v;
+  }
+}
+
+__global__ void gj_unpermute_kernel(double2* __restrict__ A, int n, const int* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      const double2 tmp = A[(size_t)i * n + k];
+      A[(size_t)i * n + k] = A[(size_t)i * n + p];
+      A[(size_t)i * n + p] = tmp;
+    }
+  }
+}
+
+template <typename R, typename DT>
+__global__ void __launch_bounds__(256) dense_apply_kernel(typename cplx<R>::T* __restrict__ out,
+                                                          const typename cplx<R>::T* __restrict__ in,
+                                                          const DT* __restrict__ D, int n, const int* run) {
+  using C = typename cplx<R>::T;
+  if (run != nullptr && *run == 0) return;
+  const int s = blockIdx.y;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + w;
+  if (row >= n) return;
+  const C* v = in + (size_t)s * n;
+  const DT* Dr = D + (size_t)row * n;
+  C acc = C{0, 0};
+  for (int j = lane; j < n; j += 32) cfma(acc, ld<R>(Dr, j), v[j]);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) out[(size_t)s * n + row] = acc;
+}
+
+unsigned grid_cap(long long total, int threads) {
+  long long g = (total + threads - 1) / threads;
+  if (g > 16384) g = 16384;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
+                  const int* run) {
+  SMG_REQUIRE(in.n == (long long)p.g.V * p.N && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
+              "coarse_apply: shape mismatch");
+  const size_t smem = (size_t)9 * p.N * prec_bytes(in.prec);
+  SMG_REQUIRE(smem <= 48 * 1024, "coarse_apply: N too large");
+  dim3 grid(p.g.V, in.nsys);
+  int4 agg = make_int4(p.agg[0], p.agg[1], p.agg[2], p.agg[3]);
+  if (in.prec == P64) {
+    SMG_REQUIRE(S.s == S64, "coarse_apply: FP64 vectors need FP64 stencil");
+    coarse_apply_kernel<double, double2><<<grid, 256, smem, st>>>((double2*)out.p, (const double2*)in.p,
+                                                                  (const double2*)S.p, nullptr, p.g, p.N, p.part,
+                                                                  agg, run);
+  } else if (S.s == S32) {
+    coarse_apply_kernel<float, float2><<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p,
+                                                                (const float2*)S.p, nullptr, p.g, p.N, p.part,
+                                                                agg, run);
+  } else {
+    SMG_REQUIRE(S.s == S16, "coarse_apply: unsupported storage");
+    coarse_apply_kernel<float, __half2><<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p,
+                                                                 (const __half2*)S.p, S.scale, p.g, p.N, p.part,
+                                                                 agg, run);
+  }
+  SMG_LAUNCH_OK();
+}
+
+void coarse_pack(Stored& dst, const double2* S64src, const Geom& g, int N, cudaStream_t st) {
+  const long long rows = (long long)g.V * N;
+  const unsigned grid = ceil_div(rows, 8);
+  if (dst.s == S64) coarse_pack_kernel<double2><<<grid, 256, 0, st>>>((double2*)dst.p, nullptr, S64src, rows, N);
+  else if (dst.s == S32) coarse_pack_kernel<float2><<<grid, 256, 0, st>>>((float2*)dst.p, nullptr, S64src, rows, N);
+  else coarse_pack_kernel<__half2><<<grid, 256, 0, st>>>((__half2*)dst.p, dst.scale, S64src, rows, N);
+  SMG_LAUNCH_OK();
+}
+
+void coarse_dagger(double2* dst, const double2* src, const Geom& g, int N, cudaStream_t st) {
+  coarse_dagger_kernel<<<grid_cap((long long)g.V * N * 9 * N, 256), 256, 0, st>>>(dst, src, g, N);
+  SMG_LAUNCH_OK();
+}
+
+void galerkin_scatter(double2* Sdst, const double2* C, const Geom& g, int N, int dir, int j0, int ncol,
+                      cudaStream_t st) {
+  galerkin_scatter_kernel<<<grid_cap((long long)ncol * g.V * N, 256), 256, 0, st>>>(Sdst, C, g.V, N, dir, j0, ncol);
+  SMG_LAUNCH_OK();
+}
+
+void unit_probes(double2* E, long long Vc, int N, int j0, int ncol, cudaStream_t st) {
+  unit_probes_kernel<<<grid_cap((long long)ncol * Vc * N, 256), 256, 0, st>>>(E, Vc, N, j0, ncol);
+  SMG_LAUNCH_OK();
+}
+
+void dense_from_stencil(double2* Dn, const double2* Ssrc, const Geom& g, int N, cudaStream_t st) {
+  const long long n = (long long)g.V * N;
+  dense_from_stencil_kernel<<<grid_cap(n * n, 256), 256, 0, st>>>(Dn, Ssrc, g, N);
+  SMG_LAUNCH_OK();
+}
+
+void dense_invert(double2* Dn, int n, double2* fac, int* perm, cudaStream_t st) {
+  SMG_CUDA_OK(cudaMemsetAsync(perm, 0, sizeof(int) * (n + 1), st));
+  for (int k = 0; k < n; ++k) {
+    gj_pivot_kernel<<<1, 1024, 0, st>>>(Dn, n, k, fac, perm);
+    gj_eliminate_kernel<<<grid_cap((long long)n * n, 256), 256, 0, st>>>(Dn, n, k, fac);
+  }
+  gj_unpermute_kernel<<<ceil_div(n, 128), 128, 0, st>>>(Dn, n, perm);
+  SMG_LAUNCH_OK();
+}
+
+void dense_apply(const Vec& out, const Vec& in, const void* Dinv, Prec dprec, int n, cudaStream_t st,
+                 const int* run) {
+  SMG_REQUIRE(in.n == n && out.n == n && in.nsys == out.nsys && in.prec == out.prec, "dense_apply: shape mismatch");
+  dim3 grid(ceil_div(n, 8), in.nsys);
+  if (in.prec == P64) {
+    SMG_REQUIRE(dprec == P64, "dense_apply: FP64 vectors need the FP64 inverse");
+    dense_apply_kernel<double, double2><<<grid, 256, 0, st>>>((double2*)out.p, (const double2*)in.p,
+                                                              (const double2*)Dinv, n, run);
+  } else {
+    SMG_REQUIRE(dprec == P32, "dense_apply: FP32 vectors need the FP32 inverse");
+    dense_apply_kernel<float, float2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p,
+                                                            (const float2*)Dinv, n, run);
+  }
+  SMG_LAUNCH_OK();
+}
+
+}  // namespace smg

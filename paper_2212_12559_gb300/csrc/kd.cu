@@ -1,0 +1,243 @@
+// Kahler-Dirac block preconditioner (Eq. 1, Eq. 2, Sec. 3.1).
+//
+// B is the part of the distance-one hopping term that stays inside an
+// aligned 2^4 hypercube, so B + m is block diagonal with one 48x48 complex
+// block per hypercube (16 sites x 3 colours, ordered 3b + a with
+// b = (x&1) + 2(y&1) + 4(z&1) + 8(t&1)).  kd_build assembles each block from
+// the fat links and inverts it in FP64 (Gauss-Jordan with partial pivoting,
+// one CTA per hypercube, the augmented 48x96 matrix in shared memory).
+// kd_apply multiplies every hypercube of a batched field by its inverse.
+#include "ops.cuh"
+
+namespace smg {
+namespace {
+
+constexpr int NB = 48;
+
+__device__ __forceinline__ int hyper_site(const Geom& g, int blk, int b) {
+  const int h0 = g.L[0] / 2, h1 = g.L[1] / 2, h2 = g.L[2] / 2;
+  int c[4];
+  c[0] = blk % h0; blk /= h0;
+  c[1] = blk % h1; blk /= h1;
+  c[2] = blk % h2; c[3] = blk / h2;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) c[mu] = 2 * c[mu] + ((b >> mu) & 1);
+  return g.index(c);
+}
+
+__global__ void __launch_bounds__(256) kd_build_kernel(double2* __restrict__ inv, const double2* __restrict__ fat,
+                                                       double mass, Geom g) {
+  extern __shared__ double2 aug[];   // [48][96]
+  __shared__ double2 fac[NB];
+  __shared__ int piv_row;
+  const int blk = blockIdx.x;
+  const int t = threadIdx.x;
+  // assemble [B + m | 1]
+  for (int e = t; e < NB * 2 * NB; e += blockDim.x) {
+    const int row = e / (2 * NB), col = e % (2 * NB);
+    double2 v = make_double2(0, 0);
+    if (col >= NB) {
+      if (col - NB == row) v.x = 1.0;
+    } else {
+      const int b = row / 3, a = row % 3, bp = col / 3, ap = col % 3;
+      if (b == bp) {
+        if (a == ap) v.x = mass;
+      } else {
+        const int diff = b ^ bp;
+        if ((diff & (diff - 1)) == 0) {
+          int mu = 0;
+          while ((1 << mu) != diff) ++mu;
+          const int xb = hyper_site(g, blk, b);
+          int c[4];
+          g.coords(xb, c);
+          int es = 0;
+          for (int nu = 0; nu < mu; ++nu) es += c[nu];
+          const double eta = (es & 1) ? -0.5 : 0.5;
+          if (((b >> mu) & 1) == 0) {
+            // forward hop inside the hypercube: +1/2 eta U_mu(x)[a][a']
+            const double2 u = fat[((size_t)mu * g.V + xb) * 9 + a * 3 + ap];
+            v = make_double2(eta * u.x, eta * u.y);
+          } else {
+            // backward hop: -1/2 eta conj(U_mu(x - mu)[a'][a])
+            const int xn = hyper_site(g, blk, bp);
+            const double2 u = fat[((size_t)mu * g.V + xn) * 9 + ap * 3 + a];
+            v = make_double2(-eta * u.x, eta * u.y);
+          }
+        }
+      }
+    }
+    aug[e] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < NB; ++k) {
+    if (t < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + t; i < NB; i += 32) {
+        const double2 v = aug[i * 2 * NB + k];
+        const double m2 = v.x * v.x + v.y * v.y;
+        if (m2 > best) { best = m2; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (t == 0) piv_row = bi;
+    }
+    __syncthreads();
+    const int p = piv_row;
+    if (p != k) {
+      for (int j = t; j < 2 * NB; j += blockDim.x) {
+        const double2 tmp = aug[k * 2 * NB + j];
+        aug[k * 2 * NB + j] = aug[p * 2 * NB + j];
+        aug[p * 2 * NB + j] = tmp;
+      }
+    }
+    __syncthreads();
+    const double2 pv = aug[k * 2 * NB + k];
+    const double d = pv.x * pv.x + pv.y * pv.y;
+    const double2 ip = make_double2(pv.x / d, -pv.y / d);
+    __syncthreads();
+    for (int j = t; j < 2 * NB; j += blockDim.x) aug[k * 2 * NB + j] = cmul(aug[k * 2 * NB + j], ip);
+    if (t < NB) fac[t] = (t == k) ? make_double2(0, 0) : aug[t * 2 * NB + k];
+    __syncthreads();
+    for (int e = t; e < NB * 2 * NB; e += blockDim.x) {
+      const int i = e / (2 * NB), j = e % (2 * NB);
+      if (i == k) continue;
+      const double2 f = fac[i];
+      double2 v = aug[e];
+      const double2 w = aug[k * 2 * NB + j];
+      v.x -= f.x * w.x - f.y * w.y;
+      v.y -= f.x * w.y + f.y * w.x;
+      aug[e] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, j = e % NB;
+    inv[(size_t)blk * NB * NB + e] = aug[i * 2 * NB + NB + j];
+  }
+}
+
+// row-major FP64 -> column-major per block, in the requested storage
+template <typename SL>
+__global__ void kd_pack_kernel(SL* __restrict__ dst, float* __restrict__ scale, const double2* __restrict__ inv,
+                               long long nblk) {
+  const long long blk = blockIdx.x;
+  const int r = threadIdx.x;   // one thread per row (48)
+  if (r >= NB) return;
+  const double2* row = inv + (size_t)blk * NB * NB + (size_t)r * NB;
+  float sc = 1.0f;
+  if (scale != nullptr) {
+    double mx = 0.0;
+    for (int c = 0; c < NB; ++c) mx = fmax(mx, fmax(fabs(row[c].x), fabs(row[c].y)));
+    sc = mx > 0 ? (float)mx : 1.0f;
+    scale[blk * NB + r] = sc;
+  }
+  const double isc = 1.0 / (double)sc;
+  for (int c = 0; c < NB; ++c) {
+    const double2 v = row[c];
+    SL* o = dst + (size_t)blk * NB * NB + (size_t)c * NB + r;
+    if constexpr (sizeof(SL) == 16) *o = SL{v.x, v.y};
+    else if constexpr (sizeof(SL) == 8) *o = SL{(float)v.x, (float)v.y};
+    else *o = __floats2half2_rn((float)(v.x * isc), (float)(v.y * isc));
+  }
+}
+
+struct KdSet {
+  const void* p[16];
+  const float* scale[16];
+};
+
+// 4 hypercubes per CTA, one thread per output row.
+template <typename R, typename SL>
+__global__ void __launch_bounds__(192) kd_apply_kernel(typename cplx<R>::T* __restrict__ out,
+                                                       const typename cplx<R>::T* __restrict__ in, KdSet kd,
+                                                       const int* __restrict__ sys_map, int dagger, long long nblk,
+                                                       Geom g, const int* run) {
+  using C = typename cplx<R>::T;
+  if (run != nullptr && *run == 0) return;
+  __shared__ C vin[4][NB];
+  const int s = blockIdx.y;
+  const int lb = threadIdx.x / NB, r = threadIdx.x % NB;
+  const long long blk = (long long)blockIdx.x * 4 + lb;
+  const long long off = (long long)s * g.V * 3;
+  const int kidx = sys_map != nullptr ? sys_map[s] : 0;
+  const SL* K = (const SL*)kd.p[kidx];
+  const float* sc = kd.scale[kidx];
+  int site = 0;
+  if (blk < nblk) {
+    site = hyper_site(g, (int)blk, r / 3);
+    vin[lb][r] = in[off + (size_t)site * 3 + (r % 3)];
+  }
+  __syncthreads();
+  if (blk >= nblk) return;
+  const SL* Kb = K + (size_t)blk * NB * NB;
+  C acc = C{0, 0};
+  if (!dagger) {
+#pragma unroll 8
+    for (int c = 0; c < NB; ++c) cfma(acc, ld<R>(Kb, (size_t)c * NB + r), vin[lb][c]);
+    if (sc != nullptr) acc = cscale(acc, (R)sc[blk * NB + r]);
+  } else {
+#pragma unroll 8
+    for (int c = 0; c < NB; ++c) {
+      C k = ld<R>(Kb, (size_t)r * NB + c);
+      if (sc != nullptr) k = cscale(k, (R)sc[blk * NB + c]);
+      cfmac(acc, k, vin[lb][c]);
+    }
+  }
+  out[off + (size_t)site * 3 + (r % 3)] = acc;
+}
+
+}  // namespace
+
+void kd_build(double2* inv64, const Geom& g, const double2* fat64, double mass, cudaStream_t st) {
+  for (int mu = 0; mu < 4; ++mu) SMG_REQUIRE(g.L[mu] % 2 == 0 && g.L[mu] >= 4, "kd_build: extents must be even and >= 4");
+  const size_t smem = sizeof(double2) * NB * 2 * NB;
+  static bool attr = false;
+  if (!attr) {
+    SMG_CUDA_OK(cudaFuncSetAttribute(kd_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  kd_build_kernel<<<g.V / 16, 256, smem, st>>>(inv64, fat64, mass, g);
+  SMG_LAUNCH_OK();
+}
+
+void kd_pack(Stored& dst, const double2* inv64, long long nblk, cudaStream_t st) {
+  if (dst.s == S64) kd_pack_kernel<double2><<<(unsigned)nblk, 64, 0, st>>>((double2*)dst.p, nullptr, inv64, nblk);
+  else if (dst.s == S32) kd_pack_kernel<float2><<<(unsigned)nblk, 64, 0, st>>>((float2*)dst.p, nullptr, inv64, nblk);
+  else kd_pack_kernel<__half2><<<(unsigned)nblk, 64, 0, st>>>((__half2*)dst.p, dst.scale, inv64, nblk);
+  SMG_LAUNCH_OK();
+}
+
+void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, const int* sys_map, int nkd,
+              int dagger, cudaStream_t st, const int* run) {
+  SMG_REQUIRE(in.n == (long long)g.V * 3 && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
+              "kd_apply: shape mismatch");
+  SMG_REQUIRE(nkd >= 1 && nkd <= 16, "kd_apply: 1..16 block inverses");
+  KdSet set{};
+  for (int i = 0; i < nkd; ++i) {
+    SMG_REQUIRE(kd[i].s == kd[0].s, "kd_apply: mixed storage");
+    set.p[i] = kd[i].p;
+    set.scale[i] = kd[i].s == S16 ? kd[i].scale : nullptr;
+  }
+  const long long nblk = g.V / 16;
+  dim3 grid(ceil_div(nblk, 4), in.nsys);
+  if (in.prec == P64) {
+    SMG_REQUIRE(kd[0].s == S64, "kd_apply: FP64 vectors need FP64 blocks");
+    kd_apply_kernel<double, double2><<<grid, 192, 0, st>>>((double2*)out.p, (const double2*)in.p, set, sys_map,
+                                                           dagger, nblk, g, run);
+  } else if (kd[0].s == S32) {
+    kd_apply_kernel<float, float2><<<grid, 192, 0, st>>>((float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
+                                                         nblk, g, run);
+  } else if (kd[0].s == S16) {
+    kd_apply_kernel<float, __half2><<<grid, 192, 0, st>>>((float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
+                                                          nblk, g, run);
+  } else {
+    SMG_REQUIRE(false, "kd_apply: unsupported precision pair");
+  }
+  SMG_LAUNCH_OK();
+}
+
+}  // namespace smg

@@ -1,0 +1,60 @@
+// Lattice maps (exported for bit-exact checks) and the fermion-force
+// outer-product kernel.
+#include "ops.cuh"
+
+namespace smg {
+namespace {
+
+__global__ void site_maps_kernel(int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_pos, Geom g,
+                                 int4 agg) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  int c[4];
+  g.coords(x, c);
+  const int a[4] = {agg.x, agg.y, agg.z, agg.w};
+  parity[x] = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int h[4] = {g.L[0] / 2, g.L[1] / 2, g.L[2] / 2, g.L[3] / 2};
+  kd_block[x] = (c[0] >> 1) + h[0] * ((c[1] >> 1) + h[1] * ((c[2] >> 1) + h[2] * (c[3] >> 1)));
+  kd_pos[x] = (c[0] & 1) + 2 * (c[1] & 1) + 4 * (c[2] & 1) + 8 * (c[3] & 1);
+  const int cd[4] = {g.L[0] / a[0], g.L[1] / a[1], g.L[2] / a[2], g.L[3] / a[3]};
+  agg_idx[x] = c[0] / a[0] + cd[0] * (c[1] / a[1] + cd[1] * (c[2] / a[2] + cd[2] * (c[3] / a[3])));
+  agg_pos[x] = c[0] % a[0] + a[0] * (c[1] % a[1] + a[1] * (c[2] % a[2] + a[2] * (c[3] % a[3])));
+}
+
+// F_mu(x)[a][b] = -c eta_mu(x) ( Y_a(x) conj(X_b(x+k mu)) - X_a(x) conj(Y_b(x+k mu)) )
+__global__ void force_kernel(double2* __restrict__ F, const double2* __restrict__ X, const double2* __restrict__ Y,
+                             Geom g, int k, double coef) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= 4LL * g.V * 9) return;
+  const int ab = (int)(e % 9);
+  const long long q = e / 9;
+  const int x = (int)(q % g.V), mu = (int)(q / g.V);
+  const int a = ab / 3, b = ab % 3;
+  int c[4];
+  g.coords(x, c);
+  int es = 0;
+  for (int nu = 0; nu < mu; ++nu) es += c[nu];
+  const double eta = (es & 1) ? -1.0 : 1.0;
+  const int xn = g.shift(c, mu, k);
+  const double2 ya = Y[(size_t)x * 3 + a], xb = X[(size_t)xn * 3 + b];
+  const double2 xa = X[(size_t)x * 3 + a], yb = Y[(size_t)xn * 3 + b];
+  double2 t1 = cmul(ya, make_double2(xb.x, -xb.y));
+  double2 t2 = cmul(xa, make_double2(yb.x, -yb.y));
+  F[e] = make_double2(-coef * eta * (t1.x - t2.x), -coef * eta * (t1.y - t2.y));
+}
+
+}  // namespace
+
+void site_maps(int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_pos, const Geom& g, const int agg[4],
+               cudaStream_t st) {
+  site_maps_kernel<<<ceil_div(g.V, 256), 256, 0, st>>>(parity, kd_block, kd_pos, agg_idx, agg_pos, g,
+                                                       make_int4(agg[0], agg[1], agg[2], agg[3]));
+  SMG_LAUNCH_OK();
+}
+
+void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, int k, double c, cudaStream_t st) {
+  force_kernel<<<ceil_div(4LL * g.V * 9, 256), 256, 0, st>>>(F, X, Y, g, k, c);
+  SMG_LAUNCH_OK();
+}
+
+}  // namespace smg

@@ -1,0 +1,110 @@
+// Launchers of the operator kernels: fine staggered dslash, Kahler-Dirac
+// block inverse, restriction / prolongation, coarse 9-point stencil and the
+// dense coarsest-level inverse.
+#pragma once
+#include "blas.cuh"
+
+namespace smg {
+
+// Stored operator data: values in one of three precisions plus optional
+// FP32 scale factors (FP16 storage only).
+struct Stored {
+  void* p = nullptr;       // double2 / float2 / __half2
+  float* scale = nullptr;  // per-row scales (layout depends on the operator)
+  float gscale = 1.0f;     // one global scale (links, null vectors)
+  Store s = S64;
+};
+
+// ------------------------------------------------------------------ dslash
+// Section 2.2: M = m + D; fat links at distance 1 and Naik links at
+// distance 3 (coefficient c_naik), staggered phases eta_mu(x).
+struct DslashParams {
+  Geom g;
+  Stored fat, naik;          // [4][V][3][3]; naik.p == nullptr for the naive operator
+  double c_naik = 0.0;
+  const double* mass = nullptr;  // per system (device), or nullptr to use mass0
+  double mass0 = 0.0;
+  int dagger = 0;            // 1: m - D
+  int part = -1;             // -1 full; 0 self + mass; 1 + 2*mu + (0 fwd | 1 bwd): crossing hops
+  int agg[4] = {1, 1, 1, 1};
+  int nsys = 1;
+};
+void dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run = nullptr);
+
+// -------------------------------------------------------- Kahler-Dirac blocks
+// Section 3.1: one dense 48x48 block (B+m)^{-1} per 2^4 hypercube, rows and
+// columns ordered (position b in hypercube, colour a) -> 3b + a.
+// Build: FP64 into `inv64` [nblk][48][48] row-major.
+void kd_build(double2* inv64, const Geom& g, const double2* fat64, double mass, cudaStream_t st);
+// Convert a row-major FP64 inverse to the apply layout (column-major per
+// block, [nblk][48 col][48 row]) in storage `dst.s` (per-(block,row) scale for FP16).
+void kd_pack(Stored& dst, const double2* inv64, long long nblk, cudaStream_t st);
+// out[s] = K[sys_map[s]] in[s] (or K^dag).  kd[] holds one packed inverse per mass.
+void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, const int* sys_map, int nkd,
+              int dagger, cudaStream_t st, const int* run = nullptr);
+
+// ------------------------------------------------------- transfer operators
+// A level's lattice with `ndof` components per site; aggregates of agg[]
+// sites.  Chirality of component d at site x: parity(x) on the fine level
+// (chi_mode 0), d >= ndof/2 on coarse levels (chi_mode 1).
+struct TransferGeom {
+  Geom fine;
+  Geom coarse;
+  int agg[4];
+  int ndof;
+  int nvec;
+  int chi_mode;
+};
+// raw: FP64 [nvec][V][ndof]; orthonormalised in place per aggregate and chirality
+// (modified Gram-Schmidt in vector order, twice).
+void block_orthonormalize(double2* raw, const TransferGeom& t, cudaStream_t st);
+// Pack orthonormal FP64 [nvec][V][ndof] into the transfer layout [V][nvec][ndof] (global scale for FP16).
+void transfer_pack(Stored& dst, const double2* raw, const TransferGeom& t, cudaStream_t st);
+// out (coarse, [Vc][2*nvec]) = R in ; R = P^dag
+void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                 const int* run = nullptr);
+// out (fine) = P in
+void prolong_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                const int* run = nullptr);
+
+// ------------------------------------------------------- coarse 9-point op
+// Stencil layout [Vc][N rows][9 dirs][N cols]; dir 0 = self, 1+2mu = hop to
+// X+mu, 2+2mu = hop to X-mu.  FP16 storage carries one scale per (site, row).
+struct CoarseParams {
+  Geom g;
+  int N;
+  int part = -1;             // as DslashParams::part
+  int agg[4] = {1, 1, 1, 1};
+};
+void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
+                  const int* run = nullptr);
+// S64 stencil -> stored copy in precision dst.s
+void coarse_pack(Stored& dst, const double2* S64, const Geom& g, int N, cudaStream_t st);
+// Adjoint stencil: X^dag, Y'_{+mu}(X) = Y_{-mu}(X+mu)^dag, Y'_{-mu}(X) = Y_{+mu}(X-mu)^dag
+void coarse_dagger(double2* dst, const double2* src, const Geom& g, int N, cudaStream_t st);
+// Scatter restricted probe columns into the stencil: C is [ncol systems][Vc][N],
+// column j0 + s of direction `dir` at every coarse site.
+void galerkin_scatter(double2* S64, const double2* C, const Geom& g, int N, int dir, int j0, int ncol,
+                      cudaStream_t st);
+// Unit coarse probes: E[s][X][i] = (i == j0 + s)
+void unit_probes(double2* E, long long Vc, int N, int j0, int ncol, cudaStream_t st);
+
+// ------------------------------------------------------- dense coarsest op
+void dense_from_stencil(double2* Dn, const double2* S64, const Geom& g, int N, cudaStream_t st);
+// In-place Gauss-Jordan inverse with partial pivoting (FP64); returns false if singular.
+void dense_invert(double2* Dn, int n, double2* scratch, int* piv_dev, cudaStream_t st);
+// out[s] = Dinv in[s] ; Dinv FP64 or FP32 [n][n] row-major
+void dense_apply(const Vec& out, const Vec& in, const void* Dinv, Prec dprec, int n, cudaStream_t st,
+                 const int* run = nullptr);
+
+// ------------------------------------------------------- maps (test hooks)
+// Per-site tables: parity, KD block, position in block, aggregate, position in aggregate.
+void site_maps(int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_pos, const Geom& g,
+               const int agg[4], cudaStream_t st);
+
+// ------------------------------------------------------- fermion force
+// F_mu(x) = -c eta_mu(x) [ Y(x) X(x+k mu)^dag - X(x) Y(x+k mu)^dag ]
+void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, int k, double c,
+                 cudaStream_t st);
+
+}  // namespace smg

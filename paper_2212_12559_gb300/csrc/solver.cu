@@ -1,0 +1,1191 @@
+// The K-cycle multigrid preconditioner inside flexible GCR (Sec. 2.1, 2.3,
+// Table 1), batched over systems, with every scalar of every Krylov method
+// kept on the device.
+//
+// Levels:
+//   0  M = m + D on the fine lattice: outer flexible GCR in FP64, restarted
+//      every nkrylov directions with the residual recomputed in FP64; its
+//      preconditioner K_0 runs in the preconditioner precision.
+//   1  A = (B+m)^{-1} M on the fine lattice ("pseudo-fine", Sec. 2.3): GCR to
+//      inner_tol or inner_maxiter iterations, preconditioned by K_1.
+//   2, 3  Galerkin stencils R A P: GCR preconditioned by the next K-cycle, or
+//      on the coarsest level an exact dense solve (dof <= dense_max) or plain
+//      GCR to inner_tol / inner_maxiter.
+// K_0(r):  e = GCR_1(A, (B+m)^{-1} r); e += CA-GCR_s(M, r - M e).
+// K_l(r):  e = P_l solve_{l+1}(R_l r); e += CA-GCR_s(A_l, r - A_l e).
+// No pre-smoothing (Table 1).  Inner loops launch a fixed kernel sequence;
+// a device flag per loop makes the remaining launches return at once after
+// convergence, so no host synchronisation happens inside K_0.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "solver.cuh"
+
+namespace smg {
+
+// ------------------------------------------------------------- allocation
+void DevBuf::alloc(size_t b) {
+  release();
+  if (b == 0) return;
+  cudaError_t e = cudaMalloc(&p, b);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    throw OomError("cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  bytes = b;
+  // fresh buffers start at zero so that no path ever reads uninitialised bits;
+  // the memset runs on the legacy stream, so wait for it before any stream uses p
+  SMG_CUDA_OK(cudaMemset(p, 0, b));
+  SMG_CUDA_OK(cudaDeviceSynchronize());
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+void StoredBuf::alloc(Store s, size_t elems, size_t nscale) {
+  v.alloc(elems * store_bytes(s));
+  if (s == S16 && nscale > 0) sc.alloc(nscale * sizeof(float));
+  else sc.release();
+  st.p = v.p;
+  st.scale = (s == S16) ? sc.as<float>() : nullptr;
+  st.gscale = 1.0f;
+  st.s = s;
+}
+
+void GcrWork::alloc(long long n, int ns, Prec p, int k) {
+  K = k; nsys = ns;
+  const size_t vb = (size_t)n * ns * prec_bytes(p);
+  const int nv = 2 * K + 3;
+  vbuf.alloc(vb * nv);
+  z.resize(K); w.resize(K);
+  auto mk = [&](int i) { Vec v; v.p = (char*)vbuf.p + vb * i; v.n = n; v.nsys = ns; v.prec = p; return v; };
+  for (int i = 0; i < K; ++i) { z[i] = mk(i); w[i] = mk(K + i); }
+  r = mk(2 * K); x = mk(2 * K + 1); b = mk(2 * K + 2);
+  const int Kk = K > 0 ? K : 1;
+  size_t nd2 = (size_t)ns * (Kk * 5 + Kk * Kk + 2 + 3);
+  size_t bytes = nd2 * sizeof(double2) + (size_t)ns * 2 * sizeof(double) + ((size_t)ns * 2 + 1) * sizeof(int);
+  sbuf.alloc(bytes);
+  double2* d = sbuf.as<double2>();
+  alpha = d; d += ns * Kk;
+  gamma = d; d += ns * Kk;
+  y = d; d += ns * Kk;
+  tmp = d; d += ns * Kk;
+  beta = d; d += ns * Kk * Kk;
+  dd = d; d += ns * 2;
+  na = d; d += ns;
+  ginv = d; d += ns;
+  r2 = d; d += ns;
+  d += ns * Kk;   // spare
+  double* dr = (double*)d;
+  r02 = dr; dr += ns;
+  thr2 = dr; dr += ns;
+  int* ip = (int*)dr;
+  active = ip; ip += ns;
+  nk = ip; ip += ns;
+  run = ip;
+}
+
+void SmoothWork::alloc(long long n, int ns, Prec p, int s_) {
+  s = s_;
+  const size_t vb = (size_t)n * ns * prec_bytes(p);
+  vbuf.alloc(vb * (s + 1));
+  V.resize(s + 1);
+  for (int i = 0; i <= s; ++i) { V[i].p = (char*)vbuf.p + vb * i; V[i].n = n; V[i].nsys = ns; V[i].prec = p; }
+  np = 0;
+  for (int i = 0; i < s; ++i)
+    for (int j = i; j < s; ++j) { pi[np] = i + 1; pj[np] = j + 1; ++np; }
+  for (int i = 0; i < s; ++i) { pi[np] = i + 1; pj[np] = 0; ++np; }
+  sbuf.alloc(sizeof(double2) * (size_t)ns * (kMaxPairs + s));
+  gram = sbuf.as<double2>();
+  coef = gram + (size_t)ns * kMaxPairs;
+}
+
+Context::~Context() {
+  engine.reset();
+  if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+namespace {
+__global__ void fill_consts(double2* ones, double2* mones, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { ones[i] = make_double2(1, 0); mones[i] = make_double2(-1, 0); }
+}
+}  // namespace
+
+void Context::ensure_consts(int n) {
+  if (n <= nconst) return;
+  consts.alloc(sizeof(double2) * 2 * n);
+  ones = consts.as<double2>();
+  mones = ones + n;
+  fill_consts<<<ceil_div(n, 128), 128, 0, stream>>>(ones, mones, n);
+  SMG_LAUNCH_OK();
+  nconst = n;
+}
+
+void upload(void* dst, const void* src, size_t bytes, int where, cudaStream_t st) {
+  SMG_CUDA_OK(cudaMemcpyAsync(dst, src, bytes, where == SMG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                              st));
+}
+void download(void* dst, const void* src, size_t bytes, int where, cudaStream_t st) {
+  SMG_CUDA_OK(cudaMemcpyAsync(dst, src, bytes, where == SMG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                              st));
+}
+
+// ------------------------------------------------------------ scalar kernels
+namespace {
+
+__device__ __forceinline__ bool off(const int* run) { return run != nullptr && *run == 0; }
+
+// r02 = ||b||^2, thresholds, active flags; run = run_outer && any(active)
+__global__ void gcr_init_kernel(int nsys, int K, const double2* __restrict__ bb, double tol2,
+                                const double* __restrict__ abs_target, double* r02, double* thr2, int* active,
+                                int* nk, double2* beta, const int* run_outer, int* run) {
+  if (threadIdx.x != 0) return;
+  const bool outer_on = !off(run_outer);
+  int any = 0;
+  for (int s = 0; s < nsys; ++s) {
+    const double b2 = bb[s].x;
+    r02[s] = b2;
+    thr2[s] = abs_target != nullptr ? abs_target[s] : tol2 * b2;
+    active[s] = (outer_on && b2 > thr2[s] && b2 > 0.0) ? 1 : 0;
+    nk[s] = 0;
+    any |= active[s];
+    for (int e = 0; e < K * K; ++e) beta[(size_t)s * K * K + e] = make_double2(0, 0);
+  }
+  *run = any;
+}
+
+// beta[s][k][j] += tmp[s][j]
+__global__ void gcr_beta_kernel(int nsys, int K, int k, const double2* __restrict__ tmp, double2* beta,
+                                const int* run) {
+  if (off(run)) return;
+  const int s = blockIdx.x;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double2& b = beta[((size_t)s * K + k) * K + j];
+    b = cadd(b, tmp[(size_t)s * K + j]);
+  }
+}
+
+// dd[s] = {||w_k||^2, <w_k, r>}: gamma_k, alpha_k (0 for inactive systems), 1/gamma, -alpha
+__global__ void gcr_alpha_kernel(int nsys, int K, int k, const double2* __restrict__ dd, const int* active,
+                                 double2* alpha, double2* gamma, double2* ginv, double2* na, const int* run) {
+  if (off(run)) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const double w2 = dd[2 * s].x;
+  const double2 wr = dd[2 * s + 1];
+  const double g = sqrt(fmax(w2, 0.0));
+  const bool ok = active[s] && g > 0.0 && isfinite(g);
+  const double2 a = ok ? make_double2(wr.x / g, wr.y / g) : make_double2(0, 0);
+  gamma[(size_t)s * K + k] = make_double2(ok ? g : 0.0, 0);
+  alpha[(size_t)s * K + k] = a;
+  ginv[s] = make_double2(g > 0.0 && isfinite(g) ? 1.0 / g : 0.0, 0);
+  na[s] = make_double2(-a.x, -a.y);
+}
+
+__global__ void gcr_check_kernel(int nsys, int k, const double2* __restrict__ r2, const double* __restrict__ thr2,
+                                 int* active, int* nk, const int* run_outer, int* run) {
+  if (off(run) || threadIdx.x != 0) return;
+  int any = 0;
+  for (int s = 0; s < nsys; ++s) {
+    if (active[s]) {
+      nk[s] = k + 1;
+      const double v = r2[s].x;
+      if (!(v > thr2[s])) active[s] = 0;   // converged, or NaN (stop and let the caller see it)
+    }
+    any |= active[s];
+  }
+  *run = (any && !off(run_outer)) ? 1 : 0;
+}
+
+// back substitution: gamma_j y_j + sum_{k>j} beta[k][j] y_k = alpha_j
+__global__ void gcr_solve_kernel(int nsys, int K, const double2* __restrict__ alpha, const double2* __restrict__ gamma,
+                                 const double2* __restrict__ beta, const int* __restrict__ nk, double2* y,
+                                 const int* run) {
+  if (off(run)) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const int n = nk[s];
+  for (int j = K - 1; j >= 0; --j) {
+    double2 v = make_double2(0, 0);
+    if (j < n) {
+      v = alpha[(size_t)s * K + j];
+      for (int k = j + 1; k < n; ++k) {
+        const double2 b = beta[((size_t)s * K + k) * K + j];
+        const double2 yk = y[(size_t)s * K + k];
+        v.x -= b.x * yk.x - b.y * yk.y;
+        v.y -= b.x * yk.y + b.y * yk.x;
+      }
+      const double g = gamma[(size_t)s * K + j].x;
+      v = g > 0 ? make_double2(v.x / g, v.y / g) : make_double2(0, 0);
+    }
+    y[(size_t)s * K + j] = v;
+  }
+}
+
+// CA-GCR(s): solve (W^dag W) a = W^dag r with a Cholesky factorisation of the
+// diagonally normalised Gram matrix; a basis vector whose pivot falls below
+// 1e-12 of its own norm (numerically dependent) is dropped.
+__global__ void ca_coef_kernel(int nsys, int s, int np, const double2* __restrict__ gram, double2* coef,
+                               const int* run) {
+  if (off(run)) return;
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= nsys) return;
+  double2 G[16][16], c[16], L[16][16];
+  double dsc[16];
+  bool drop[16];
+  const double2* g = gram + (size_t)sys * kMaxPairs;
+  int p = 0;
+  for (int i = 0; i < s; ++i)
+    for (int j = i; j < s; ++j) {
+      G[i][j] = g[p];
+      G[j][i] = make_double2(g[p].x, -g[p].y);
+      ++p;
+    }
+  for (int i = 0; i < s; ++i) c[i] = g[p++];
+  for (int i = 0; i < s; ++i) dsc[i] = G[i][i].x > 0 ? 1.0 / sqrt(G[i][i].x) : 0.0;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) G[i][j] = cscale(G[i][j], dsc[i] * dsc[j]);
+  for (int i = 0; i < s; ++i) c[i] = cscale(c[i], dsc[i]);
+  for (int j = 0; j < s; ++j) {
+    double d = G[j][j].x;
+    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
+    drop[j] = !(d > 1e-12) || dsc[j] == 0.0;
+    const double ljj = drop[j] ? 1.0 : sqrt(d);
+    L[j][j] = make_double2(ljj, 0);
+    for (int i = j + 1; i < s; ++i) {
+      if (drop[j]) { L[i][j] = make_double2(0, 0); continue; }
+      double2 v = G[i][j];
+      for (int k = 0; k < j; ++k) {
+        // v -= L[i][k] * conj(L[j][k])
+        const double2 a = L[i][k], b = L[j][k];
+        v.x -= a.x * b.x + a.y * b.y;
+        v.y -= a.y * b.x - a.x * b.y;
+      }
+      L[i][j] = make_double2(v.x / ljj, v.y / ljj);
+    }
+  }
+  double2 yv[16];
+  for (int i = 0; i < s; ++i) {   // L y = c
+    double2 v = drop[i] ? make_double2(0, 0) : c[i];
+    if (!drop[i])
+      for (int k = 0; k < i; ++k) { const double2 a = L[i][k], b = yv[k]; v.x -= a.x * b.x - a.y * b.y; v.y -= a.x * b.y + a.y * b.x; }
+    yv[i] = drop[i] ? make_double2(0, 0) : make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
+  }
+  double2 a[16];
+  for (int i = s - 1; i >= 0; --i) {   // L^dag a = y
+    double2 v = yv[i];
+    if (!drop[i])
+      for (int k = i + 1; k < s; ++k) {
+        // v -= conj(L[k][i]) * a[k]
+        const double2 l = L[k][i], b = a[k];
+        v.x -= l.x * b.x + l.y * b.y;
+        v.y -= l.x * b.y - l.y * b.x;
+      }
+    a[i] = drop[i] ? make_double2(0, 0) : make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
+  }
+  for (int i = 0; i < s; ++i) {
+    const double2 v = cscale(a[i], dsc[i]);
+    coef[(size_t)sys * s + i] = (isfinite(v.x) && isfinite(v.y)) ? v : make_double2(0, 0);
+  }
+}
+
+// CGNE scalars
+__global__ void cgne_init_kernel(int nsys, const double2* __restrict__ rr, double* rr_prev, double* rr0, int* active,
+                                 int* iters, int* run) {
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  for (int s = 0; s < nsys; ++s) {
+    rr_prev[s] = rr[s].x;
+    rr0[s] = rr[s].x;
+    active[s] = rr[s].x > 0.0 ? 1 : 0;
+    iters[s] = 0;
+    any |= active[s];
+  }
+  *run = any;
+}
+
+__global__ void cgne_alpha_kernel(int nsys, const double2* __restrict__ pp, const double* __restrict__ rr_prev,
+                                  const int* __restrict__ active, double2* alpha, double2* nalpha, const int* run) {
+  if (off(run)) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const double d = pp[s].x;
+  const double a = (active[s] && d > 0.0) ? rr_prev[s] / d : 0.0;
+  alpha[s] = make_double2(a, 0);
+  nalpha[s] = make_double2(-a, 0);
+}
+
+__global__ void cgne_beta_kernel(int nsys, int it, const double2* __restrict__ rr, double* rr_prev,
+                                 const double* __restrict__ rr0, double tol2, int* active, int* iters,
+                                 double2* bcoef, int* run) {
+  if (off(run) || threadIdx.x != 0) return;
+  int any = 0;
+  for (int s = 0; s < nsys; ++s) {
+    const double v = rr[s].x;
+    double b = 0.0;
+    if (active[s]) {
+      b = rr_prev[s] > 0 ? v / rr_prev[s] : 0.0;
+      rr_prev[s] = v;
+      iters[s] = it + 1;
+      if (!(v > tol2 * rr0[s])) active[s] = 0;
+    }
+    bcoef[2 * s] = make_double2(active[s] ? b : 0.0, 0);
+    bcoef[2 * s + 1] = make_double2(1.0, 0);
+    any |= active[s];
+  }
+  *run = any;
+}
+
+}  // namespace
+
+bool trace_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("SMG_TRACE");
+    v = (e != nullptr && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// -------------------------------------------------------------------- engine
+// Work areas and operator closures for one batch size and mass set.
+struct Engine {
+  Context& c;
+  int nsys;
+  int nlev;                         // number of coarse levels
+  Prec vp;                          // preconditioner vector precision
+  Store sp;                         // preconditioner storage
+  DevBuf mass_dev, map_dev;
+  const int* sys_map = nullptr;
+  std::vector<double> masses;       // per shift
+  std::vector<StoredBuf> kd_shift;  // per-shift block inverses (multi-mass)
+  std::vector<Stored> kd_s;         // descriptors handed to kd_apply
+  int nkd = 1;
+  // level 0
+  GcrWork outer;
+  DevBuf target_buf;
+  Vec r_s, tmpA, tmp_f, tmp64, zbuf;
+  DevBuf fbuf;
+  SmoothWork sm_f;
+  // levels 1..nlev+1 (index = level)
+  std::vector<GcrWork> lev;
+  std::vector<SmoothWork> sm_c;     // smoother of coarse level l at index l
+  std::vector<Vec> tmp_c;
+  DevBuf cbuf;
+  Workspace ws;                     // reduction partials, sized once so captured graphs stay valid
+  // graph of K_0
+  cudaGraphExec_t graph = nullptr;
+  bool graph_tried = false;
+
+  Engine(Context& ctx, int ns, const std::vector<double>& ms, int nrhs) : c(ctx), nsys(ns), masses(ms) {
+    const auto& P = c.params;
+    nlev = P.n_coarse;
+    vp = c.vprec();
+    sp = c.sstore();
+    const long long nf = (long long)c.g.V * 3;
+    // per-system masses and block inverses
+    std::vector<double> m(ns);
+    std::vector<int> map(ns);
+    for (int s = 0; s < ns; ++s) { map[s] = s / nrhs; m[s] = ms[map[s]]; }
+    mass_dev.alloc(sizeof(double) * ns);
+    SMG_CUDA_OK(cudaMemcpyAsync(mass_dev.p, m.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c.stream));
+    nkd = (int)ms.size();
+    if (nkd == 1 && ms[0] == c.mass) {
+      kd_s.push_back(c.kd_of(sp));
+    } else {
+      SMG_REQUIRE(nkd <= 16, "multi_solve: at most 16 masses");
+      map_dev.alloc(sizeof(int) * ns);
+      SMG_CUDA_OK(cudaMemcpyAsync(map_dev.p, map.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, c.stream));
+      sys_map = map_dev.as<int>();
+      DevBuf row;
+      row.alloc((size_t)(c.g.V / 16) * 48 * 48 * sizeof(double2));
+      kd_shift.resize(nkd);
+      for (int i = 0; i < nkd; ++i) {
+        kd_build(row.as<double2>(), c.g, c.fat64.as<double2>(), ms[i], c.stream);
+        kd_shift[i].alloc(sp, (size_t)(c.g.V / 16) * 48 * 48, (size_t)(c.g.V / 16) * 48);
+        kd_pack(kd_shift[i].st, row.as<double2>(), c.g.V / 16, c.stream);
+        kd_s.push_back(kd_shift[i].st);
+      }
+      SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    }
+    outer.alloc(nf, ns, P64, P.nkrylov);
+    target_buf.alloc(sizeof(double) * ns);
+    const size_t fb = (size_t)nf * ns * prec_bytes(vp);
+    fbuf.alloc(fb * 3 + (size_t)nf * ns * 16 * 2);
+    auto mkv = [&](void* p, long long n, Prec pr) { Vec v; v.p = p; v.n = n; v.nsys = ns; v.prec = pr; return v; };
+    r_s = mkv(fbuf.p, nf, vp);
+    tmpA = mkv((char*)fbuf.p + fb, nf, vp);
+    tmp_f = mkv((char*)fbuf.p + 2 * fb, nf, vp);
+    tmp64 = mkv((char*)fbuf.p + 3 * fb, nf, P64);
+    zbuf = mkv((char*)fbuf.p + 3 * fb + (size_t)nf * ns * 16, nf, P64);
+    sm_f.alloc(nf, ns, vp, P.smoother_s);
+    lev.resize(nlev + 2);
+    sm_c.resize(nlev + 2);
+    tmp_c.resize(nlev + 2);
+    lev[1].alloc(nf, ns, vp, P.inner_maxiter);
+    size_t cb = 0;
+    for (int l = 2; l <= nlev + 1; ++l) cb += (size_t)c.coarse[l - 2].g.V * c.coarse[l - 2].N * ns * prec_bytes(vp);
+    cbuf.alloc(cb > 0 ? cb : 16);
+    size_t off = 0;
+    for (int l = 2; l <= nlev + 1; ++l) {
+      const CoarseLevel& C = c.coarse[l - 2];
+      const long long n = (long long)C.g.V * C.N;
+      const bool coarsest = (l == nlev + 1);
+      lev[l].alloc(n, ns, vp, (coarsest && C.dense) ? 0 : P.inner_maxiter);
+      if (!coarsest) sm_c[l].alloc(n, ns, vp, P.smoother_s);
+      tmp_c[l] = mkv((char*)cbuf.p + off, n, vp);
+      off += (size_t)n * ns * prec_bytes(vp);
+    }
+    c.ensure_consts(ns * 2 + 2);
+    ws.get(sizeof(double2) * (size_t)(152 * 4) * kMaxPairs * ns);
+  }
+
+  ~Engine() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+
+  cudaStream_t st() const { return c.stream; }
+
+  // debugging aid (SMG_TRACE=1, never inside a capture): prints ||v||^2 of system 0
+  void dbg(const char* tag, const Vec& v) {
+    if (!trace_enabled()) return;
+    cudaStreamCaptureStatus cs;
+    SMG_CUDA_OK(cudaStreamIsCapturing(st(), &cs));
+    if (cs != cudaStreamCaptureStatusNone) return;
+    const int p0[1] = {0};
+    double2 h;
+    blas_pair_dots(&v, 1, p0, p0, 1, outer.ginv, 1, ws, st());
+    SMG_CUDA_OK(cudaMemcpyAsync(&h, outer.ginv, sizeof(double2), cudaMemcpyDeviceToHost, st()));
+    SMG_CUDA_OK(cudaStreamSynchronize(st()));
+    fprintf(stderr, "[smg]   %-12s |v|^2 = %.6e\n", tag, h.x);
+  }
+
+  // ---------------------------------------------------------------- operators
+  DslashParams dparams(Store s, int dagger) const {
+    DslashParams p;
+    p.g = c.g;
+    p.fat = c.fat_of(s);
+    if (c.has_naik) p.naik = c.naik_of(s);
+    p.c_naik = c.c_naik;
+    p.mass = mass_dev.as<double>();
+    p.dagger = dagger;
+    p.nsys = nsys;
+    return p;
+  }
+  void M64(const Vec& out, const Vec& in, const int* run = nullptr) {
+    dslash(out, in, dparams(S64, 0), st(), run);
+  }
+  void Ms(const Vec& out, const Vec& in, const int* run) { dslash(out, in, dparams(sp, 0), st(), run); }
+  void Binv(const Vec& out, const Vec& in, const int* run) {
+    kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run);
+  }
+  void As(const Vec& out, const Vec& in, const int* run) {
+    Ms(tmpA, in, run);
+    Binv(out, tmpA, run);
+  }
+  void op(int l, const Vec& out, const Vec& in, const int* run) {
+    if (l == 0) Ms(out, in, run);
+    else if (l == 1) As(out, in, run);
+    else {
+      const CoarseLevel& C = c.coarse[l - 2];
+      CoarseParams p;
+      p.g = C.g; p.N = C.N;
+      coarse_apply(out, in, p, C.Ss.st, st(), run);
+    }
+  }
+
+  // CA-GCR(s) post-smoother: e += sum_i a_i A^i V0 with V0 = r - A e preset in S.V[0]
+  void smooth(int l, SmoothWork& S, const Vec& e, const int* run) {
+    for (int i = 1; i <= S.s; ++i) op(l, S.V[i], S.V[i - 1], run);
+    blas_pair_dots(S.V.data(), S.s + 1, S.pi, S.pj, S.np, S.gram, kMaxPairs, ws, st(), run);
+    ca_coef_kernel<<<ceil_div(nsys, 32), 32, 0, st()>>>(nsys, S.s, S.np, S.gram, S.coef, run);
+    SMG_LAUNCH_OK();
+    blas_maxpy(e, S.V.data(), S.s, S.coef, S.s, 1.0, true, st(), run);
+  }
+
+  // Batched GCR on level l from G.b into G.x.  `abs_target` (device, per
+  // system) replaces tol^2 ||b||^2 when given.  Host checks only when `host`.
+  template <class Pre, class Op>
+  int gcr(GcrWork& G, Op&& A, Pre&& precond, double tol, const double* abs_target, const int* run_outer,
+          bool host, bool accumulate_x, int* iters_done = nullptr) {
+    const int K = G.K;
+    if (!accumulate_x) blas_zero(G.x, st(), run_outer);
+    if (!host) blas_copy(G.r, G.b, st(), run_outer);
+    {
+      const int p0[1] = {0}, p1[1] = {0};
+      blas_pair_dots(&G.r, 1, p0, p1, 1, G.dd, 1, ws, st(), run_outer);
+    }
+    gcr_init_kernel<<<1, 32, 0, st()>>>(nsys, K, G.dd, tol * tol, abs_target, G.r02, G.thr2, G.active, G.nk, G.beta,
+                                        run_outer, G.run);
+    SMG_LAUNCH_OK();
+    int done = 0;
+    for (int k = 0; k < K; ++k) {
+      if (host) {
+        int runv = 0;
+        SMG_CUDA_OK(cudaMemcpyAsync(&runv, G.run, sizeof(int), cudaMemcpyDeviceToHost, st()));
+        SMG_CUDA_OK(cudaStreamSynchronize(st()));
+        if (!runv) break;
+      }
+      precond(G.z[k], G.r, G.run);
+      dbg("gcr.z", G.z[k]);
+      A(G.w[k], G.z[k], G.run);
+      dbg("gcr.w", G.w[k]);
+      if (k > 0) {
+        int pi[kMaxPairs], pj[kMaxPairs];
+        for (int j = 0; j < k; ++j) { pi[j] = j; pj[j] = k; }
+        for (int pass = 0; pass < 2; ++pass) {
+          blas_pair_dots(G.w.data(), k + 1, pi, pj, k, G.tmp, K, ws, st(), G.run);
+          blas_maxpy(G.w[k], G.w.data(), k, G.tmp, K, -1.0, true, st(), G.run);
+          gcr_beta_kernel<<<nsys, 32, 0, st()>>>(nsys, K, k, G.tmp, G.beta, G.run);
+          SMG_LAUNCH_OK();
+        }
+      }
+      {
+        Vec vv[2] = {G.w[k], G.r};
+        const int pi[2] = {0, 0}, pj[2] = {0, 1};
+        blas_pair_dots(vv, 2, pi, pj, 2, G.dd, 2, ws, st(), G.run);
+      }
+      gcr_alpha_kernel<<<ceil_div(nsys, 64), 64, 0, st()>>>(nsys, K, k, G.dd, G.active, G.alpha, G.gamma, G.ginv,
+                                                            G.na, G.run);
+      SMG_LAUNCH_OK();
+      blas_scale(G.w[k], G.ginv, false, st(), G.run);
+      blas_maxpy(G.r, &G.w[k], 1, G.na, 1, 1.0, true, st(), G.run);
+      {
+        const int p0[1] = {0}, p1[1] = {0};
+        blas_pair_dots(&G.r, 1, p0, p1, 1, G.r2, 1, ws, st(), G.run);
+      }
+      gcr_check_kernel<<<1, 32, 0, st()>>>(nsys, k, G.r2, G.thr2, G.active, G.nk, run_outer, G.run);
+      SMG_LAUNCH_OK();
+      if (host && trace_enabled()) {
+        double2 h[3];
+        SMG_CUDA_OK(cudaMemcpyAsync(h, G.dd, sizeof(double2) * 2, cudaMemcpyDeviceToHost, st()));
+        SMG_CUDA_OK(cudaMemcpyAsync(h + 2, G.r2, sizeof(double2), cudaMemcpyDeviceToHost, st()));
+        SMG_CUDA_OK(cudaStreamSynchronize(st()));
+        fprintf(stderr, "[smg] outer k=%d |w|^2=%.3e <w,r>=(%.3e,%.3e) |r|^2=%.3e\n", k, h[0].x, h[1].x, h[1].y,
+                h[2].x);
+      }
+      ++done;
+    }
+    gcr_solve_kernel<<<ceil_div(nsys, 64), 64, 0, st()>>>(nsys, K, G.alpha, G.gamma, G.beta, G.nk, G.y, run_outer);
+    SMG_LAUNCH_OK();
+    blas_maxpy(G.x, G.z.data(), K, G.y, K, 1.0, true, st(), run_outer);
+    if (iters_done) *iters_done = done;
+    return done;
+  }
+
+  // solve on level l (>= 2): G = lev[l], input lev[l].b, output lev[l].x
+  void coarse_solve(int l, const int* run) {
+    const CoarseLevel& C = c.coarse[l - 2];
+    GcrWork& G = lev[l];
+    const bool coarsest = (l == nlev + 1);
+    if (coarsest && C.dense) {
+      if (vp == P64) dense_apply(G.x, G.b, C.D64.p, P64, C.nd, st(), run);
+      else dense_apply(G.x, G.b, C.D32.p, P32, C.nd, st(), run);
+      return;
+    }
+    auto A = [&](const Vec& o, const Vec& i, const int* r) { op(l, o, i, r); };
+    if (coarsest) {
+      auto pre = [&](const Vec& z, const Vec& r, const int* rr) { blas_copy(z, r, st(), rr); };
+      gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
+    } else {
+      auto pre = [&](const Vec& z, const Vec& r, const int* rr) { kcycle(l, z, r, rr); };
+      gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
+    }
+  }
+
+  // K_l for l >= 1: e = P solve(R r); e += CA-GCR(A_l, r - A_l e)
+  void kcycle(int l, const Vec& e, const Vec& r, const int* run) {
+    const CoarseLevel& C = c.coarse[l - 1];
+    dbg("K.r", r);
+    restrict_op(lev[l + 1].b, r, C.tg, C.Ps.st, st(), run);
+    dbg("K.rc", lev[l + 1].b);
+    coarse_solve(l + 1, run);
+    dbg("K.ec", lev[l + 1].x);
+    prolong_op(e, lev[l + 1].x, C.tg, C.Ps.st, st(), run);
+    dbg("K.e", e);
+    SmoothWork& S = (l == 1) ? sm_f : sm_c[l];
+    const Vec& t = (l == 1) ? tmp_f : tmp_c[l];
+    op(l, t, e, run);
+    dbg("K.Ae", t);
+    blas_sub(S.V[0], r, t, st(), run);
+    smooth(l, S, e, run);
+    dbg("K.e+smooth", e);
+  }
+
+  // K_0: z (FP64) from r (FP64)
+  void precond0_body(const Vec& z, const Vec& r) {
+    blas_copy(r_s, r, st());
+    dbg("K0.r_s", r_s);
+    GcrWork& G = lev[1];
+    Binv(G.b, r_s, nullptr);
+    dbg("K0.b1", G.b);
+    auto A = [&](const Vec& o, const Vec& i, const int* rr) { As(o, i, rr); };
+    auto pre = [&](const Vec& zz, const Vec& rr, const int* run) { kcycle(1, zz, rr, run); };
+    gcr(G, A, pre, c.params.inner_tol, nullptr, nullptr, false, false);
+    dbg("K0.x1", G.x);
+    Ms(tmp_f, G.x, nullptr);
+    dbg("K0.Mx1", tmp_f);
+    blas_sub(sm_f.V[0], r_s, tmp_f, st());
+    smooth(0, sm_f, G.x, nullptr);
+    blas_copy(z, G.x, st());
+  }
+
+  void precond0(const Vec& z, const Vec& r) {
+    if (!c.params.use_graph) { precond0_body(z, r); return; }
+    if (!graph && !graph_tried) {
+      graph_tried = true;
+      // first call runs eagerly so that every scratch buffer exists before capture
+      precond0_body(zbuf, r);
+      SMG_CUDA_OK(cudaStreamSynchronize(st()));
+      cudaGraph_t gr = nullptr;
+      SMG_CUDA_OK(cudaStreamBeginCapture(st(), cudaStreamCaptureModeThreadLocal));
+      precond0_body(zbuf, outer.r);
+      SMG_CUDA_OK(cudaStreamEndCapture(st(), &gr));
+      SMG_CUDA_OK(cudaGraphInstantiate(&graph, gr, 0));
+      cudaGraphDestroy(gr);
+      blas_copy(z, zbuf, st());
+      return;
+    }
+    if (graph && r.p == outer.r.p) {
+      SMG_CUDA_OK(cudaGraphLaunch(graph, st()));
+      blas_copy(z, zbuf, st());
+    } else {
+      precond0_body(z, r);
+    }
+  }
+
+  // Outer flexible GCR on M in FP64.  b, x: device FP64 [nsys][V][3].
+  // Returns per-system true residuals through `res`.
+  void solve(const Vec& b, const Vec& x, double tol, std::vector<double>& res, int& iters, int& restarts) {
+    const auto& P = c.params;
+    outer.x = x;
+    blas_zero(x, st());
+    blas_copy(outer.r, b, st());
+    const int p0[1] = {0};
+    blas_pair_dots(&b, 1, p0, p0, 1, outer.dd, 1, ws, st());
+    std::vector<double2> hb(nsys);
+    SMG_CUDA_OK(cudaMemcpyAsync(hb.data(), outer.dd, sizeof(double2) * nsys, cudaMemcpyDeviceToHost, st()));
+    SMG_CUDA_OK(cudaStreamSynchronize(st()));
+    std::vector<double> tgt(nsys), b2(nsys);
+    for (int s = 0; s < nsys; ++s) { b2[s] = hb[s].x; tgt[s] = tol * tol * b2[s]; }
+    SMG_CUDA_OK(cudaMemcpyAsync(target_buf.p, tgt.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st()));
+    iters = 0;
+    restarts = 0;
+    res.assign(nsys, 0.0);
+    std::vector<double2> hr(nsys);
+    while (true) {
+      auto A = [&](const Vec& o, const Vec& i, const int*) { M64(o, i); };
+      auto pre = [&](const Vec& z, const Vec& r, const int*) { precond0(z, r); };
+      const int left = P.max_outer - iters;
+      if (left <= 0) break;
+      const int Ksave = outer.K;
+      if (left < outer.K) outer.K = left;
+      int done = 0;
+      gcr(outer, A, pre, 0.0, target_buf.as<double>(), nullptr, true, true, &done);
+      outer.K = Ksave;
+      iters += done;
+      // true residual in FP64
+      M64(tmp64, x);
+      blas_sub(outer.r, b, tmp64, st());
+      blas_pair_dots(&outer.r, 1, p0, p0, 1, outer.r2, 1, ws, st());
+      SMG_CUDA_OK(cudaMemcpyAsync(hr.data(), outer.r2, sizeof(double2) * nsys, cudaMemcpyDeviceToHost, st()));
+      SMG_CUDA_OK(cudaStreamSynchronize(st()));
+      bool all = true, bad = false;
+      for (int s = 0; s < nsys; ++s) {
+        res[s] = b2[s] > 0 ? std::sqrt(hr[s].x / b2[s]) : 0.0;
+        if (!std::isfinite(res[s])) bad = true;
+        if (!(hr[s].x <= tgt[s])) all = false;
+      }
+      if (bad) throw StateError("breakdown: non-finite residual");
+      if (all || done == 0) break;
+      ++restarts;
+    }
+  }
+};
+
+void EngineDeleter::operator()(Engine* e) const { delete e; }
+
+// ------------------------------------------------------------------ context
+void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik, int where) {
+  const size_t nl = (size_t)4 * c.g.V * 9;
+  c.engine.reset();
+  c.fat64.alloc(nl * sizeof(double2));
+  upload(c.fat64.p, fat, nl * sizeof(double2), where, c.stream);
+  c.has_naik = naik != nullptr;
+  c.c_naik = c.has_naik ? c_naik : 0.0;
+  if (c.has_naik) {
+    c.naik64.alloc(nl * sizeof(double2));
+    upload(c.naik64.p, naik, nl * sizeof(double2), where, c.stream);
+  } else {
+    c.naik64.release();
+  }
+  c.fat64_st = Stored{c.fat64.p, nullptr, 1.0f, S64};
+  c.naik64_st = Stored{c.naik64.p, nullptr, 1.0f, S64};
+  // lower-precision copies; FP16 links carry one global scale (max |entry|)
+  auto make_lp = [&](const DevBuf& s64, StoredBuf& d32, StoredBuf& d16) {
+    d32.alloc(S32, nl, 0);
+    Vec a; a.p = s64.p; a.n = (long long)nl; a.prec = P64;
+    Vec b; b.p = d32.v.p; b.n = (long long)nl; b.prec = P32;
+    blas_copy(b, a, c.stream);
+    // FP16 from FP32 with global scale = max |entry|
+    std::vector<float2> h(nl);
+    SMG_CUDA_OK(cudaMemcpyAsync(h.data(), d32.v.p, nl * sizeof(float2), cudaMemcpyDeviceToHost, c.stream));
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    float mx = 0.f;
+    for (auto& v : h) mx = std::fmax(mx, std::fmax(std::fabs(v.x), std::fabs(v.y)));
+    const float sc = mx > 0 ? mx : 1.f;
+    std::vector<__half2> hh(nl);
+    for (size_t i = 0; i < nl; ++i) hh[i] = __floats2half2_rn(h[i].x / sc, h[i].y / sc);
+    d16.alloc(S16, nl, 0);
+    d16.st.gscale = sc;
+    SMG_CUDA_OK(cudaMemcpyAsync(d16.v.p, hh.data(), nl * sizeof(__half2), cudaMemcpyHostToDevice, c.stream));
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+  };
+  make_lp(c.fat64, c.fat32, c.fat16);
+  if (c.has_naik) make_lp(c.naik64, c.naik32, c.naik16);
+  else { c.naik32 = StoredBuf(); c.naik16 = StoredBuf(); }
+  c.gauge_set = true;
+  c.kd_valid = false;
+  c.setup_done = false;
+  c.coarse.clear();
+  if (c.mass_set) ctx_build_kd(c);
+  SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+}
+
+void ctx_build_kd(Context& c) {
+  SMG_REQUIRE(c.gauge_set, "set_gauge must come before the KD blocks are built");
+  const long long nblk = c.g.V / 16;
+  const size_t ne = (size_t)nblk * 48 * 48;
+  c.kd_row64.alloc(ne * sizeof(double2));
+  kd_build(c.kd_row64.as<double2>(), c.g, c.fat64.as<double2>(), c.mass, c.stream);
+  c.kd64.alloc(S64, ne, 0);
+  c.kd32.alloc(S32, ne, 0);
+  c.kd16.alloc(S16, ne, (size_t)nblk * 48);
+  kd_pack(c.kd64.st, c.kd_row64.as<double2>(), nblk, c.stream);
+  kd_pack(c.kd32.st, c.kd_row64.as<double2>(), nblk, c.stream);
+  kd_pack(c.kd16.st, c.kd_row64.as<double2>(), nblk, c.stream);
+  c.kd_valid = true;
+}
+
+void ctx_set_mass(Context& c, double m) {
+  SMG_REQUIRE(std::isfinite(m), "mass must be finite");
+  c.mass = m;
+  c.mass_set = true;
+  c.engine.reset();
+  if (c.gauge_set) ctx_build_kd(c);
+  SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+}
+
+namespace {
+
+// Operator of level l (1 = A on the fine lattice, >= 2 coarse) in FP64 on a
+// batch, restricted to one aggregate-crossing part (Galerkin probing).
+void op_part64(Context& c, int l, const Vec& out, const Vec& in, Vec& tmp, int part, const int agg[4]) {
+  if (l == 1) {
+    DslashParams p;
+    p.g = c.g;
+    p.fat = c.fat64_st;
+    if (c.has_naik) p.naik = c.naik64_st;
+    p.c_naik = c.c_naik;
+    p.mass0 = c.mass;
+    p.part = part;
+    for (int mu = 0; mu < 4; ++mu) p.agg[mu] = agg[mu];
+    p.nsys = in.nsys;
+    dslash(tmp, in, p, c.stream);
+    const Stored kd = c.kd64.st;
+    kd_apply(out, tmp, c.g, &kd, nullptr, 1, 0, c.stream);
+  } else {
+    const CoarseLevel& C = c.coarse[l - 2];
+    CoarseParams p;
+    p.g = C.g; p.N = C.N; p.part = part;
+    for (int mu = 0; mu < 4; ++mu) p.agg[mu] = agg[mu];
+    Stored s{C.S64.p, nullptr, 1.0f, S64};
+    coarse_apply(out, in, p, s, c.stream);
+  }
+}
+
+// Level-l operator (and adjoint) in preconditioner precision for the setup CGNE.
+struct SetupOp {
+  Context& c;
+  int l;
+  Vec tmp;
+  DevBuf tbuf;
+  void apply(const Vec& out, const Vec& in, int dagger, const int* run) {
+    const Store sp = c.sstore();
+    if (l == 1) {
+      DslashParams p;
+      p.g = c.g;
+      p.fat = c.fat_of(sp);
+      if (c.has_naik) p.naik = c.naik_of(sp);
+      p.c_naik = c.c_naik;
+      p.mass0 = c.mass;
+      p.nsys = in.nsys;
+      const Stored kd = c.kd_of(sp);
+      if (!dagger) {
+        p.dagger = 0;
+        dslash(tmp, in, p, c.stream, run);
+        kd_apply(out, tmp, c.g, &kd, nullptr, 1, 0, c.stream, run);
+      } else {
+        kd_apply(tmp, in, c.g, &kd, nullptr, 1, 1, c.stream, run);
+        p.dagger = 1;
+        dslash(out, tmp, p, c.stream, run);
+      }
+    } else {
+      const CoarseLevel& C = c.coarse[l - 2];
+      CoarseParams p;
+      p.g = C.g; p.N = C.N;
+      coarse_apply(out, in, p, dagger ? C.Sdags.st : C.Ss.st, c.stream, run);
+    }
+  }
+};
+
+}  // namespace
+
+void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, int where) {
+  SMG_REQUIRE(c.gauge_set && c.mass_set, "mg_setup needs set_gauge and set_mass first");
+  SMG_REQUIRE(P.n_coarse >= 1 && P.n_coarse <= SMG_MAX_COARSE, "n_coarse must be 1..3");
+  SMG_REQUIRE(P.inner_maxiter >= 1 && P.inner_maxiter <= 16, "inner_maxiter must be 1..16");
+  SMG_REQUIRE(P.nkrylov >= 1 && P.nkrylov <= 16, "nkrylov must be 1..16");
+  SMG_REQUIRE(P.smoother_s >= 1 && P.smoother_s <= 10, "smoother_s must be 1..10");
+  SMG_REQUIRE(P.precision >= SMG_PREC_DOUBLE && P.precision <= SMG_PREC_HALF, "bad precision");
+  SMG_REQUIRE(P.setup_maxiter >= 0 && P.max_outer >= 1, "bad iteration caps");
+  SMG_REQUIRE(phi0 != nullptr, "phi0 must hold one start array per coarsening");
+  c.engine.reset();
+  c.setup_done = false;
+  c.params = P;
+  c.coarse.clear();
+  c.coarse.resize(P.n_coarse);
+  if (!c.kd_valid) ctx_build_kd(c);
+  c.setup_mass = c.mass;
+  const Prec vp = c.vprec();
+  const Store sp = c.sstore();
+  cudaStream_t st = c.stream;
+  Geom fg = c.g;
+  int ndof = 3;
+  for (int l = 0; l < P.n_coarse; ++l) {
+    CoarseLevel& C = c.coarse[l];
+    const int nvec = P.nvec[l];
+    SMG_REQUIRE(nvec >= 1 && nvec <= 64, "nvec must be 1..64");
+    Geom cg;
+    for (int mu = 0; mu < 4; ++mu) {
+      const int a = P.agg[l][mu];
+      SMG_REQUIRE(a >= 1 && fg.L[mu] % a == 0, "aggregate extents must divide the level's lattice");
+      if (l == 0) SMG_REQUIRE(a % 2 == 0 && a >= 4 - (c.has_naik ? 0 : 2),
+                              "first aggregates must hold whole hypercubes (even, >= 4 with Naik links)");
+      cg.L[mu] = fg.L[mu] / a;
+    }
+    cg.V = cg.L[0] * cg.L[1] * cg.L[2] * cg.L[3];
+    C.g = cg;
+    C.N = 2 * nvec;
+    C.tg.fine = fg; C.tg.coarse = cg;
+    for (int mu = 0; mu < 4; ++mu) C.tg.agg[mu] = P.agg[l][mu];
+    C.tg.ndof = ndof; C.tg.nvec = nvec; C.tg.chi_mode = (l == 0) ? 0 : 1;
+    if (l > 0) SMG_REQUIRE(ndof % 2 == 0, "coarse dof must be even");
+    const long long n = (long long)fg.V * ndof;
+    // ---- near-null vectors: CGNE on A_l phi = 0 from phi0 (Table 1)
+    DevBuf raw;
+    raw.alloc((size_t)n * nvec * sizeof(double2));
+    upload(raw.p, phi0[l], (size_t)n * nvec * sizeof(double2), where, st);
+    C.setup_iters = 0;
+    if (P.setup_maxiter > 0) {
+      SetupOp A{c, l + 1, {}, {}};
+      const size_t vb = (size_t)n * nvec * prec_bytes(vp);
+      A.tbuf.alloc(vb);
+      A.tmp.p = A.tbuf.p; A.tmp.n = n; A.tmp.nsys = nvec; A.tmp.prec = vp;
+      DevBuf vbuf;
+      vbuf.alloc(vb * 4);
+      Vec x, r, p, q;
+      Vec* vs[4] = {&x, &r, &p, &q};
+      for (int i = 0; i < 4; ++i) { vs[i]->p = (char*)vbuf.p + vb * i; vs[i]->n = n; vs[i]->nsys = nvec; vs[i]->prec = vp; }
+      Vec raw64; raw64.p = raw.p; raw64.n = n; raw64.nsys = nvec; raw64.prec = P64;
+      blas_copy(x, raw64, st);
+      DevBuf sb;
+      sb.alloc(sizeof(double2) * nvec * 8 + sizeof(double) * nvec * 2 + sizeof(int) * (2 * nvec + 1));
+      double2* rr = sb.as<double2>();
+      double2* pp = rr + nvec;
+      double2* alpha = pp + nvec;
+      double2* nalpha = alpha + nvec;
+      double2* bcoef = nalpha + nvec;    // [nvec][2]
+      double* rr_prev = (double*)(bcoef + 2 * nvec + 2 * nvec);
+      double* rr0 = rr_prev + nvec;
+      int* active = (int*)(rr0 + nvec);
+      int* iters = active + nvec;
+      int* run = iters + nvec;
+      c.ensure_consts(nvec);
+      // r = -A x ; p = A^dag r
+      A.apply(q, x, 0, nullptr);
+      blas_maxpy(r, &q, 1, c.mones, 1, 1.0, false, st);
+      A.apply(p, r, 1, nullptr);
+      const int p0[1] = {0};
+      blas_pair_dots(&r, 1, p0, p0, 1, rr, 1, c.ws, st);
+      cgne_init_kernel<<<1, 32, 0, st>>>(nvec, rr, rr_prev, rr0, active, iters, run);
+      SMG_LAUNCH_OK();
+      const double tol2 = P.setup_tol * P.setup_tol;
+      for (int it = 0; it < P.setup_maxiter; ++it) {
+        if (it % 32 == 0) {
+          int runv = 0;
+          SMG_CUDA_OK(cudaMemcpyAsync(&runv, run, sizeof(int), cudaMemcpyDeviceToHost, st));
+          SMG_CUDA_OK(cudaStreamSynchronize(st));
+          if (!runv) break;
+        }
+        A.apply(q, p, 0, run);
+        blas_pair_dots(&p, 1, p0, p0, 1, pp, 1, c.ws, st, run);
+        cgne_alpha_kernel<<<ceil_div(nvec, 64), 64, 0, st>>>(nvec, pp, rr_prev, active, alpha, nalpha, run);
+        SMG_LAUNCH_OK();
+        blas_maxpy(x, &p, 1, alpha, 1, 1.0, true, st, run);
+        blas_maxpy(r, &q, 1, nalpha, 1, 1.0, true, st, run);
+        blas_pair_dots(&r, 1, p0, p0, 1, rr, 1, c.ws, st, run);
+        cgne_beta_kernel<<<1, 32, 0, st>>>(nvec, it, rr, rr_prev, rr0, tol2, active, iters, bcoef, run);
+        SMG_LAUNCH_OK();
+        A.apply(q, r, 1, run);
+        Vec pq[2] = {p, q};
+        blas_maxpy(p, pq, 2, bcoef, 2, 1.0, false, st, run);
+      }
+      std::vector<int> hit(nvec);
+      SMG_CUDA_OK(cudaMemcpyAsync(hit.data(), iters, sizeof(int) * nvec, cudaMemcpyDeviceToHost, st));
+      blas_copy(raw64, x, st);
+      SMG_CUDA_OK(cudaStreamSynchronize(st));
+      for (int v : hit) C.setup_iters = std::max(C.setup_iters, v);
+    }
+    // ---- chiral doubling + block orthonormalisation (FP64)
+    block_orthonormalize(raw.as<double2>(), C.tg, st);
+    C.raw64 = std::move(raw);
+    C.P64.alloc(S64, (size_t)n * nvec, 0);
+    transfer_pack(C.P64.st, C.raw64.as<double2>(), C.tg, st);
+    if (sp != S64) {
+      C.Ps.alloc(sp, (size_t)n * nvec, 0);
+      transfer_pack(C.Ps.st, C.raw64.as<double2>(), C.tg, st);
+    } else {
+      C.Ps.st = C.P64.st;
+    }
+    // ---- Galerkin stencil by probing R A_part P e_j, FP64
+    const int N = C.N;
+    const long long nc = (long long)cg.V * N;
+    C.S64.alloc((size_t)nc * 9 * N * sizeof(double2));
+    SMG_CUDA_OK(cudaMemsetAsync(C.S64.p, 0, C.S64.bytes, st));
+    {
+      int chunk = N;
+      const size_t per_col = (size_t)n * 16 * 3 + (size_t)nc * 16 * 2;
+      while (chunk > 1 && per_col * chunk > ((size_t)8 << 30)) chunk = (chunk + 1) / 2;
+      DevBuf pb;
+      pb.alloc(per_col * chunk);
+      for (int j0 = 0; j0 < N; j0 += chunk) {
+        const int ncol = std::min(chunk, N - j0);
+        Vec E, F, T, T2, Cm;
+        char* base = (char*)pb.p;
+        E.p = base; E.n = nc; E.nsys = ncol; E.prec = P64;
+        Cm.p = base + (size_t)nc * 16 * chunk; Cm.n = nc; Cm.nsys = ncol; Cm.prec = P64;
+        F.p = base + (size_t)nc * 16 * chunk * 2; F.n = n; F.nsys = ncol; F.prec = P64;
+        T.p = (char*)F.p + (size_t)n * 16 * chunk; T.n = n; T.nsys = ncol; T.prec = P64;
+        T2.p = (char*)T.p + (size_t)n * 16 * chunk; T2.n = n; T2.nsys = ncol; T2.prec = P64;
+        unit_probes(E.p ? (double2*)E.p : nullptr, cg.V, N, j0, ncol, st);
+        prolong_op(F, E, C.tg, C.P64.st, st);
+        for (int dir = 0; dir < 9; ++dir) {
+          op_part64(c, l + 1, T, F, T2, dir, C.tg.agg);
+          restrict_op(Cm, T, C.tg, C.P64.st, st);
+          galerkin_scatter(C.S64.as<double2>(), (const double2*)Cm.p, cg, N, dir, j0, ncol, st);
+        }
+      }
+      SMG_CUDA_OK(cudaStreamSynchronize(st));
+    }
+    C.Sdag64.alloc(C.S64.bytes);
+    coarse_dagger(C.Sdag64.as<double2>(), C.S64.as<double2>(), cg, N, st);
+    if (sp != S64) {
+      C.Ss.alloc(sp, (size_t)nc * 9 * N, (size_t)nc);
+      coarse_pack(C.Ss.st, C.S64.as<double2>(), cg, N, st);
+      C.Sdags.alloc(sp, (size_t)nc * 9 * N, (size_t)nc);
+      coarse_pack(C.Sdags.st, C.Sdag64.as<double2>(), cg, N, st);
+    } else {
+      C.Ss.st = Stored{C.S64.p, nullptr, 1.0f, S64};
+      C.Sdags.st = Stored{C.Sdag64.p, nullptr, 1.0f, S64};
+    }
+    // ---- dense coarsest inverse
+    C.dense = false;
+    if (l == P.n_coarse - 1 && nc <= P.dense_max) {
+      C.nd = (int)nc;
+      C.D64.alloc((size_t)nc * nc * sizeof(double2));
+      dense_from_stencil(C.D64.as<double2>(), C.S64.as<double2>(), cg, N, st);
+      DevBuf fac, perm;
+      fac.alloc(sizeof(double2) * nc);
+      perm.alloc(sizeof(int) * (nc + 1));
+      dense_invert(C.D64.as<double2>(), (int)nc, fac.as<double2>(), perm.as<int>(), st);
+      int sing = 0;
+      SMG_CUDA_OK(cudaMemcpyAsync(&sing, perm.as<int>() + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SMG_CUDA_OK(cudaStreamSynchronize(st));
+      SMG_REQUIRE(!sing, "coarsest operator is singular");
+      C.D32.alloc((size_t)nc * nc * sizeof(float2));
+      Vec a; a.p = C.D64.p; a.n = nc * nc; a.prec = P64;
+      Vec b; b.p = C.D32.p; b.n = nc * nc; b.prec = P32;
+      blas_copy(b, a, st);
+      C.dense = true;
+    }
+    SMG_CUDA_OK(cudaStreamSynchronize(st));
+    fg = cg;
+    ndof = N;
+  }
+  c.setup_done = true;
+}
+
+int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* masses, void* x, double tol, int where,
+              smg_solve_info* info) {
+  SMG_REQUIRE(c.setup_done, "solve needs mg_setup first");
+  SMG_REQUIRE(nrhs >= 1 && nshift >= 1 && nrhs * nshift <= 256, "1 <= nrhs*nshift <= 256");
+  SMG_REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<double> ms;
+  if (masses == nullptr) ms.push_back(c.mass);
+  else for (int i = 0; i < nshift; ++i) { SMG_REQUIRE(std::isfinite(masses[i]), "masses must be finite"); ms.push_back(masses[i]); }
+  const int ns = nrhs * nshift;
+  bool reuse = c.engine && c.engine->nsys == ns && c.engine->masses == ms;
+  if (!reuse) {
+    c.engine.reset();
+    c.engine.reset(new Engine(c, ns, ms, nrhs));
+  }
+  Engine& E = *c.engine;
+  const long long nf = (long long)c.g.V * 3;
+  const size_t vbytes = (size_t)nf * sizeof(double2);
+  DevBuf bx;
+  bx.alloc(vbytes * ns * 2);
+  Vec bv; bv.p = bx.p; bv.n = nf; bv.nsys = ns; bv.prec = P64;
+  Vec xv; xv.p = (char*)bx.p + vbytes * ns; xv.n = nf; xv.nsys = ns; xv.prec = P64;
+  for (int sh = 0; sh < nshift; ++sh) upload(bv.sys(sh * nrhs), b, vbytes * nrhs, where, c.stream);
+  std::vector<double> res;
+  int iters = 0, restarts = 0;
+  E.solve(bv, xv, tol, res, iters, restarts);
+  download(x, xv.p, vbytes * ns, where, c.stream);
+  SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  bool all = true;
+  for (int s = 0; s < ns; ++s) {
+    const bool conv = res[s] <= tol;
+    all = all && conv;
+    if (info) {
+      info[s].converged = conv ? 1 : 0;
+      info[s].iterations = iters;
+      info[s].restarts = restarts;
+      info[s].true_residual = res[s];
+      info[s].seconds = secs;
+    }
+  }
+  return all ? SMG_OK : SMG_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------- test hooks
+namespace {
+struct Scratch {
+  DevBuf a, b, t;
+};
+Vec conv_in(Context& c, DevBuf& buf, const void* in, long long n, int nsys, Prec p, int where) {
+  DevBuf stage;
+  stage.alloc((size_t)n * nsys * sizeof(double2));
+  upload(stage.p, in, stage.bytes, where, c.stream);
+  buf.alloc((size_t)n * nsys * prec_bytes(p));
+  Vec s; s.p = stage.p; s.n = n; s.nsys = nsys; s.prec = P64;
+  Vec d; d.p = buf.p; d.n = n; d.nsys = nsys; d.prec = p;
+  blas_copy(d, s, c.stream);
+  SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+  return d;
+}
+void conv_out(Context& c, void* out, const Vec& v, int where) {
+  DevBuf stage;
+  stage.alloc((size_t)v.n * v.nsys * sizeof(double2));
+  Vec d; d.p = stage.p; d.n = v.n; d.nsys = v.nsys; d.prec = P64;
+  blas_copy(d, v, c.stream);
+  download(out, stage.p, stage.bytes, where, c.stream);
+  SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+}
+Store store_of(int prec) { return prec == SMG_PREC_DOUBLE ? S64 : (prec == SMG_PREC_SINGLE ? S32 : S16); }
+Prec vprec_of(int prec) { return prec == SMG_PREC_DOUBLE ? P64 : P32; }
+}  // namespace
+
+void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void* out, int where) {
+  SMG_REQUIRE(c.gauge_set && c.mass_set, "set_gauge and set_mass first");
+  SMG_REQUIRE(op >= SMG_OP_M && op <= SMG_OP_ADAG, "bad operator");
+  SMG_REQUIRE(prec >= SMG_PREC_DOUBLE && prec <= SMG_PREC_HALF, "bad precision");
+  SMG_REQUIRE(nsys >= 1 && nsys <= 65535, "bad nsys");
+  if (!c.kd_valid) ctx_build_kd(c);
+  const long long n = (long long)c.g.V * 3;
+  const Prec vp = vprec_of(prec);
+  const Store sp = store_of(prec);
+  Scratch s;
+  Vec vin = conv_in(c, s.a, in, n, nsys, vp, where);
+  s.b.alloc(vin.bytes());
+  s.t.alloc(vin.bytes());
+  Vec vout = vin; vout.p = s.b.p;
+  Vec tmp = vin; tmp.p = s.t.p;
+  DslashParams p;
+  p.g = c.g;
+  p.fat = c.fat_of(sp);
+  if (c.has_naik) p.naik = c.naik_of(sp);
+  p.c_naik = c.c_naik;
+  p.mass0 = c.mass;
+  p.nsys = nsys;
+  const Stored kd = c.kd_of(sp);
+  switch (op) {
+    case SMG_OP_M: p.dagger = 0; dslash(vout, vin, p, c.stream); break;
+    case SMG_OP_MDAG: p.dagger = 1; dslash(vout, vin, p, c.stream); break;
+    case SMG_OP_KD: kd_apply(vout, vin, c.g, &kd, nullptr, 1, 0, c.stream); break;
+    case SMG_OP_KDDAG: kd_apply(vout, vin, c.g, &kd, nullptr, 1, 1, c.stream); break;
+    case SMG_OP_A: dslash(tmp, vin, p, c.stream); kd_apply(vout, tmp, c.g, &kd, nullptr, 1, 0, c.stream); break;
+    case SMG_OP_ADAG:
+      kd_apply(tmp, vin, c.g, &kd, nullptr, 1, 1, c.stream);
+      p.dagger = 1;
+      dslash(vout, tmp, p, c.stream);
+      break;
+  }
+  conv_out(c, out, vout, where);
+}
+
+// which: 0 restrict, 1 prolong, 2 coarse apply
+void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* in, void* out, int where) {
+  SMG_REQUIRE(c.setup_done, "mg_setup first");
+  SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "bad level");
+  SMG_REQUIRE(prec >= SMG_PREC_DOUBLE && prec <= SMG_PREC_HALF, "bad precision");
+  SMG_REQUIRE(nsys >= 1 && nsys <= 65535, "bad nsys");
+  CoarseLevel& C = c.coarse[l];
+  const Prec vp = vprec_of(prec);
+  const Store sp = store_of(prec);
+  const long long nfine = (long long)C.tg.fine.V * C.tg.ndof;
+  const long long ncoarse = (long long)C.g.V * C.N;
+  // the transfer and stencil are kept in FP64 and in the setup's preconditioner precision
+  auto pick_P = [&]() -> Stored {
+    if (sp == S64) return C.P64.st;
+    SMG_REQUIRE(C.Ps.st.s == sp, "that precision was not built by mg_setup");
+    return C.Ps.st;
+  };
+  Scratch s;
+  if (which == 0) {
+    Vec vin = conv_in(c, s.a, in, nfine, nsys, vp, where);
+    s.b.alloc((size_t)ncoarse * nsys * prec_bytes(vp));
+    Vec vout; vout.p = s.b.p; vout.n = ncoarse; vout.nsys = nsys; vout.prec = vp;
+    restrict_op(vout, vin, C.tg, pick_P(), c.stream);
+    conv_out(c, out, vout, where);
+  } else if (which == 1) {
+    Vec vin = conv_in(c, s.a, in, ncoarse, nsys, vp, where);
+    s.b.alloc((size_t)nfine * nsys * prec_bytes(vp));
+    Vec vout; vout.p = s.b.p; vout.n = nfine; vout.nsys = nsys; vout.prec = vp;
+    prolong_op(vout, vin, C.tg, pick_P(), c.stream);
+    conv_out(c, out, vout, where);
+  } else {
+    Vec vin = conv_in(c, s.a, in, ncoarse, nsys, vp, where);
+    s.b.alloc((size_t)ncoarse * nsys * prec_bytes(vp));
+    Vec vout = vin; vout.p = s.b.p;
+    CoarseParams p;
+    p.g = C.g; p.N = C.N;
+    Stored S;
+    if (sp == S64) S = Stored{C.S64.p, nullptr, 1.0f, S64};
+    else { SMG_REQUIRE(C.Ss.st.s == sp, "that precision was not built by mg_setup"); S = C.Ss.st; }
+    coarse_apply(vout, vin, p, S, c.stream);
+    conv_out(c, out, vout, where);
+  }
+}
+
+}  // namespace smg

@@ -1,0 +1,137 @@
+// Host-side solver state: the context behind the C ABI, the multigrid
+// hierarchy and the batched Krylov work areas.
+#pragma once
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ops.cuh"
+#include "smg.h"
+
+namespace smg {
+
+struct OomError {
+  std::string what;
+  explicit OomError(std::string w) : what(std::move(w)) {}
+};
+struct StateError {
+  std::string what;
+  explicit StateError(std::string w) : what(std::move(w)) {}
+};
+
+// Owning device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t b);
+  void release();
+  template <class T> T* as() const { return (T*)p; }
+};
+
+// Operator data in one storage precision (values + optional FP16 scales).
+struct StoredBuf {
+  DevBuf v, sc;
+  Stored st;
+  void alloc(Store s, size_t elems, size_t nscale);
+};
+
+struct CoarseLevel {
+  TransferGeom tg;          // fine side = the previous level
+  StoredBuf P64, Ps;        // prolongator, FP64 and preconditioner precision
+  DevBuf raw64;             // block-orthonormal vectors, FP64 [nvec][V][ndof]
+  Geom g;                   // coarse lattice
+  int N = 0;                // coarse dof per site
+  DevBuf S64, Sdag64;       // FP64 stencil and its adjoint
+  StoredBuf Ss, Sdags;      // preconditioner-precision copies
+  bool dense = false;       // exact coarsest solve
+  DevBuf D64, D32;          // dense inverse
+  int nd = 0;
+  int setup_iters = 0;
+};
+
+// Per-system scalars and vectors of one batched GCR.
+struct GcrWork {
+  int K = 0, nsys = 0;
+  std::vector<Vec> z, w;
+  Vec r, x, b;
+  DevBuf vbuf, sbuf;
+  double2 *alpha, *beta, *gamma, *y, *tmp, *dd, *na, *ginv, *r2;
+  double *r02, *thr2;
+  int *active, *nk, *run;
+  void alloc(long long n, int nsys, Prec p, int K);
+};
+
+struct SmoothWork {
+  int s = 0;
+  std::vector<Vec> V;
+  DevBuf vbuf, sbuf;
+  double2 *gram, *coef;
+  int pi[kMaxPairs], pj[kMaxPairs], np = 0;
+  void alloc(long long n, int nsys, Prec p, int s);
+};
+
+struct Engine;
+struct EngineDeleter {
+  void operator()(Engine* e) const;
+};
+
+struct Context {
+  Geom g{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::string err;
+  // gauge field
+  bool gauge_set = false, has_naik = false;
+  double c_naik = 0.0;
+  DevBuf fat64, naik64;
+  StoredBuf fat32, naik32, fat16, naik16;
+  // mass and KD blocks
+  double mass = 0.0;
+  bool mass_set = false, kd_valid = false;
+  DevBuf kd_row64;            // [nblk][48][48] row-major FP64 (B+m)^{-1}
+  StoredBuf kd64, kd32, kd16; // apply layout
+  // multigrid
+  bool setup_done = false;
+  smg_mg_params params{};
+  double setup_mass = 0.0;
+  std::vector<CoarseLevel> coarse;
+  Workspace ws;
+  std::unique_ptr<Engine, EngineDeleter> engine;
+  DevBuf consts;               // +1 / -1 coefficient arrays
+  double2 *ones = nullptr, *mones = nullptr;
+  int nconst = 0;
+  ~Context();
+
+  Prec vprec() const { return params.precision == SMG_PREC_DOUBLE ? P64 : P32; }
+  Store sstore() const {
+    return params.precision == SMG_PREC_DOUBLE ? S64 : (params.precision == SMG_PREC_SINGLE ? S32 : S16);
+  }
+  const Stored& fat_of(Store s) const { return s == S64 ? fat64_st : (s == S32 ? fat32.st : fat16.st); }
+  const Stored& naik_of(Store s) const { return s == S64 ? naik64_st : (s == S32 ? naik32.st : naik16.st); }
+  const Stored& kd_of(Store s) const { return s == S64 ? kd64.st : (s == S32 ? kd32.st : kd16.st); }
+  Stored fat64_st, naik64_st;
+  void ensure_consts(int n);
+};
+
+// Host entry points used by the C ABI (api.cu).
+void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik, int where);
+void ctx_set_mass(Context& c, double m);
+void ctx_mg_setup(Context& c, const smg_mg_params& p, const void* const* phi0, int where);
+int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* masses, void* x, double tol, int where,
+              smg_solve_info* info);
+void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void* out, int where);
+void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* in, void* out, int where);
+void ctx_build_kd(Context& c);
+void upload(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);
+void download(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);
+
+}  // namespace smg

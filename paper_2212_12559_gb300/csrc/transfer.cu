@@ -1,0 +1,264 @@
+// Restriction R, prolongation P = R^dag and block orthonormalisation of the
+// chirally doubled near-null vectors (Sec. 2.1, 2.3).
+//
+// A level has `ndof` components per site; the chirality of component d at
+// site x is parity(x) on the fine lattice and (d >= ndof/2) on coarse
+// lattices.  Each near-null vector v_k yields two prolongator columns, its
+// projections on the two chiralities, so the coarse site carries
+// N = 2 nvec components, (s, k) -> s*nvec + k.  The prolongator is stored
+// as [V][nvec][ndof]: column (s, k) at (x, d) is P[x][k][d] if chi(x,d) == s
+// and zero otherwise.
+#include "ops.cuh"
+
+namespace smg {
+namespace {
+
+__device__ __forceinline__ int agg_site(const TransferGeom& t, int X, int p) {
+  int Xc[4], c[4];
+  t.coarse.coords(X, Xc);
+  int q = p;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int lc = q % t.agg[mu];
+    q /= t.agg[mu];
+    c[mu] = Xc[mu] * t.agg[mu] + lc;
+  }
+  return t.fine.index(c);
+}
+
+__device__ __forceinline__ int site_parity(const Geom& g, int x) {
+  int c[4];
+  g.coords(x, c);
+  return (c[0] + c[1] + c[2] + c[3]) & 1;
+}
+
+__device__ __forceinline__ int chirality(const TransferGeom& t, int x, int d) {
+  return t.chi_mode == 0 ? site_parity(t.fine, x) : (d >= t.ndof / 2 ? 1 : 0);
+}
+
+__device__ __forceinline__ int coarse_of(const TransferGeom& t, int x) {
+  int c[4];
+  t.fine.coords(x, c);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) c[mu] /= t.agg[mu];
+  return t.coarse.index(c);
+}
+
+template <int NT>
+__device__ double2 block_sum(double2 v, double2* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double2 s = make_double2(0, 0);
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s = cadd(s, sh[i]);
+  return s;
+}
+
+// One CTA per (aggregate, chirality): MGS in vector order, two passes.
+__global__ void __launch_bounds__(256) orthonormalize_kernel(double2* __restrict__ raw, TransferGeom t) {
+  __shared__ double2 sh[8];
+  const int X = blockIdx.x, chi = blockIdx.y;
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  const int nel = npos * t.ndof;
+  const size_t vstride = (size_t)t.fine.V * t.ndof;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int k = 0; k < t.nvec; ++k) {
+      double2* vk = raw + (size_t)k * vstride;
+      for (int j = 0; j < k; ++j) {
+        const double2* vj = raw + (size_t)j * vstride;
+        double2 acc = make_double2(0, 0);
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+          const int p = e / t.ndof, d = e % t.ndof;
+          const int x = agg_site(t, X, p);
+          if (chirality(t, x, d) != chi) continue;
+          const size_t i = (size_t)x * t.ndof + d;
+          cfmac(acc, vj[i], vk[i]);
+        }
+        const double2 dot = block_sum<256>(acc, sh);
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+          const int p = e / t.ndof, d = e % t.ndof;
+          const int x = agg_site(t, X, p);
+          if (chirality(t, x, d) != chi) continue;
+          const size_t i = (size_t)x * t.ndof + d;
+          const double2 u = vj[i];
+          double2 v = vk[i];
+          v.x -= dot.x * u.x - dot.y * u.y;
+          v.y -= dot.x * u.y + dot.y * u.x;
+          vk[i] = v;
+        }
+        __syncthreads();
+      }
+      double2 acc = make_double2(0, 0);
+      for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int p = e / t.ndof, d = e % t.ndof;
+        const int x = agg_site(t, X, p);
+        if (chirality(t, x, d) != chi) continue;
+        const size_t i = (size_t)x * t.ndof + d;
+        cfmac(acc, vk[i], vk[i]);
+      }
+      const double2 n2 = block_sum<256>(acc, sh);
+      const double inv = n2.x > 0 ? 1.0 / sqrt(n2.x) : 0.0;
+      for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int p = e / t.ndof, d = e % t.ndof;
+        const int x = agg_site(t, X, p);
+        if (chirality(t, x, d) != chi) continue;
+        const size_t i = (size_t)x * t.ndof + d;
+        vk[i] = cscale(vk[i], inv);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename SL>
+__global__ void transfer_pack_kernel(SL* __restrict__ dst, const double2* __restrict__ raw, TransferGeom t) {
+  const long long total = (long long)t.fine.V * t.nvec * t.ndof;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int d = (int)(e % t.ndof);
+    const long long q = e / t.ndof;
+    const int k = (int)(q % t.nvec);
+    const long long x = q / t.nvec;
+    const double2 v = raw[(size_t)k * t.fine.V * t.ndof + (size_t)x * t.ndof + d];
+    if constexpr (sizeof(SL) == 16) dst[e] = SL{v.x, v.y};
+    else if constexpr (sizeof(SL) == 8) dst[e] = SL{(float)v.x, (float)v.y};
+    else dst[e] = __floats2half2_rn((float)v.x, (float)v.y);
+  }
+}
+
+// One CTA (4 warps) per (aggregate, system); lanes own vectors k = lane, lane + 32.
+template <typename R, typename SL>
+__global__ void __launch_bounds__(128) restrict_kernel(typename cplx<R>::T* __restrict__ out,
+                                                       const typename cplx<R>::T* __restrict__ in,
+                                                       const SL* __restrict__ P, R pscale, TransferGeom t,
+                                                       const int* run) {
+  using C = typename cplx<R>::T;
+  if (run != nullptr && *run == 0) return;
+  __shared__ C part[4][2][64];
+  const int X = blockIdx.x, s = blockIdx.y;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  const long long nf = (long long)t.fine.V * t.ndof;
+  const C* vin = in + (size_t)s * nf;
+  C acc[2][2] = {{C{0, 0}, C{0, 0}}, {C{0, 0}, C{0, 0}}};   // [chirality][k slot]
+  for (int p = w; p < npos; p += 4) {
+    const int x = agg_site(t, X, p);
+    const int par = site_parity(t.fine, x);
+    const SL* Px = P + (size_t)x * t.nvec * t.ndof;
+    for (int d = 0; d < t.ndof; ++d) {
+      const C v = vin[(size_t)x * t.ndof + d];
+      const int chi = t.chi_mode == 0 ? par : (d >= t.ndof / 2 ? 1 : 0);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int k = lane + 32 * q;
+        if (k < t.nvec) {
+          const C pv = ld<R>(Px, (size_t)k * t.ndof + d);
+          if (chi == 0) cfmac(acc[0][q], pv, v);
+          else cfmac(acc[1][q], pv, v);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    part[w][0][lane + 32 * q] = acc[0][q];
+    part[w][1][lane + 32 * q] = acc[1][q];
+  }
+  __syncthreads();
+  const int N = 2 * t.nvec;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int chi = i / t.nvec, k = i % t.nvec;
+    C sum = C{0, 0};
+#pragma unroll
+    for (int ww = 0; ww < 4; ++ww) sum = cadd(sum, part[ww][chi][k]);
+    out[(size_t)s * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
+  }
+}
+
+template <typename R, typename SL>
+__global__ void prolong_kernel(typename cplx<R>::T* __restrict__ out, const typename cplx<R>::T* __restrict__ in,
+                               const SL* __restrict__ P, R pscale, TransferGeom t, const int* run) {
+  using C = typename cplx<R>::T;
+  if (run != nullptr && *run == 0) return;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nf = (long long)t.fine.V * t.ndof;
+  if (e >= nf) return;
+  const int s = blockIdx.y;
+  const int x = (int)(e / t.ndof), d = (int)(e % t.ndof);
+  const int X = coarse_of(t, x);
+  const int chi = chirality(t, x, d);
+  const int N = 2 * t.nvec;
+  const C* vc = in + (size_t)s * t.coarse.V * N + (size_t)X * N + chi * t.nvec;
+  const SL* Px = P + (size_t)x * t.nvec * t.ndof + d;
+  C acc = C{0, 0};
+  for (int k = 0; k < t.nvec; ++k) cfma(acc, ld<R>(Px, (size_t)k * t.ndof), vc[k]);
+  out[(size_t)s * nf + e] = cscale(acc, pscale);
+}
+
+}  // namespace
+
+void block_orthonormalize(double2* raw, const TransferGeom& t, cudaStream_t st) {
+  orthonormalize_kernel<<<dim3(t.coarse.V, 2), 256, 0, st>>>(raw, t);
+  SMG_LAUNCH_OK();
+}
+
+void transfer_pack(Stored& dst, const double2* raw, const TransferGeom& t, cudaStream_t st) {
+  const long long total = (long long)t.fine.V * t.nvec * t.ndof;
+  unsigned grid = ceil_div(total, 256);
+  if (grid > 8192) grid = 8192;
+  dst.gscale = 1.0f;   // orthonormal columns: every entry has modulus <= 1
+  if (dst.s == S64) transfer_pack_kernel<double2><<<grid, 256, 0, st>>>((double2*)dst.p, raw, t);
+  else if (dst.s == S32) transfer_pack_kernel<float2><<<grid, 256, 0, st>>>((float2*)dst.p, raw, t);
+  else transfer_pack_kernel<__half2><<<grid, 256, 0, st>>>((__half2*)dst.p, raw, t);
+  SMG_LAUNCH_OK();
+}
+
+void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                 const int* run) {
+  SMG_REQUIRE(in.n == (long long)t.fine.V * t.ndof && out.n == (long long)t.coarse.V * 2 * t.nvec,
+              "restrict: field sizes do not match the transfer");
+  SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec && t.nvec <= 64, "restrict: batch/precision mismatch");
+  dim3 grid(t.coarse.V, in.nsys);
+  if (in.prec == P64) {
+    SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
+    restrict_kernel<double, double2><<<grid, 128, 0, st>>>((double2*)out.p, (const double2*)in.p,
+                                                           (const double2*)P.p, (double)P.gscale, t, run);
+  } else if (P.s == S32) {
+    restrict_kernel<float, float2><<<grid, 128, 0, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p,
+                                                         P.gscale, t, run);
+  } else {
+    SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
+    restrict_kernel<float, __half2><<<grid, 128, 0, st>>>((float2*)out.p, (const float2*)in.p,
+                                                          (const __half2*)P.p, P.gscale, t, run);
+  }
+  SMG_LAUNCH_OK();
+}
+
+void prolong_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                const int* run) {
+  SMG_REQUIRE(out.n == (long long)t.fine.V * t.ndof && in.n == (long long)t.coarse.V * 2 * t.nvec,
+              "prolong: field sizes do not match the transfer");
+  SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec, "prolong: batch/precision mismatch");
+  dim3 grid(ceil_div(out.n, 256), in.nsys);
+  if (in.prec == P64) {
+    SMG_REQUIRE(P.s == S64, "prolong: FP64 vectors need FP64 prolongator");
+    prolong_kernel<double, double2><<<grid, 256, 0, st>>>((double2*)out.p, (const double2*)in.p,
+                                                          (const double2*)P.p, (double)P.gscale, t, run);
+  } else if (P.s == S32) {
+    prolong_kernel<float, float2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p,
+                                                        P.gscale, t, run);
+  } else {
+    SMG_REQUIRE(P.s == S16, "prolong: unsupported storage");
+    prolong_kernel<float, __half2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p,
+                                                         (const __half2*)P.p, P.gscale, t, run);
+  }
+  SMG_LAUNCH_OK();
+}
+
+}  // namespace smg

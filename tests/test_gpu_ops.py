@@ -1,0 +1,177 @@
+"""GPU parity of the operator kernels against the FP64 oracle, through the C ABI.
+
+Bars: bit-exact maps; FP64 kernels to rounding (1e-12 relative); FP32 dslash
+within 1e-6 and FP16-storage dslash within 5e-3 (relative 2-norm error of the
+whole output); the KD and coarse operators at the same bars as their storage.
+Lattices span several CTAs and end in a partial one.
+"""
+import numpy as np
+import pytest
+
+from oracle.coarse import CoarseStencil, FineLevelOp, Transfer, galerkin
+from oracle.dirac import KahlerDirac, Staggered
+from oracle.force import link_gradient
+from oracle.lattice import Lattice
+from paper_2212_12559_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-6, 2: 5e-3}
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def make(dims, hisq, mass, seed=7):
+    thin = inputs.random_su3_links(dims, seed)
+    if hisq:
+        fat, naik, c = inputs.fat_links(thin, dims), inputs.naik_links(thin, dims), -1 / 24
+    else:
+        fat, naik, c = thin, None, 0.0
+    return fat, naik, c, Staggered(Lattice(dims), fat, naik, c, mass)
+
+
+@pytest.fixture(scope="module")
+def binding(lib):
+    from paper_2212_12559_gb300 import binding as b
+    return b
+
+
+@pytest.mark.parametrize("dims,agg", [((8, 4, 6, 10), (4, 2, 2, 2)), ((8, 12, 4, 8), (4, 4, 2, 4))])
+def test_maps_bit_exact(binding, dims, agg):
+    s = binding.Solver(dims)
+    par, blk, pos, aidx, apos = s.maps(agg)
+    lat = Lattice(dims)
+    kb, kp = lat.kd_block()
+    ai, ap = lat.aggregate(agg)
+    assert np.array_equal(par, lat.parity())
+    assert np.array_equal(blk, kb) and np.array_equal(pos, kp)
+    assert np.array_equal(aidx, ai) and np.array_equal(apos, ap)
+
+
+@pytest.mark.parametrize("hisq", [False, True])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_fine_operators(binding, hisq, prec):
+    dims = (8, 4, 6, 10)
+    fat, naik, c, op = make(dims, hisq, 0.05)
+    kd = KahlerDirac(op)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(0.05)
+    V = op.lat.V
+    v = inputs.gaussian_fields(3, V, 3, 11)
+    refs = {
+        binding.OP_M: [op.M(x) for x in v],
+        binding.OP_MDAG: [op.Mdag(x) for x in v],
+        binding.OP_KD: [kd.apply_inv(x) for x in v],
+        binding.OP_KDDAG: [kd.apply_inv_dag(x) for x in v],
+        binding.OP_A: [kd.A(x) for x in v],
+        binding.OP_ADAG: [kd.Adag(x) for x in v],
+    }
+    for o, ref in refs.items():
+        got = s.apply(o, v, prec)
+        for k in range(3):
+            assert rel(got[k], ref[k]) <= TOL[prec], (o, k, rel(got[k], ref[k]))
+
+
+def test_kd_inverse_matches_oracle(binding):
+    dims = (4, 4, 8, 4)
+    fat, naik, c, op = make(dims, True, 0.01)
+    kd = KahlerDirac(op)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(0.01)
+    got = s.kd_inverse()
+    assert rel(got, kd.inv) <= 1e-12
+    s.set_mass(0.3)       # rebuild at another mass
+    kd2 = KahlerDirac(Staggered(op.lat, fat, naik, c, 0.3))
+    assert rel(s.kd_inverse(), kd2.inv) <= 1e-12
+
+
+def oracle_stencil_layout(S: CoarseStencil):
+    Vc, N = S.X.shape[0], S.X.shape[1]
+    out = np.empty((Vc, N, 9, N), dtype=np.complex128)
+    out[:, :, 0, :] = S.X
+    for mu in range(4):
+        out[:, :, 1 + 2 * mu, :] = S.Yf[mu]
+        out[:, :, 2 + 2 * mu, :] = S.Yb[mu]
+    return out
+
+
+@pytest.mark.parametrize("dims,hisq", [((8, 8, 8, 8), False), ((12, 8, 4, 8), True)])
+def test_setup_cross_fed(binding, dims, hisq):
+    """Same raw near-null vectors on both sides (setup_maxiter = 0): the block
+    orthonormal vectors, the Galerkin stencils, R, P and the coarse apply agree."""
+    mass = 0.1
+    fat, naik, c, op = make(dims, hisq, mass)
+    lat = op.lat
+    nv1, nv2 = 4, 3
+    phi1 = inputs.gaussian_fields(nv1, lat.V, 3, 31)
+    agg1 = (4, 4, 4, 4)
+    cd = lat.coarse_dims(agg1)
+    agg2 = tuple(2 if d % 2 == 0 else 1 for d in cd)
+    phi2 = inputs.gaussian_fields(nv2, int(np.prod(cd)), 2 * nv1, 32)
+    # oracle
+    lop = FineLevelOp(KahlerDirac(op))
+    T1 = Transfer(lat, 3, lop.chirality(), agg1, phi1)
+    S1 = galerkin(lop, T1)
+    T2 = Transfer(S1.lat, S1.n, S1.chirality(), agg2, phi2)
+    S2 = galerkin(S1, T2)
+    # GPU
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(mass)
+    p = binding.default_params(n_coarse=2, agg=[agg1, agg2], nvec=[nv1, nv2], setup_maxiter=0,
+                               precision=binding.PREC_HALF)
+    s.mg_setup(p, [phi1, phi2])
+    assert rel(s.null_vectors(0), T1.P) <= 1e-12
+    assert rel(s.null_vectors(1), T2.P) <= 1e-12
+    assert rel(s.coarse_op(0), oracle_stencil_layout(S1)) <= 1e-11
+    assert rel(s.coarse_op(1), oracle_stencil_layout(S2)) <= 1e-11
+    v = inputs.gaussian_fields(2, lat.V, 3, 5)
+    vc = inputs.gaussian_fields(2, S1.lat.V, S1.n, 6)
+    vc2 = inputs.gaussian_fields(2, S2.lat.V, S2.n, 7)
+    for prec in (0, 2):
+        tol = TOL[prec]
+        r = s.restrict(0, v, prec)
+        pr = s.prolong(0, vc, prec)
+        ca = s.coarse_apply(0, vc, prec)
+        r2 = s.restrict(1, vc, prec)
+        pr2 = s.prolong(1, vc2, prec)
+        ca2 = s.coarse_apply(1, vc2, prec)
+        for k in range(2):
+            assert rel(r[k], T1.restrict(v[k])) <= tol
+            assert rel(pr[k], T1.prolong(vc[k])) <= tol
+            assert rel(ca[k], S1.apply(vc[k])) <= tol
+            assert rel(r2[k], T2.restrict(vc[k])) <= tol
+            assert rel(pr2[k], T2.prolong(vc2[k])) <= tol
+            assert rel(ca2[k], S2.apply(vc2[k])) <= tol
+
+
+@pytest.mark.parametrize("hisq", [False, True])
+def test_force_kernel(binding, hisq):
+    dims = (4, 6, 4, 8)
+    fat, naik, c, op = make(dims, hisq, 0.1)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    X = inputs.gaussian_field(op.lat.V, 3, 1)
+    Y = inputs.gaussian_field(op.lat.V, 3, 2)
+    assert rel(s.force(X, Y, 0), link_gradient(op, X, Y)) <= 1e-14
+    if hisq:
+        assert rel(s.force(X, Y, 1), link_gradient(op, X, Y, naik=True)) <= 1e-14
+
+
+def test_device_buffers_torch(binding):
+    """The same hook on torch CUDA tensors (device pointers) gives the host result."""
+    import torch
+    dims = (8, 4, 4, 4)
+    fat, naik, c, op = make(dims, False, 0.2)
+    s = binding.Solver(dims)
+    s.set_gauge(torch.from_numpy(fat).cuda(), None, 0.0)
+    s.set_mass(0.2)
+    v = inputs.gaussian_fields(2, op.lat.V, 3, 3)
+    got = s.apply(binding.OP_A, torch.from_numpy(v).cuda(), 0).cpu().numpy()
+    kd = KahlerDirac(op)
+    for k in range(2):
+        assert rel(got[k], kd.A(v[k])) <= 1e-12
