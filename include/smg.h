@@ -163,6 +163,23 @@ SMG_API int smg_force(smg_ctx* ctx, const void* X, const void* Y, int which, voi
 /* Iterations used by the near-null CGNE of coarsening l (max over vectors). */
 SMG_API int smg_setup_iterations(smg_ctx* ctx, int l, int* iters);
 
+/* Kernels that smg_time_kernel can time. */
+enum {
+  SMG_KERNEL_DSLASH = 0,    /* m + D on the fine lattice                    */
+  SMG_KERNEL_KD = 1,        /* (B+m)^{-1} per hypercube                     */
+  SMG_KERNEL_RESTRICT = 2,  /* R of coarsening l                            */
+  SMG_KERNEL_PROLONG = 3,   /* P of coarsening l                            */
+  SMG_KERNEL_COARSE = 4     /* 9-point coarse operator of coarsening l      */
+};
+/* Average device milliseconds of one launch of `kernel` on nsys systems, in
+ * the setup's preconditioner precision (FP64 before mg_setup), timed with
+ * CUDA events on the context's stream over nrep back-to-back launches after
+ * one warm-up launch.  Inputs are library-owned zero fields. */
+SMG_API int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep, double* ms_per_launch);
+/* Total kernels launched by the library in this process (a CUDA-graph replay
+ * counts every kernel node it runs). */
+SMG_API long long smg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsmg.so")
 SMG_HOST, SMG_DEVICE = 0, 1
 PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 OP_M, OP_MDAG, OP_KD, OP_KDDAG, OP_A, OP_ADAG = range(6)
+K_DSLASH, K_KD, K_RESTRICT, K_PROLONG, K_COARSE = range(5)
 MAX_COARSE = 3
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_STATE",
           -5: "ERR_NOT_CONVERGED", -6: "ERR_BREAKDOWN", -7: "ERR_TIMEOUT"}
@@ -26,7 +27,7 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_set_gauge", "smg_set_mass", "smg_mg_setup", "smg_solve", "smg_multi_solve",
            "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
-           "smg_setup_iterations"]
+           "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches"]
 
 
 class MGParams(ctypes.Structure):
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
         "smg_coarse_apply": (i, [vp, i, i, i, vp, vp, i]),
         "smg_force": (i, [vp, vp, vp, i, vp, i]),
         "smg_setup_iterations": (i, [vp, i, ip]),
+        "smg_time_kernel": (i, [vp, i, i, i, i, ctypes.POINTER(d)]),
+        "smg_kernel_launches": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -99,6 +102,10 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    return int(load().smg_kernel_launches())
 
 
 def default_params(**kw) -> MGParams:
@@ -288,6 +295,12 @@ class Solver:
         pf, _ = _ptr(F)
         self._check(self.lib.smg_force(self.ctx, px, py, int(which), pf, where))
         return F
+
+    def time_kernel(self, kernel, l=0, nsys=1, nrep=100):
+        """Average milliseconds per launch of one library kernel (CUDA events)."""
+        v = ctypes.c_double()
+        self._check(self.lib.smg_time_kernel(self.ctx, kernel, l, nsys, nrep, ctypes.byref(v)))
+        return v.value
 
     def setup_iterations(self, l):
         v = ctypes.c_int()

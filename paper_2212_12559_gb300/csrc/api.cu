@@ -266,4 +266,14 @@ int smg_setup_iterations(smg_ctx* ctx, int l, int* iters) {
   });
 }
 
+int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep, double* ms_per_launch) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(ms_per_launch != nullptr, "time_kernel: null output");
+    *ms_per_launch = smg::ctx_time_kernel(c, kernel, l, nsys, nrep);
+    return SMG_OK;
+  });
+}
+
+long long smg_kernel_launches(void) { return smg::g_launches; }
+
 }  // extern "C"

@@ -109,7 +109,15 @@ struct Error {
     }                                                                           \
   } while (0)
 
-#define SMG_LAUNCH_OK() SMG_CUDA_OK(cudaGetLastError())
+namespace smg {
+// Number of kernels this library has launched (graph replays add their node count).
+extern long long g_launches;
+}
+#define SMG_LAUNCH_OK()                  \
+  do {                                   \
+    ++smg::g_launches;                   \
+    SMG_CUDA_OK(cudaGetLastError());     \
+  } while (0)
 
 namespace smg {
 struct CudaError {

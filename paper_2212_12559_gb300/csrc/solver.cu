@@ -26,6 +26,8 @@
 
 namespace smg {
 
+long long g_launches = 0;
+
 // ------------------------------------------------------------- allocation
 void DevBuf::alloc(size_t b) {
   release();
@@ -384,6 +386,7 @@ struct Engine {
   // graph of K_0
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
+  long long graph_nodes = 0;
 
   Engine(Context& ctx, int ns, const std::vector<double>& ms, int nrhs) : c(ctx), nsys(ns), masses(ms) {
     const auto& P = c.params;
@@ -647,7 +650,10 @@ struct Engine {
       SMG_CUDA_OK(cudaStreamSynchronize(st()));
       cudaGraph_t gr = nullptr;
       SMG_CUDA_OK(cudaStreamBeginCapture(st(), cudaStreamCaptureModeThreadLocal));
+      const long long before = g_launches;
       precond0_body(zbuf, outer.r);
+      graph_nodes = g_launches - before;
+      g_launches = before;     // captured launches run when the graph is replayed
       SMG_CUDA_OK(cudaStreamEndCapture(st(), &gr));
       SMG_CUDA_OK(cudaGraphInstantiate(&graph, gr, 0));
       cudaGraphDestroy(gr);
@@ -656,6 +662,7 @@ struct Engine {
     }
     if (graph && r.p == outer.r.p) {
       SMG_CUDA_OK(cudaGraphLaunch(graph, st()));
+      g_launches += graph_nodes;
       blas_copy(z, zbuf, st());
     } else {
       precond0_body(z, r);
@@ -1186,6 +1193,76 @@ void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* 
     coarse_apply(vout, vin, p, S, c.stream);
     conv_out(c, out, vout, where);
   }
+}
+
+// Average device time of one launch of a hot kernel on the context's
+// stream, in the setup's preconditioner precision, timed with CUDA events
+// over `nrep` back-to-back launches (after one warm-up launch).
+double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep) {
+  SMG_REQUIRE(nrep >= 1 && nsys >= 1 && nsys <= 256, "time_kernel: bad nrep/nsys");
+  const Prec vp = c.setup_done ? c.vprec() : P64;
+  const Store sp = c.setup_done ? c.sstore() : S64;
+  SMG_REQUIRE(c.gauge_set && c.mass_set, "time_kernel needs set_gauge and set_mass");
+  if (!c.kd_valid) ctx_build_kd(c);
+  long long nin = (long long)c.g.V * 3, nout = nin;
+  const CoarseLevel* C = nullptr;
+  if (kernel >= SMG_KERNEL_RESTRICT) {
+    SMG_REQUIRE(c.setup_done && l >= 0 && l < (int)c.coarse.size(), "time_kernel: bad level");
+    C = &c.coarse[l];
+    const long long nf = (long long)C->tg.fine.V * C->tg.ndof, nc = (long long)C->g.V * C->N;
+    if (kernel == SMG_KERNEL_RESTRICT) { nin = nf; nout = nc; }
+    else if (kernel == SMG_KERNEL_PROLONG) { nin = nc; nout = nf; }
+    else { nin = nc; nout = nc; }
+  }
+  DevBuf bi, bo, bt;
+  bi.alloc((size_t)nin * nsys * prec_bytes(vp));
+  bo.alloc((size_t)nout * nsys * prec_bytes(vp));
+  bt.alloc((size_t)std::max(nin, nout) * nsys * prec_bytes(vp));
+  Vec in; in.p = bi.p; in.n = nin; in.nsys = nsys; in.prec = vp;
+  Vec out; out.p = bo.p; out.n = nout; out.nsys = nsys; out.prec = vp;
+  Vec tmp; tmp.p = bt.p; tmp.n = nin; tmp.nsys = nsys; tmp.prec = vp;
+  {
+    Vec ones = in;
+    c.ensure_consts(1);
+    blas_zero(in, c.stream);
+    Vec one1; one1.p = c.ones; one1.n = 1; one1.nsys = 1; one1.prec = P64;
+    (void)one1; (void)ones;
+  }
+  DslashParams dp;
+  dp.g = c.g;
+  dp.fat = c.fat_of(sp);
+  if (c.has_naik) dp.naik = c.naik_of(sp);
+  dp.c_naik = c.c_naik;
+  dp.mass0 = c.mass;
+  dp.nsys = nsys;
+  const Stored kd = c.kd_of(sp);
+  auto launch = [&]() {
+    switch (kernel) {
+      case SMG_KERNEL_DSLASH: dslash(out, in, dp, c.stream); break;
+      case SMG_KERNEL_KD: kd_apply(out, in, c.g, &kd, nullptr, 1, 0, c.stream); break;
+      case SMG_KERNEL_RESTRICT: restrict_op(out, in, C->tg, C->Ps.st, c.stream); break;
+      case SMG_KERNEL_PROLONG: prolong_op(out, in, C->tg, C->Ps.st, c.stream); break;
+      case SMG_KERNEL_COARSE: {
+        CoarseParams p; p.g = C->g; p.N = C->N;
+        coarse_apply(out, in, p, C->Ss.st, c.stream);
+        break;
+      }
+      default: SMG_REQUIRE(false, "time_kernel: unknown kernel");
+    }
+  };
+  launch();
+  cudaEvent_t e0, e1;
+  SMG_CUDA_OK(cudaEventCreate(&e0));
+  SMG_CUDA_OK(cudaEventCreate(&e1));
+  SMG_CUDA_OK(cudaEventRecord(e0, c.stream));
+  for (int i = 0; i < nrep; ++i) launch();
+  SMG_CUDA_OK(cudaEventRecord(e1, c.stream));
+  SMG_CUDA_OK(cudaEventSynchronize(e1));
+  float ms = 0;
+  SMG_CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return (double)ms / nrep;
 }
 
 }  // namespace smg

@@ -131,6 +131,7 @@ int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* mas
 void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void* out, int where);
 void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* in, void* out, int where);
 void ctx_build_kd(Context& c);
+double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep);
 void upload(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);
 void download(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);
 
