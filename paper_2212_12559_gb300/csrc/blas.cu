@@ -110,14 +110,155 @@ __global__ void sub_kernel(C* __restrict__ z, const C* __restrict__ x, const C* 
 }
 
 // ---------------------------------------------------------------- reductions
-// partial[s][block][p] = sum over this CTA's rows of conj(v[pi[p]]) * v[pj[p]]
+__device__ __forceinline__ bool off_flag(const int* run) { return run != nullptr && *run == 0; }
+
+// Cholesky solve of the CA-GCR normal equations for one system: (W^dag W) a =
+// W^dag r with the Gram matrix normalised to unit diagonal; a basis vector
+// whose pivot falls below 1e-12 of its norm (numerically dependent) is dropped.
+// In place, lower triangle only (s <= kMaxS).
+constexpr int kMaxS = 10;
+__device__ void ca_solve(const double2* g, int s, double2* coef) {
+  double2 L[kMaxS][kMaxS], c[kMaxS];
+  double dsc[kMaxS];
+  bool drop[kMaxS];
+  int p = 0;
+  for (int i = 0; i < s; ++i)
+    for (int j = i; j < s; ++j) {   // pair (i, j), i <= j: <W_i, W_j>; keep L[j][i] = conj
+      L[j][i] = make_double2(g[p].x, -g[p].y);
+      ++p;
+    }
+  for (int i = 0; i < s; ++i) c[i] = g[p++];
+  for (int i = 0; i < s; ++i) dsc[i] = L[i][i].x > 0 ? 1.0 / sqrt(L[i][i].x) : 0.0;
+  for (int i = 0; i < s; ++i) {
+    c[i] = cscale(c[i], dsc[i]);
+    for (int j = 0; j <= i; ++j) L[i][j] = cscale(L[i][j], dsc[i] * dsc[j]);
+  }
+  for (int j = 0; j < s; ++j) {
+    double d = L[j][j].x;
+    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
+    drop[j] = !(d > 1e-12) || dsc[j] == 0.0;
+    const double ljj = drop[j] ? 1.0 : sqrt(d);
+    L[j][j] = make_double2(ljj, 0);
+    for (int i = j + 1; i < s; ++i) {
+      if (drop[j]) { L[i][j] = make_double2(0, 0); continue; }
+      double2 v = L[i][j];
+      for (int k = 0; k < j; ++k) {
+        const double2 x = L[i][k], y = L[j][k];   // v -= x * conj(y)
+        v.x -= x.x * y.x + x.y * y.y;
+        v.y -= x.y * y.x - x.x * y.y;
+      }
+      L[i][j] = make_double2(v.x / ljj, v.y / ljj);
+    }
+  }
+  for (int i = 0; i < s; ++i) {   // L y = c
+    if (drop[i]) { c[i] = make_double2(0, 0); continue; }
+    double2 v = c[i];
+    for (int k = 0; k < i; ++k) { const double2 x = L[i][k], y = c[k]; v.x -= x.x * y.x - x.y * y.y; v.y -= x.x * y.y + x.y * y.x; }
+    c[i] = make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
+  }
+  for (int i = s - 1; i >= 0; --i) {   // L^dag a = y
+    if (drop[i]) { c[i] = make_double2(0, 0); continue; }
+    double2 v = c[i];
+    for (int k = i + 1; k < s; ++k) { const double2 l = L[k][i], b = c[k]; v.x -= l.x * b.x + l.y * b.y; v.y -= l.x * b.y - l.y * b.x; }
+    c[i] = make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
+  }
+  for (int i = 0; i < s; ++i) {
+    const double2 v = cscale(c[i], dsc[i]);
+    coef[i] = (isfinite(v.x) && isfinite(v.y)) ? v : make_double2(0, 0);
+  }
+}
+
+// Per-system scalar logic of the solvers, on the finished sums `o` (row ldo).
+__device__ void epilogue_system(const Epilogue& e, int s, const double2* o) {
+  switch (e.kind) {
+    case EPI_GCR_INIT: {
+      const double b2 = o[0].x;
+      const double thr = e.abs_target != nullptr ? e.abs_target[s] : e.tol2 * b2;
+      e.da[s] = b2;
+      e.db[s] = b2;
+      e.dc[s] = thr;
+      e.ia[s] = (!off_flag(e.run_outer) && b2 > thr && b2 > 0.0) ? 1 : 0;
+      e.ib[s] = 0;
+      break;
+    }
+    case EPI_GCR_BETA1: {
+      for (int j = 0; j < e.k; ++j) e.d2a[((size_t)s * e.K + e.k) * e.K + j] = o[j];
+      break;
+    }
+    case EPI_GCR_STEP: {
+      const int k = e.k, K = e.K;
+      double sumc = 0.0;
+      for (int j = 0; j < k; ++j) {
+        double2& b = e.d2a[((size_t)s * K + k) * K + j];
+        b = cadd(b, o[j]);
+        sumc += o[j].x * o[j].x + o[j].y * o[j].y;
+      }
+      const double ww = o[k].x - sumc;
+      const double2 wr = o[k + 1];
+      const double g = sqrt(fmax(ww, 0.0));
+      const bool gfin = g > 0.0 && isfinite(g);
+      const bool ok = e.ia[s] && gfin;
+      const double2 a = ok ? make_double2(wr.x / g, wr.y / g) : make_double2(0, 0);
+      e.d2b[(size_t)s * K + k] = make_double2(ok ? g : 0.0, 0);
+      e.d2c[(size_t)s * K + k] = a;
+      e.d2d[s] = make_double2(gfin ? 1.0 / g : 0.0, 0);
+      e.d2e[s] = make_double2(-a.x, -a.y);
+      if (e.ia[s]) {
+        e.ib[s] = k + 1;
+        const double r2 = e.db[s] - (a.x * a.x + a.y * a.y);
+        e.db[s] = r2;
+        // converged, stagnated (w_k in the span of w_0..w_{k-1}) or non-finite
+        if (!(r2 > e.dc[s]) || !gfin) e.ia[s] = 0;
+      }
+      break;
+    }
+    case EPI_CA: {
+      ca_solve(o, e.s, e.d2a + (size_t)s * e.s);
+      break;
+    }
+    case EPI_CGNE_INIT: {
+      e.da[s] = o[0].x;
+      e.db[s] = o[0].x;
+      e.ia[s] = o[0].x > 0.0 ? 1 : 0;
+      e.ib[s] = 0;
+      break;
+    }
+    case EPI_CGNE_ALPHA: {
+      const double d = o[0].x;
+      const double a = (e.ia[s] && d > 0.0) ? e.da[s] / d : 0.0;
+      e.d2a[s] = make_double2(a, 0);
+      e.d2b[s] = make_double2(-a, 0);
+      break;
+    }
+    case EPI_CGNE_BETA: {
+      const double v = o[0].x;
+      double b = 0.0;
+      if (e.ia[s]) {
+        b = e.da[s] > 0 ? v / e.da[s] : 0.0;
+        e.da[s] = v;
+        e.ib[s] = e.it + 1;
+        if (!(v > e.tol2 * e.db[s])) e.ia[s] = 0;
+      }
+      e.d2a[2 * s] = make_double2(e.ia[s] ? b : 0.0, 0);
+      e.d2a[2 * s + 1] = make_double2(1.0, 0);
+      break;
+    }
+    default: break;
+  }
+}
+
+// partial[s][block][p] = this CTA's share of conj(v[pi[p]]) * v[pj[p]]; the
+// last CTA to arrive adds the partials in a fixed order and runs the epilogue.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, double2* __restrict__ partial,
+                                                            double2* __restrict__ out, int ldo,
+                                                            unsigned* __restrict__ counter, Epilogue epi,
                                                             const int* run) {
   if (skip(run)) return;
   constexpr int TR = 128;   // rows per tile
   __shared__ double2 tile[kMaxVecs][TR];
   __shared__ double2 red[kThreads];
+  __shared__ bool last;
   const int s = blockIdx.y;
   const int np = a.npairs;
   const int groups = kThreads / np;               // row groups per pair
@@ -147,21 +288,109 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   }
   red[t] = active ? acc : make_double2(0, 0);
   __syncthreads();
+  const int nb = gridDim.x, nsys = gridDim.y;
   if (t < np) {
     double2 sum = make_double2(0, 0);
     for (int g = 0; g < groups; ++g) sum = cadd(sum, red[g * np + t]);
-    partial[((long long)s * gridDim.x + blockIdx.x) * np + t] = sum;
+    partial[((long long)s * nb + blockIdx.x) * np + t] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (t == 0) {
+    const unsigned ticket = atomicAdd(counter, 1u);
+    last = (ticket == (unsigned)(nb * nsys) - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = t; e < nsys * np; e += kThreads) {
+    const int ss = e / np, pp = e % np;
+    double2 sum = make_double2(0, 0);
+    for (int b = 0; b < nb; ++b) sum = cadd(sum, __ldcg(&partial[((long long)ss * nb + b) * np + pp]));
+    out[(long long)ss * ldo + pp] = sum;
+  }
+  if (t == 0) *counter = 0;
+  if (epi.kind == EPI_NONE) return;
+  __threadfence_block();
+  __syncthreads();
+  for (int ss = t; ss < nsys; ss += kThreads) epilogue_system(epi, ss, out + (long long)ss * ldo);
+  __syncthreads();
+  if (t == 0 && epi.run != nullptr &&
+      (epi.kind == EPI_GCR_INIT || epi.kind == EPI_GCR_STEP || epi.kind == EPI_CGNE_INIT ||
+       epi.kind == EPI_CGNE_BETA)) {
+    int any = 0;
+    for (int ss = 0; ss < nsys; ++ss) any |= epi.ia[ss];
+    *epi.run = (any && !off_flag(epi.run_outer)) ? 1 : 0;
   }
 }
 
-__global__ void pair_dot_finish(const double2* __restrict__ partial, int nblocks, int np, double2* __restrict__ out,
-                                int ldo, const int* run) {
+template <typename C>
+__global__ void gcr_update_kernel(MultiPtr W, int k, const double2* __restrict__ c, int ldc,
+                                  const double2* __restrict__ ginv, C* __restrict__ r, const double2* __restrict__ na,
+                                  long long n, const int* run) {
   if (skip(run)) return;
-  const int s = blockIdx.x;
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    double2 sum = make_double2(0, 0);
-    for (int b = 0; b < nblocks; ++b) sum = cadd(sum, partial[((long long)s * nblocks + b) * np + p]);
-    out[(long long)s * ldo + p] = sum;
+  using R = typename RealOf<C>::R;
+  const int s = blockIdx.y;
+  __shared__ C coef[kMaxVecs];
+  __shared__ C gi, nal;
+  if (threadIdx.x < k) {
+    const double2 v = c[(long long)s * ldc + threadIdx.x];
+    coef[threadIdx.x] = C{(R)(-v.x), (R)(-v.y)};
+  }
+  if (threadIdx.x == 0) {
+    gi = C{(R)ginv[s].x, (R)0};
+    nal = C{(R)na[s].x, (R)na[s].y};
+  }
+  __syncthreads();
+  C* wk = (C*)W.p[k];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    C acc = wk[s * n + i];
+    for (int j = 0; j < k; ++j) cfma(acc, coef[j], ((const C*)W.p[j])[s * n + i]);
+    acc = cmul(acc, gi);
+    wk[s * n + i] = acc;
+    C rv = r[s * n + i];
+    cfma(rv, nal, acc);
+    r[s * n + i] = rv;
+  }
+}
+
+template <typename C>
+__global__ void gcr_finish_kernel(C* __restrict__ x, MultiPtr Z, int K, const double2* __restrict__ alpha,
+                                  const double2* __restrict__ gamma, const double2* __restrict__ beta,
+                                  const int* __restrict__ nk, long long n, const int* run) {
+  if (skip(run)) return;
+  using R = typename RealOf<C>::R;
+  const int s = blockIdx.y;
+  __shared__ C yc[kMaxVecs];
+  __shared__ int nks;
+  if (threadIdx.x == 0) {
+    const int m = nk[s];
+    nks = m;
+    double2 y[kMaxVecs];
+    for (int j = K - 1; j >= 0; --j) {
+      double2 v = make_double2(0, 0);
+      if (j < m) {
+        v = alpha[(size_t)s * K + j];
+        for (int q = j + 1; q < m; ++q) {
+          const double2 b = beta[((size_t)s * K + q) * K + j];
+          v.x -= b.x * y[q].x - b.y * y[q].y;
+          v.y -= b.x * y[q].y + b.y * y[q].x;
+        }
+        const double g = gamma[(size_t)s * K + j].x;
+        v = g > 0 ? make_double2(v.x / g, v.y / g) : make_double2(0, 0);
+      }
+      y[j] = v;
+      yc[j] = C{(R)v.x, (R)v.y};
+    }
+  }
+  __syncthreads();
+  const int m = nks;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    C acc = x[s * n + i];
+    for (int j = 0; j < m; ++j) cfma(acc, yc[j], ((const C*)Z.p[j])[s * n + i]);
+    x[s * n + i] = acc;
   }
 }
 
@@ -231,7 +460,7 @@ void blas_sub(const Vec& z, const Vec& x, const Vec& y, cudaStream_t st, const i
 }
 
 void blas_pair_dots(const Vec* vs, int nv, const int* pi, const int* pj, int np, double2* out, int ldo,
-                    Workspace& ws, cudaStream_t st, const int* run) {
+                    Workspace& ws, cudaStream_t st, const int* run, const Epilogue& epi) {
   SMG_REQUIRE(nv >= 1 && nv <= kMaxVecs && np >= 1 && np <= kMaxPairs, "pair_dots: bad sizes");
   PairDotArgs a{};
   a.nv = nv; a.npairs = np; a.n = vs[0].n;
@@ -242,18 +471,52 @@ void blas_pair_dots(const Vec* vs, int nv, const int* pi, const int* pj, int np,
   for (int p = 0; p < np; ++p) { a.pi[p] = pi[p]; a.pj[p] = pj[p]; }
   const int nsys = vs[0].nsys;
   long long nb = (a.n + 4 * 128 - 1) / (4 * 128);
-  if (nb > 152 * 4) nb = 152 * 4;
+  if (nb > 152 * 2) nb = 152 * 2;
   if (nb < 1) nb = 1;
   double2* partial = (double2*)ws.get(sizeof(double2) * (size_t)nb * np * nsys);
   dim3 grid((unsigned)nb, nsys);
-  if (vs[0].prec == P64) pair_dot_kernel<double2><<<grid, kThreads, 0, st>>>(a, partial, run);
-  else pair_dot_kernel<float2><<<grid, kThreads, 0, st>>>(a, partial, run);
+  if (vs[0].prec == P64)
+    pair_dot_kernel<double2><<<grid, kThreads, 0, st>>>(a, partial, out, ldo, ws.counter, epi, run);
+  else
+    pair_dot_kernel<float2><<<grid, kThreads, 0, st>>>(a, partial, out, ldo, ws.counter, epi, run);
   SMG_LAUNCH_OK();
-  pair_dot_finish<<<nsys, 64, 0, st>>>(partial, (int)nb, np, out, ldo, run);
+}
+
+void blas_gcr_update(const Vec* W, int k, const double2* c, int ldc, const double2* ginv, const Vec& r,
+                     const double2* na, cudaStream_t st, const int* run) {
+  SMG_REQUIRE(k >= 0 && k < kMaxVecs, "gcr_update: bad k");
+  MultiPtr mp{};
+  for (int j = 0; j <= k; ++j) {
+    SMG_REQUIRE(W[j].n == r.n && W[j].prec == r.prec && W[j].nsys == r.nsys, "gcr_update: mismatch");
+    mp.p[j] = W[j].p;
+  }
+  dim3 grid(grid_for(r.n), r.nsys);
+  if (r.prec == P64)
+    gcr_update_kernel<<<grid, kThreads, 0, st>>>(mp, k, c, ldc, ginv, (double2*)r.p, na, r.n, run);
+  else
+    gcr_update_kernel<<<grid, kThreads, 0, st>>>(mp, k, c, ldc, ginv, (float2*)r.p, na, r.n, run);
+  SMG_LAUNCH_OK();
+}
+
+void blas_gcr_finish(const Vec& x, const Vec* Z, int K, const double2* alpha, const double2* gamma,
+                     const double2* beta, const int* nk, cudaStream_t st, const int* run) {
+  SMG_REQUIRE(K >= 1 && K <= kMaxVecs, "gcr_finish: bad K");
+  MultiPtr mp{};
+  for (int j = 0; j < K; ++j) mp.p[j] = Z[j].p;
+  dim3 grid(grid_for(x.n), x.nsys);
+  if (x.prec == P64)
+    gcr_finish_kernel<<<grid, kThreads, 0, st>>>((double2*)x.p, mp, K, alpha, gamma, beta, nk, x.n, run);
+  else
+    gcr_finish_kernel<<<grid, kThreads, 0, st>>>((float2*)x.p, mp, K, alpha, gamma, beta, nk, x.n, run);
   SMG_LAUNCH_OK();
 }
 
 void* Workspace::get(size_t bytes) {
+  if (counter == nullptr) {
+    SMG_CUDA_OK(cudaMalloc(&counter, sizeof(unsigned)));
+    SMG_CUDA_OK(cudaMemset(counter, 0, sizeof(unsigned)));
+    SMG_CUDA_OK(cudaDeviceSynchronize());
+  }
   if (bytes > cap) {
     if (ptr) SMG_CUDA_OK(cudaFree(ptr));
     ptr = nullptr;
@@ -266,6 +529,7 @@ void* Workspace::get(size_t bytes) {
 
 Workspace::~Workspace() {
   if (ptr) cudaFree(ptr);
+  if (counter) cudaFree(counter);
 }
 
 }  // namespace smg

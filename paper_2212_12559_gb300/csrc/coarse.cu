@@ -33,7 +33,9 @@ template <typename R, typename SL>
 __global__ void __launch_bounds__(256) coarse_apply_kernel(typename cplx<R>::T* __restrict__ out,
                                                            const typename cplx<R>::T* __restrict__ in,
                                                            const SL* __restrict__ S, const float* __restrict__ rs,
-                                                           Geom g, int N, int part, int4 agg4, const int* run) {
+                                                           Geom g, int N, int part, int4 agg4,
+                                                           const typename cplx<R>::T* __restrict__ sub_from,
+                                                           const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
   extern __shared__ unsigned char smem_raw[];
@@ -61,7 +63,9 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(typename cplx<R>::T* 
     }
     if (lane == 0) {
       if (rs != nullptr) acc = cscale(acc, (R)rs[(size_t)X * N + i]);
-      out[(size_t)s * n + (size_t)X * N + i] = acc;
+      const size_t oi = (size_t)s * n + (size_t)X * N + i;
+      if (sub_from != nullptr) acc = csub(sub_from[oi], acc);
+      out[oi] = acc;
     }
   }
 }
@@ -274,16 +278,16 @@ void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const St
     SMG_REQUIRE(S.s == S64, "coarse_apply: FP64 vectors need FP64 stencil");
     coarse_apply_kernel<double, double2><<<grid, 256, smem, st>>>((double2*)out.p, (const double2*)in.p,
                                                                   (const double2*)S.p, nullptr, p.g, p.N, p.part,
-                                                                  agg, run);
+                                                                  agg, (const double2*)p.sub_from, run);
   } else if (S.s == S32) {
     coarse_apply_kernel<float, float2><<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p,
                                                                 (const float2*)S.p, nullptr, p.g, p.N, p.part,
-                                                                agg, run);
+                                                                agg, (const float2*)p.sub_from, run);
   } else {
     SMG_REQUIRE(S.s == S16, "coarse_apply: unsupported storage");
     coarse_apply_kernel<float, __half2><<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p,
                                                                  (const __half2*)S.p, S.scale, p.g, p.N, p.part,
-                                                                 agg, run);
+                                                                 agg, (const float2*)p.sub_from, run);
   }
   SMG_LAUNCH_OK();
 }

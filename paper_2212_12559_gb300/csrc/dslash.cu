@@ -49,7 +49,9 @@ __global__ void __launch_bounds__(192) dslash_kernel(typename cplx<R>::T* __rest
                                                      const SL* __restrict__ fat, const SL* __restrict__ naik,
                                                      R fat_scale, R naik_scale, R half_c_naik,
                                                      const double* __restrict__ mass, double mass0, int dagger,
-                                                     int part, int4 agg, Geom g, const int* run) {
+                                                     int part, int4 agg, Geom g,
+                                                     const typename cplx<R>::T* __restrict__ sub_from,
+                                                     const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(192) dslash_kernel(typename cplx<R>::T* __rest
     acc.x = fma(m, v.x, acc.x);
     acc.y = fma(m, v.y, acc.y);
   }
+  if (sub_from != nullptr) acc = csub(sub_from[off + (size_t)x * 3 + a], acc);
   out[off + (size_t)x * 3 + a] = acc;
 }
 
@@ -110,7 +113,7 @@ void launch(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t s
   int4 agg = make_int4(p.agg[0], p.agg[1], p.agg[2], p.agg[3]);
   dslash_kernel<R, SL><<<grid, 192, 0, st>>>((C*)out.p, (const C*)in.p, (const SL*)p.fat.p, (const SL*)p.naik.p,
                                              (R)p.fat.gscale, (R)p.naik.gscale, (R)(0.5 * p.c_naik), p.mass,
-                                             p.mass0, p.dagger, p.part, agg, p.g, run);
+                                             p.mass0, p.dagger, p.part, agg, p.g, (const C*)p.sub_from, run);
   SMG_LAUNCH_OK();
 }
 

@@ -155,7 +155,8 @@ template <typename R, typename SL>
 __global__ void __launch_bounds__(192) kd_apply_kernel(typename cplx<R>::T* __restrict__ out,
                                                        const typename cplx<R>::T* __restrict__ in, KdSet kd,
                                                        const int* __restrict__ sys_map, int dagger, long long nblk,
-                                                       Geom g, const int* run) {
+                                                       Geom g, const typename cplx<R>::T* __restrict__ sub_from,
+                                                       const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
   __shared__ C vin[4][NB];
@@ -187,7 +188,9 @@ __global__ void __launch_bounds__(192) kd_apply_kernel(typename cplx<R>::T* __re
       cfmac(acc, k, vin[lb][c]);
     }
   }
-  out[off + (size_t)site * 3 + (r % 3)] = acc;
+  const size_t oi = off + (size_t)site * 3 + (r % 3);
+  if (sub_from != nullptr) acc = csub(sub_from[oi], acc);
+  out[oi] = acc;
 }
 
 }  // namespace
@@ -212,7 +215,7 @@ void kd_pack(Stored& dst, const double2* inv64, long long nblk, cudaStream_t st)
 }
 
 void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, const int* sys_map, int nkd,
-              int dagger, cudaStream_t st, const int* run) {
+              int dagger, cudaStream_t st, const int* run, const void* sub_from) {
   SMG_REQUIRE(in.n == (long long)g.V * 3 && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
               "kd_apply: shape mismatch");
   SMG_REQUIRE(nkd >= 1 && nkd <= 16, "kd_apply: 1..16 block inverses");
@@ -227,13 +230,13 @@ void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, co
   if (in.prec == P64) {
     SMG_REQUIRE(kd[0].s == S64, "kd_apply: FP64 vectors need FP64 blocks");
     kd_apply_kernel<double, double2><<<grid, 192, 0, st>>>((double2*)out.p, (const double2*)in.p, set, sys_map,
-                                                           dagger, nblk, g, run);
+                                                           dagger, nblk, g, (const double2*)sub_from, run);
   } else if (kd[0].s == S32) {
     kd_apply_kernel<float, float2><<<grid, 192, 0, st>>>((float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
-                                                         nblk, g, run);
+                                                         nblk, g, (const float2*)sub_from, run);
   } else if (kd[0].s == S16) {
     kd_apply_kernel<float, __half2><<<grid, 192, 0, st>>>((float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
-                                                          nblk, g, run);
+                                                          nblk, g, (const float2*)sub_from, run);
   } else {
     SMG_REQUIRE(false, "kd_apply: unsupported precision pair");
   }

@@ -28,6 +28,7 @@ struct DslashParams {
   int part = -1;             // -1 full; 0 self + mass; 1 + 2*mu + (0 fwd | 1 bwd): crossing hops
   int agg[4] = {1, 1, 1, 1};
   int nsys = 1;
+  const void* sub_from = nullptr;   // when set: out = sub_from - M in (residual form)
 };
 void dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run = nullptr);
 
@@ -40,8 +41,9 @@ void kd_build(double2* inv64, const Geom& g, const double2* fat64, double mass, 
 // block, [nblk][48 col][48 row]) in storage `dst.s` (per-(block,row) scale for FP16).
 void kd_pack(Stored& dst, const double2* inv64, long long nblk, cudaStream_t st);
 // out[s] = K[sys_map[s]] in[s] (or K^dag).  kd[] holds one packed inverse per mass.
+// With sub_from: out = sub_from - K in (residual form).
 void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, const int* sys_map, int nkd,
-              int dagger, cudaStream_t st, const int* run = nullptr);
+              int dagger, cudaStream_t st, const int* run = nullptr, const void* sub_from = nullptr);
 
 // ------------------------------------------------------- transfer operators
 // A level's lattice with `ndof` components per site; aggregates of agg[]
@@ -75,6 +77,7 @@ struct CoarseParams {
   int N;
   int part = -1;             // as DslashParams::part
   int agg[4] = {1, 1, 1, 1};
+  const void* sub_from = nullptr;   // when set: out = sub_from - A_hat in
 };
 void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
                   const int* run = nullptr);

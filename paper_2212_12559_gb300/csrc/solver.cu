@@ -71,14 +71,14 @@ void GcrWork::alloc(long long n, int ns, Prec p, int k) {
   for (int i = 0; i < K; ++i) { z[i] = mk(i); w[i] = mk(K + i); }
   r = mk(2 * K); x = mk(2 * K + 1); b = mk(2 * K + 2);
   const int Kk = K > 0 ? K : 1;
-  size_t nd2 = (size_t)ns * (Kk * 5 + Kk * Kk + 2 + 3);
+  size_t nd2 = (size_t)ns * (Kk * 5 + 2 + Kk * Kk + 2 + 3);
   size_t bytes = nd2 * sizeof(double2) + (size_t)ns * 2 * sizeof(double) + ((size_t)ns * 2 + 1) * sizeof(int);
   sbuf.alloc(bytes);
   double2* d = sbuf.as<double2>();
   alpha = d; d += ns * Kk;
   gamma = d; d += ns * Kk;
   y = d; d += ns * Kk;
-  tmp = d; d += ns * Kk;
+  tmp = d; d += ns * (Kk + 2);
   beta = d; d += ns * Kk * Kk;
   dd = d; d += ns * 2;
   na = d; d += ns;
@@ -139,214 +139,6 @@ void download(void* dst, const void* src, size_t bytes, int where, cudaStream_t 
   SMG_CUDA_OK(cudaMemcpyAsync(dst, src, bytes, where == SMG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                               st));
 }
-
-// ------------------------------------------------------------ scalar kernels
-namespace {
-
-__device__ __forceinline__ bool off(const int* run) { return run != nullptr && *run == 0; }
-
-// r02 = ||b||^2, thresholds, active flags; run = run_outer && any(active)
-__global__ void gcr_init_kernel(int nsys, int K, const double2* __restrict__ bb, double tol2,
-                                const double* __restrict__ abs_target, double* r02, double* thr2, int* active,
-                                int* nk, double2* beta, const int* run_outer, int* run) {
-  if (threadIdx.x != 0) return;
-  const bool outer_on = !off(run_outer);
-  int any = 0;
-  for (int s = 0; s < nsys; ++s) {
-    const double b2 = bb[s].x;
-    r02[s] = b2;
-    thr2[s] = abs_target != nullptr ? abs_target[s] : tol2 * b2;
-    active[s] = (outer_on && b2 > thr2[s] && b2 > 0.0) ? 1 : 0;
-    nk[s] = 0;
-    any |= active[s];
-    for (int e = 0; e < K * K; ++e) beta[(size_t)s * K * K + e] = make_double2(0, 0);
-  }
-  *run = any;
-}
-
-// beta[s][k][j] += tmp[s][j]
-__global__ void gcr_beta_kernel(int nsys, int K, int k, const double2* __restrict__ tmp, double2* beta,
-                                const int* run) {
-  if (off(run)) return;
-  const int s = blockIdx.x;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    double2& b = beta[((size_t)s * K + k) * K + j];
-    b = cadd(b, tmp[(size_t)s * K + j]);
-  }
-}
-
-// dd[s] = {||w_k||^2, <w_k, r>}: gamma_k, alpha_k (0 for inactive systems), 1/gamma, -alpha
-__global__ void gcr_alpha_kernel(int nsys, int K, int k, const double2* __restrict__ dd, const int* active,
-                                 double2* alpha, double2* gamma, double2* ginv, double2* na, const int* run) {
-  if (off(run)) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nsys) return;
-  const double w2 = dd[2 * s].x;
-  const double2 wr = dd[2 * s + 1];
-  const double g = sqrt(fmax(w2, 0.0));
-  const bool ok = active[s] && g > 0.0 && isfinite(g);
-  const double2 a = ok ? make_double2(wr.x / g, wr.y / g) : make_double2(0, 0);
-  gamma[(size_t)s * K + k] = make_double2(ok ? g : 0.0, 0);
-  alpha[(size_t)s * K + k] = a;
-  ginv[s] = make_double2(g > 0.0 && isfinite(g) ? 1.0 / g : 0.0, 0);
-  na[s] = make_double2(-a.x, -a.y);
-}
-
-__global__ void gcr_check_kernel(int nsys, int k, const double2* __restrict__ r2, const double* __restrict__ thr2,
-                                 int* active, int* nk, const int* run_outer, int* run) {
-  if (off(run) || threadIdx.x != 0) return;
-  int any = 0;
-  for (int s = 0; s < nsys; ++s) {
-    if (active[s]) {
-      nk[s] = k + 1;
-      const double v = r2[s].x;
-      if (!(v > thr2[s])) active[s] = 0;   // converged, or NaN (stop and let the caller see it)
-    }
-    any |= active[s];
-  }
-  *run = (any && !off(run_outer)) ? 1 : 0;
-}
-
-// back substitution: gamma_j y_j + sum_{k>j} beta[k][j] y_k = alpha_j
-__global__ void gcr_solve_kernel(int nsys, int K, const double2* __restrict__ alpha, const double2* __restrict__ gamma,
-                                 const double2* __restrict__ beta, const int* __restrict__ nk, double2* y,
-                                 const int* run) {
-  if (off(run)) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nsys) return;
-  const int n = nk[s];
-  for (int j = K - 1; j >= 0; --j) {
-    double2 v = make_double2(0, 0);
-    if (j < n) {
-      v = alpha[(size_t)s * K + j];
-      for (int k = j + 1; k < n; ++k) {
-        const double2 b = beta[((size_t)s * K + k) * K + j];
-        const double2 yk = y[(size_t)s * K + k];
-        v.x -= b.x * yk.x - b.y * yk.y;
-        v.y -= b.x * yk.y + b.y * yk.x;
-      }
-      const double g = gamma[(size_t)s * K + j].x;
-      v = g > 0 ? make_double2(v.x / g, v.y / g) : make_double2(0, 0);
-    }
-    y[(size_t)s * K + j] = v;
-  }
-}
-
-// CA-GCR(s): solve (W^dag W) a = W^dag r with a Cholesky factorisation of the
-// diagonally normalised Gram matrix; a basis vector whose pivot falls below
-// 1e-12 of its own norm (numerically dependent) is dropped.
-__global__ void ca_coef_kernel(int nsys, int s, int np, const double2* __restrict__ gram, double2* coef,
-                               const int* run) {
-  if (off(run)) return;
-  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sys >= nsys) return;
-  double2 G[16][16], c[16], L[16][16];
-  double dsc[16];
-  bool drop[16];
-  const double2* g = gram + (size_t)sys * kMaxPairs;
-  int p = 0;
-  for (int i = 0; i < s; ++i)
-    for (int j = i; j < s; ++j) {
-      G[i][j] = g[p];
-      G[j][i] = make_double2(g[p].x, -g[p].y);
-      ++p;
-    }
-  for (int i = 0; i < s; ++i) c[i] = g[p++];
-  for (int i = 0; i < s; ++i) dsc[i] = G[i][i].x > 0 ? 1.0 / sqrt(G[i][i].x) : 0.0;
-  for (int i = 0; i < s; ++i)
-    for (int j = 0; j < s; ++j) G[i][j] = cscale(G[i][j], dsc[i] * dsc[j]);
-  for (int i = 0; i < s; ++i) c[i] = cscale(c[i], dsc[i]);
-  for (int j = 0; j < s; ++j) {
-    double d = G[j][j].x;
-    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
-    drop[j] = !(d > 1e-12) || dsc[j] == 0.0;
-    const double ljj = drop[j] ? 1.0 : sqrt(d);
-    L[j][j] = make_double2(ljj, 0);
-    for (int i = j + 1; i < s; ++i) {
-      if (drop[j]) { L[i][j] = make_double2(0, 0); continue; }
-      double2 v = G[i][j];
-      for (int k = 0; k < j; ++k) {
-        // v -= L[i][k] * conj(L[j][k])
-        const double2 a = L[i][k], b = L[j][k];
-        v.x -= a.x * b.x + a.y * b.y;
-        v.y -= a.y * b.x - a.x * b.y;
-      }
-      L[i][j] = make_double2(v.x / ljj, v.y / ljj);
-    }
-  }
-  double2 yv[16];
-  for (int i = 0; i < s; ++i) {   // L y = c
-    double2 v = drop[i] ? make_double2(0, 0) : c[i];
-    if (!drop[i])
-      for (int k = 0; k < i; ++k) { const double2 a = L[i][k], b = yv[k]; v.x -= a.x * b.x - a.y * b.y; v.y -= a.x * b.y + a.y * b.x; }
-    yv[i] = drop[i] ? make_double2(0, 0) : make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
-  }
-  double2 a[16];
-  for (int i = s - 1; i >= 0; --i) {   // L^dag a = y
-    double2 v = yv[i];
-    if (!drop[i])
-      for (int k = i + 1; k < s; ++k) {
-        // v -= conj(L[k][i]) * a[k]
-        const double2 l = L[k][i], b = a[k];
-        v.x -= l.x * b.x + l.y * b.y;
-        v.y -= l.x * b.y - l.y * b.x;
-      }
-    a[i] = drop[i] ? make_double2(0, 0) : make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
-  }
-  for (int i = 0; i < s; ++i) {
-    const double2 v = cscale(a[i], dsc[i]);
-    coef[(size_t)sys * s + i] = (isfinite(v.x) && isfinite(v.y)) ? v : make_double2(0, 0);
-  }
-}
-
-// CGNE scalars
-__global__ void cgne_init_kernel(int nsys, const double2* __restrict__ rr, double* rr_prev, double* rr0, int* active,
-                                 int* iters, int* run) {
-  if (threadIdx.x != 0) return;
-  int any = 0;
-  for (int s = 0; s < nsys; ++s) {
-    rr_prev[s] = rr[s].x;
-    rr0[s] = rr[s].x;
-    active[s] = rr[s].x > 0.0 ? 1 : 0;
-    iters[s] = 0;
-    any |= active[s];
-  }
-  *run = any;
-}
-
-__global__ void cgne_alpha_kernel(int nsys, const double2* __restrict__ pp, const double* __restrict__ rr_prev,
-                                  const int* __restrict__ active, double2* alpha, double2* nalpha, const int* run) {
-  if (off(run)) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nsys) return;
-  const double d = pp[s].x;
-  const double a = (active[s] && d > 0.0) ? rr_prev[s] / d : 0.0;
-  alpha[s] = make_double2(a, 0);
-  nalpha[s] = make_double2(-a, 0);
-}
-
-__global__ void cgne_beta_kernel(int nsys, int it, const double2* __restrict__ rr, double* rr_prev,
-                                 const double* __restrict__ rr0, double tol2, int* active, int* iters,
-                                 double2* bcoef, int* run) {
-  if (off(run) || threadIdx.x != 0) return;
-  int any = 0;
-  for (int s = 0; s < nsys; ++s) {
-    const double v = rr[s].x;
-    double b = 0.0;
-    if (active[s]) {
-      b = rr_prev[s] > 0 ? v / rr_prev[s] : 0.0;
-      rr_prev[s] = v;
-      iters[s] = it + 1;
-      if (!(v > tol2 * rr0[s])) active[s] = 0;
-    }
-    bcoef[2 * s] = make_double2(active[s] ? b : 0.0, 0);
-    bcoef[2 * s + 1] = make_double2(1.0, 0);
-    any |= active[s];
-  }
-  *run = any;
-}
-
-}  // namespace
 
 bool trace_enabled() {
   static int v = -1;
@@ -483,39 +275,56 @@ struct Engine {
     p.nsys = nsys;
     return p;
   }
-  void M64(const Vec& out, const Vec& in, const int* run = nullptr) {
-    dslash(out, in, dparams(S64, 0), st(), run);
+  void M64(const Vec& out, const Vec& in, const int* run = nullptr, const Vec* sub = nullptr) {
+    DslashParams p = dparams(S64, 0);
+    p.sub_from = sub ? sub->p : nullptr;
+    dslash(out, in, p, st(), run);
   }
-  void Ms(const Vec& out, const Vec& in, const int* run) { dslash(out, in, dparams(sp, 0), st(), run); }
-  void Binv(const Vec& out, const Vec& in, const int* run) {
-    kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run);
+  void Ms(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
+    DslashParams p = dparams(sp, 0);
+    p.sub_from = sub ? sub->p : nullptr;
+    dslash(out, in, p, st(), run);
   }
-  void As(const Vec& out, const Vec& in, const int* run) {
+  void Binv(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
+    kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run, sub ? sub->p : nullptr);
+  }
+  void As(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
     Ms(tmpA, in, run);
-    Binv(out, tmpA, run);
+    Binv(out, tmpA, run, sub);
   }
-  void op(int l, const Vec& out, const Vec& in, const int* run) {
-    if (l == 0) Ms(out, in, run);
-    else if (l == 1) As(out, in, run);
+  // out = A_l in, or out = sub - A_l in
+  void op(int l, const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
+    if (l == 0) Ms(out, in, run, sub);
+    else if (l == 1) As(out, in, run, sub);
     else {
       const CoarseLevel& C = c.coarse[l - 2];
       CoarseParams p;
       p.g = C.g; p.N = C.N;
+      p.sub_from = sub ? sub->p : nullptr;
       coarse_apply(out, in, p, C.Ss.st, st(), run);
     }
   }
 
-  // CA-GCR(s) post-smoother: e += sum_i a_i A^i V0 with V0 = r - A e preset in S.V[0]
+  // CA-GCR(s) post-smoother: e += sum_i a_i A^i V0 with V0 = r - A e preset in
+  // S.V[0]; one reduction for the whole Gram system (its Cholesky solve runs
+  // in the reduction's last CTA).
   void smooth(int l, SmoothWork& S, const Vec& e, const int* run) {
     for (int i = 1; i <= S.s; ++i) op(l, S.V[i], S.V[i - 1], run);
-    blas_pair_dots(S.V.data(), S.s + 1, S.pi, S.pj, S.np, S.gram, kMaxPairs, ws, st(), run);
-    ca_coef_kernel<<<ceil_div(nsys, 32), 32, 0, st()>>>(nsys, S.s, S.np, S.gram, S.coef, run);
-    SMG_LAUNCH_OK();
+    Epilogue ep;
+    ep.kind = EPI_CA;
+    ep.s = S.s;
+    ep.d2a = S.coef;
+    blas_pair_dots(S.V.data(), S.s + 1, S.pi, S.pj, S.np, S.gram, kMaxPairs, ws, st(), run, ep);
     blas_maxpy(e, S.V.data(), S.s, S.coef, S.s, 1.0, true, st(), run);
   }
 
-  // Batched GCR on level l from G.b into G.x.  `abs_target` (device, per
-  // system) replaces tol^2 ||b||^2 when given.  Host checks only when `host`.
+  // Batched flexible GCR from G.b into G.x (Sec. 2.1), classical Gram-Schmidt
+  // with one re-orthogonalisation pass.  Per iteration: preconditioner,
+  // operator, two reductions (the second one's last CTA computes gamma_k,
+  // alpha_k, the recursive |r|^2 and the convergence flags), one projection
+  // and one fused normalise-and-update kernel.  `abs_target` (device, per
+  // system) replaces tol^2 ||b||^2.  With `host`, r already holds the
+  // residual and the host polls the run flag before each iteration.
   template <class Pre, class Op>
   int gcr(GcrWork& G, Op&& A, Pre&& precond, double tol, const double* abs_target, const int* run_outer,
           bool host, bool accumulate_x, int* iters_done = nullptr) {
@@ -523,12 +332,15 @@ struct Engine {
     if (!accumulate_x) blas_zero(G.x, st(), run_outer);
     if (!host) blas_copy(G.r, G.b, st(), run_outer);
     {
-      const int p0[1] = {0}, p1[1] = {0};
-      blas_pair_dots(&G.r, 1, p0, p1, 1, G.dd, 1, ws, st(), run_outer);
+      Epilogue ep;
+      ep.kind = EPI_GCR_INIT;
+      ep.tol2 = tol * tol;
+      ep.abs_target = abs_target;
+      ep.da = G.r02; ep.db = (double*)G.r2; ep.dc = G.thr2;
+      ep.ia = G.active; ep.ib = G.nk; ep.run = G.run; ep.run_outer = run_outer;
+      const int p0[1] = {0};
+      blas_pair_dots(&G.r, 1, p0, p0, 1, G.dd, 1, ws, st(), run_outer, ep);
     }
-    gcr_init_kernel<<<1, 32, 0, st()>>>(nsys, K, G.dd, tol * tol, abs_target, G.r02, G.thr2, G.active, G.nk, G.beta,
-                                        run_outer, G.run);
-    SMG_LAUNCH_OK();
     int done = 0;
     for (int k = 0; k < K; ++k) {
       if (host) {
@@ -541,45 +353,41 @@ struct Engine {
       dbg("gcr.z", G.z[k]);
       A(G.w[k], G.z[k], G.run);
       dbg("gcr.w", G.w[k]);
+      int pi[kMaxPairs], pj[kMaxPairs];
       if (k > 0) {
-        int pi[kMaxPairs], pj[kMaxPairs];
         for (int j = 0; j < k; ++j) { pi[j] = j; pj[j] = k; }
-        for (int pass = 0; pass < 2; ++pass) {
-          blas_pair_dots(G.w.data(), k + 1, pi, pj, k, G.tmp, K, ws, st(), G.run);
-          blas_maxpy(G.w[k], G.w.data(), k, G.tmp, K, -1.0, true, st(), G.run);
-          gcr_beta_kernel<<<nsys, 32, 0, st()>>>(nsys, K, k, G.tmp, G.beta, G.run);
-          SMG_LAUNCH_OK();
-        }
+        Epilogue ep;
+        ep.kind = EPI_GCR_BETA1;
+        ep.k = k; ep.K = K; ep.d2a = G.beta;
+        blas_pair_dots(G.w.data(), k + 1, pi, pj, k, G.tmp, K + 2, ws, st(), G.run, ep);
+        blas_maxpy(G.w[k], G.w.data(), k, G.tmp, K + 2, -1.0, true, st(), G.run);
       }
+      // second pass: <w_j, w_k>, |w_k|^2, <w_k, r>
+      Vec vv[kMaxVecs + 1];
+      for (int j = 0; j <= k; ++j) vv[j] = G.w[j];
+      vv[k + 1] = G.r;
+      for (int j = 0; j < k; ++j) { pi[j] = j; pj[j] = k; }
+      pi[k] = k; pj[k] = k;
+      pi[k + 1] = k; pj[k + 1] = k + 1;
       {
-        Vec vv[2] = {G.w[k], G.r};
-        const int pi[2] = {0, 0}, pj[2] = {0, 1};
-        blas_pair_dots(vv, 2, pi, pj, 2, G.dd, 2, ws, st(), G.run);
+        Epilogue ep;
+        ep.kind = EPI_GCR_STEP;
+        ep.k = k; ep.K = K;
+        ep.d2a = G.beta; ep.d2b = G.gamma; ep.d2c = G.alpha; ep.d2d = G.ginv; ep.d2e = G.na;
+        ep.db = (double*)G.r2; ep.dc = G.thr2;
+        ep.ia = G.active; ep.ib = G.nk; ep.run = G.run; ep.run_outer = run_outer;
+        blas_pair_dots(vv, k + 2, pi, pj, k + 2, G.tmp, K + 2, ws, st(), G.run, ep);
       }
-      gcr_alpha_kernel<<<ceil_div(nsys, 64), 64, 0, st()>>>(nsys, K, k, G.dd, G.active, G.alpha, G.gamma, G.ginv,
-                                                            G.na, G.run);
-      SMG_LAUNCH_OK();
-      blas_scale(G.w[k], G.ginv, false, st(), G.run);
-      blas_maxpy(G.r, &G.w[k], 1, G.na, 1, 1.0, true, st(), G.run);
-      {
-        const int p0[1] = {0}, p1[1] = {0};
-        blas_pair_dots(&G.r, 1, p0, p1, 1, G.r2, 1, ws, st(), G.run);
-      }
-      gcr_check_kernel<<<1, 32, 0, st()>>>(nsys, k, G.r2, G.thr2, G.active, G.nk, run_outer, G.run);
-      SMG_LAUNCH_OK();
+      blas_gcr_update(G.w.data(), k, G.tmp, K + 2, G.ginv, G.r, G.na, st(), G.run);
       if (host && trace_enabled()) {
-        double2 h[3];
-        SMG_CUDA_OK(cudaMemcpyAsync(h, G.dd, sizeof(double2) * 2, cudaMemcpyDeviceToHost, st()));
-        SMG_CUDA_OK(cudaMemcpyAsync(h + 2, G.r2, sizeof(double2), cudaMemcpyDeviceToHost, st()));
+        double h[1];
+        SMG_CUDA_OK(cudaMemcpyAsync(h, G.r2, sizeof(double), cudaMemcpyDeviceToHost, st()));
         SMG_CUDA_OK(cudaStreamSynchronize(st()));
-        fprintf(stderr, "[smg] outer k=%d |w|^2=%.3e <w,r>=(%.3e,%.3e) |r|^2=%.3e\n", k, h[0].x, h[1].x, h[1].y,
-                h[2].x);
+        fprintf(stderr, "[smg] outer k=%d |r|^2 (recursive) = %.3e\n", k, h[0]);
       }
       ++done;
     }
-    gcr_solve_kernel<<<ceil_div(nsys, 64), 64, 0, st()>>>(nsys, K, G.alpha, G.gamma, G.beta, G.nk, G.y, run_outer);
-    SMG_LAUNCH_OK();
-    blas_maxpy(G.x, G.z.data(), K, G.y, K, 1.0, true, st(), run_outer);
+    blas_gcr_finish(G.x, G.z.data(), K, G.alpha, G.gamma, G.beta, G.nk, st(), run_outer);
     if (iters_done) *iters_done = done;
     return done;
   }
@@ -615,10 +423,7 @@ struct Engine {
     prolong_op(e, lev[l + 1].x, C.tg, C.Ps.st, st(), run);
     dbg("K.e", e);
     SmoothWork& S = (l == 1) ? sm_f : sm_c[l];
-    const Vec& t = (l == 1) ? tmp_f : tmp_c[l];
-    op(l, t, e, run);
-    dbg("K.Ae", t);
-    blas_sub(S.V[0], r, t, st(), run);
+    op(l, S.V[0], e, run, &r);          // V0 = r - A_l e
     smooth(l, S, e, run);
     dbg("K.e+smooth", e);
   }
@@ -634,9 +439,7 @@ struct Engine {
     auto pre = [&](const Vec& zz, const Vec& rr, const int* run) { kcycle(1, zz, rr, run); };
     gcr(G, A, pre, c.params.inner_tol, nullptr, nullptr, false, false);
     dbg("K0.x1", G.x);
-    Ms(tmp_f, G.x, nullptr);
-    dbg("K0.Mx1", tmp_f);
-    blas_sub(sm_f.V[0], r_s, tmp_f, st());
+    Ms(sm_f.V[0], G.x, nullptr, &r_s);   // V0 = r - M e
     smooth(0, sm_f, G.x, nullptr);
     blas_copy(z, G.x, st());
   }
@@ -700,10 +503,9 @@ struct Engine {
       outer.K = Ksave;
       iters += done;
       // true residual in FP64
-      M64(tmp64, x);
-      blas_sub(outer.r, b, tmp64, st());
-      blas_pair_dots(&outer.r, 1, p0, p0, 1, outer.r2, 1, ws, st());
-      SMG_CUDA_OK(cudaMemcpyAsync(hr.data(), outer.r2, sizeof(double2) * nsys, cudaMemcpyDeviceToHost, st()));
+      M64(outer.r, x, nullptr, &b);
+      blas_pair_dots(&outer.r, 1, p0, p0, 1, outer.dd, 1, ws, st());
+      SMG_CUDA_OK(cudaMemcpyAsync(hr.data(), outer.dd, sizeof(double2) * nsys, cudaMemcpyDeviceToHost, st()));
       SMG_CUDA_OK(cudaStreamSynchronize(st()));
       bool all = true, bad = false;
       for (int s = 0; s < nsys; ++s) {
@@ -932,9 +734,10 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
       blas_maxpy(r, &q, 1, c.mones, 1, 1.0, false, st);
       A.apply(p, r, 1, nullptr);
       const int p0[1] = {0};
-      blas_pair_dots(&r, 1, p0, p0, 1, rr, 1, c.ws, st);
-      cgne_init_kernel<<<1, 32, 0, st>>>(nvec, rr, rr_prev, rr0, active, iters, run);
-      SMG_LAUNCH_OK();
+      Epilogue e0;
+      e0.kind = EPI_CGNE_INIT;
+      e0.da = rr_prev; e0.db = rr0; e0.ia = active; e0.ib = iters; e0.run = run;
+      blas_pair_dots(&r, 1, p0, p0, 1, rr, 1, c.ws, st, nullptr, e0);
       const double tol2 = P.setup_tol * P.setup_tol;
       for (int it = 0; it < P.setup_maxiter; ++it) {
         if (it % 32 == 0) {
@@ -944,14 +747,17 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
           if (!runv) break;
         }
         A.apply(q, p, 0, run);
-        blas_pair_dots(&p, 1, p0, p0, 1, pp, 1, c.ws, st, run);
-        cgne_alpha_kernel<<<ceil_div(nvec, 64), 64, 0, st>>>(nvec, pp, rr_prev, active, alpha, nalpha, run);
-        SMG_LAUNCH_OK();
+        Epilogue ea;
+        ea.kind = EPI_CGNE_ALPHA;
+        ea.da = rr_prev; ea.ia = active; ea.d2a = alpha; ea.d2b = nalpha;
+        blas_pair_dots(&p, 1, p0, p0, 1, pp, 1, c.ws, st, run, ea);
         blas_maxpy(x, &p, 1, alpha, 1, 1.0, true, st, run);
         blas_maxpy(r, &q, 1, nalpha, 1, 1.0, true, st, run);
-        blas_pair_dots(&r, 1, p0, p0, 1, rr, 1, c.ws, st, run);
-        cgne_beta_kernel<<<1, 32, 0, st>>>(nvec, it, rr, rr_prev, rr0, tol2, active, iters, bcoef, run);
-        SMG_LAUNCH_OK();
+        Epilogue eb;
+        eb.kind = EPI_CGNE_BETA;
+        eb.it = it; eb.tol2 = tol2;
+        eb.da = rr_prev; eb.db = rr0; eb.ia = active; eb.ib = iters; eb.d2a = bcoef; eb.run = run;
+        blas_pair_dots(&r, 1, p0, p0, 1, rr, 1, c.ws, st, run, eb);
         A.apply(q, r, 1, run);
         Vec pq[2] = {p, q};
         blas_maxpy(p, pq, 2, bcoef, 2, 1.0, false, st, run);

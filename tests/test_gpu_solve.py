@@ -168,3 +168,27 @@ def test_error_paths(binding):
     with pytest.raises(binding.SmgError) as e:
         s.solve(b, 2.0)
     assert e.value.code == -1
+
+
+def test_iteration_count_matches_oracle(binding):
+    """Same near-null vectors on both sides (oracle CGNE output fed to the GPU
+    with setup_maxiter = 0): the FP64 GPU K-cycle needs the oracle's number of
+    outer iterations (rounding may move an inner stop by one step)."""
+    from oracle.coarse import FineLevelOp, near_null_vectors
+    from oracle.dirac import KahlerDirac
+    from oracle.mg import MGParams, MultigridSolver
+    dims = (8, 8, 8, 8)
+    fat, naik, c, op = problem(dims, False, 0.05, seed=1003)
+    phi0 = inputs.gaussian_fields(8, op.lat.V, 3, 77)
+    raw, _ = near_null_vectors(FineLevelOp(KahlerDirac(op)), phi0, 1e-6, 40)
+    mg = MultigridSolver(op, MGParams(agg=[(4, 4, 4, 4)], nvec=[8], setup_maxiter=0), [raw])
+    b = inputs.gaussian_field(op.lat.V, 3, 78)
+    x_o, it_o, res_o = mg.solve(b, 1e-10)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(0.05)
+    s.mg_setup(binding.default_params(nvec=[8], setup_maxiter=0), [raw])
+    x, info = s.solve(b, 1e-10)
+    assert info.converged == 1 and res_o <= 1e-10
+    assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
+    check_solution(op, b, x, x_o, res_o)
