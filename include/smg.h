@@ -77,6 +77,8 @@ typedef struct smg_mg_params {
   int max_outer;                   /* outer GCR iteration cap */
   int precision;                   /* SMG_PREC_* of the preconditioner */
   int use_graph;                   /* 1: replay the K-cycle from a captured CUDA graph */
+  int persistent;                  /* 1: run the last coarse GCR level as one cooperative launch
+                                      (FP32 preconditioner, at most 16 systems) */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */
@@ -160,6 +162,15 @@ SMG_API int smg_coarse_apply(smg_ctx* ctx, int l, int prec, int nsys, const void
  * with k = 1, c = 1 (which = 0, fat links) or k = 3, c = c_naik (which = 1, Naik links).
  * X, Y: V*3 complex FP64; F: [4][V][3][3] complex FP64. */
 SMG_API int smg_force(smg_ctx* ctx, const void* X, const void* Y, int which, void* F, int where);
+/* Fermion action S = phi^dag (M^dag M)^{-1} phi for the current gauge field
+ * and mass, by two multigrid solves to `tol`: Z = M^{-1} (eps phi),
+ * Y = eps Z = M^{-dag} phi (eps M eps = M^dag), X = M^{-1} Y, S = |Y|^2, and
+ * dS/dm = -2 m |X|^2.  X, Y (V*3 complex FP64, may be NULL) receive the
+ * vectors that smg_force turns into the link derivative (HMC fermion force;
+ * Sec. 4 names gauge generation as a use of the solver).  info: 2 entries
+ * (may be NULL).  Returns SMG_ERR_NOT_CONVERGED if a solve missed tol. */
+SMG_API int smg_fermion_action(smg_ctx* ctx, const void* phi, void* X, void* Y, double tol, int where, double* S,
+                               double* dSdm, smg_solve_info* info);
 /* Iterations used by the near-null CGNE of coarsening l (max over vectors). */
 SMG_API int smg_setup_iterations(smg_ctx* ctx, int l, int* iters);
 

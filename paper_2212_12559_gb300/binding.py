@@ -27,7 +27,7 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_set_gauge", "smg_set_mass", "smg_mg_setup", "smg_solve", "smg_multi_solve",
            "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
-           "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches"]
+           "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action"]
 
 
 class MGParams(ctypes.Structure):
@@ -45,6 +45,7 @@ class MGParams(ctypes.Structure):
         ("max_outer", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("use_graph", ctypes.c_int),
+        ("persistent", ctypes.c_int),
     ]
 
 
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH):
         "smg_setup_iterations": (i, [vp, i, ip]),
         "smg_time_kernel": (i, [vp, i, i, i, i, ctypes.POINTER(d)]),
         "smg_kernel_launches": (ctypes.c_longlong, []),
+        "smg_fermion_action": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
+                                   ctypes.POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -301,6 +304,19 @@ class Solver:
         v = ctypes.c_double()
         self._check(self.lib.smg_time_kernel(self.ctx, kernel, l, nsys, nrep, ctypes.byref(v)))
         return v.value
+
+    def fermion_action(self, phi, tol=1e-10):
+        """S, dS/dm, X, Y for S = phi^dag (M^dag M)^{-1} phi (two MG solves in the library)."""
+        phi = _prep(phi)
+        X, Y = _like(phi), _like(phi)
+        pp, where = _ptr(phi)
+        px, _ = _ptr(X)
+        py, _ = _ptr(Y)
+        S, dm = ctypes.c_double(), ctypes.c_double()
+        infos = (SolveInfo * 2)()
+        self._check(self.lib.smg_fermion_action(self.ctx, pp, px, py, float(tol), where, ctypes.byref(S),
+                                                ctypes.byref(dm), infos), allow=(-5,))
+        return S.value, dm.value, X, Y, list(infos)
 
     def setup_iterations(self, l):
         v = ctypes.c_int()

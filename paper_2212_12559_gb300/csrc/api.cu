@@ -25,7 +25,9 @@ int guarded(smg_ctx* ctx, F&& f) {
     return SMG_ERR_OOM;
   } catch (const smg::StateError& e) {
     ctx->c.err = e.what;
-    return e.what.rfind("breakdown", 0) == 0 ? SMG_ERR_BREAKDOWN : SMG_ERR_STATE;
+    if (e.what.rfind("breakdown", 0) == 0) return SMG_ERR_BREAKDOWN;
+    if (e.what.rfind("timeout", 0) == 0) return SMG_ERR_TIMEOUT;
+    return SMG_ERR_STATE;
   } catch (const smg::CudaError& e) {
     ctx->c.err = e.what;
     return SMG_ERR_CUDA;
@@ -59,6 +61,7 @@ void smg_default_params(smg_mg_params* p) {
   p->max_outer = 500;
   p->precision = SMG_PREC_DOUBLE;
   p->use_graph = 0;
+  p->persistent = 1;
 }
 
 int smg_create(const int dims[4], smg_ctx** out) {
@@ -263,6 +266,16 @@ int smg_setup_iterations(smg_ctx* ctx, int l, int* iters) {
     SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "setup_iterations: bad level");
     *iters = c.coarse[l].setup_iters;
     return SMG_OK;
+  });
+}
+
+int smg_fermion_action(smg_ctx* ctx, const void* phi, void* X, void* Y, double tol, int where, double* S,
+                       double* dSdm, smg_solve_info* info) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(phi && S && dSdm && valid_where(where), "fermion_action: null argument");
+    if (!c.setup_done) throw smg::StateError("fermion_action needs mg_setup first");
+    SMG_REQUIRE(tol > 0 && tol < 1, "fermion_action: tol must be in (0, 1)");
+    return smg::ctx_fermion_action(c, phi, X, Y, tol, where, S, dSdm, info);
   });
 }
 

@@ -249,14 +249,24 @@ __device__ void epilogue_system(const Epilogue& e, int s, const double2* o) {
 
 // partial[s][block][p] = this CTA's share of conj(v[pi[p]]) * v[pj[p]]; the
 // last CTA to arrive adds the partials in a fixed order and runs the epilogue.
+// Accumulator type of a reduction: FP64 for FP64 vectors, FP32 per thread for
+// FP32 vectors (each thread sums at most a few hundred products; the CTA and
+// grid sums are FP64).  GB300's FP64 rate is a small fraction of its FP32 rate.
+template <typename C> struct AccOf;
+template <> struct AccOf<double2> { using T = double2; };
+template <> struct AccOf<float2> { using T = float2; };
+
+// partial[s][block][p] = this CTA's share of conj(v[pi[p]]) * v[pj[p]]; the
+// last CTA to arrive adds the partials in a fixed order and runs the epilogue.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, double2* __restrict__ partial,
                                                             double2* __restrict__ out, int ldo,
                                                             unsigned* __restrict__ counter, Epilogue epi,
                                                             const int* run) {
+  using A = typename AccOf<C>::T;
   if (skip(run)) return;
   constexpr int TR = 128;   // rows per tile
-  __shared__ double2 tile[kMaxVecs][TR];
+  __shared__ C tile[kMaxVecs][TR];
   __shared__ double2 red[kThreads];
   __shared__ bool last;
   const int s = blockIdx.y;
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   const int p = t % np;
   const int grp = t / np;
   const bool active = grp < groups;
-  double2 acc = make_double2(0, 0);
+  A acc = A{0, 0};
   const long long n = a.n;
   const long long rows_per_block = (n + gridDim.x - 1) / gridDim.x;
   const long long r0 = blockIdx.x * rows_per_block;
@@ -275,8 +285,8 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
     const int cnt = (int)min((long long)TR, r1 - base);
     for (int e = t; e < a.nv * TR; e += kThreads) {
       const int v = e / TR, r = e % TR;
-      double2 val = make_double2(0, 0);
-      if (r < cnt) val = to_d(((const C*)a.v.p[v])[s * n + base + r]);
+      C val = C{0, 0};
+      if (r < cnt) val = ((const C*)a.v.p[v])[s * n + base + r];
       tile[v][r] = val;
     }
     __syncthreads();
@@ -286,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
     }
     __syncthreads();
   }
-  red[t] = active ? acc : make_double2(0, 0);
+  red[t] = active ? make_double2(acc.x, acc.y) : make_double2(0, 0);
   __syncthreads();
   const int nb = gridDim.x, nsys = gridDim.y;
   if (t < np) {

@@ -8,6 +8,7 @@
 // sit in shared memory.  FP16 storage keeps one FP32 scale per (site, row),
 // the 16-bit analogue of the paper's fixed-point coarse links with a norm.
 #include "ops.cuh"
+#include "stencil_row.cuh"
 
 namespace smg {
 namespace {
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(typename cplx<R>::T* 
                                                            const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* vin = (C*)smem_raw;   // [9][N]
   const int X = blockIdx.x, s = blockIdx.y;
   const int agg[4] = {agg4.x, agg4.y, agg4.z, agg4.w};
@@ -56,7 +57,15 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(typename cplx<R>::T* 
   for (int i = w; i < N; i += nw) {
     const SL* row = S + ((size_t)X * N + i) * 9 * N;
     C acc = C{0, 0};
-    for (int e = lane; e < 9 * N; e += 32) cfma(acc, ld<R>(row, e), vin[e]);
+    if constexpr (sizeof(R) == 4 && sizeof(SL) <= 8) {
+      if (N % 4 == 0) {
+        acc = stencil_row_dot<SL>(row, N, lane, [&](int dir, int j) { return vin + dir * N + j; });
+      } else {
+        for (int e = lane; e < 9 * N; e += 32) cfma(acc, ld<R>(row, e), vin[e]);
+      }
+    } else {
+      for (int e = lane; e < 9 * N; e += 32) cfma(acc, ld<R>(row, e), vin[e]);
+    }
     for (int o = 16; o > 0; o >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);

@@ -43,7 +43,21 @@ __global__ void force_kernel(double2* __restrict__ F, const double2* __restrict_
   F[e] = make_double2(-coef * eta * (t1.x - t2.x), -coef * eta * (t1.y - t2.y));
 }
 
+__global__ void eps_mul_kernel(double2* out, const double2* in, Geom g) {   // may run in place
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.V * 3) return;
+  int c[4];
+  g.coords(e / 3, c);
+  const double sg = ((c[0] + c[1] + c[2] + c[3]) & 1) ? -1.0 : 1.0;
+  out[e] = make_double2(sg * in[e].x, sg * in[e].y);
+}
+
 }  // namespace
+
+void eps_mul(double2* out, const double2* in, const Geom& g, cudaStream_t st) {
+  eps_mul_kernel<<<ceil_div((long long)g.V * 3, 256), 256, 0, st>>>(out, in, g);
+  SMG_LAUNCH_OK();
+}
 
 void site_maps(int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_pos, const Geom& g, const int agg[4],
                cudaStream_t st) {

@@ -60,7 +60,8 @@ struct TransferGeom {
 // raw: FP64 [nvec][V][ndof]; orthonormalised in place per aggregate and chirality
 // (modified Gram-Schmidt in vector order, twice).
 void block_orthonormalize(double2* raw, const TransferGeom& t, cudaStream_t st);
-// Pack orthonormal FP64 [nvec][V][ndof] into the transfer layout [V][nvec][ndof] (global scale for FP16).
+// Pack orthonormal FP64 [nvec][V][ndof] into the transfer layout [V][ndof][nvec] (global scale 1 for FP16:
+// orthonormal columns have entries of modulus <= 1).
 void transfer_pack(Stored& dst, const double2* raw, const TransferGeom& t, cudaStream_t st);
 // out (coarse, [Vc][2*nvec]) = R in ; R = P^dag
 void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
@@ -109,5 +110,7 @@ void site_maps(int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_p
 // F_mu(x) = -c eta_mu(x) [ Y(x) X(x+k mu)^dag - X(x) Y(x+k mu)^dag ]
 void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, int k, double c,
                  cudaStream_t st);
+// out = eps(x) in, eps(x) = (-1)^(x+y+z+t) (Sec. 2.2), one FP64 colour field
+void eps_mul(double2* out, const double2* in, const Geom& g, cudaStream_t st);
 
 }  // namespace smg

@@ -22,6 +22,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "persist.cuh"
 #include "solver.cuh"
 
 namespace smg {
@@ -175,6 +176,8 @@ struct Engine {
   std::vector<Vec> tmp_c;
   DevBuf cbuf;
   Workspace ws;                     // reduction partials, sized once so captured graphs stay valid
+  DevBuf pbuf;                      // persistent coarse solver: partials, barrier words, error word
+  bool persistent = false;          // last GCR level solved by one cooperative launch
   // graph of K_0
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
@@ -241,6 +244,19 @@ struct Engine {
     }
     c.ensure_consts(ns * 2 + 2);
     ws.get(sizeof(double2) * (size_t)(152 * 4) * kMaxPairs * ns);
+    // one cooperative launch for the last GCR level when its coarser level is
+    // the dense coarsest (or it is itself the coarsest without a dense solve)
+    {
+      const int l = c.coarse.back().dense ? nlev : nlev + 1;
+      if (P.persistent && vp == P32 && l >= 2) {
+        const CoarseLevel& C = c.coarse[l - 2];
+        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, sp);
+        if (persistent) {
+          const size_t np = (size_t)persist_grid_size() * kPersistMaxSys * 64;
+          pbuf.alloc(np * sizeof(double2) + 64);
+        }
+      }
+    }
   }
 
   ~Engine() {
@@ -392,11 +408,55 @@ struct Engine {
     return done;
   }
 
+  // The level-l GCR (with its K-cycle down to the dense coarsest level) as
+  // one cooperative launch.
+  bool persistent_solve(int l, const int* run) {
+    const bool coarsest = (l == nlev + 1);
+    const int target = c.coarse.back().dense ? nlev : nlev + 1;
+    if (!persistent || l != target) return false;
+    const CoarseLevel& C = c.coarse[l - 2];
+    GcrWork& G = lev[l];
+    PersistArgs a{};
+    a.g = C.g; a.N = C.N; a.S = C.Ss.st.p; a.Srs = C.Ss.st.s == S16 ? C.Ss.st.scale : nullptr;
+    a.n = (long long)C.g.V * C.N;
+    a.has_pre = coarsest ? 0 : 1;
+    if (!coarsest) {
+      const CoarseLevel& Cn = c.coarse[l - 1];
+      a.tg = Cn.tg; a.P = Cn.Ps.st.p; a.D = Cn.D32.as<float2>(); a.nd = Cn.nd;
+      a.rc = (float2*)lev[l + 1].b.p;
+      a.ec = (float2*)lev[l + 1].x.p;
+    }
+    a.s = c.params.smoother_s;
+    a.K = G.K;
+    a.tol2 = c.params.inner_tol * c.params.inner_tol;
+    a.nsys = nsys;
+    a.b = (float2*)G.b.p; a.x = (float2*)G.x.p; a.r = (float2*)G.r.p;
+    for (int k = 0; k < G.K; ++k) { a.z[k] = (float2*)G.z[k].p; a.w[k] = (float2*)G.w[k].p; }
+    if (!coarsest)
+      for (int i = 0; i <= a.s; ++i) a.V[i] = (float2*)sm_c[l].V[i].p;
+    a.partial = pbuf.as<double2>();
+    a.bar = (unsigned*)((char*)pbuf.p + pbuf.bytes - 64);
+    a.err = (int*)(a.bar + 4);
+    a.run = run;
+    persist_gcr(a, sp, st());
+    return true;
+  }
+
+  void check_persistent_error() {
+    if (!persistent) return;
+    int err = 0;
+    SMG_CUDA_OK(cudaMemcpyAsync(&err, (char*)pbuf.p + pbuf.bytes - 64 + 16, sizeof(int), cudaMemcpyDeviceToHost,
+                                st()));
+    SMG_CUDA_OK(cudaStreamSynchronize(st()));
+    if (err) throw StateError("timeout: a grid barrier of the persistent coarse solver gave up");
+  }
+
   // solve on level l (>= 2): G = lev[l], input lev[l].b, output lev[l].x
   void coarse_solve(int l, const int* run) {
     const CoarseLevel& C = c.coarse[l - 2];
     GcrWork& G = lev[l];
     const bool coarsest = (l == nlev + 1);
+    if (persistent_solve(l, run)) return;
     if (coarsest && C.dense) {
       if (vp == P64) dense_apply(G.x, G.b, C.D64.p, P64, C.nd, st(), run);
       else dense_apply(G.x, G.b, C.D32.p, P32, C.nd, st(), run);
@@ -513,6 +573,7 @@ struct Engine {
         if (!std::isfinite(res[s])) bad = true;
         if (!(hr[s].x <= tgt[s])) all = false;
       }
+      check_persistent_error();
       if (bad) throw StateError("breakdown: non-finite residual");
       if (all || done == 0) break;
       ++restarts;
@@ -999,6 +1060,47 @@ void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* 
     coarse_apply(vout, vin, p, S, c.stream);
     conv_out(c, out, vout, where);
   }
+}
+
+// Fermion action S = phi^dag (M^dag M)^{-1} phi with its vectors:
+// Z = M^{-1} (eps phi), Y = eps Z (= M^{-dag} phi since eps M eps = M^dag),
+// X = M^{-1} Y, S = |Y|^2, dS/dm = -2 m |X|^2.  Two multigrid solves.
+int ctx_fermion_action(Context& c, const void* phi, void* X, void* Y, double tol, int where, double* S,
+                       double* dSdm, smg_solve_info* info) {
+  SMG_REQUIRE(c.setup_done, "fermion_action needs mg_setup first");
+  const size_t nb = (size_t)c.g.V * 3 * sizeof(double2);
+  DevBuf buf;
+  buf.alloc(nb * 4);
+  char* b = (char*)buf.p;
+  double2* dphi = (double2*)b;
+  double2* dz = (double2*)(b + nb);
+  double2* dy = (double2*)(b + 2 * nb);
+  double2* dx = (double2*)(b + 3 * nb);
+  upload(dphi, phi, nb, where, c.stream);
+  eps_mul(dz, dphi, c.g, c.stream);                 // eps phi
+  smg_solve_info i1{}, i2{};
+  int rc1 = ctx_solve(c, 1, dz, 1, nullptr, dy, tol, SMG_DEVICE, &i1);   // Z
+  eps_mul(dy, dy, c.g, c.stream);                   // Y = eps Z
+  int rc2 = ctx_solve(c, 1, dy, 1, nullptr, dx, tol, SMG_DEVICE, &i2);   // X = M^{-1} Y
+  Vec vy; vy.p = dy; vy.n = (long long)c.g.V * 3; vy.prec = P64;
+  Vec vx = vy; vx.p = dx;
+  Vec vv[2] = {vy, vx};
+  const int pi[2] = {0, 1}, pj[2] = {0, 1};
+  DevBuf ob;
+  ob.alloc(sizeof(double2) * 2);
+  blas_pair_dots(vv, 2, pi, pj, 2, ob.as<double2>(), 2, c.ws, c.stream);
+  double2 h[2];
+  SMG_CUDA_OK(cudaMemcpyAsync(h, ob.p, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+  if (X) download(X, dx, nb, where, c.stream);
+  if (Y) download(Y, dy, nb, where, c.stream);
+  SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+  *S = h[0].x;
+  *dSdm = -2.0 * c.mass * h[1].x;
+  if (info) {
+    info[0] = i1;
+    info[1] = i2;
+  }
+  return (rc1 == SMG_OK && rc2 == SMG_OK) ? SMG_OK : SMG_ERR_NOT_CONVERGED;
 }
 
 // Average device time of one launch of a hot kernel on the context's

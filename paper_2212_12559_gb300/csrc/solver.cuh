@@ -132,6 +132,8 @@ void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void
 void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* in, void* out, int where);
 void ctx_build_kd(Context& c);
 double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep);
+int ctx_fermion_action(Context& c, const void* phi, void* X, void* Y, double tol, int where, double* S,
+                       double* dSdm, smg_solve_info* info);
 void upload(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);
 void download(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);
 

@@ -6,8 +6,10 @@
 // lattices.  Each near-null vector v_k yields two prolongator columns, its
 // projections on the two chiralities, so the coarse site carries
 // N = 2 nvec components, (s, k) -> s*nvec + k.  The prolongator is stored
-// as [V][nvec][ndof]: column (s, k) at (x, d) is P[x][k][d] if chi(x,d) == s
-// and zero otherwise.
+// as [V][ndof][nvec] (vector index fastest): column (s, k) at (x, d) is
+// P[x][d][k] if chi(x,d) == s and zero otherwise.  With k fastest the
+// restriction's threads (one per k) read consecutive entries and each
+// prolongation thread (one per (x, d)) reads one contiguous run.
 #include "ops.cuh"
 
 namespace smg {
@@ -121,10 +123,10 @@ __global__ void transfer_pack_kernel(SL* __restrict__ dst, const double2* __rest
   const long long total = (long long)t.fine.V * t.nvec * t.ndof;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int d = (int)(e % t.ndof);
-    const long long q = e / t.ndof;
-    const int k = (int)(q % t.nvec);
-    const long long x = q / t.nvec;
+    const int k = (int)(e % t.nvec);
+    const long long q = e / t.nvec;
+    const int d = (int)(q % t.ndof);
+    const long long x = q / t.ndof;
     const double2 v = raw[(size_t)k * t.fine.V * t.ndof + (size_t)x * t.ndof + d];
     if constexpr (sizeof(SL) == 16) dst[e] = SL{v.x, v.y};
     else if constexpr (sizeof(SL) == 8) dst[e] = SL{(float)v.x, (float)v.y};
@@ -132,51 +134,50 @@ __global__ void transfer_pack_kernel(SL* __restrict__ dst, const double2* __rest
   }
 }
 
-// One CTA (4 warps) per (aggregate, system); lanes own vectors k = lane, lane + 32.
+// One CTA per (aggregate, system).  Thread t owns vector k = t % nvec and the
+// rows (p, d) of the aggregate with (p*ndof + d) = t / nvec mod groups; it keeps
+// one accumulator per chirality, then the CTA adds the row groups.
 template <typename R, typename SL>
-__global__ void __launch_bounds__(128) restrict_kernel(typename cplx<R>::T* __restrict__ out,
+__global__ void __launch_bounds__(256) restrict_kernel(typename cplx<R>::T* __restrict__ out,
                                                        const typename cplx<R>::T* __restrict__ in,
                                                        const SL* __restrict__ P, R pscale, TransferGeom t,
                                                        const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
-  __shared__ C part[4][2][64];
+  __shared__ C part[2][256];
   const int X = blockIdx.x, s = blockIdx.y;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nv = t.nvec;
+  const int k = threadIdx.x % nv, grp = threadIdx.x / nv, groups = blockDim.x / nv;
   const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  const int rows = npos * t.ndof;
   const long long nf = (long long)t.fine.V * t.ndof;
   const C* vin = in + (size_t)s * nf;
-  C acc[2][2] = {{C{0, 0}, C{0, 0}}, {C{0, 0}, C{0, 0}}};   // [chirality][k slot]
-  for (int p = w; p < npos; p += 4) {
-    const int x = agg_site(t, X, p);
-    const int par = site_parity(t.fine, x);
-    const SL* Px = P + (size_t)x * t.nvec * t.ndof;
-    for (int d = 0; d < t.ndof; ++d) {
-      const C v = vin[(size_t)x * t.ndof + d];
-      const int chi = t.chi_mode == 0 ? par : (d >= t.ndof / 2 ? 1 : 0);
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int k = lane + 32 * q;
-        if (k < t.nvec) {
-          const C pv = ld<R>(Px, (size_t)k * t.ndof + d);
-          if (chi == 0) cfmac(acc[0][q], pv, v);
-          else cfmac(acc[1][q], pv, v);
-        }
+  C acc0 = C{0, 0}, acc1 = C{0, 0};
+  if (grp < groups) {
+    int last_p = -1, x = 0, par = 0;
+    for (int r = grp; r < rows; r += groups) {
+      const int p = r / t.ndof, d = r - p * t.ndof;
+      if (p != last_p) {
+        x = agg_site(t, X, p);
+        par = site_parity(t.fine, x);
+        last_p = p;
       }
+      const int chi = t.chi_mode == 0 ? par : (d >= t.ndof / 2 ? 1 : 0);
+      const size_t row = (size_t)x * t.ndof + d;
+      const C v = vin[row];
+      const C pv = ld<R>(P, row * nv + k);
+      if (chi == 0) cfmac(acc0, pv, v);
+      else cfmac(acc1, pv, v);
     }
   }
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    part[w][0][lane + 32 * q] = acc[0][q];
-    part[w][1][lane + 32 * q] = acc[1][q];
-  }
+  part[0][threadIdx.x] = acc0;   // blockDim.x == 256 (see restrict_op)
+  part[1][threadIdx.x] = acc1;
   __syncthreads();
-  const int N = 2 * t.nvec;
+  const int N = 2 * nv;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const int chi = i / t.nvec, k = i % t.nvec;
+    const int chi = i / nv, kk = i % nv;
     C sum = C{0, 0};
-#pragma unroll
-    for (int ww = 0; ww < 4; ++ww) sum = cadd(sum, part[ww][chi][k]);
+    for (int g = 0; g < groups; ++g) sum = cadd(sum, part[chi][g * nv + kk]);
     out[(size_t)s * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
   }
 }
@@ -195,9 +196,10 @@ __global__ void prolong_kernel(typename cplx<R>::T* __restrict__ out, const type
   const int chi = chirality(t, x, d);
   const int N = 2 * t.nvec;
   const C* vc = in + (size_t)s * t.coarse.V * N + (size_t)X * N + chi * t.nvec;
-  const SL* Px = P + (size_t)x * t.nvec * t.ndof + d;
+  const SL* Px = P + (size_t)e * t.nvec;
   C acc = C{0, 0};
-  for (int k = 0; k < t.nvec; ++k) cfma(acc, ld<R>(Px, (size_t)k * t.ndof), vc[k]);
+#pragma unroll 4
+  for (int k = 0; k < t.nvec; ++k) cfma(acc, ld<R>(Px, k), vc[k]);
   out[(size_t)s * nf + e] = cscale(acc, pscale);
 }
 
@@ -223,18 +225,18 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
                  const int* run) {
   SMG_REQUIRE(in.n == (long long)t.fine.V * t.ndof && out.n == (long long)t.coarse.V * 2 * t.nvec,
               "restrict: field sizes do not match the transfer");
-  SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec && t.nvec <= 64, "restrict: batch/precision mismatch");
+  SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec && t.nvec <= 128, "restrict: batch/precision mismatch");
   dim3 grid(t.coarse.V, in.nsys);
   if (in.prec == P64) {
     SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
-    restrict_kernel<double, double2><<<grid, 128, 0, st>>>((double2*)out.p, (const double2*)in.p,
+    restrict_kernel<double, double2><<<grid, 256, 0, st>>>((double2*)out.p, (const double2*)in.p,
                                                            (const double2*)P.p, (double)P.gscale, t, run);
   } else if (P.s == S32) {
-    restrict_kernel<float, float2><<<grid, 128, 0, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p,
+    restrict_kernel<float, float2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p,
                                                          P.gscale, t, run);
   } else {
     SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
-    restrict_kernel<float, __half2><<<grid, 128, 0, st>>>((float2*)out.p, (const float2*)in.p,
+    restrict_kernel<float, __half2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p,
                                                           (const __half2*)P.p, P.gscale, t, run);
   }
   SMG_LAUNCH_OK();

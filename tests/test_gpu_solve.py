@@ -192,3 +192,31 @@ def test_iteration_count_matches_oracle(binding):
     assert info.converged == 1 and res_o <= 1e-10
     assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
     check_solution(op, b, x, x_o, res_o)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_persistent_coarse_solver_matches_launch_path(binding, nrhs):
+    """The cooperative single-launch coarse GCR and the launch-per-kernel path
+    run the same algorithm: both converge with (nearly) the same outer count."""
+    dims = (8, 8, 8, 8)
+    fat, naik, c, op = problem(dims, True, 0.05, seed=1002)
+    b = inputs.gaussian_fields(nrhs, op.lat.V, 3, 2002)
+    its = {}
+    for pers in (0, 1):
+        s = binding.Solver(dims)
+        s.set_gauge(fat, naik, c)
+        s.set_mass(0.05)
+        p = binding.default_params(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[8, 8], setup_maxiter=200,
+                                   precision=binding.PREC_HALF, persistent=pers, use_graph=1)
+        s.mg_setup(p, [inputs.gaussian_fields(8, op.lat.V, 3, 3002), inputs.gaussian_fields(8, 16, 16, 3003)])
+        if nrhs == 1:
+            x, info = s.solve(b[0], 1e-10)
+            infos, xs = [info], x[None]
+        else:
+            x, infos = s.multi_solve(b, [0.05], 1e-10)
+            xs = x[0]
+        its[pers] = infos[0].iterations
+        for r in range(nrhs):
+            assert infos[r].converged == 1
+            assert np.linalg.norm(b[r] - op.M(xs[r])) <= 1e-10 * np.linalg.norm(b[r])
+    assert abs(its[0] - its[1]) <= max(2, 0.25 * max(its.values())), its
