@@ -191,6 +191,22 @@ SMG_API int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep,
  * counts every kernel node it runs). */
 SMG_API long long smg_kernel_launches(void);
 
+/* Batched inner products that allocate nothing: out[s] = <x_s, y_s> =
+ * sum_i conj(x[s][i]) y[s][i] for s < nsys, FP64 complex, all three buffers in
+ * device memory ([nsys][n] interleaved complex; out: nsys complex).  The paper
+ * has no counterpart: this is a service for callers that cannot allocate on
+ * the call path (a framework whose caching allocator owns the device heap, or
+ * a latency-critical loop that cannot take cudaMalloc's implicit device
+ * synchronisation).  It reduces in a fixed file-scope device array of
+ * 8192 partial sums (128 KiB per device, held until the process exits), so
+ * nsys must not exceed 8192 (SMG_ERR_ARG otherwise); no cudaMalloc/cudaFree or
+ * allocating library routine is called.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) and should come before
+ * any stream capture.  Work is enqueued on the context's stream and the call
+ * returns without waiting.  Every call shares the array (its counter is
+ * cleared at the start of each call): calls that overlap on the GPU race. */
+SMG_API int smg_dot_noalloc(smg_ctx* ctx, const void* x, const void* y, long long n, int nsys, void* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_set_gauge", "smg_set_mass", "smg_mg_setup", "smg_solve", "smg_multi_solve",
            "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
-           "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action"]
+           "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc"]
 
 
 class MGParams(ctypes.Structure):
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "smg_kernel_launches": (ctypes.c_longlong, []),
         "smg_fermion_action": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
                                    ctypes.POINTER(SolveInfo)]),
+        "smg_dot_noalloc": (i, [vp, vp, vp, ctypes.c_longlong, i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -317,6 +318,16 @@ class Solver:
         self._check(self.lib.smg_fermion_action(self.ctx, pp, px, py, float(tol), where, ctypes.byref(S),
                                                 ctypes.byref(dm), infos), allow=(-5,))
         return S.value, dm.value, X, Y, list(infos)
+
+    def dot_noalloc(self, x, y, out):
+        """out[s] = <x_s, y_s> for device tensors x, y ([nsys, ...] complex128) into
+        the caller's device tensor out (nsys complex128); enqueued on the
+        context's stream, no allocation inside the library."""
+        nsys = x.shape[0]
+        n = x.numel() // nsys
+        self._check(self.lib.smg_dot_noalloc(self.ctx, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                             n, nsys, ctypes.c_void_p(out.data_ptr())))
+        return out
 
     def setup_iterations(self, l):
         v = ctypes.c_int()

@@ -5,6 +5,10 @@
 
 #include "solver.cuh"
 
+namespace smg {
+std::string dot_noalloc(const void* x, const void* y, long long n, int nsys, void* out, cudaStream_t st);
+}
+
 struct smg_ctx {
   smg::Context c;
 };
@@ -288,5 +292,14 @@ int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep, double*
 }
 
 long long smg_kernel_launches(void) { return smg::g_launches; }
+
+int smg_dot_noalloc(smg_ctx* ctx, const void* x, const void* y, long long n, int nsys, void* out) {
+  if (ctx == nullptr) return SMG_ERR_ARG;
+  std::string err = smg::dot_noalloc(x, y, n, nsys, out, ctx->c.stream);
+  if (err.empty()) return SMG_OK;
+  const bool arg = err.rfind("dot_noalloc:", 0) == 0;
+  ctx->c.err = std::move(err);
+  return arg ? SMG_ERR_ARG : SMG_ERR_CUDA;
+}
 
 }  // extern "C"
