@@ -43,7 +43,11 @@ WORKLOADS = {
 # Outer GCR iterations a solve of the default workload takes with this
 # algorithm and these parameters (measured by the GPU path); scales the
 # oracle's per-iteration time in --impl reference, where no GPU runs.
-REF_OUTER_ITERS = {2: 12, 1: 10}
+REF_OUTER_ITERS = {2: 62, 1: 10}
+# dram__bytes_read.sum + dram__bytes_write.sum of one coarse_apply_kernel launch
+# on the 4096-site, N=128 FP16 stencil (ncu, see profiles/); None once the
+# kernel changes until it is captured again.
+NCU_TRAFFIC_COARSE_CFG3 = 2.428485e9 + 0.078377e9
 
 
 # ------------------------------------------------------------------ helpers
@@ -202,6 +206,45 @@ def kd_bytes(nsys, store_bytes=4):
     return 144 * store_bytes + 3 * 4 + 2 * 3 * 8 * nsys
 
 
+# ------------------------------------------------------ coarse apply alone
+COARSE_SHAPES = {
+    # coarse level of each workload: extents, components per site
+    "cfg3": ((8, 8, 8, 8), 128),      # 32^4 / 4^4 aggregates, 64 vectors: 2.42 GB FP16 stencil
+    "cfg4": ((6, 6, 6, 12), 48),      # 24^3x48 / 4^4 aggregates, 24 vectors: 215 MB
+    "cfg2": ((4, 4, 4, 4), 48),       # 16^4 / 4^4 aggregates, 24 vectors: 21.5 MB (L2-resident)
+}
+
+
+def coarse_roofline(binding, solver, shape, nsys, nrep, hbm):
+    """Times the 9-point coarse apply on a synthetic FP16 stencil of one
+    workload's coarse-level shape; returns a roofline dict (algorithmic bytes:
+    9 N^2 complex FP16 entries + N FP32 row scales per site, input and output
+    FP32 vectors of nsys systems, each counted once)."""
+    cd, N = COARSE_SHAPES[shape]
+    Vc = int(np.prod(cd))
+    ms = solver.bench_coarse_apply(cd, N, nsys, binding.PREC_HALF, nrep)
+    alg = coarse_bytes(N, nsys) * Vc
+    ach = alg / (ms * 1e-3) / 1e9
+    flops = 8 * 9 * N * N * nsys * Vc
+    return {"shape": shape, "N": N, "coarse_sites": Vc, "nrhs": nsys, "ms_per_launch": ms,
+            "alg_bytes_per_launch": alg, "achieved_GBs": ach, "frac_of_hbm": ach / hbm,
+            "TFLOPs": flops / (ms * 1e-3) / 1e12}
+
+
+def run_coarse_only(args):
+    """Coarse apply alone on the workloads' coarse-level shapes (profiling aid)."""
+    import torch
+    from paper_2212_12559_gb300 import binding
+    torch.cuda.set_device(0)
+    s = binding.Solver((4, 4, 4, 4))
+    hbm, _ = measured_peaks()
+    shapes = [args.shape] if args.shape else list(COARSE_SHAPES)
+    for sh in shapes:
+        for nsys in args.nrhs:
+            print(json.dumps(coarse_roofline(binding, s, sh, nsys, args.nrep, hbm)), flush=True)
+    return 0
+
+
 # --------------------------------------------------------- oracle sample
 def oracle_sample(cfg, n_iter, out_path, sub=0):
     """Runs in a child process with one BLAS thread: times the oracle's outer
@@ -344,22 +387,28 @@ def run_ours(args):
     e2e = statistics.mean(e2e_times)
     nbytes = V * 3 * 16
 
-    # roofline: the dominant kernel, timed alone with CUDA events on the library's stream
+    # roofline: the coarse 9-point apply (the operator kernel the K-cycle runs
+    # most), timed with CUDA events on the library's stream on the HBM-resident
+    # coarse level of the 32^4 workload (2.42 GB FP16 stencil), plus this
+    # workload's own L2-resident coarse level and fine kernels for context.
     hbm, peak_kind = measured_peaks()
     roof = None
     if rank == 0:
-        N = 2 * c["nvec"][0]
-        Vc = int(np.prod([d // a for d, a in zip(c["dims"], c["agg"][0])]))
+        r3 = coarse_roofline(binding, s, "cfg3", 1, 10, hbm)
+        roof = {"bound": "hbm", "kernel": "coarse_apply_kernel<float, __half2>, coarse level of the 32^4 workload "
+                                          "(4096 sites, N=128, FP16 stencil 2.42 GB), 1 RHS",
+                "achieved": r3["achieved_GBs"], "peak": hbm, "unit": "GB/s", "frac": r3["frac_of_hbm"],
+                "traffic": NCU_TRAFFIC_COARSE_CFG3, "peak_kind": peak_kind + " HBM copy bandwidth",
+                "ms_per_launch": r3["ms_per_launch"], "alg_bytes_per_launch": r3["alg_bytes_per_launch"]}
         ms = s.time_kernel(binding.K_COARSE, 0, 1, 200)
-        alg = coarse_bytes(N, 1) * Vc
-        achieved = alg / (ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "coarse_apply (level 1, 1 RHS, FP16 stencil)", "achieved": achieved,
-                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "peak_kind": peak_kind + " (HBM copy)", "ms_per_launch": ms, "alg_bytes_per_launch": alg,
-                "note": "stencil of this workload is L2-resident (%.1f MB)" % (alg / 1e6)}
+        Vc = int(np.prod([d // a for d, a in zip(c["dims"], c["agg"][0])]))
+        N = 2 * c["nvec"][0]
         ms_d = s.time_kernel(binding.K_DSLASH, 0, 1, 200)
         ms_k = s.time_kernel(binding.K_KD, 0, 1, 200)
         roof["others"] = {
+            "coarse_apply_this_workload_L2_resident": {"ms": ms, "GB/s": coarse_bytes(N, 1) * Vc / (ms * 1e-3) / 1e9},
+            "coarse_apply_cfg3_12rhs": coarse_roofline(binding, s, "cfg3", 12, 3, hbm),
+            "coarse_apply_cfg4_1rhs": coarse_roofline(binding, s, "cfg4", 1, 20, hbm),
             "dslash_hisq_fp16": {"ms": ms_d, "GB/s": dslash_bytes(True, 1) * V / (ms_d * 1e-3) / 1e9},
             "kd_apply_fp16": {"ms": ms_k, "GB/s": kd_bytes(1) * V / (ms_k * 1e-3) / 1e9},
         }
@@ -439,11 +488,18 @@ def main():
                     help="near-null CGNE cap (Table 1: 2000); lower only to bound profiler runs")
     ap.add_argument("--max-outer", type=int, default=500,
                     help="outer GCR cap; lower only to bound profiler runs")
+    ap.add_argument("--coarse-only", action="store_true",
+                    help="time only the coarse apply on the workloads' coarse-level shapes")
+    ap.add_argument("--shape", default=None, choices=[None, "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--nrhs", type=int, nargs="+", default=[1, 12])
+    ap.add_argument("--nrep", type=int, default=10)
     ap.add_argument("--profile", type=int, default=0,
                     help="bracket the timed solves with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.coarse_only:
+        return run_coarse_only(args)
     return run_ours(args)
 
 

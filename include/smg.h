@@ -187,6 +187,13 @@ enum {
  * CUDA events on the context's stream over nrep back-to-back launches after
  * one warm-up launch.  Inputs are library-owned zero fields. */
 SMG_API int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep, double* ms_per_launch);
+/* The 9-point coarse apply (Sec. 3.1) on a synthetic stencil of coarse
+ * extents cdims[4] with N components per site, nsys right-hand sides, storage
+ * precision `prec` (FP32 vectors; FP64 for SMG_PREC_DOUBLE): average device
+ * milliseconds per launch over nrep back-to-back launches (CUDA events on the
+ * context's stream).  Allocates and frees its own stencil and fields. */
+SMG_API int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int nsys, int prec, int nrep,
+                                   double* ms_per_launch);
 /* Total kernels launched by the library in this process (a CUDA-graph replay
  * counts every kernel node it runs). */
 SMG_API long long smg_kernel_launches(void);

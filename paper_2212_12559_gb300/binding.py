@@ -27,7 +27,8 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_set_gauge", "smg_set_mass", "smg_mg_setup", "smg_solve", "smg_multi_solve",
            "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
-           "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc"]
+           "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc",
+           "smg_bench_coarse_apply"]
 
 
 class MGParams(ctypes.Structure):
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH):
         "smg_fermion_action": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
                                    ctypes.POINTER(SolveInfo)]),
         "smg_dot_noalloc": (i, [vp, vp, vp, ctypes.c_longlong, i, vp]),
+        "smg_bench_coarse_apply": (i, [vp, ctypes.POINTER(ctypes.c_int), i, i, i, i, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -328,6 +330,14 @@ class Solver:
         self._check(self.lib.smg_dot_noalloc(self.ctx, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                              n, nsys, ctypes.c_void_p(out.data_ptr())))
         return out
+
+    def bench_coarse_apply(self, cdims, N, nsys=1, prec=PREC_HALF, nrep=20):
+        """ms per launch of the coarse apply on a synthetic stencil of this shape."""
+        v = ctypes.c_double()
+        arr = (ctypes.c_int * 4)(*cdims)
+        self._check(self.lib.smg_bench_coarse_apply(self.ctx, arr, int(N), int(nsys), int(prec), int(nrep),
+                                                    ctypes.byref(v)))
+        return v.value
 
     def setup_iterations(self, l):
         v = ctypes.c_int()

@@ -293,6 +293,16 @@ int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep, double*
 
 long long smg_kernel_launches(void) { return smg::g_launches; }
 
+int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int nsys, int prec, int nrep,
+                           double* ms_per_launch) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(cdims != nullptr && ms_per_launch != nullptr, "bench_coarse_apply: null argument");
+    SMG_REQUIRE(prec >= SMG_PREC_DOUBLE && prec <= SMG_PREC_HALF, "bench_coarse_apply: bad precision");
+    *ms_per_launch = smg::ctx_bench_coarse(c, cdims, N, nsys, prec, nrep);
+    return SMG_OK;
+  });
+}
+
 int smg_dot_noalloc(smg_ctx* ctx, const void* x, const void* y, long long n, int nsys, void* out) {
   if (ctx == nullptr) return SMG_ERR_ARG;
   std::string err = smg::dot_noalloc(x, y, n, nsys, out, ctx->c.stream);

@@ -266,7 +266,9 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   using A = typename AccOf<C>::T;
   if (skip(run)) return;
   constexpr int TR = 128;   // rows per tile
-  __shared__ C tile[kMaxVecs][TR];
+  // one padding entry per vector row: the pairs of one row (same r, different
+  // vectors) then fall in different shared-memory banks
+  __shared__ C tile[kMaxVecs][TR + 1];
   __shared__ double2 red[kThreads];
   __shared__ bool last;
   const int s = blockIdx.y;

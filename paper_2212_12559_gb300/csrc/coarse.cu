@@ -266,6 +266,19 @@ __global__ void __launch_bounds__(256) dense_apply_kernel(typename cplx<R>::T* _
   if (lane == 0) out[(size_t)s * n + row] = acc;
 }
 
+// Synthetic stencil values in [-1, 1) from a hash of the index (timing only).
+template <typename SL>
+__global__ void synth_fill_kernel(SL* __restrict__ dst, long long n, unsigned seed) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    unsigned h = (unsigned)(e * 2654435761ull) ^ seed;
+    h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
+    const float a = (float)(h & 0xffff) / 32768.f - 1.f, b = (float)(h >> 16) / 32768.f - 1.f;
+    if constexpr (sizeof(SL) == 4) dst[e] = __floats2half2_rn(a, b);
+    else if constexpr (sizeof(SL) == 8) dst[e] = SL{a, b};
+    else dst[e] = SL{(double)a, (double)b};
+  }
+}
+
 unsigned grid_cap(long long total, int threads) {
   long long g = (total + threads - 1) / threads;
   if (g > 16384) g = 16384;
@@ -298,6 +311,14 @@ void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const St
                                                                  (const __half2*)S.p, S.scale, p.g, p.N, p.part,
                                                                  agg, (const float2*)p.sub_from, run);
   }
+  SMG_LAUNCH_OK();
+}
+
+void synth_fill(void* dst, Store s, long long n, unsigned seed, cudaStream_t st) {
+  const unsigned g = grid_cap(n, 256);
+  if (s == S16) synth_fill_kernel<__half2><<<g, 256, 0, st>>>((__half2*)dst, n, seed);
+  else if (s == S32) synth_fill_kernel<float2><<<g, 256, 0, st>>>((float2*)dst, n, seed);
+  else synth_fill_kernel<double2><<<g, 256, 0, st>>>((double2*)dst, n, seed);
   SMG_LAUNCH_OK();
 }
 

@@ -82,6 +82,8 @@ struct CoarseParams {
 };
 void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
                   const int* run = nullptr);
+// Hash-based synthetic values in [-1, 1) (benchmark inputs of a given shape)
+void synth_fill(void* dst, Store s, long long n, unsigned seed, cudaStream_t st);
 // S64 stencil -> stored copy in precision dst.s
 void coarse_pack(Stored& dst, const double2* S64, const Geom& g, int N, cudaStream_t st);
 // Adjoint stencil: X^dag, Y'_{+mu}(X) = Y_{-mu}(X+mu)^dag, Y'_{-mu}(X) = Y_{+mu}(X-mu)^dag

@@ -70,7 +70,7 @@ __device__ __forceinline__ float2 ldh(const __half2* p, size_t i) { return __hal
 __device__ __forceinline__ float2 ldh(const float2* p, size_t i) { return p[i]; }
 
 struct Shared {
-  float2 tile[kMaxP][TR];
+  float2 tile[kMaxP][TR + 1];   // padded: the pairs of one row sit in different banks
   double2 red[PT];
   // per-system solver state (identical in every CTA)
   double2 alpha[kPersistMaxSys][kPersistMaxK];
@@ -81,6 +81,7 @@ struct Shared {
   double r2[kPersistMaxSys], thr2[kPersistMaxSys];
   int active[kPersistMaxSys], nk[kPersistMaxSys];
   int any;
+  int xs[256];                  // aggregate sites (restriction)
 };
 
 // ------------------------------------------------------------------ phases
@@ -153,18 +154,24 @@ __device__ void restrict_phase(const PersistArgs& a, Shared& sh, float2* rc, con
   const SL* P = (const SL*)a.P;
   double2* part = &sh.red[0];   // reused: [2][PT] FP32 pairs fit in PT double2
   float2* pf = reinterpret_cast<float2*>(part);
+  int* xs = sh.xs;              // fine site of each aggregate position
   for (long long job = blockIdx.x; job < (long long)a.nsys * t.coarse.V; job += gridDim.x) {
     const int s = (int)(job / t.coarse.V), X = (int)(job % t.coarse.V);
     int Xc[4];
     t.coarse.coords(X, Xc);
+    for (int p = threadIdx.x; p < npos; p += PT) {
+      int q = p, cc[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) { cc[mu] = Xc[mu] * t.agg[mu] + q % t.agg[mu]; q /= t.agg[mu]; }
+      xs[p] = t.fine.index(cc);
+    }
+    __syncthreads();
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     if (grp < groups) {
+#pragma unroll 8
       for (int rr = grp; rr < rows; rr += groups) {
         const int p = rr / t.ndof, d = rr - p * t.ndof;
-        int q = p, cc[4];
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) { cc[mu] = Xc[mu] * t.agg[mu] + q % t.agg[mu]; q /= t.agg[mu]; }
-        const size_t row = (size_t)t.fine.index(cc) * t.ndof + d;
+        const size_t row = (size_t)xs[p] * t.ndof + d;
         const float2 v = r[(size_t)s * nf + row];
         const float2 pv = ldh(P, row * nv + k);
         if (d < half) cfmac(acc0, pv, v);
@@ -551,9 +558,9 @@ int occupancy_grid(int dev_sms) {
 
 size_t persist_smem_bytes() { return sizeof(Shared); }
 
-bool persist_supported(int nsys, int K, int s, int N, Store st) {
+bool persist_supported(int nsys, int K, int s, int N, Store st, int npos) {
   return (st == S16 || st == S32) && nsys >= 1 && nsys <= kPersistMaxSys && K >= 1 && K <= kPersistMaxK &&
-         s >= 1 && s + 1 <= kMaxP && K + 2 <= kMaxP && N >= 2;
+         s >= 1 && s + 1 <= kMaxP && K + 2 <= kMaxP && N >= 2 && npos <= 256;
 }
 
 void persist_gcr(const PersistArgs& a, Store st, cudaStream_t stream) {

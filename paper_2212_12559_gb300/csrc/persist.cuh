@@ -36,7 +36,7 @@ struct PersistArgs {
   const int* run;            // skip the launch when *run == 0
 };
 
-bool persist_supported(int nsys, int K, int s, int N, Store st);
+bool persist_supported(int nsys, int K, int s, int N, Store st, int npos);
 void persist_gcr(const PersistArgs& a, Store st, cudaStream_t stream);
 int persist_grid_size();
 size_t persist_smem_bytes();

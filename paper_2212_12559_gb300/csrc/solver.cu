@@ -250,7 +250,10 @@ struct Engine {
       const int l = c.coarse.back().dense ? nlev : nlev + 1;
       if (P.persistent && vp == P32 && l >= 2) {
         const CoarseLevel& C = c.coarse[l - 2];
-        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, sp);
+        int npos = 1;
+        if (l <= nlev)
+          for (int mu = 0; mu < 4; ++mu) npos *= c.coarse[l - 1].tg.agg[mu];
+        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, sp, npos);
         if (persistent) {
           const size_t np = (size_t)persist_grid_size() * kPersistMaxSys * 64;
           pbuf.alloc(np * sizeof(double2) + 64);
@@ -1101,6 +1104,48 @@ int ctx_fermion_action(Context& c, const void* phi, void* X, void* Y, double tol
     info[1] = i2;
   }
   return (rc1 == SMG_OK && rc2 == SMG_OK) ? SMG_OK : SMG_ERR_NOT_CONVERGED;
+}
+
+// Coarse 9-point apply on a synthetic stencil of a given shape (storage per
+// `prec`, FP32 vectors or FP64 for SMG_PREC_DOUBLE), timed over nrep launches.
+double ctx_bench_coarse(Context& c, const int cdims[4], int N, int nsys, int prec, int nrep) {
+  SMG_REQUIRE(N >= 2 && N <= 256 && nsys >= 1 && nsys <= 64 && nrep >= 1, "bench_coarse: bad sizes");
+  Geom g;
+  g.V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    SMG_REQUIRE(cdims[mu] >= 1, "bench_coarse: bad extents");
+    g.L[mu] = cdims[mu];
+    g.V *= cdims[mu];
+  }
+  const Store st = prec == SMG_PREC_DOUBLE ? S64 : (prec == SMG_PREC_SINGLE ? S32 : S16);
+  const Prec vp = prec == SMG_PREC_DOUBLE ? P64 : P32;
+  const long long ns = (long long)g.V * N * 9 * N;
+  StoredBuf S;
+  S.alloc(st, (size_t)ns, (size_t)g.V * N);
+  synth_fill(S.v.p, st, ns, 12345u, c.stream);
+  if (st == S16) synth_fill(S.sc.p, S32, (long long)g.V * N / 2, 777u, c.stream);   // scales: any finite values
+  const long long n = (long long)g.V * N;
+  DevBuf bi, bo;
+  bi.alloc((size_t)n * nsys * prec_bytes(vp));
+  bo.alloc((size_t)n * nsys * prec_bytes(vp));
+  synth_fill(bi.p, vp == P64 ? S64 : S32, n * nsys, 99u, c.stream);
+  Vec in; in.p = bi.p; in.n = n; in.nsys = nsys; in.prec = vp;
+  Vec out = in; out.p = bo.p;
+  CoarseParams p;
+  p.g = g; p.N = N;
+  coarse_apply(out, in, p, S.st, c.stream);
+  cudaEvent_t e0, e1;
+  SMG_CUDA_OK(cudaEventCreate(&e0));
+  SMG_CUDA_OK(cudaEventCreate(&e1));
+  SMG_CUDA_OK(cudaEventRecord(e0, c.stream));
+  for (int i = 0; i < nrep; ++i) coarse_apply(out, in, p, S.st, c.stream);
+  SMG_CUDA_OK(cudaEventRecord(e1, c.stream));
+  SMG_CUDA_OK(cudaEventSynchronize(e1));
+  float ms = 0;
+  SMG_CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return (double)ms / nrep;
 }
 
 // Average device time of one launch of a hot kernel on the context's

@@ -132,6 +132,7 @@ void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void
 void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* in, void* out, int where);
 void ctx_build_kd(Context& c);
 double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep);
+double ctx_bench_coarse(Context& c, const int cdims[4], int N, int nsys, int prec, int nrep);
 int ctx_fermion_action(Context& c, const void* phi, void* X, void* Y, double tol, int where, double* S,
                        double* dSdm, smg_solve_info* info);
 void upload(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);

@@ -134,9 +134,11 @@ __global__ void transfer_pack_kernel(SL* __restrict__ dst, const double2* __rest
   }
 }
 
-// One CTA per (aggregate, system).  Thread t owns vector k = t % nvec and the
-// rows (p, d) of the aggregate with (p*ndof + d) = t / nvec mod groups; it keeps
-// one accumulator per chirality, then the CTA adds the row groups.
+// One CTA per (aggregate, system).  The aggregate's sites and input entries
+// are staged in shared memory first; then thread t owns vector k = t % nvec
+// and every (t / nvec)-th row (p, d) of the aggregate, with one accumulator
+// per chirality, its prolongator loads independent across iterations; the
+// CTA finally adds the row groups.
 template <typename R, typename SL>
 __global__ void __launch_bounds__(256) restrict_kernel(typename cplx<R>::T* __restrict__ out,
                                                        const typename cplx<R>::T* __restrict__ in,
@@ -144,7 +146,10 @@ __global__ void __launch_bounds__(256) restrict_kernel(typename cplx<R>::T* __re
                                                        const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
-  __shared__ C part[2][256];
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  C* part = reinterpret_cast<C*>(rs_smem);                    // [2][256]
+  C* vx = part + 512;                                         // [rows]
+  int* xs = reinterpret_cast<int*>(vx + (size_t)t.ndof * t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3]);
   const int X = blockIdx.x, s = blockIdx.y;
   const int nv = t.nvec;
   const int k = threadIdx.x % nv, grp = threadIdx.x / nv, groups = blockDim.x / nv;
@@ -152,32 +157,33 @@ __global__ void __launch_bounds__(256) restrict_kernel(typename cplx<R>::T* __re
   const int rows = npos * t.ndof;
   const long long nf = (long long)t.fine.V * t.ndof;
   const C* vin = in + (size_t)s * nf;
+  for (int p = threadIdx.x; p < npos; p += blockDim.x) xs[p] = agg_site(t, X, p);
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
+    const int p = rr / t.ndof, d = rr - p * t.ndof;
+    vx[rr] = vin[(size_t)xs[p] * t.ndof + d];
+  }
+  __syncthreads();
   C acc0 = C{0, 0}, acc1 = C{0, 0};
   if (grp < groups) {
-    int last_p = -1, x = 0, par = 0;
-    for (int r = grp; r < rows; r += groups) {
-      const int p = r / t.ndof, d = r - p * t.ndof;
-      if (p != last_p) {
-        x = agg_site(t, X, p);
-        par = site_parity(t.fine, x);
-        last_p = p;
-      }
-      const int chi = t.chi_mode == 0 ? par : (d >= t.ndof / 2 ? 1 : 0);
-      const size_t row = (size_t)x * t.ndof + d;
-      const C v = vin[row];
-      const C pv = ld<R>(P, row * nv + k);
-      if (chi == 0) cfmac(acc0, pv, v);
-      else cfmac(acc1, pv, v);
+#pragma unroll 8
+    for (int rr = grp; rr < rows; rr += groups) {
+      const int p = rr / t.ndof, d = rr - p * t.ndof;
+      const int x = xs[p];
+      const int chi = t.chi_mode == 0 ? site_parity(t.fine, x) : (d >= t.ndof / 2 ? 1 : 0);
+      const C pv = ld<R>(P, ((size_t)x * t.ndof + d) * nv + k);
+      if (chi == 0) cfmac(acc0, pv, vx[rr]);
+      else cfmac(acc1, pv, vx[rr]);
     }
   }
-  part[0][threadIdx.x] = acc0;   // blockDim.x == 256 (see restrict_op)
-  part[1][threadIdx.x] = acc1;
+  part[threadIdx.x] = acc0;   // blockDim.x == 256 (see restrict_op)
+  part[256 + threadIdx.x] = acc1;
   __syncthreads();
   const int N = 2 * nv;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const int chi = i / nv, kk = i % nv;
     C sum = C{0, 0};
-    for (int g = 0; g < groups; ++g) sum = cadd(sum, part[chi][g * nv + kk]);
+    for (int g = 0; g < groups; ++g) sum = cadd(sum, part[chi * 256 + g * nv + kk]);
     out[(size_t)s * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
   }
 }
@@ -201,6 +207,17 @@ __global__ void prolong_kernel(typename cplx<R>::T* __restrict__ out, const type
 #pragma unroll 4
   for (int k = 0; k < t.nvec; ++k) cfma(acc, ld<R>(Px, k), vc[k]);
   out[(size_t)s * nf + e] = cscale(acc, pscale);
+}
+
+// Raise a kernel's dynamic shared-memory limit once (not a stream operation,
+// so it is never issued while a stream is being captured).
+template <typename K>
+void ensure_smem(K kernel, size_t bytes) {
+  static size_t set = 0;
+  if (bytes > 48 * 1024 && bytes > set) {
+    SMG_CUDA_OK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    set = bytes;
+  }
 }
 
 }  // namespace
@@ -227,17 +244,23 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
               "restrict: field sizes do not match the transfer");
   SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec && t.nvec <= 128, "restrict: batch/precision mismatch");
   dim3 grid(t.coarse.V, in.nsys);
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  const size_t smem = prec_bytes(in.prec) * (512 + (size_t)npos * t.ndof) + sizeof(int) * npos;
+  SMG_REQUIRE(smem <= 200 * 1024, "restrict: aggregate too large for shared memory");
   if (in.prec == P64) {
     SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
-    restrict_kernel<double, double2><<<grid, 256, 0, st>>>((double2*)out.p, (const double2*)in.p,
-                                                           (const double2*)P.p, (double)P.gscale, t, run);
+    auto k = restrict_kernel<double, double2>;
+    ensure_smem(k, smem);
+    k<<<grid, 256, smem, st>>>((double2*)out.p, (const double2*)in.p, (const double2*)P.p, (double)P.gscale, t, run);
   } else if (P.s == S32) {
-    restrict_kernel<float, float2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p,
-                                                         P.gscale, t, run);
+    auto k = restrict_kernel<float, float2>;
+    ensure_smem(k, smem);
+    k<<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t, run);
   } else {
     SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
-    restrict_kernel<float, __half2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p,
-                                                          (const __half2*)P.p, P.gscale, t, run);
+    auto k = restrict_kernel<float, __half2>;
+    ensure_smem(k, smem);
+    k<<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t, run);
   }
   SMG_LAUNCH_OK();
 }
