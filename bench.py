@@ -39,6 +39,10 @@ UNIT = "s/solve"
 WORKLOADS = {
     2: "16^4 HISQ-shaped, m=0.01, 3-level KD-MG (4^4/2^4 aggregates, 24/32 vectors), FP32 + FP16 storage, FP64 outer GCR",
     1: "8^4 naive staggered, m=0.1, 2-level KD-MG (4^4 aggregates, 24 vectors), FP64",
+    3: "32^4 naive staggered, m=0.001, 2-level KD-MG (4^4 aggregates, 64 vectors), 12 Gaussian RHS solved together, "
+       "FP32 + FP16 storage (tensor-core multi-RHS coarse apply), FP64 outer GCR",
+    4: "24^3x48 HISQ-shaped, 8 masses log-spaced 0.001-0.05 x 4 sources = 32 systems in one batch, 3-level KD-MG "
+       "(4^4/2^4 aggregates, 24/32 vectors, operators of the lightest mass), FP32 + FP16 storage, FP64 outer GCR",
 }
 # Outer GCR iterations a solve of the default workload takes with this
 # algorithm and these parameters (measured by the GPU path); scales the
@@ -51,6 +55,12 @@ NCU_TRAFFIC_COARSE_CFG3 = 2.428485e9 + 0.078377e9
 
 
 # ------------------------------------------------------------------ helpers
+def log(msg):
+    """Progress on stderr (the JSON line stays the only stdout output)."""
+    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
+    sys.stderr.flush()
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -125,9 +135,9 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------- GPU problem
-def build_problem(cfg, torch, dev, seed_offset=0):
+def build_problem(cfg, torch, dev, seed_offset=0, dims=None):
     from paper_2212_12559_gb300 import binding, inputs
-    c = inputs.config_inputs(cfg)
+    c = inputs.config_inputs(cfg, dims=tuple(dims) if dims else None)
     dims = c["dims"]
     V = int(np.prod(dims))
     s = binding.Solver(dims)
@@ -326,6 +336,81 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """Configurations 3 and 4: one multi_solve of all systems per step; the
+    value is the batch time divided by the number of systems."""
+    import torch
+    from paper_2212_12559_gb300 import binding, inputs
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = args.config
+    log(f"config {cfg}: building inputs")
+    c, s, phi0, _ = build_problem(cfg, torch, dev, dims=args.dims)
+    V = int(np.prod(c["dims"]))
+    masses = np.array([c["mass"]]) if c["masses"] is None else inputs.log_masses(0.001, 0.05, 8)
+    log(f"inputs ready (dims {c['dims']}); setup")
+    t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer)
+    setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
+    log(f"setup {t_setup:.1f} s, CGNE iterations {setup_iters}")
+    b = torch.from_numpy(c["sources"]).to(dev)
+    nsys = b.shape[0] * len(masses)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        t0 = time.perf_counter()
+        _, inf = s.multi_solve(b, masses, 1e-10)
+        log(f"warm-up batch {time.perf_counter() - t0:.2f} s, outer {inf[0].iterations}, "
+            f"max residual {max(i.true_residual for i in inf):.2e}")
+    torch.cuda.synchronize()
+    launches0 = binding.kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, infos = [], None
+    st = torch.cuda.current_stream()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        x, infos = s.multi_solve(b, masses, 1e-10)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        log(f"timed batch {times[-1]:.2f} s, outer {infos[0].iterations}")
+    clk = clocks.stop()
+    launches = binding.kernel_launches() - launches0
+    value = statistics.mean(times) / nsys
+    # end to end with pinned host buffers
+    bh = torch.from_numpy(c["sources"]).pin_memory()
+    xh = torch.empty((len(masses),) + tuple(bh.shape), dtype=torch.complex128).pin_memory()
+    t0 = time.perf_counter()
+    s.multi_solve(bh, masses, 1e-10, x=xh)
+    e2e = (time.perf_counter() - t0) / nsys
+    hbm, peak_kind = measured_peaks()
+    shape = "cfg3" if cfg == 3 else "cfg4"
+    r = coarse_roofline(binding, s, shape, min(nsys, 16), 5, hbm)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f16 storage, f64 outer", "data": "synthetic",
+        "config": {"workload": WORKLOADS[cfg], "dims": list(c["dims"]), "systems_per_step": nsys,
+                   "masses": [float(m) for m in masses], "setup_s": t_setup, "setup_cgne_iters": setup_iters,
+                   "outer_iters": infos[0].iterations, "all_converged": all(i.converged for i in infos),
+                   "max_true_residual": max(i.true_residual for i in infos),
+                   "l2": "flushed (512 MB write) before every timed batch"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 16),
+                "d2h_bytes_per_step": int(xh.numel() * 16)},
+        "gpu_launches": launches // max(1, args.steps),
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "kernel": f"coarse apply, {r['nrhs']} RHS, this workload's coarse shape",
+                     "achieved": r["achieved_GBs"], "peak": hbm, "unit": "GB/s", "frac": r["frac_of_hbm"],
+                     "traffic": None, "TFLOPs": r["TFLOPs"], "ms_per_launch": r["ms_per_launch"]},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as tdist
@@ -337,9 +422,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cfg = args.config
+    log(f"config {cfg}: building inputs")
     c, s, phi0, src = build_problem(cfg, torch, dev, seed_offset=rank)
     V = int(np.prod(c["dims"]))
+    log("setup")
     t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer)
+    log(f"setup {t_setup:.1f} s")
     setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
     b_dev = torch.from_numpy(src).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -479,7 +567,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--compare-fp64", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -488,6 +576,8 @@ def main():
                     help="near-null CGNE cap (Table 1: 2000); lower only to bound profiler runs")
     ap.add_argument("--max-outer", type=int, default=500,
                     help="outer GCR cap; lower only to bound profiler runs")
+    ap.add_argument("--dims", type=int, nargs=4, default=None,
+                    help="other lattice extents for the batched workloads (probing only)")
     ap.add_argument("--coarse-only", action="store_true",
                     help="time only the coarse apply on the workloads' coarse-level shapes")
     ap.add_argument("--shape", default=None, choices=[None, "cfg2", "cfg3", "cfg4"])
@@ -500,6 +590,8 @@ def main():
         return run_reference(args)
     if args.coarse_only:
         return run_coarse_only(args)
+    if args.config in (3, 4):
+        return run_batched(args)
     return run_ours(args)
 
 

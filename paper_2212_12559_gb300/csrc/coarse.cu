@@ -7,6 +7,9 @@
 // consecutive lanes on consecutive entries while the nine neighbour vectors
 // sit in shared memory.  FP16 storage keeps one FP32 scale per (site, row),
 // the 16-bit analogue of the paper's fixed-point coarse links with a norm.
+#include <algorithm>
+#include <cstdlib>
+
 #include "ops.cuh"
 #include "stencil_row.cuh"
 
@@ -279,6 +282,154 @@ __global__ void synth_fill_kernel(SL* __restrict__ dst, long long n, unsigned se
   }
 }
 
+
+// ---------------------------------------------------------- multi-RHS, tensor cores
+// For nsys right-hand sides the stencil is read once per site: per site the
+// apply is the real GEMM  D[N][2 nsys] = A[N][18N] * B[18N][2 nsys]  with
+// A the FP16 stencil rows as stored (complex entries = (re, im) pairs along K)
+// and B the gathered neighbour vectors embedded as real 2x2 blocks
+// (B[2j][2r] = Re v, B[2j+1][2r] = -Im v, B[2j][2r+1] = Im v, B[2j+1][2r+1] = Re v),
+// so D[i][2r] = Re (A v_r)_i and D[i][2r+1] = Im (A v_r)_i.
+// Each warp owns 16 rows and issues m16n8k16 FP16 MMAs with FP32 accumulation.
+// A is loaded straight from global memory, 16 bytes (4 complex) per thread;
+// the K order inside each 16-complex block is permuted identically in A and B
+// (slot t <- complex 4t + 2ks, slot t+4 <- 4t + 2ks + 1 for k-step ks).  B is
+// built once per site in shared memory, in fragment order, scaled per system
+// by a power of two sigma_r that puts the site's largest gathered entry in
+// [0.5, 1) (FP16 range), and the scale is undone in the FP32 epilogue.
+constexpr int kMmaMaxRhs = 16;
+
+__device__ __forceinline__ unsigned h2u(__half2 h) { return *reinterpret_cast<unsigned*>(&h); }
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+               "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int NT>
+__global__ void __launch_bounds__(256) coarse_apply_mma_kernel(float2* __restrict__ out, const float2* __restrict__ in,
+                                                              const __half2* __restrict__ S,
+                                                              const float* __restrict__ rs, Geom g, int N,
+                                                              int nsys, int s0, long long sys_stride,
+                                                              const float2* __restrict__ sub_from,
+                                                              const int* run) {
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ __align__(16) unsigned char mma_smem[];
+  uint2* Bf = reinterpret_cast<uint2*>(mma_smem);   // [kb][NT][ks][lane]
+  __shared__ unsigned vmax[kMmaMaxRhs];
+  __shared__ float sig[kMmaMaxRhs];
+  __shared__ int nb[9];
+  const int X = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nrhs = min(kMmaMaxRhs, nsys - s0);
+  const int nkb = 9 * N / 16;
+  const long long n = (long long)g.V * N;
+  if (tid < 9) {
+    int c[4];
+    g.coords(X, c);
+    nb[tid] = tid == 0 ? X : g.shift(c, (tid - 1) >> 1, ((tid - 1) & 1) ? -1 : 1);
+  }
+  if (tid < kMmaMaxRhs) vmax[tid] = 0u;
+  __syncthreads();
+  // pass 1: largest |re|, |im| of the gathered entries per system
+  for (int e = tid; e < nrhs * 9 * N; e += blockDim.x) {
+    const int r = e / (9 * N), q = e - r * 9 * N;
+    const int dir = q / N, j = q - dir * N;
+    const float2 v = in[(size_t)(s0 + r) * sys_stride + (size_t)nb[dir] * N + j];
+    const float m = fmaxf(fabsf(v.x), fabsf(v.y));
+    atomicMax(&vmax[r], __float_as_uint(m));
+  }
+  __syncthreads();
+  if (tid < kMmaMaxRhs) {
+    const float m = tid < nrhs ? __uint_as_float(vmax[tid]) : 0.f;
+    int e2 = 0;
+    if (m > 0.f) frexpf(m, &e2);
+    sig[tid] = ldexpf(1.f, -e2);
+  }
+  __syncthreads();
+  // pass 2: B fragments in shared memory
+  const int nfrag = nkb * NT * 2 * 32;
+  for (int f = tid; f < nfrag; f += blockDim.x) {
+    const int ln = f & 31, ks = (f >> 5) & 1;
+    const int nt = (f >> 6) % NT, kb = (f >> 6) / NT;
+    const int gg = ln >> 2, tt = ln & 3;
+    const int col = nt * 8 + gg, r = col >> 1, im_out = col & 1;
+    unsigned h[2] = {0u, 0u};
+    if (r < nrhs) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int jj = kb * 16 + 4 * tt + 2 * ks + q;        // complex index along K
+        const int dir = jj / N, j = jj - dir * N;
+        float2 v = in[(size_t)(s0 + r) * sys_stride + (size_t)nb[dir] * N + j];
+        v.x *= sig[r];
+        v.y *= sig[r];
+        h[q] = im_out ? h2u(__floats2half2_rn(v.y, v.x)) : h2u(__floats2half2_rn(v.x, -v.y));
+      }
+    }
+    Bf[f] = make_uint2(h[0], h[1]);
+  }
+  __syncthreads();
+  // MMA: warp w owns rows 16w .. 16w+15
+  const int rows_w = 16 * w;
+  if (rows_w >= N) return;
+  const int gq = lane >> 2, tq = lane & 3;
+  const __half2* A0 = S + ((size_t)X * N + rows_w + gq) * 9 * N + 4 * tq;
+  const __half2* A1 = A0 + (size_t)8 * 9 * N;
+  float acc[NT][4];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+#pragma unroll 4
+  for (int kb = 0; kb < nkb; ++kb) {
+    const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(A0 + kb * 16));
+    const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(A1 + kb * 16));
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      unsigned a[4];
+      a[0] = ks ? r0.z : r0.x;   // row g,   slot t
+      a[1] = ks ? r1.z : r1.x;   // row g+8, slot t
+      a[2] = ks ? r0.w : r0.y;   // row g,   slot t+4
+      a[3] = ks ? r1.w : r1.y;   // row g+8, slot t+4
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const uint2 b = Bf[((kb * NT + nt) * 2 + ks) * 32 + lane];
+        mma16816(acc[nt], a, b.x, b.y);
+      }
+    }
+  }
+  // epilogue: D fragment (row g / g+8, columns 2t, 2t+1 of tile nt) = (Re, Im) of system nt*4 + t
+  const float sc0 = rs[(size_t)X * N + rows_w + gq], sc1 = rs[(size_t)X * N + rows_w + gq + 8];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const int r = nt * 4 + tq;
+    if (r >= nrhs) continue;
+    const float inv = 1.f / sig[r];
+    const size_t o0 = (size_t)(s0 + r) * sys_stride + (size_t)X * N + rows_w + gq;
+    const size_t o1 = o0 + 8;
+    float2 v0 = make_float2(acc[nt][0] * sc0 * inv, acc[nt][1] * sc0 * inv);
+    float2 v1 = make_float2(acc[nt][2] * sc1 * inv, acc[nt][3] * sc1 * inv);
+    if (sub_from != nullptr) {
+      v0 = csub(sub_from[o0], v0);
+      v1 = csub(sub_from[o1], v1);
+    }
+    out[o0] = v0;
+    out[o1] = v1;
+  }
+  (void)n;
+}
+
+bool coarse_mma_disabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("SMG_NO_TENSOR_COARSE");
+    v = (e != nullptr && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
 unsigned grid_cap(long long total, int threads) {
   long long g = (total + threads - 1) / threads;
   if (g > 16384) g = 16384;
@@ -288,10 +439,46 @@ unsigned grid_cap(long long total, int threads) {
 
 }  // namespace
 
+template <int NT>
+void launch_mma(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
+                const int* run, int s0) {
+  const int nkb = 9 * p.N / 16;
+  const size_t smem = (size_t)nkb * NT * 2 * 32 * sizeof(uint2);
+  static size_t set = 0;
+  if (smem > 48 * 1024 && smem > set) {
+    SMG_CUDA_OK(cudaFuncSetAttribute(coarse_apply_mma_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    set = smem;
+  }
+  const int threads = 32 * (p.N / 16);
+  coarse_apply_mma_kernel<NT><<<p.g.V, threads, smem, st>>>((float2*)out.p, (const float2*)in.p,
+                                                            (const __half2*)S.p, S.scale, p.g, p.N, in.nsys, s0,
+                                                            in.n, (const float2*)p.sub_from, run);
+  SMG_LAUNCH_OK();
+}
+
+// Tensor-core multi-RHS path: FP32 vectors, FP16 stencil, N a multiple of 16
+// (at most 128: 8 warps per CTA), full operator.
+bool coarse_mma_ok(const Vec& in, const CoarseParams& p, const Stored& S) {
+  return in.prec == P32 && S.s == S16 && in.nsys >= 2 && p.part < 0 && p.N % 16 == 0 && p.N <= 128 &&
+         S.scale != nullptr;
+}
+
 void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
                   const int* run) {
   SMG_REQUIRE(in.n == (long long)p.g.V * p.N && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
               "coarse_apply: shape mismatch");
+  if (coarse_mma_ok(in, p, S) && !coarse_mma_disabled()) {
+    for (int s0 = 0; s0 < in.nsys; s0 += kMmaMaxRhs) {
+      const int nr = std::min(kMmaMaxRhs, in.nsys - s0);
+      const int nt = (2 * nr + 7) / 8;
+      if (nt <= 1) launch_mma<1>(out, in, p, S, st, run, s0);
+      else if (nt == 2) launch_mma<2>(out, in, p, S, st, run, s0);
+      else if (nt == 3) launch_mma<3>(out, in, p, S, st, run, s0);
+      else launch_mma<4>(out, in, p, S, st, run, s0);
+    }
+    return;
+  }
   const size_t smem = (size_t)9 * p.N * prec_bytes(in.prec);
   SMG_REQUIRE(smem <= 48 * 1024, "coarse_apply: N too large");
   dim3 grid(p.g.V, in.nsys);

@@ -175,3 +175,26 @@ def test_device_buffers_torch(binding):
     kd = KahlerDirac(op)
     for k in range(2):
         assert rel(got[k], kd.A(v[k])) <= 1e-12
+
+
+@pytest.mark.parametrize("nvec,nsys", [(8, 2), (8, 5), (8, 17), (24, 12), (32, 33)])
+def test_multi_rhs_coarse_apply(binding, nvec, nsys):
+    """Batched coarse apply (tensor-core path for N % 16 == 0, FP16 stencil):
+    every system equals the oracle's stencil apply within the FP16 bar, for
+    batches below, at and above one 16-system pass."""
+    dims = (8, 8, 8, 8)
+    fat, naik, c, op = make(dims, False, 0.1)
+    lat = op.lat
+    phi = inputs.gaussian_fields(nvec, lat.V, 3, 41)
+    lop = FineLevelOp(KahlerDirac(op))
+    T = Transfer(lat, 3, lop.chirality(), (4, 4, 4, 4), phi)
+    S = galerkin(lop, T)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(0.1)
+    s.mg_setup(binding.default_params(nvec=[nvec], setup_maxiter=0, precision=binding.PREC_HALF), [phi])
+    v = inputs.gaussian_fields(nsys, S.lat.V, S.n, 8)
+    v *= np.logspace(-6, 3, nsys)[:, None, None]          # systems of very different size
+    got = s.coarse_apply(0, v, binding.PREC_HALF)
+    for k in range(nsys):
+        assert rel(got[k], S.apply(v[k])) <= TOL[2], (k, rel(got[k], S.apply(v[k])))
