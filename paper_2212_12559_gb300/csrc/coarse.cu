@@ -421,13 +421,15 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(float2* __restric
   (void)n;
 }
 
-bool coarse_mma_disabled() {
+// Multi-RHS coarse apply path: 0 CUDA cores only, 1 mma.sync, 2 tcgen05 where it
+// applies (N = 128) else mma.sync.  SMG_COARSE_TC selects; default 2.
+int coarse_tc_mode() {
   static int v = -1;
   if (v < 0) {
-    const char* e = getenv("SMG_NO_TENSOR_COARSE");
-    v = (e != nullptr && e[0] == '1') ? 1 : 0;
+    const char* e = getenv("SMG_COARSE_TC");
+    v = (e != nullptr && e[0] >= '0' && e[0] <= '2') ? e[0] - '0' : 2;
   }
-  return v == 1;
+  return v;
 }
 
 unsigned grid_cap(long long total, int threads) {
@@ -468,7 +470,18 @@ void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const St
                   const int* run) {
   SMG_REQUIRE(in.n == (long long)p.g.V * p.N && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
               "coarse_apply: shape mismatch");
-  if (coarse_mma_ok(in, p, S) && !coarse_mma_disabled()) {
+  const int tc = coarse_tc_mode();
+  if (tc == 2 && coarse_umma_ok(in, p, S)) {
+    static int* err = nullptr;
+    if (err == nullptr) {
+      SMG_CUDA_OK(cudaMalloc(&err, sizeof(int)));
+      SMG_CUDA_OK(cudaMemset(err, 0, sizeof(int)));
+      SMG_CUDA_OK(cudaDeviceSynchronize());
+    }
+    coarse_apply_umma(out, in, p, S, err, st, run);
+    return;
+  }
+  if (tc >= 1 && coarse_mma_ok(in, p, S)) {
     for (int s0 = 0; s0 < in.nsys; s0 += kMmaMaxRhs) {
       const int nr = std::min(kMmaMaxRhs, in.nsys - s0);
       const int nt = (2 * nr + 7) / 8;

@@ -82,6 +82,10 @@ struct CoarseParams {
 };
 void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
                   const int* run = nullptr);
+// tcgen05 / TMA multi-RHS path (N = 128, FP16 stencil, FP32 vectors, >= 2 systems); err: device int
+bool coarse_umma_ok(const Vec& in, const CoarseParams& p, const Stored& S);
+void coarse_apply_umma(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, int* err,
+                       cudaStream_t st, const int* run = nullptr);
 // Hash-based synthetic values in [-1, 1) (benchmark inputs of a given shape)
 void synth_fill(void* dst, Store s, long long n, unsigned seed, cudaStream_t st);
 // S64 stencil -> stored copy in precision dst.s

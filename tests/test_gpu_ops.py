@@ -177,7 +177,7 @@ def test_device_buffers_torch(binding):
         assert rel(got[k], kd.A(v[k])) <= 1e-12
 
 
-@pytest.mark.parametrize("nvec,nsys", [(8, 2), (8, 5), (8, 17), (24, 12), (32, 33)])
+@pytest.mark.parametrize("nvec,nsys", [(8, 2), (8, 5), (8, 17), (24, 12), (32, 33), (64, 2), (64, 12), (64, 20)])
 def test_multi_rhs_coarse_apply(binding, nvec, nsys):
     """Batched coarse apply (tensor-core path for N % 16 == 0, FP16 stencil):
     every system equals the oracle's stencil apply within the FP16 bar, for
