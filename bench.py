@@ -125,6 +125,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, tdist, device):
+    """Largest value of x over the process group (timing of the slowest rank)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(tmax, steps, world_size):
+    """Seconds per solve of the whole job: every rank solves `steps` systems
+    independently (replicas, weak scaling), the job takes the slowest rank's time."""
+    return tmax / (steps * world_size)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -447,16 +461,12 @@ def run_ours(args):
     if ws > 1:
         tdist.barrier()
     total = sum(times)
-    tmax = total
-    if ws > 1:
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        tmax = float(t.item())
+    tmax = max_over_ranks(total, tdist, dev) if ws > 1 else total
     timed_infos = infos[args.warmup:]
     iters = [i.iterations for i in timed_infos]
     conv = all(i.converged for i in infos)
     res = max(i.true_residual for i in infos)
-    value = tmax / (args.steps * ws)
+    value = replica_value(tmax, args.steps, ws)
     # gpu launches inside the timed solves only (warm-up launches excluded by proportion)
     launches_timed = int(round(launches * args.steps / max(1, args.steps + args.warmup)))
 

@@ -470,7 +470,7 @@ void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const St
                   const int* run) {
   SMG_REQUIRE(in.n == (long long)p.g.V * p.N && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
               "coarse_apply: shape mismatch");
-  const int tc = coarse_tc_mode();
+  const int tc = p.allow_tc ? coarse_tc_mode() : 0;
   if (tc == 2 && coarse_umma_ok(in, p, S)) {
     static int* err = nullptr;
     if (err == nullptr) {

@@ -79,6 +79,7 @@ struct CoarseParams {
   int part = -1;             // as DslashParams::part
   int agg[4] = {1, 1, 1, 1};
   const void* sub_from = nullptr;   // when set: out = sub_from - A_hat in
+  int allow_tc = 1;          // 0: keep FP32 inputs (no FP16 rounding of the vectors), e.g. for the setup
 };
 void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
                   const int* run = nullptr);

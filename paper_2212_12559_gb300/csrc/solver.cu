@@ -715,6 +715,8 @@ struct SetupOp {
       const CoarseLevel& C = c.coarse[l - 2];
       CoarseParams p;
       p.g = C.g; p.N = C.N;
+      p.allow_tc = 0;   // near-null iterations keep FP32 inputs (CGNE's recursive residual would
+                        // otherwise run below the FP16 input rounding)
       coarse_apply(out, in, p, dagger ? C.Sdags.st : C.Ss.st, c.stream, run);
     }
   }
