@@ -10,6 +10,7 @@
 // Reductions accumulate in FP64 whatever the vector precision and are
 // deterministic: per-CTA partial sums, then one finishing pass.
 #include "blas.cuh"
+#include "ca_solve.cuh"
 
 namespace smg {
 
@@ -112,62 +113,6 @@ __global__ void sub_kernel(C* __restrict__ z, const C* __restrict__ x, const C* 
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ bool off_flag(const int* run) { return run != nullptr && *run == 0; }
 
-// Cholesky solve of the CA-GCR normal equations for one system: (W^dag W) a =
-// W^dag r with the Gram matrix normalised to unit diagonal; a basis vector
-// whose pivot falls below 1e-12 of its norm (numerically dependent) is dropped.
-// In place, lower triangle only (s <= kMaxS).
-constexpr int kMaxS = 10;
-__device__ void ca_solve(const double2* g, int s, double2* coef) {
-  double2 L[kMaxS][kMaxS], c[kMaxS];
-  double dsc[kMaxS];
-  bool drop[kMaxS];
-  int p = 0;
-  for (int i = 0; i < s; ++i)
-    for (int j = i; j < s; ++j) {   // pair (i, j), i <= j: <W_i, W_j>; keep L[j][i] = conj
-      L[j][i] = make_double2(g[p].x, -g[p].y);
-      ++p;
-    }
-  for (int i = 0; i < s; ++i) c[i] = g[p++];
-  for (int i = 0; i < s; ++i) dsc[i] = L[i][i].x > 0 ? 1.0 / sqrt(L[i][i].x) : 0.0;
-  for (int i = 0; i < s; ++i) {
-    c[i] = cscale(c[i], dsc[i]);
-    for (int j = 0; j <= i; ++j) L[i][j] = cscale(L[i][j], dsc[i] * dsc[j]);
-  }
-  for (int j = 0; j < s; ++j) {
-    double d = L[j][j].x;
-    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
-    drop[j] = !(d > 1e-12) || dsc[j] == 0.0;
-    const double ljj = drop[j] ? 1.0 : sqrt(d);
-    L[j][j] = make_double2(ljj, 0);
-    for (int i = j + 1; i < s; ++i) {
-      if (drop[j]) { L[i][j] = make_double2(0, 0); continue; }
-      double2 v = L[i][j];
-      for (int k = 0; k < j; ++k) {
-        const double2 x = L[i][k], y = L[j][k];   // v -= x * conj(y)
-        v.x -= x.x * y.x + x.y * y.y;
-        v.y -= x.y * y.x - x.x * y.y;
-      }
-      L[i][j] = make_double2(v.x / ljj, v.y / ljj);
-    }
-  }
-  for (int i = 0; i < s; ++i) {   // L y = c
-    if (drop[i]) { c[i] = make_double2(0, 0); continue; }
-    double2 v = c[i];
-    for (int k = 0; k < i; ++k) { const double2 x = L[i][k], y = c[k]; v.x -= x.x * y.x - x.y * y.y; v.y -= x.x * y.y + x.y * y.x; }
-    c[i] = make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
-  }
-  for (int i = s - 1; i >= 0; --i) {   // L^dag a = y
-    if (drop[i]) { c[i] = make_double2(0, 0); continue; }
-    double2 v = c[i];
-    for (int k = i + 1; k < s; ++k) { const double2 l = L[k][i], b = c[k]; v.x -= l.x * b.x + l.y * b.y; v.y -= l.x * b.y - l.y * b.x; }
-    c[i] = make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
-  }
-  for (int i = 0; i < s; ++i) {
-    const double2 v = cscale(c[i], dsc[i]);
-    coef[i] = (isfinite(v.x) && isfinite(v.y)) ? v : make_double2(0, 0);
-  }
-}
-
 // Per-system scalar logic of the solvers, on the finished sums `o` (row ldo).
 __device__ void epilogue_system(const Epilogue& e, int s, const double2* o) {
   switch (e.kind) {
@@ -212,10 +157,7 @@ __device__ void epilogue_system(const Epilogue& e, int s, const double2* o) {
       }
       break;
     }
-    case EPI_CA: {
-      ca_solve(o, e.s, e.d2a + (size_t)s * e.s);
-      break;
-    }
+    case EPI_CA: break;   // one warp per system, see pair_dot_kernel
     case EPI_CGNE_INIT: {
       e.da[s] = o[0].x;
       e.db[s] = o[0].x;
@@ -268,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   constexpr int TR = 128;   // rows per tile
   // one padding entry per vector row: the pairs of one row (same r, different
   // vectors) then fall in different shared-memory banks
-  __shared__ C tile[kMaxVecs][TR + 1];
+  __shared__ __align__(16) C tile[kMaxVecs][TR + 1];
   __shared__ double2 red[kThreads];
   __shared__ bool last;
   const int s = blockIdx.y;
@@ -283,15 +225,29 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   const long long rows_per_block = (n + gridDim.x - 1) / gridDim.x;
   const long long r0 = blockIdx.x * rows_per_block;
   const long long r1 = min(n, r0 + rows_per_block);
+  // the next tile's loads are issued before the current tile is used
+  constexpr int PF = (kMaxVecs * TR + kThreads - 1) / kThreads;
+  C buf[PF];
+  const int nload = a.nv * TR;
+  auto fetch = [&](long long base) {
+    const int cnt = (int)min((long long)TR, r1 - base);
+#pragma unroll
+    for (int m = 0; m < PF; ++m) {
+      const int e = t + m * kThreads;
+      const int v = e / TR, r = e % TR;
+      buf[m] = (e < nload && r < cnt) ? ((const C*)a.v.p[v])[s * n + base + r] : C{0, 0};
+    }
+  };
+  if (r0 < r1) fetch(r0);
   for (long long base = r0; base < r1; base += TR) {
     const int cnt = (int)min((long long)TR, r1 - base);
-    for (int e = t; e < a.nv * TR; e += kThreads) {
-      const int v = e / TR, r = e % TR;
-      C val = C{0, 0};
-      if (r < cnt) val = ((const C*)a.v.p[v])[s * n + base + r];
-      tile[v][r] = val;
+#pragma unroll
+    for (int m = 0; m < PF; ++m) {
+      const int e = t + m * kThreads;
+      if (e < nload) tile[e / TR][e % TR] = buf[m];
     }
     __syncthreads();
+    if (base + TR < r1) fetch(base + TR);
     if (active) {
       const int vi = a.pi[p], vj = a.pj[p];
       for (int r = grp; r < cnt; r += groups) cfmac(acc, tile[vi][r], tile[vj][r]);
@@ -315,17 +271,34 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int e = t; e < nsys * np; e += kThreads) {
-    const int ss = e / np, pp = e % np;
-    double2 sum = make_double2(0, 0);
-    for (int b = 0; b < nb; ++b) sum = cadd(sum, __ldcg(&partial[((long long)ss * nb + b) * np + pp]));
-    out[(long long)ss * ldo + pp] = sum;
+  // one warp per output: lanes take every 32nd partial, then a fixed-order
+  // shuffle tree (deterministic, and the loads of a lane are independent)
+  {
+    const int warp = t >> 5, lane = t & 31;
+    for (int o = warp; o < nsys * np; o += kThreads / 32) {
+      const int ss = o / np, pp = o % np;
+      double2 sum = make_double2(0, 0);
+      for (int b = lane; b < nb; b += 32) sum = cadd(sum, __ldcg(&partial[((long long)ss * nb + b) * np + pp]));
+      for (int off = 16; off > 0; off >>= 1) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+      }
+      if (lane == 0) out[(long long)ss * ldo + pp] = sum;
+    }
   }
   if (t == 0) *counter = 0;
   if (epi.kind == EPI_NONE) return;
   __threadfence_block();
   __syncthreads();
-  for (int ss = t; ss < nsys; ss += kThreads) epilogue_system(epi, ss, out + (long long)ss * ldo);
+  if (epi.kind == EPI_CA) {
+    // the reduction tiles are free now: one factor scratch per warp
+    static_assert(sizeof(tile) >= sizeof(double2) * kCaMaxS * kCaMaxS * (kThreads / 32), "CA scratch");
+    double2(*Ls)[kCaMaxS] = reinterpret_cast<double2(*)[kCaMaxS]>(&tile[0][0]) + (t >> 5) * kCaMaxS;
+    for (int ss = t >> 5; ss < nsys; ss += kThreads / 32)
+      ca_solve_warp(out + (long long)ss * ldo, epi.s, epi.d2a + (size_t)ss * epi.s, Ls);
+  } else {
+    for (int ss = t; ss < nsys; ss += kThreads) epilogue_system(epi, ss, out + (long long)ss * ldo);
+  }
   __syncthreads();
   if (t == 0 && epi.run != nullptr &&
       (epi.kind == EPI_GCR_INIT || epi.kind == EPI_GCR_STEP || epi.kind == EPI_CGNE_INIT ||
@@ -482,8 +455,9 @@ void blas_pair_dots(const Vec* vs, int nv, const int* pi, const int* pj, int np,
   }
   for (int p = 0; p < np; ++p) { a.pi[p] = pi[p]; a.pj[p] = pj[p]; }
   const int nsys = vs[0].nsys;
-  long long nb = (a.n + 4 * 128 - 1) / (4 * 128);
-  if (nb > 152 * 2) nb = 152 * 2;
+  // two or more 128-row tiles per CTA, at most two CTAs per SM
+  long long nb = (a.n + 2 * 128 - 1) / (2 * 128);
+  if (nb > 2 * 152) nb = 2 * 152;
   if (nb < 1) nb = 1;
   double2* partial = (double2*)ws.get(sizeof(double2) * (size_t)nb * np * nsys);
   dim3 grid((unsigned)nb, nsys);

@@ -1,32 +1,52 @@
 // Persistent coarse-level solver: the whole GCR solve of one coarse level
-// (Sec. 2.1 "iterate on the coarser level linear system to some fixed
-// tolerance"; Table 1: GCR to 0.25 or 8 iterations with CA-GCR(s)
-// post-smoothing and an exact coarsest solve) in ONE cooperative launch.
+// (Sec. 2.1: the coarse system is iterated to a fixed tolerance; Table 1:
+// GCR to 0.25 or 8 iterations with CA-GCR(s) post-smoothing and an exact
+// coarsest solve) in ONE cooperative launch.
 //
-// On one GPU the coarse levels are latency bound: a 256-site level holds
-// 12k unknowns per vector, and launching each stencil apply, reduction and
-// axpy separately costs more than the work.  Here every CTA of a grid that
-// fills the GPU walks the same sequence of phases:
-//   restrict -> dense coarsest solve -> prolong -> residual -> s smoother
-//   applies -> Gram reduction -> correction -> operator apply -> two
-//   Gram-Schmidt reductions -> update
-// separated by grid barriers.  Reduction partials are written per CTA and
-// every CTA adds them in the same order, so all CTAs hold bit-identical
-// solver scalars in shared memory and no broadcast is needed.  Elementwise
-// work uses the same contiguous per-CTA row ranges as the reductions, so it
-// needs no grid barrier before the next reduction.
+// On one GPU the coarse levels are latency bound: a 256-site level holds 12k
+// unknowns per vector, and launching each stencil apply, reduction and axpy
+// separately costs more than the work.  Here every CTA of a grid of one CTA
+// per SM owns the same contiguous range of rows [c*per, (c+1)*per) of every
+// vector, and all CTAs walk the same sequence of phases separated by grid
+// barriers.  Per GCR iteration k (with the K-cycle preconditioner):
 //
-// Every barrier wait is bounded (2 s of %globaltimer); on expiry the kernel
-// sets an error word that the host reads, and returns.
+//   assemble R r from the CTAs' partial restrictions | dense coarsest solve |
+//   prolong z = P e (own rows) | V0 = r - A z | V_i = A V_{i-1}, i = 1..s,
+//   with the smoother's Gram partials after V_s | smoother correction
+//   z += sum c_q V_q and w = A z = r - V0 + sum c_q V_{q+1} (no apply) |
+//   Gram-Schmidt pass 1 | pass 2 | update w, r and the partial restriction of
+//   the new r (own rows).
+//
+// Reduction partials are written per CTA and every CTA adds them in the same
+// order, so all CTAs hold bit-identical solver scalars in shared memory and
+// no broadcast is needed.  Elementwise work and reduction partials use the
+// CTA's own rows, so they need no barrier between them.
+//
+// Resident mode (when it fits): the CTA's rows of the stencil (FP16 with row
+// scales, or FP32) and of the prolongator are copied into shared memory once
+// per launch; a stencil apply then stages the neighbour entries of its input
+// in shared memory (one round trip to L2) and reads everything else on chip.
+// Otherwise the stencil rows stream from global memory, each row once for all
+// systems of the batch.
+//
+// Grid barriers use one 64-bit arrival counter that only grows during a
+// launch (barrier b completes when it reaches b * gridDim); the last CTA to
+// exit clears it.  Every wait is bounded (2 s of %globaltimer); on expiry the
+// kernel sets an error word that the host reads, and returns.
+#include "ca_solve.cuh"
 #include "persist.cuh"
 #include "stencil_row.cuh"
+
+#include <algorithm>
 
 namespace smg {
 namespace {
 
 constexpr int PT = 512;          // threads per CTA
+constexpr int NW = PT / 32;      // warps per CTA
 constexpr int TR = 64;           // rows per reduction tile
 constexpr int kMaxP = 12;        // vectors per reduction
+constexpr int kCaWarps = 8;      // warps that solve the smoother's normal equations
 
 __device__ __forceinline__ unsigned long long gtime() {
   unsigned long long t;
@@ -34,77 +54,167 @@ __device__ __forceinline__ unsigned long long gtime() {
   return t;
 }
 
-// Grid barrier: arrival counter + generation word.  Returns false (and sets
-// *err) when the wait exceeds the time limit.
-__device__ bool grid_sync(unsigned* bar, int* err) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd((unsigned*)gen, 1u);
-    } else {
-      const unsigned long long t0 = gtime();
-      while (*gen == g) {
-        if (*(volatile int*)err != 0 || gtime() - t0 > 2000000000ull) {
-          atomicExch(err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ float2 ldh(const __half2* p, size_t i) { return __half22float2(p[i]); }
 __device__ __forceinline__ float2 ldh(const float2* p, size_t i) { return p[i]; }
 
 struct Shared {
-  float2 tile[kMaxP][TR + 1];   // padded: the pairs of one row sit in different banks
-  double2 red[PT];
+  union {
+    struct {
+      float2 tile[kMaxP][TR + 1];   // padded: the pairs of one row sit in different banks
+      double2 red[PT];
+    } d;
+    double2 ca[kCaWarps][kCaMaxS][kCaMaxS];   // CA-GCR factor scratch, one per warp
+  } u;
   // per-system solver state (identical in every CTA)
   double2 alpha[kPersistMaxSys][kPersistMaxK];
   double2 gamma[kPersistMaxSys][kPersistMaxK];
   double2 beta[kPersistMaxSys][kPersistMaxK][kPersistMaxK];
-  double2 sums[kPersistMaxSys][kMaxP + kPersistMaxK];
+  double2 sums[kPersistMaxSys][kPersistSums];
   double2 coef[kPersistMaxSys][16];
   double r2[kPersistMaxSys], thr2[kPersistMaxSys];
   int active[kPersistMaxSys], nk[kPersistMaxSys];
   int any;
-  int xs[256];                  // aggregate sites (restriction)
+  int ok;
+  int nbt[kPersistMaxTouch][9];   // neighbour sites of the touched sites (resident mode)
 };
 
-// ------------------------------------------------------------------ phases
-// This CTA's contiguous share [r0, r1) of a per-system vector of length n.
-__device__ __forceinline__ void my_rows(long long n, long long& r0, long long& r1) {
-  const long long per = (n + gridDim.x - 1) / gridDim.x;
-  r0 = blockIdx.x * per;
-  r1 = min(n, r0 + per);
+// This CTA's rows and the lattice sites they touch.
+struct Own {
+  long long r0, r1;
+  int xs0, nts;
+};
+
+__device__ __forceinline__ Own own_rows(const PersistArgs& a) {
+  Own o;
+  const long long per = a.plan.per;
+  o.r0 = min(a.n, (long long)blockIdx.x * per);
+  o.r1 = min(a.n, o.r0 + per);
+  o.xs0 = (int)(o.r0 / a.N);
+  o.nts = o.r1 > o.r0 ? (int)((o.r1 - 1) / a.N) - o.xs0 + 1 : 0;
+  return o;
 }
 
-// out = A_hat in (or sub - A_hat in): one warp per (system, site, row)
+// Grid barrier.  `target` (thread 0's copy) counts the arrivals expected so
+// far.  Returns false (and sets *err) when the wait exceeds the time limit or
+// another CTA already gave up.
+__device__ bool grid_sync(const PersistArgs& a, Shared& sh, unsigned long long& target) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sh.ok = 1;
+    target += gridDim.x;
+    __threadfence();
+    atomicAdd(a.bar, 1ull);
+    const unsigned long long t0 = gtime();
+    while (ld_acquire(a.bar) < target) {
+      if (*(volatile int*)a.err != 0 || gtime() - t0 > 2000000000ull) {
+        atomicExch(a.err, 1);
+        sh.ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return sh.ok != 0;
+}
+
+// acc += S chunk (C entries) . v[0..C)
+__device__ __forceinline__ void fma_chunk(float2& acc, const uint4& raw, const __half2*, const float2* v) {
+  const __half2* h = reinterpret_cast<const __half2*>(&raw);
+  const float4 v01 = *reinterpret_cast<const float4*>(v);
+  const float4 v23 = *reinterpret_cast<const float4*>(v + 2);
+  cfma(acc, __half22float2(h[0]), make_float2(v01.x, v01.y));
+  cfma(acc, __half22float2(h[1]), make_float2(v01.z, v01.w));
+  cfma(acc, __half22float2(h[2]), make_float2(v23.x, v23.y));
+  cfma(acc, __half22float2(h[3]), make_float2(v23.z, v23.w));
+}
+__device__ __forceinline__ void fma_chunk(float2& acc, const uint4& raw, const float2*, const float2* v) {
+  const float2* f = reinterpret_cast<const float2*>(&raw);
+  const float4 v01 = *reinterpret_cast<const float4*>(v);
+  cfma(acc, f[0], make_float2(v01.x, v01.y));
+  cfma(acc, f[1], make_float2(v01.z, v01.w));
+}
+
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// ------------------------------------------------------------------ phases
+// out = A_hat in (or sub - A_hat in) on the CTA's own rows, stencil rows in
+// shared memory.  Inputs of the touched sites' nine neighbours are staged in
+// shared memory in the stencil's own [dir][col] order, so a row is one
+// contiguous dot product of 9N entries.  N is a multiple of 4.
 template <typename SL>
-__device__ void stencil_phase(const PersistArgs& a, float2* out, const float2* in, const float2* sub) {
-  const int lane = threadIdx.x & 31;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int N = a.N;
-  const long long n = (long long)a.g.V * N;
-  const long long rows = (long long)a.nsys * n;
-  const SL* S = (const SL*)a.S;
-  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nw) {
-    const int s = (int)(row / n);
-    const long long rem = row - (long long)s * n;
-    const int X = (int)(rem / N), i = (int)(rem % N);
+__device__ void stencil_resident(const PersistArgs& a, Shared& sh, const Own& o, unsigned char* smem,
+                                 float2* out, const float2* in, const float2* sub) {
+  constexpr int C = Chunk<SL>::C;
+  const int N = a.N, W = 9 * N, nq = W / C;
+  const SL* Sres = reinterpret_cast<const SL*>(smem + a.plan.off_S);
+  const float* Ssc = reinterpret_cast<const float*>(smem + a.plan.off_sc);
+  float2* stg = reinterpret_cast<float2*>(smem + a.plan.off_stg);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int per_sys = o.nts * W;
+  for (int s0 = 0; s0 < a.nsys; s0 += a.plan.sg) {
+    const int ns = min(a.plan.sg, a.nsys - s0);
+    for (int e = 2 * t; e < ns * per_sys; e += 2 * PT) {
+      const int sl = e / per_sys, rem = e - sl * per_sys;
+      const int xl = rem / W, rr = rem - xl * W;
+      const int dir = rr / N, j = rr - dir * N;
+      const float2* src = in + (size_t)(s0 + sl) * a.n + (size_t)sh.nbt[xl][dir] * N + j;
+      *reinterpret_cast<float4*>(stg + e) = *reinterpret_cast<const float4*>(src);
+    }
+    __syncthreads();
+    for (long long row = o.r0 + warp; row < o.r1; row += NW) {
+      const int x = (int)(row / N), xl = x - o.xs0;
+      const SL* sr = Sres + (size_t)(row - o.r0) * W;
+      float2 acc[kPersistMaxSys];
+#pragma unroll
+      for (int sl = 0; sl < kPersistMaxSys; ++sl) acc[sl] = make_float2(0.f, 0.f);
+      for (int q = lane; q < nq; q += 32) {
+        const int e = q * C;
+        const uint4 raw = *reinterpret_cast<const uint4*>(sr + e);
+#pragma unroll
+        for (int sl = 0; sl < kPersistMaxSys; ++sl)
+          if (sl < ns) fma_chunk(acc[sl], raw, sr, stg + ((size_t)sl * o.nts + xl) * W + e);
+      }
+      const float sc = a.Srs != nullptr ? Ssc[row - o.r0] : 1.0f;
+#pragma unroll
+      for (int sl = 0; sl < kPersistMaxSys; ++sl) {
+        if (sl >= ns) break;
+        float2 v = warp_sum(acc[sl]);
+        if (lane == 0) {
+          v = make_float2(v.x * sc, v.y * sc);
+          const size_t oi = (size_t)(s0 + sl) * a.n + row;
+          if (sub != nullptr) v = csub(sub[oi], v);
+          out[oi] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The same from global memory: each stencil row is read once for all systems.
+template <typename SL>
+__device__ void stencil_stream(const PersistArgs& a, const Own& o, float2* out, const float2* in,
+                               const float2* sub) {
+  constexpr int C = Chunk<SL>::C;
+  const int N = a.N, W = 9 * N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const SL* S = reinterpret_cast<const SL*>(a.S);
+  for (long long row = o.r0 + warp; row < o.r1; row += NW) {
+    const int X = (int)(row / N);
     int c[4];
     a.g.coords(X, c);
     int nb[9];
@@ -114,81 +224,109 @@ __device__ void stencil_phase(const PersistArgs& a, float2* out, const float2* i
       nb[1 + 2 * mu] = a.g.shift(c, mu, 1);
       nb[2 + 2 * mu] = a.g.shift(c, mu, -1);
     }
-    const SL* sr = S + ((size_t)X * N + i) * 9 * N;
-    const float2* vin = in + (size_t)s * n;
-    float2 acc;
+    const SL* sr = S + (size_t)row * W;
+    float2 acc[kPersistMaxSys];
+#pragma unroll
+    for (int sl = 0; sl < kPersistMaxSys; ++sl) acc[sl] = make_float2(0.f, 0.f);
     if (N % 4 == 0) {
-      acc = stencil_row_dot<SL>(sr, N, lane,
-                                [&](int dir, int j) { return vin + (size_t)pick_site(nb, dir) * N + j; });
-    } else {
-      acc = make_float2(0.f, 0.f);
-      for (int e = lane; e < 9 * N; e += 32) {
+      for (int q = lane; q < W / C; q += 32) {
+        const int e = q * C;
         const int dir = e / N, j = e - dir * N;
-        cfma(acc, ldh(sr, e), vin[(size_t)pick_site(nb, dir) * N + j]);
+        const size_t off = (size_t)pick_site(nb, dir) * N + j;
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(sr + e));
+#pragma unroll
+        for (int sl = 0; sl < kPersistMaxSys; ++sl)
+          if (sl < a.nsys) fma_chunk(acc[sl], raw, sr, in + (size_t)sl * a.n + off);
+      }
+    } else {
+      for (int e = lane; e < W; e += 32) {
+        const int dir = e / N, j = e - dir * N;
+        const size_t off = (size_t)pick_site(nb, dir) * N + j;
+        const float2 sv = ldh(sr, e);
+#pragma unroll
+        for (int sl = 0; sl < kPersistMaxSys; ++sl)
+          if (sl < a.nsys) cfma(acc[sl], sv, in[(size_t)sl * a.n + off]);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    const float sc = a.Srs != nullptr ? a.Srs[row] : 1.0f;
+#pragma unroll
+    for (int sl = 0; sl < kPersistMaxSys; ++sl) {
+      if (sl >= a.nsys) break;
+      float2 v = warp_sum(acc[sl]);
+      if (lane == 0) {
+        v = make_float2(v.x * sc, v.y * sc);
+        const size_t oi = (size_t)sl * a.n + row;
+        if (sub != nullptr) v = csub(sub[oi], v);
+        out[oi] = v;
+      }
     }
-    if (lane == 0) {
-      if (a.Srs != nullptr) acc = cscale(acc, a.Srs[(size_t)X * N + i]);
-      const size_t oi = (size_t)s * n + rem;
-      if (sub != nullptr) acc = csub(sub[oi], acc);
-      out[oi] = acc;
-    }
+  }
+  __syncthreads();
+}
+
+template <typename SL>
+__device__ __forceinline__ void stencil_phase(const PersistArgs& a, Shared& sh, const Own& o, unsigned char* smem,
+                                              float2* out, const float2* in, const float2* sub) {
+  if (a.plan.resident) stencil_resident<SL>(a, sh, o, smem, out, in, sub);
+  else stencil_stream<SL>(a, o, out, in, sub);
+}
+
+// Prolongator row `row` of this level (resident copy or global).
+template <typename SL>
+__device__ __forceinline__ const SL* prolongator_row(const PersistArgs& a, const Own& o, unsigned char* smem,
+                                                     long long row) {
+  const int nv = a.tg.nvec;
+  if (a.plan.resident) return reinterpret_cast<const SL*>(smem + a.plan.off_P) + (size_t)(row - o.r0) * nv;
+  return reinterpret_cast<const SL*>(a.P) + (size_t)row * nv;
+}
+
+// rpart[c][xl][s][i] = sum over this CTA's rows of touched site xs0 + xl of
+// conj(P[row][k]) r[s][row], i = chi * nvec + k, chirality chi = (d >= N/2).
+template <typename SL>
+__device__ void restrict_partial(const PersistArgs& a, const Own& o, unsigned char* smem, const float2* r) {
+  const int N = a.N, nv = a.tg.nvec, Nc = 2 * nv, half = N / 2;
+  const int total = a.nsys * o.nts * Nc;
+  for (int e = threadIdx.x; e < total; e += PT) {
+    const int s = e / (o.nts * Nc), rem = e - s * (o.nts * Nc);
+    const int xl = rem / Nc, i = rem - xl * Nc;
+    const int chi = i / nv, k = i - chi * nv;
+    const long long x0 = (long long)(o.xs0 + xl) * N;
+    const long long lo = max(o.r0, x0 + chi * half), hi = min(o.r1, x0 + chi * half + half);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (long long row = lo; row < hi; ++row)
+      cfmac(acc, ldh(prolongator_row<SL>(a, o, smem, row), k), r[(size_t)s * a.n + row]);
+    a.rpart[(((size_t)blockIdx.x * a.plan.nslot + xl) * kPersistMaxSys + s) * Nc + i] = acc;
   }
 }
 
-// rc = R r : one CTA per (system, coarse site) at a time; thread t owns vector
-// k = t % nvec and a strided set of the aggregate's rows (prolongator layout
-// [site][dof][vector], so the nvec threads of a row read consecutive entries).
-template <typename SL>
-__device__ void restrict_phase(const PersistArgs& a, Shared& sh, float2* rc, const float2* r) {
+// rc = R r: each entry adds, in a fixed order, the partials of the CTAs that
+// own rows of the aggregate's sites.
+__device__ void assemble_rc(const PersistArgs& a, float2* rc) {
   const TransferGeom& t = a.tg;
-  const int nv = t.nvec, Nc = 2 * nv, half = t.ndof / 2;
-  const int k = threadIdx.x % nv, grp = threadIdx.x / nv, groups = PT / nv;
+  const int N = a.N, Nc = 2 * t.nvec;
   const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
-  const int rows = npos * t.ndof;
-  const long long nf = (long long)t.fine.V * t.ndof;
-  const SL* P = (const SL*)a.P;
-  double2* part = &sh.red[0];   // reused: [2][PT] FP32 pairs fit in PT double2
-  float2* pf = reinterpret_cast<float2*>(part);
-  int* xs = sh.xs;              // fine site of each aggregate position
-  for (long long job = blockIdx.x; job < (long long)a.nsys * t.coarse.V; job += gridDim.x) {
-    const int s = (int)(job / t.coarse.V), X = (int)(job % t.coarse.V);
+  const long long per = a.plan.per;
+  const long long total = (long long)a.nsys * t.coarse.V * Nc;
+  for (long long e = (long long)blockIdx.x * PT + threadIdx.x; e < total; e += (long long)gridDim.x * PT) {
+    const int s = (int)(e / ((long long)t.coarse.V * Nc));
+    const int rem = (int)(e - (long long)s * t.coarse.V * Nc);
+    const int X = rem / Nc, i = rem - X * Nc;
     int Xc[4];
     t.coarse.coords(X, Xc);
-    for (int p = threadIdx.x; p < npos; p += PT) {
+    float2 sum = make_float2(0.f, 0.f);
+    for (int p = 0; p < npos; ++p) {
       int q = p, cc[4];
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) { cc[mu] = Xc[mu] * t.agg[mu] + q % t.agg[mu]; q /= t.agg[mu]; }
-      xs[p] = t.fine.index(cc);
-    }
-    __syncthreads();
-    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-    if (grp < groups) {
-#pragma unroll 8
-      for (int rr = grp; rr < rows; rr += groups) {
-        const int p = rr / t.ndof, d = rr - p * t.ndof;
-        const size_t row = (size_t)xs[p] * t.ndof + d;
-        const float2 v = r[(size_t)s * nf + row];
-        const float2 pv = ldh(P, row * nv + k);
-        if (d < half) cfmac(acc0, pv, v);
-        else cfmac(acc1, pv, v);
+      const long long x = t.fine.index(cc);
+      const int c_lo = (int)(x * N / per), c_hi = (int)((x * N + N - 1) / per);
+      for (int c = c_lo; c <= c_hi; ++c) {
+        const int slot = (int)(x - (long long)c * per / N);
+        sum = cadd(sum, a.rpart[(((size_t)c * a.plan.nslot + slot) * kPersistMaxSys + s) * Nc + i]);
       }
     }
-    __syncthreads();
-    pf[threadIdx.x] = acc0;
-    pf[PT + threadIdx.x] = acc1;
-    __syncthreads();
-    for (int i = threadIdx.x; i < Nc; i += PT) {
-      const int chi = i / nv, kk = i % nv;
-      float2 sum = make_float2(0.f, 0.f);
-      for (int g = 0; g < groups; ++g) sum = cadd(sum, pf[chi * PT + g * nv + kk]);
-      rc[(size_t)s * t.coarse.V * Nc + (size_t)X * Nc + i] = sum;
-    }
-    __syncthreads();
+    rc[e] = sum;
   }
 }
 
@@ -203,166 +341,150 @@ __device__ void dense_phase(const PersistArgs& a, float2* ec, const float2* rc) 
     const float2* v = rc + (size_t)s * nd;
     float2 acc = make_float2(0.f, 0.f);
     for (int j = lane; j < nd; j += 32) cfma(acc, Dr[j], v[j]);
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
+    acc = warp_sum(acc);
     if (lane == 0) ec[o] = acc;
   }
 }
 
-// z = P ec : one thread per (system, site, component), contiguous prolongator run
+// z = P ec on the CTA's own rows, one thread per (system, row)
 template <typename SL>
-__device__ void prolong_phase(const PersistArgs& a, float2* z, const float2* ec) {
+__device__ void prolong_own(const PersistArgs& a, const Own& o, unsigned char* smem, float2* z, const float2* ec) {
   const TransferGeom& t = a.tg;
-  const long long nf = (long long)t.fine.V * t.ndof;
-  const int Nc = 2 * t.nvec, half = t.ndof / 2;
-  const SL* P = (const SL*)a.P;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)a.nsys * nf;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e / nf);
-    const long long rem = e - (long long)s * nf;
-    const int x = (int)(rem / t.ndof), d = (int)(rem % t.ndof);
+  const int N = a.N, nv = t.nvec, Nc = 2 * nv, half = N / 2;
+  const long long rows = o.r1 - o.r0;
+  for (long long e = threadIdx.x; e < a.nsys * rows; e += PT) {
+    const int s = (int)(e / rows);
+    const long long row = o.r0 + (e - (long long)s * rows);
+    const int x = (int)(row / N), d = (int)(row - (long long)x * N);
     int c[4];
     t.fine.coords(x, c);
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) c[mu] /= t.agg[mu];
-    const int X = t.coarse.index(c);
     const int chi = d >= half ? 1 : 0;
-    const float2* v = ec + (size_t)s * t.coarse.V * Nc + (size_t)X * Nc + chi * t.nvec;
-    const SL* Px = P + (size_t)rem * t.nvec;
+    const float2* v = ec + (size_t)s * t.coarse.V * Nc + (size_t)t.coarse.index(c) * Nc + chi * nv;
+    const SL* Pr = prolongator_row<SL>(a, o, smem, row);
     float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int k = 0; k < t.nvec; ++k) cfma(acc, ldh(Px, k), v[k]);
-    z[e] = acc;
+#pragma unroll 8
+    for (int k = 0; k < nv; ++k) cfma(acc, ldh(Pr, k), v[k]);
+    z[(size_t)s * a.n + row] = acc;
   }
 }
 
-// Per-CTA partial sums of conj(v[pi[p]]) v[pj[p]] over this CTA's rows, for
-// every system, accumulated in FP32 per thread and FP64 across threads;
+// Per-CTA partial sums of conj(v[pi[p]]) v[pj[p]] over the CTA's own rows,
+// for every system, accumulated in FP32 per thread and FP64 across threads;
 // written to partial[cta][s][p].
-__device__ void dots_partial(const PersistArgs& a, Shared& sh, float2* const* v, int nv, const int* pi,
-                             const int* pj, int np) {
+__device__ void dots_partial(const PersistArgs& a, Shared& sh, const Own& o, float2* const* v, int nv,
+                             const int* pi, const int* pj, int np) {
   const int t = threadIdx.x;
   const int groups = PT / np;
   const int p = t % np, grp = t / np;
   const bool act = grp < groups;
   const long long n = a.n;
-  long long r0, r1;
-  my_rows(n, r0, r1);
   for (int s = 0; s < a.nsys; ++s) {
     float2 acc = make_float2(0.f, 0.f);
-    for (long long base = r0; base < r1; base += TR) {
-      const int cnt = (int)min((long long)TR, r1 - base);
+    for (long long base = o.r0; base < o.r1; base += TR) {
+      const int cnt = (int)min((long long)TR, o.r1 - base);
       for (int e = t; e < nv * TR; e += PT) {
         const int vi = e / TR, r = e % TR;
         float2 val = make_float2(0.f, 0.f);
         if (r < cnt) val = v[vi][(size_t)s * n + base + r];
-        sh.tile[vi][r] = val;
+        sh.u.d.tile[vi][r] = val;
       }
       __syncthreads();
       if (act)
-        for (int r = grp; r < cnt; r += groups) cfmac(acc, sh.tile[pi[p]][r], sh.tile[pj[p]][r]);
+        for (int r = grp; r < cnt; r += groups) cfmac(acc, sh.u.d.tile[pi[p]][r], sh.u.d.tile[pj[p]][r]);
       __syncthreads();
     }
-    sh.red[t] = act ? make_double2(acc.x, acc.y) : make_double2(0, 0);
+    sh.u.d.red[t] = act ? make_double2(acc.x, acc.y) : make_double2(0, 0);
     __syncthreads();
     if (t < np) {
       double2 sum = make_double2(0, 0);
-      for (int g = 0; g < groups; ++g) sum = cadd(sum, sh.red[g * np + t]);
-      a.partial[((size_t)blockIdx.x * kPersistMaxSys + s) * 64 + t] = sum;
+      for (int g = 0; g < groups; ++g) sum = cadd(sum, sh.u.d.red[g * np + t]);
+      a.partial[((size_t)blockIdx.x * kPersistMaxSys + s) * kPersistSums + t] = sum;
     }
     __syncthreads();
   }
 }
 
-// After a barrier: every CTA adds all CTAs' partials in the same order.
+// After a barrier: every CTA adds all CTAs' partials in the same order (one
+// warp per output, lanes over the CTAs, fixed shuffle tree).
 __device__ void dots_final(const PersistArgs& a, Shared& sh, int np) {
-  for (int e = threadIdx.x; e < a.nsys * np; e += PT) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = warp; e < a.nsys * np; e += NW) {
     const int s = e / np, p = e % np;
     double2 sum = make_double2(0, 0);
-    for (int b = 0; b < (int)gridDim.x; ++b)
-      sum = cadd(sum, __ldcg(&a.partial[((size_t)b * kPersistMaxSys + s) * 64 + p]));
-    sh.sums[s][p] = sum;
+    for (int b = lane; b < (int)gridDim.x; b += 32)
+      sum = cadd(sum, __ldcg(&a.partial[((size_t)b * kPersistMaxSys + s) * kPersistSums + p]));
+    for (int off = 16; off > 0; off >>= 1) {
+      sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+      sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+    }
+    if (lane == 0) sh.sums[s][p] = sum;
   }
   __syncthreads();
 }
 
-// CA-GCR normal equations (same algorithm as the launch-based path)
-__device__ void ca_solve_sh(const double2* g, int s, double2* coef) {
-  constexpr int MS = 10;
-  double2 L[MS][MS], c[MS];
-  double dsc[MS];
-  bool drop[MS];
-  int p = 0;
-  for (int i = 0; i < s; ++i)
-    for (int j = i; j < s; ++j) { L[j][i] = make_double2(g[p].x, -g[p].y); ++p; }
-  for (int i = 0; i < s; ++i) c[i] = g[p++];
-  for (int i = 0; i < s; ++i) dsc[i] = L[i][i].x > 0 ? 1.0 / sqrt(L[i][i].x) : 0.0;
-  for (int i = 0; i < s; ++i) {
-    c[i] = cscale(c[i], dsc[i]);
-    for (int j = 0; j <= i; ++j) L[i][j] = cscale(L[i][j], dsc[i] * dsc[j]);
+// Resident mode: the CTA's stencil rows, row scales and prolongator rows,
+// and the neighbour table of its touched sites.
+template <typename SL>
+__device__ void load_resident(const PersistArgs& a, Shared& sh, const Own& o, unsigned char* smem) {
+  const int t = threadIdx.x;
+  const int N = a.N, W = 9 * N;
+  const long long rows = o.r1 - o.r0;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const SL*>(a.S) + (size_t)o.r0 * W);
+    uint4* dst = reinterpret_cast<uint4*>(smem + a.plan.off_S);
+    const long long nchunk = rows * W * (long long)sizeof(SL) / 16;
+    for (long long i = t; i < nchunk; i += PT) dst[i] = __ldg(src + i);
   }
-  for (int j = 0; j < s; ++j) {
-    double d = L[j][j].x;
-    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
-    drop[j] = !(d > 1e-12) || dsc[j] == 0.0;
-    const double ljj = drop[j] ? 1.0 : sqrt(d);
-    L[j][j] = make_double2(ljj, 0);
-    for (int i = j + 1; i < s; ++i) {
-      if (drop[j]) { L[i][j] = make_double2(0, 0); continue; }
-      double2 v = L[i][j];
-      for (int k = 0; k < j; ++k) {
-        const double2 x = L[i][k], y = L[j][k];
-        v.x -= x.x * y.x + x.y * y.y;
-        v.y -= x.y * y.x - x.x * y.y;
-      }
-      L[i][j] = make_double2(v.x / ljj, v.y / ljj);
-    }
+  if (a.Srs != nullptr) {
+    float* dst = reinterpret_cast<float*>(smem + a.plan.off_sc);
+    for (long long i = t; i < rows; i += PT) dst[i] = a.Srs[o.r0 + i];
   }
-  for (int i = 0; i < s; ++i) {
-    if (drop[i]) { c[i] = make_double2(0, 0); continue; }
-    double2 v = c[i];
-    for (int k = 0; k < i; ++k) { const double2 x = L[i][k], y = c[k]; v.x -= x.x * y.x - x.y * y.y; v.y -= x.x * y.y + x.y * y.x; }
-    c[i] = make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
+  if (a.has_pre) {
+    const int nv = a.tg.nvec;
+    const SL* src = reinterpret_cast<const SL*>(a.P) + (size_t)o.r0 * nv;
+    SL* dst = reinterpret_cast<SL*>(smem + a.plan.off_P);
+    for (long long i = t; i < rows * nv; i += PT) dst[i] = src[i];
   }
-  for (int i = s - 1; i >= 0; --i) {
-    if (drop[i]) { c[i] = make_double2(0, 0); continue; }
-    double2 v = c[i];
-    for (int k = i + 1; k < s; ++k) { const double2 l = L[k][i], b = c[k]; v.x -= l.x * b.x + l.y * b.y; v.y -= l.x * b.y - l.y * b.x; }
-    c[i] = make_double2(v.x / L[i][i].x, v.y / L[i][i].x);
+  for (int e = t; e < o.nts * 9; e += PT) {
+    const int xl = e / 9, dir = e % 9;
+    const int X = o.xs0 + xl;
+    int c[4];
+    a.g.coords(X, c);
+    int site = X;
+    if (dir > 0) site = a.g.shift(c, (dir - 1) / 2, (dir & 1) ? 1 : -1);
+    sh.nbt[xl][dir] = site;
   }
-  for (int i = 0; i < s; ++i) {
-    const double2 v = cscale(c[i], dsc[i]);
-    coef[i] = (isfinite(v.x) && isfinite(v.y)) ? v : make_double2(0, 0);
-  }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------ kernel
 template <typename SL>
-__global__ void __launch_bounds__(PT, 1) persist_gcr_kernel(PersistArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Shared& sh = *reinterpret_cast<Shared*>(smem);
-  if (a.run != nullptr && *a.run == 0) return;   // uniform across the grid
+__device__ void persist_body(const PersistArgs& a, Shared& sh, unsigned char* smem) {
   const long long n = a.n;
   const int K = a.K, S = a.s, nsys = a.nsys;
-  long long r0, r1;
-  my_rows(n, r0, r1);
-  const int t = threadIdx.x;
-#define BARRIER() do { if (!grid_sync(a.bar, a.err)) return; } while (0)
+  const Own o = own_rows(a);
+  const int t = threadIdx.x, warp = t >> 5;
+  unsigned long long target = 0;
+#define BARRIER() do { if (!grid_sync(a, sh, target)) return; } while (0)
 
-  // r = b, x = 0 on this CTA's rows; |r|^2
+  if (a.plan.resident) load_resident<SL>(a, sh, o, smem);
+  // r = b, x = 0 (z_0 = r without a preconditioner) on the own rows; |r|^2
   for (int s = 0; s < nsys; ++s)
-    for (long long i = r0 + t; i < r1; i += PT) {
-      a.r[(size_t)s * n + i] = a.b[(size_t)s * n + i];
+    for (long long i = o.r0 + t; i < o.r1; i += PT) {
+      const float2 bv = a.b[(size_t)s * n + i];
+      a.r[(size_t)s * n + i] = bv;
       a.x[(size_t)s * n + i] = make_float2(0.f, 0.f);
+      if (!a.has_pre) a.z[0][(size_t)s * n + i] = bv;
     }
   __syncthreads();
   {
     float2* vv[1] = {a.r};
     const int pi[1] = {0}, pj[1] = {0};
-    dots_partial(a, sh, vv, 1, pi, pj, 1);
+    dots_partial(a, sh, o, vv, 1, pi, pj, 1);
   }
+  if (a.has_pre) restrict_partial<SL>(a, o, smem, a.r);
   BARRIER();
   dots_final(a, sh, 1);
   if (t == 0) {
@@ -382,69 +504,70 @@ __global__ void __launch_bounds__(PT, 1) persist_gcr_kernel(PersistArgs a) {
   for (int k = 0; k < K && sh.any; ++k) {
     float2* zk = a.z[k];
     float2* wk = a.w[k];
-    // ---- preconditioner z_k = K(r)
     if (a.has_pre) {
-      restrict_phase<SL>(a, sh, a.rc, a.r);
+      // ---- z_k = K(r): coarse correction, then CA-GCR(s) on this level
+      assemble_rc(a, a.rc);
       BARRIER();
       dense_phase(a, a.ec, a.rc);
       BARRIER();
-      prolong_phase<SL>(a, zk, a.ec);
+      prolong_own<SL>(a, o, smem, zk, a.ec);
       BARRIER();
-      stencil_phase<SL>(a, a.V[0], zk, a.r);          // V0 = r - A z
-      BARRIER();
+      stencil_phase<SL>(a, sh, o, smem, a.V[0], zk, a.r);          // V0 = r - A z
       for (int i = 1; i <= S; ++i) {
-        stencil_phase<SL>(a, a.V[i], a.V[i - 1], nullptr);
         BARRIER();
+        stencil_phase<SL>(a, sh, o, smem, a.V[i], a.V[i - 1], nullptr);
       }
       {
-        int pi[kMaxP * kMaxP], pj[kMaxP * kMaxP], np = 0;
+        int pi[kPersistSums], pj[kPersistSums], np = 0;
         for (int i = 0; i < S; ++i)
           for (int j = i; j < S; ++j) { pi[np] = i + 1; pj[np] = j + 1; ++np; }
         for (int i = 0; i < S; ++i) { pi[np] = i + 1; pj[np] = 0; ++np; }
-        dots_partial(a, sh, a.V, S + 1, pi, pj, np);
+        dots_partial(a, sh, o, a.V, S + 1, pi, pj, np);
         BARRIER();
         dots_final(a, sh, np);
       }
-      if (t < nsys) ca_solve_sh(sh.sums[t], S, sh.coef[t]);
+      for (int s = warp; s < nsys && warp < kCaWarps; s += kCaWarps)
+        ca_solve_warp(sh.sums[s], S, sh.coef[s], sh.u.ca[warp]);
       __syncthreads();
+      // z += sum_q c_q V_q ;  w = A z = (r - V0) + sum_q c_q V_{q+1}
       for (int s = 0; s < nsys; ++s)
-        for (long long i = r0 + t; i < r1; i += PT) {
-          const size_t o = (size_t)s * n + i;
-          float2 acc = zk[o];
+        for (long long i = o.r0 + t; i < o.r1; i += PT) {
+          const size_t oi = (size_t)s * n + i;
+          float2 zacc = zk[oi];
+          float2 wacc = csub(a.r[oi], a.V[0][oi]);
           for (int q = 0; q < S; ++q) {
             const double2 cq = sh.coef[s][q];
-            cfma(acc, make_float2((float)cq.x, (float)cq.y), a.V[q][o]);
+            const float2 cf = make_float2((float)cq.x, (float)cq.y);
+            cfma(zacc, cf, a.V[q][oi]);
+            cfma(wacc, cf, a.V[q + 1][oi]);
           }
-          zk[o] = acc;
+          zk[oi] = zacc;
+          wk[oi] = wacc;
         }
-      BARRIER();
+      __syncthreads();
     } else {
-      for (int s = 0; s < nsys; ++s)
-        for (long long i = r0 + t; i < r1; i += PT) zk[(size_t)s * n + i] = a.r[(size_t)s * n + i];
-      BARRIER();
+      // ---- z_k = r (set on the own rows before the last barrier); w_k = A z_k
+      stencil_phase<SL>(a, sh, o, smem, wk, zk, nullptr);
     }
-    // ---- w_k = A z_k
-    stencil_phase<SL>(a, wk, zk, nullptr);
-    BARRIER();
     // ---- classical Gram-Schmidt, pass 1
     if (k > 0) {
       int pi[kPersistMaxK], pj[kPersistMaxK];
       for (int j = 0; j < k; ++j) { pi[j] = j; pj[j] = k; }
-      dots_partial(a, sh, a.w, k + 1, pi, pj, k);
+      dots_partial(a, sh, o, a.w, k + 1, pi, pj, k);
       BARRIER();
       dots_final(a, sh, k);
       if (t < nsys)
         for (int j = 0; j < k; ++j) sh.beta[t][k][j] = sh.sums[t][j];
       __syncthreads();
       for (int s = 0; s < nsys; ++s)
-        for (long long i = r0 + t; i < r1; i += PT) {
-          const size_t o = (size_t)s * n + i;
-          float2 acc = wk[o];
+        for (long long i = o.r0 + t; i < o.r1; i += PT) {
+          const size_t oi = (size_t)s * n + i;
+          float2 acc = wk[oi];
           for (int j = 0; j < k; ++j) {
             const double2 b = sh.beta[s][k][j];
-            cfma(acc, make_float2((float)-b.x, (float)-b.y), a.w[j][o]);
+            cfma(acc, make_float2((float)-b.x, (float)-b.y), a.w[j][oi]);
           }
-          wk[o] = acc;
+          wk[oi] = acc;
         }
       __syncthreads();
     }
@@ -457,7 +580,7 @@ __global__ void __launch_bounds__(PT, 1) persist_gcr_kernel(PersistArgs a) {
       for (int j = 0; j < k; ++j) { pi[j] = j; pj[j] = k; }
       pi[k] = k; pj[k] = k;
       pi[k + 1] = k; pj[k + 1] = k + 1;
-      dots_partial(a, sh, vv, k + 2, pi, pj, k + 2);
+      dots_partial(a, sh, o, vv, k + 2, pi, pj, k + 2);
       BARRIER();
       dots_final(a, sh, k + 2);
     }
@@ -492,25 +615,29 @@ __global__ void __launch_bounds__(PT, 1) persist_gcr_kernel(PersistArgs a) {
       sh.any = any;
     }
     // ---- w_k <- (w_k - sum c2_j w_j) / gamma ; r <- r - alpha w_k
+    const bool next = k + 1 < K;
     for (int s = 0; s < nsys; ++s) {
       const float gi = (float)sh.coef[s][0].x;
       const double2 al = sh.alpha[s][k];
       const float2 na = make_float2((float)-al.x, (float)-al.y);
-      for (long long i = r0 + t; i < r1; i += PT) {
-        const size_t o = (size_t)s * n + i;
-        float2 acc = wk[o];
+      for (long long i = o.r0 + t; i < o.r1; i += PT) {
+        const size_t oi = (size_t)s * n + i;
+        float2 acc = wk[oi];
         for (int j = 0; j < k; ++j) {
           const double2 c2 = sh.sums[s][j];
-          cfma(acc, make_float2((float)-c2.x, (float)-c2.y), a.w[j][o]);
+          cfma(acc, make_float2((float)-c2.x, (float)-c2.y), a.w[j][oi]);
         }
         acc = make_float2(acc.x * gi, acc.y * gi);
-        wk[o] = acc;
-        float2 rv = a.r[o];
+        wk[oi] = acc;
+        float2 rv = a.r[oi];
         cfma(rv, na, acc);
-        a.r[o] = rv;
+        a.r[oi] = rv;
+        if (!a.has_pre && next) a.z[k + 1][oi] = rv;
       }
     }
     __syncthreads();
+    if (!sh.any || !next) break;
+    if (a.has_pre) restrict_partial<SL>(a, o, smem, a.r);
     BARRIER();
   }
   // ---- x = sum_k y_k z_k with gamma_j y_j + sum_{q>j} beta[q][j] y_q = alpha_j
@@ -534,82 +661,139 @@ __global__ void __launch_bounds__(PT, 1) persist_gcr_kernel(PersistArgs a) {
   __syncthreads();
   for (int s = 0; s < nsys; ++s) {
     const int m = sh.nk[s];
-    for (long long i = r0 + t; i < r1; i += PT) {
-      const size_t o = (size_t)s * n + i;
+    for (long long i = o.r0 + t; i < o.r1; i += PT) {
+      const size_t oi = (size_t)s * n + i;
       float2 acc = make_float2(0.f, 0.f);
       for (int q = 0; q < m; ++q) {
         const double2 y = sh.coef[s][q];
-        cfma(acc, make_float2((float)y.x, (float)y.y), a.z[q][o]);
+        cfma(acc, make_float2((float)y.x, (float)y.y), a.z[q][oi]);
       }
-      a.x[o] = acc;
+      a.x[oi] = acc;
     }
   }
 #undef BARRIER
 }
 
 template <typename SL>
-int occupancy_grid(int dev_sms) {
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persist_gcr_kernel<SL>, PT, sizeof(Shared));
-  return per >= 1 ? dev_sms : 0;
+__global__ void __launch_bounds__(PT, 1) persist_gcr_kernel(PersistArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Shared& sh = *reinterpret_cast<Shared*>(smem);
+  if (a.run != nullptr && *a.run == 0) return;   // uniform across the grid
+  persist_body<SL>(a, sh, smem);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // every arrival of this launch precedes its CTA's exit count, so the
+    // last CTA out may clear the barrier for the next launch
+    __threadfence();
+    if (atomicAdd(a.exitc, 1u) == gridDim.x - 1) {
+      atomicExch(a.bar, 0ull);
+      atomicExch(a.exitc, 0u);
+      __threadfence();
+    }
+  }
 }
 
-}  // namespace
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-size_t persist_smem_bytes() { return sizeof(Shared); }
-
-bool persist_supported(int nsys, int K, int s, int N, Store st, int npos) {
-  return (st == S16 || st == S32) && nsys >= 1 && nsys <= kPersistMaxSys && K >= 1 && K <= kPersistMaxK &&
-         s >= 1 && s + 1 <= kMaxP && K + 2 <= kMaxP && N >= 2 && npos <= 256;
-}
-
-void persist_gcr(const PersistArgs& a, Store st, cudaStream_t stream) {
+int device_sms() {
   static int sms = 0;
-  static bool attr16 = false, attr32 = false;
   if (sms == 0) {
     int dev = 0;
     SMG_CUDA_OK(cudaGetDevice(&dev));
     SMG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  const size_t smem = sizeof(Shared);
+  return sms;
+}
+
+int smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    SMG_CUDA_OK(cudaGetDevice(&dev));
+    SMG_CUDA_OK(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  }
+  return v;
+}
+
+}  // namespace
+
+bool persist_supported(int nsys, int K, int s, int N, Store st) {
+  return (st == S16 || st == S32) && nsys >= 1 && nsys <= kPersistMaxSys && K >= 1 && K <= kPersistMaxK &&
+         s >= 1 && s <= kCaMaxS && s + 1 <= kMaxP && K + 2 <= kMaxP && N >= 2 && N % 2 == 0;
+}
+
+PersistPlan persist_plan(const Geom& g, int N, int nsys, int nvec_next, Store st) {
+  PersistPlan p;
+  const long long n = (long long)g.V * N;
+  p.grid = std::min(device_sms(), g.V);
+  p.per = (n + p.grid - 1) / p.grid;
+  p.nslot = (int)((p.per - 1 + N - 1) / N) + 1;
+  const size_t sl = store_bytes(st);
+  const size_t base = align16(sizeof(Shared));
+  p.smem = base;
+  p.resident = 0;
+  p.sg = 0;
+  if (N % 4 == 0 && p.nslot <= kPersistMaxTouch) {
+    const size_t sres = align16((size_t)p.per * 9 * N * sl);
+    const size_t scl = align16((size_t)p.per * sizeof(float));
+    const size_t pres = nvec_next > 0 ? align16((size_t)p.per * nvec_next * sl) : 0;
+    const size_t stage1 = (size_t)p.nslot * 9 * N * sizeof(float2);
+    const size_t fixed = base + sres + scl + pres;
+    const size_t cap = (size_t)smem_optin();
+    if (fixed + stage1 <= cap) {
+      p.resident = 1;
+      p.sg = (int)std::min<size_t>((size_t)nsys, (cap - fixed) / stage1);
+      p.off_S = base;
+      p.off_sc = base + sres;
+      p.off_P = base + sres + scl;
+      p.off_stg = fixed;
+      p.smem = fixed + (size_t)p.sg * stage1;
+    }
+  }
+  return p;
+}
+
+size_t persist_buffer_bytes(const PersistPlan& p, int nvec_next) {
+  const size_t part = (size_t)p.grid * kPersistMaxSys * kPersistSums * sizeof(double2);
+  const size_t rp = nvec_next > 0 ? (size_t)p.grid * p.nslot * kPersistMaxSys * 2 * nvec_next * sizeof(float2) : 0;
+  return align16(part) + align16(rp) + 64;
+}
+
+void persist_gcr(const PersistArgs& a, Store st, cudaStream_t stream) {
+  static bool attr16 = false, attr32 = false;
+  const PersistPlan& p = a.plan;
+  SMG_REQUIRE(p.grid >= 1 && p.grid <= device_sms(), "persistent coarse solver: bad grid");
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(p.grid);
   cfg.blockDim = dim3(PT);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = p.smem;
   cfg.stream = stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  int per = 0;
   if (st == S16) {
     if (!attr16) {
       SMG_CUDA_OK(cudaFuncSetAttribute(persist_gcr_kernel<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+                                       smem_optin()));
       attr16 = true;
     }
-    const int g = occupancy_grid<__half2>(sms);
-    SMG_REQUIRE(g > 0, "persistent coarse solver does not fit on an SM");
-    cfg.gridDim = dim3(g);
+    SMG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persist_gcr_kernel<__half2>, PT, p.smem));
+    SMG_REQUIRE(per >= 1, "persistent coarse solver does not fit on an SM");
     SMG_CUDA_OK(cudaLaunchKernelEx(&cfg, persist_gcr_kernel<__half2>, a));
   } else {
     if (!attr32) {
       SMG_CUDA_OK(cudaFuncSetAttribute(persist_gcr_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+                                       smem_optin()));
       attr32 = true;
     }
-    const int g = occupancy_grid<float2>(sms);
-    SMG_REQUIRE(g > 0, "persistent coarse solver does not fit on an SM");
-    cfg.gridDim = dim3(g);
+    SMG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persist_gcr_kernel<float2>, PT, p.smem));
+    SMG_REQUIRE(per >= 1, "persistent coarse solver does not fit on an SM");
     SMG_CUDA_OK(cudaLaunchKernelEx(&cfg, persist_gcr_kernel<float2>, a));
   }
   SMG_LAUNCH_OK();
-}
-
-int persist_grid_size() {
-  int dev = 0, sms = 0;
-  SMG_CUDA_OK(cudaGetDevice(&dev));
-  SMG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  return sms;
 }
 
 }  // namespace smg

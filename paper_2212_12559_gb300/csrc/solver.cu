@@ -150,6 +150,59 @@ bool trace_enabled() {
   return v == 1;
 }
 
+bool phase_profile_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("SMG_PHASES");
+    v = (e != nullptr && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// Opt-in (SMG_PHASES=1) device time per solver phase, from CUDA events
+// recorded around each phase on the solver's stream; printed after each
+// solve.  Only meaningful without the CUDA graph (use_graph = 0).
+struct PhaseTimer {
+  struct Rec { const char* name; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      SMG_CUDA_OK(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(const char* name, cudaStream_t st) {
+    Rec r{name, ev(), nullptr};
+    SMG_CUDA_OK(cudaEventRecord(r.a, st));
+    recs.push_back(r);
+  }
+  void end(cudaStream_t st) {
+    for (auto it = recs.rbegin(); it != recs.rend(); ++it)
+      if (it->b == nullptr) { it->b = ev(); SMG_CUDA_OK(cudaEventRecord(it->b, st)); return; }
+  }
+  void report(cudaStream_t st) {
+    SMG_CUDA_OK(cudaStreamSynchronize(st));
+    std::vector<std::pair<std::string, std::pair<double, int>>> acc;
+    for (auto& r : recs) {
+      float ms = 0;
+      if (r.b) cudaEventElapsedTime(&ms, r.a, r.b);
+      bool found = false;
+      for (auto& a : acc)
+        if (a.first == r.name) { a.second.first += ms; a.second.second++; found = true; }
+      if (!found) acc.push_back({r.name, {ms, 1}});
+    }
+    for (auto& a : acc)
+      fprintf(stderr, "[smg phases] %-22s %10.3f ms  %6d calls\n", a.first.c_str(), a.second.first, a.second.second);
+    recs.clear();
+    used = 0;
+  }
+  ~PhaseTimer() { for (auto e : pool) cudaEventDestroy(e); }
+};
+
 // -------------------------------------------------------------------- engine
 // Work areas and operator closures for one batch size and mass set.
 struct Engine {
@@ -177,6 +230,11 @@ struct Engine {
   DevBuf cbuf;
   Workspace ws;                     // reduction partials, sized once so captured graphs stay valid
   DevBuf pbuf;                      // persistent coarse solver: partials, barrier words, error word
+  PersistPlan pplan;                // its launch shape
+  PhaseTimer phases;
+  bool prof = false;
+  void pb(const char* n) { if (prof) phases.begin(n, st()); }
+  void pe() { if (prof) phases.end(st()); }
   bool persistent = false;          // last GCR level solved by one cooperative launch
   // graph of K_0
   cudaGraphExec_t graph = nullptr;
@@ -250,13 +308,14 @@ struct Engine {
       const int l = c.coarse.back().dense ? nlev : nlev + 1;
       if (P.persistent && vp == P32 && l >= 2) {
         const CoarseLevel& C = c.coarse[l - 2];
-        int npos = 1;
-        if (l <= nlev)
-          for (int mu = 0; mu < 4; ++mu) npos *= c.coarse[l - 1].tg.agg[mu];
-        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, sp, npos);
+        const int nvec_next = l <= nlev ? c.coarse[l - 1].tg.nvec : 0;
+        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, sp);
         if (persistent) {
-          const size_t np = (size_t)persist_grid_size() * kPersistMaxSys * 64;
-          pbuf.alloc(np * sizeof(double2) + 64);
+          pplan = persist_plan(C.g, C.N, ns, nvec_next, sp);
+          pbuf.alloc(persist_buffer_bytes(pplan, nvec_next));
+          if (trace_enabled() || phase_profile_enabled())
+            fprintf(stderr, "[smg] persistent level %d: grid %d, %lld rows/CTA, %s, %d systems/stage, %zu B smem\n", l,
+                    pplan.grid, pplan.per, pplan.resident ? "resident" : "streaming", pplan.sg, pplan.smem);
         }
       }
     }
@@ -370,7 +429,10 @@ struct Engine {
       }
       precond(G.z[k], G.r, G.run);
       dbg("gcr.z", G.z[k]);
+      const bool lvl1 = (&G == &lev[1]) || (&G == &outer);
+      if (lvl1) pb(&G == &outer ? "outer.M64" : "L1.A");
       A(G.w[k], G.z[k], G.run);
+      if (lvl1) { pe(); pb(&G == &outer ? "outer.gcr_ops" : "L1.gcr_ops"); }
       dbg("gcr.w", G.w[k]);
       int pi[kMaxPairs], pj[kMaxPairs];
       if (k > 0) {
@@ -398,6 +460,7 @@ struct Engine {
         blas_pair_dots(vv, k + 2, pi, pj, k + 2, G.tmp, K + 2, ws, st(), G.run, ep);
       }
       blas_gcr_update(G.w.data(), k, G.tmp, K + 2, G.ginv, G.r, G.na, st(), G.run);
+      if (lvl1) pe();
       if (host && trace_enabled()) {
         double h[1];
         SMG_CUDA_OK(cudaMemcpyAsync(h, G.r2, sizeof(double), cudaMemcpyDeviceToHost, st()));
@@ -437,9 +500,13 @@ struct Engine {
     for (int k = 0; k < G.K; ++k) { a.z[k] = (float2*)G.z[k].p; a.w[k] = (float2*)G.w[k].p; }
     if (!coarsest)
       for (int i = 0; i <= a.s; ++i) a.V[i] = (float2*)sm_c[l].V[i].p;
+    const size_t part = ((size_t)pplan.grid * kPersistMaxSys * kPersistSums * sizeof(double2) + 15) & ~(size_t)15;
     a.partial = pbuf.as<double2>();
-    a.bar = (unsigned*)((char*)pbuf.p + pbuf.bytes - 64);
-    a.err = (int*)(a.bar + 4);
+    a.rpart = (float2*)((char*)pbuf.p + part);
+    a.plan = pplan;
+    a.bar = (unsigned long long*)((char*)pbuf.p + pbuf.bytes - 64);
+    a.exitc = (unsigned*)((char*)pbuf.p + pbuf.bytes - 64 + 8);
+    a.err = (int*)((char*)pbuf.p + pbuf.bytes - 64 + 16);
     a.run = run;
     persist_gcr(a, sp, st());
     return true;
@@ -451,7 +518,12 @@ struct Engine {
     SMG_CUDA_OK(cudaMemcpyAsync(&err, (char*)pbuf.p + pbuf.bytes - 64 + 16, sizeof(int), cudaMemcpyDeviceToHost,
                                 st()));
     SMG_CUDA_OK(cudaStreamSynchronize(st()));
-    if (err) throw StateError("timeout: a grid barrier of the persistent coarse solver gave up");
+    if (err) {
+      // clear the barrier words so that a later solve starts from a clean state
+      SMG_CUDA_OK(cudaMemsetAsync((char*)pbuf.p + pbuf.bytes - 64, 0, 64, st()));
+      SMG_CUDA_OK(cudaStreamSynchronize(st()));
+      throw StateError("timeout: a grid barrier of the persistent coarse solver gave up");
+    }
   }
 
   // solve on level l (>= 2): G = lev[l], input lev[l].b, output lev[l].x
@@ -479,15 +551,20 @@ struct Engine {
   void kcycle(int l, const Vec& e, const Vec& r, const int* run) {
     const CoarseLevel& C = c.coarse[l - 1];
     dbg("K.r", r);
+    if (l == 1) pb("K1.restrict");
     restrict_op(lev[l + 1].b, r, C.tg, C.Ps.st, st(), run);
+    if (l == 1) { pe(); pb("K1.coarse_solve"); }
     dbg("K.rc", lev[l + 1].b);
     coarse_solve(l + 1, run);
+    if (l == 1) { pe(); pb("K1.prolong"); }
     dbg("K.ec", lev[l + 1].x);
     prolong_op(e, lev[l + 1].x, C.tg, C.Ps.st, st(), run);
+    if (l == 1) { pe(); pb("K1.smoother(A)"); }
     dbg("K.e", e);
     SmoothWork& S = (l == 1) ? sm_f : sm_c[l];
     op(l, S.V[0], e, run, &r);          // V0 = r - A_l e
     smooth(l, S, e, run);
+    if (l == 1) pe();
     dbg("K.e+smooth", e);
   }
 
@@ -502,8 +579,10 @@ struct Engine {
     auto pre = [&](const Vec& zz, const Vec& rr, const int* run) { kcycle(1, zz, rr, run); };
     gcr(G, A, pre, c.params.inner_tol, nullptr, nullptr, false, false);
     dbg("K0.x1", G.x);
+    pb("K0.smoother(M)");
     Ms(sm_f.V[0], G.x, nullptr, &r_s);   // V0 = r - M e
     smooth(0, sm_f, G.x, nullptr);
+    pe();
     blas_copy(z, G.x, st());
   }
 
@@ -553,6 +632,7 @@ struct Engine {
     iters = 0;
     restarts = 0;
     res.assign(nsys, 0.0);
+    prof = phase_profile_enabled() && !c.params.use_graph;
     std::vector<double2> hr(nsys);
     while (true) {
       auto A = [&](const Vec& o, const Vec& i, const int*) { M64(o, i); };
@@ -577,6 +657,7 @@ struct Engine {
         if (!(hr[s].x <= tgt[s])) all = false;
       }
       check_persistent_error();
+      if (prof) phases.report(st());
       if (bad) throw StateError("breakdown: non-finite residual");
       if (all || done == 0) break;
       ++restarts;

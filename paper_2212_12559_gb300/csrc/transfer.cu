@@ -148,32 +148,39 @@ __global__ void __launch_bounds__(256) restrict_kernel(typename cplx<R>::T* __re
   if (run != nullptr && *run == 0) return;
   extern __shared__ __align__(16) unsigned char rs_smem[];
   C* part = reinterpret_cast<C*>(rs_smem);                    // [2][256]
-  C* vx = part + 512;                                         // [rows]
-  int* xs = reinterpret_cast<int*>(vx + (size_t)t.ndof * t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3]);
+  C* vx = part + 512;                                         // [npos][ndof]
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  int* xs = reinterpret_cast<int*>(vx + (size_t)t.ndof * npos);   // site of each position
+  int* xpar = xs + npos;                                          // its parity
   const int X = blockIdx.x, s = blockIdx.y;
   const int nv = t.nvec;
   const int k = threadIdx.x % nv, grp = threadIdx.x / nv, groups = blockDim.x / nv;
-  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
-  const int rows = npos * t.ndof;
-  const long long nf = (long long)t.fine.V * t.ndof;
+  const int nd = t.ndof, half = nd / 2;
+  const long long nf = (long long)t.fine.V * nd;
   const C* vin = in + (size_t)s * nf;
-  for (int p = threadIdx.x; p < npos; p += blockDim.x) xs[p] = agg_site(t, X, p);
+  for (int p = threadIdx.x; p < npos; p += blockDim.x) {
+    const int x = agg_site(t, X, p);
+    xs[p] = x;
+    xpar[p] = site_parity(t.fine, x);
+  }
   __syncthreads();
-  for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
-    const int p = rr / t.ndof, d = rr - p * t.ndof;
-    vx[rr] = vin[(size_t)xs[p] * t.ndof + d];
+  for (int rr = threadIdx.x; rr < npos * nd; rr += blockDim.x) {
+    const int p = rr / nd, d = rr - p * nd;
+    vx[rr] = vin[(size_t)xs[p] * nd + d];
   }
   __syncthreads();
   C acc0 = C{0, 0}, acc1 = C{0, 0};
   if (grp < groups) {
-#pragma unroll 8
-    for (int rr = grp; rr < rows; rr += groups) {
-      const int p = rr / t.ndof, d = rr - p * t.ndof;
-      const int x = xs[p];
-      const int chi = t.chi_mode == 0 ? site_parity(t.fine, x) : (d >= t.ndof / 2 ? 1 : 0);
-      const C pv = ld<R>(P, ((size_t)x * t.ndof + d) * nv + k);
-      if (chi == 0) cfmac(acc0, pv, vx[rr]);
-      else cfmac(acc1, pv, vx[rr]);
+    for (int p = grp; p < npos; p += groups) {
+      const size_t base = (size_t)xs[p] * nd;
+      const int par = xpar[p];
+#pragma unroll 4
+      for (int d = 0; d < nd; ++d) {
+        const int chi = t.chi_mode == 0 ? par : (d >= half ? 1 : 0);
+        const C pv = ld<R>(P, (base + d) * nv + k);
+        if (chi == 0) cfmac(acc0, pv, vx[p * nd + d]);
+        else cfmac(acc1, pv, vx[p * nd + d]);
+      }
     }
   }
   part[threadIdx.x] = acc0;   // blockDim.x == 256 (see restrict_op)
@@ -184,6 +191,85 @@ __global__ void __launch_bounds__(256) restrict_kernel(typename cplx<R>::T* __re
     const int chi = i / nv, kk = i % nv;
     C sum = C{0, 0};
     for (int g = 0; g < groups; ++g) sum = cadd(sum, part[chi * 256 + g * nv + kk]);
+    out[(size_t)s * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
+  }
+}
+
+// The same with 16-byte prolongator loads (nvec a multiple of the entries per
+// 16 bytes): thread t owns the chunk of vectors kc = t % (nvec / VPC) and
+// every (t / (nvec / VPC))-th row of the aggregate, so a CTA of 512 threads
+// keeps ~10 independent loads per thread in flight; the row groups are then
+// added in two fixed-order passes.
+template <typename R, typename SL>
+__global__ void __launch_bounds__(512) restrict_vec_kernel(typename cplx<R>::T* __restrict__ out,
+                                                           const typename cplx<R>::T* __restrict__ in,
+                                                           const SL* __restrict__ P, R pscale, TransferGeom t,
+                                                           const int* run) {
+  using C = typename cplx<R>::T;
+  constexpr int VPC = 16 / (int)sizeof(SL);
+  constexpr int kRed = 8;                                     // first-pass partial sums per output
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  const int nv = t.nvec, nch = nv / VPC;
+  const int groups = blockDim.x / nch;
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  const int nd = t.ndof, half = nd / 2;
+  C* part = reinterpret_cast<C*>(rs_smem);                    // [groups][2][nv]
+  C* red = part + (size_t)groups * 2 * nv;                    // [kRed][2][nv]
+  C* vx = red + (size_t)kRed * 2 * nv;                        // [npos][nd]
+  int* xs = reinterpret_cast<int*>(vx + (size_t)npos * nd);   // site of each position
+  int* xpar = xs + npos;                                      // its parity
+  const int X = blockIdx.x, s = blockIdx.y;
+  const long long nf = (long long)t.fine.V * nd;
+  const C* vin = in + (size_t)s * nf;
+  for (int p = threadIdx.x; p < npos; p += blockDim.x) {
+    const int x = agg_site(t, X, p);
+    xs[p] = x;
+    xpar[p] = site_parity(t.fine, x);
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < npos * nd; rr += blockDim.x) {
+    const int p = rr / nd, d = rr - p * nd;
+    vx[rr] = vin[(size_t)xs[p] * nd + d];
+  }
+  __syncthreads();
+  const int kc = threadIdx.x % nch, g = threadIdx.x / nch;
+  if (g < groups) {
+    C acc0[VPC], acc1[VPC];
+#pragma unroll
+    for (int u = 0; u < VPC; ++u) { acc0[u] = C{0, 0}; acc1[u] = C{0, 0}; }
+#pragma unroll 4
+    for (int rr = g; rr < npos * nd; rr += groups) {
+      const int p = rr / nd, d = rr - p * nd;
+      const int chi = t.chi_mode == 0 ? xpar[p] : (d >= half ? 1 : 0);
+      const uint4 raw = __ldg(reinterpret_cast<const uint4*>(P + ((size_t)xs[p] * nd + d) * nv) + kc);
+      const SL* pe = reinterpret_cast<const SL*>(&raw);
+      const C v = vx[rr];
+#pragma unroll
+      for (int u = 0; u < VPC; ++u) {
+        const C pv = ld<R>(pe, u);
+        if (chi == 0) cfmac(acc0[u], pv, v);
+        else cfmac(acc1[u], pv, v);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < VPC; ++u) {
+      part[((size_t)g * 2 + 0) * nv + kc * VPC + u] = acc0[u];
+      part[((size_t)g * 2 + 1) * nv + kc * VPC + u] = acc1[u];
+    }
+  }
+  __syncthreads();
+  const int N = 2 * nv;
+  for (int e = threadIdx.x; e < kRed * N; e += blockDim.x) {
+    const int j = e / N, i = e - j * N;
+    C sum = C{0, 0};
+    for (int gg = j; gg < groups; gg += kRed) sum = cadd(sum, part[(size_t)gg * N + i]);
+    red[(size_t)j * N + i] = sum;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    C sum = C{0, 0};
+    for (int j = 0; j < kRed; ++j) sum = cadd(sum, red[(size_t)j * N + i]);
     out[(size_t)s * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
   }
 }
@@ -213,11 +299,17 @@ __global__ void prolong_kernel(typename cplx<R>::T* __restrict__ out, const type
 // so it is never issued while a stream is being captured).
 template <typename K>
 void ensure_smem(K kernel, size_t bytes) {
-  static size_t set = 0;
-  if (bytes > 48 * 1024 && bytes > set) {
-    SMG_CUDA_OK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    set = bytes;
-  }
+  static std::vector<std::pair<const void*, size_t>> set;
+  if (bytes <= 48 * 1024) return;
+  for (auto& e : set)
+    if (e.first == (const void*)kernel) {
+      if (bytes <= e.second) return;
+      SMG_CUDA_OK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      e.second = bytes;
+      return;
+    }
+  SMG_CUDA_OK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  set.emplace_back((const void*)kernel, bytes);
 }
 
 }  // namespace
@@ -245,7 +337,35 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
   SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec && t.nvec <= 128, "restrict: batch/precision mismatch");
   dim3 grid(t.coarse.V, in.nsys);
   const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
-  const size_t smem = prec_bytes(in.prec) * (512 + (size_t)npos * t.ndof) + sizeof(int) * npos;
+  const size_t cb = prec_bytes(in.prec);
+  const int vpc = (int)(16 / store_bytes(P.s));
+  if (t.nvec % vpc == 0) {
+    // vectorised kernel: 512 threads, nvec / vpc threads per row
+    const int groups = 512 / (t.nvec / vpc);
+    const size_t smem = cb * ((size_t)groups * 2 * t.nvec + 8 * 2 * t.nvec + (size_t)npos * t.ndof) +
+                        sizeof(int) * 2 * npos;
+    if (smem <= 200 * 1024) {
+      if (in.prec == P64) {
+        SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
+        auto k = restrict_vec_kernel<double, double2>;
+        ensure_smem(k, smem);
+        k<<<grid, 512, smem, st>>>((double2*)out.p, (const double2*)in.p, (const double2*)P.p, (double)P.gscale,
+                                   t, run);
+      } else if (P.s == S32) {
+        auto k = restrict_vec_kernel<float, float2>;
+        ensure_smem(k, smem);
+        k<<<grid, 512, smem, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t, run);
+      } else {
+        SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
+        auto k = restrict_vec_kernel<float, __half2>;
+        ensure_smem(k, smem);
+        k<<<grid, 512, smem, st>>>((float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t, run);
+      }
+      SMG_LAUNCH_OK();
+      return;
+    }
+  }
+  const size_t smem = cb * (512 + (size_t)npos * t.ndof) + sizeof(int) * 2 * npos;
   SMG_REQUIRE(smem <= 200 * 1024, "restrict: aggregate too large for shared memory");
   if (in.prec == P64) {
     SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
