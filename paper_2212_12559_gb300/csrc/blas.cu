@@ -257,11 +257,14 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   red[t] = active ? make_double2(acc.x, acc.y) : make_double2(0, 0);
   __syncthreads();
   const int nb = gridDim.x, nsys = gridDim.y;
-  if (t < np) {
-    double2 sum = make_double2(0, 0);
-    for (int g = 0; g < groups; ++g) sum = cadd(sum, red[g * np + t]);
-    partial[((long long)s * nb + blockIdx.x) * np + t] = sum;
+  // fixed-order tree over the row groups
+  for (int gc = groups; gc > 1;) {
+    const int half = (gc + 1) / 2;
+    for (int e = t; e < (gc - half) * np; e += kThreads) red[e] = cadd(red[e], red[e + half * np]);
+    gc = half;
+    __syncthreads();
   }
+  if (t < np) partial[((long long)s * nb + blockIdx.x) * np + t] = red[t];
   __threadfence();
   __syncthreads();
   if (t == 0) {
@@ -291,11 +294,14 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   __threadfence_block();
   __syncthreads();
   if (epi.kind == EPI_CA) {
-    // the reduction tiles are free now: one factor scratch per warp
-    static_assert(sizeof(tile) >= sizeof(double2) * kCaMaxS * kCaMaxS * (kThreads / 32), "CA scratch");
-    double2(*Ls)[kCaMaxS] = reinterpret_cast<double2(*)[kCaMaxS]>(&tile[0][0]) + (t >> 5) * kCaMaxS;
+    // the reduction tiles are free now: one factor scratch per warp, in the
+    // arithmetic of the vectors
+    using R = typename RealOf<C>::R;
+    using CR = typename cplx<R>::T;
+    static_assert(sizeof(tile) >= sizeof(CR) * kCaMaxS * kCaMaxS * (kThreads / 32), "CA scratch");
+    CR(*Ls)[kCaMaxS] = reinterpret_cast<CR(*)[kCaMaxS]>(&tile[0][0]) + (t >> 5) * kCaMaxS;
     for (int ss = t >> 5; ss < nsys; ss += kThreads / 32)
-      ca_solve_warp(out + (long long)ss * ldo, epi.s, epi.d2a + (size_t)ss * epi.s, Ls);
+      ca_solve_warp<R>(out + (long long)ss * ldo, epi.s, epi.d2a + (size_t)ss * epi.s, Ls);
   } else {
     for (int ss = t; ss < nsys; ss += kThreads) epilogue_system(epi, ss, out + (long long)ss * ldo);
   }

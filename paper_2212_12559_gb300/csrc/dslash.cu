@@ -124,6 +124,10 @@ void dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t s
   SMG_REQUIRE(in.nsys == p.nsys && out.nsys == p.nsys, "dslash: batch mismatch");
   SMG_REQUIRE(in.prec == out.prec, "dslash: precision mismatch");
   SMG_REQUIRE(p.naik.p == nullptr || p.naik.s == p.fat.s, "dslash: fat/naik storage mismatch");
+  if (hop_dslash_ok(in, p)) {
+    hop_dslash(out, in, p, st, run);
+    return;
+  }
   if (in.prec == P64) {
     SMG_REQUIRE(p.fat.s == S64, "dslash: FP64 vectors need FP64 links");
     launch<double, double2>(out, in, p, st, run);

@@ -29,8 +29,18 @@ struct DslashParams {
   int agg[4] = {1, 1, 1, 1};
   int nsys = 1;
   const void* sub_from = nullptr;   // when set: out = sub_from - M in (residual form)
+  // phase-folded copy of the links (FP16 / FP32, see hop.cu); used for FP32 vectors and part < 0
+  Stored hop;                // gscale = fat scale (FP16)
+  int hop_kinds = 0;         // 1 (naive) or 2 (with Naik links)
+  float hop_naik_scale = 1.0f;
 };
 void dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run = nullptr);
+// Phase-folded links: per (site, mu) eta_mu(x) V_mu(x) and eta_mu(x) W_mu(x), 16-byte padded.
+size_t hop_link_entries(const Geom& g, bool naik, Store s);
+void build_hop_links(void* H, Store s, const double2* fat, const double2* naik, const Geom& g, float fat_scale,
+                     float naik_scale, cudaStream_t st);
+bool hop_dslash_ok(const Vec& in, const DslashParams& p);
+void hop_dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run);
 
 // -------------------------------------------------------- Kahler-Dirac blocks
 // Section 3.1: one dense 48x48 block (B+m)^{-1} per 2^4 hypercube, rows and

@@ -44,16 +44,21 @@ struct PersistArgs {
   float2* w[kPersistMaxK];
   float2* V[11];
   float2 *rc, *ec;
-  double2* partial;          // [grid][kPersistMaxSys][kPersistSums]
+  float2* partial;           // [grid][kPersistMaxSys][kPersistSums]
   float2* rpart;             // [grid][nslot][kPersistMaxSys][2 nvec] per-CTA partial restrictions
   PersistPlan plan;
   unsigned long long* bar;   // barrier arrival counter, 0 between launches
   unsigned* exitc;           // CTAs that finished (the last one clears both counters)
   int* err;                  // set to 1 when a barrier wait times out
   const int* run;            // skip the launch when *run == 0
+  unsigned long long* trace; // optional phase trace (see persist.cu), or nullptr
+  int trace_cap;
 };
+// names of the traced phase ids (index = id)
+const char* persist_phase_name(int id, bool has_pre);
 
-bool persist_supported(int nsys, int K, int s, int N, Store st);
+// n: unknowns per system on the level
+bool persist_supported(int nsys, int K, int s, int N, long long n, Store st);
 // nvec_next: null vectors of the next level (0 for the coarsest GCR level, no preconditioner)
 PersistPlan persist_plan(const Geom& g, int N, int nsys, int nvec_next, Store st);
 // bytes of the device buffer behind partial, rpart and the barrier words

@@ -184,6 +184,13 @@ struct PhaseTimer {
     for (auto it = recs.rbegin(); it != recs.rend(); ++it)
       if (it->b == nullptr) { it->b = ev(); SMG_CUDA_OK(cudaEventRecord(it->b, st)); return; }
   }
+  // durations measured elsewhere (the persistent kernel's own trace)
+  std::vector<std::pair<std::string, std::pair<double, int>>> ext;
+  void add(const std::string& name, double ms) {
+    for (auto& a : ext)
+      if (a.first == name) { a.second.first += ms; a.second.second++; return; }
+    ext.push_back({name, {ms, 1}});
+  }
   void report(cudaStream_t st) {
     SMG_CUDA_OK(cudaStreamSynchronize(st));
     std::vector<std::pair<std::string, std::pair<double, int>>> acc;
@@ -195,6 +202,8 @@ struct PhaseTimer {
         if (a.first == r.name) { a.second.first += ms; a.second.second++; found = true; }
       if (!found) acc.push_back({r.name, {ms, 1}});
     }
+    for (auto& a : ext) acc.push_back(a);
+    ext.clear();
     for (auto& a : acc)
       fprintf(stderr, "[smg phases] %-22s %10.3f ms  %6d calls\n", a.first.c_str(), a.second.first, a.second.second);
     recs.clear();
@@ -231,6 +240,7 @@ struct Engine {
   Workspace ws;                     // reduction partials, sized once so captured graphs stay valid
   DevBuf pbuf;                      // persistent coarse solver: partials, barrier words, error word
   PersistPlan pplan;                // its launch shape
+  DevBuf trace_buf;                 // its phase trace (SMG_PHASES=1)
   PhaseTimer phases;
   bool prof = false;
   void pb(const char* n) { if (prof) phases.begin(n, st()); }
@@ -309,7 +319,7 @@ struct Engine {
       if (P.persistent && vp == P32 && l >= 2) {
         const CoarseLevel& C = c.coarse[l - 2];
         const int nvec_next = l <= nlev ? c.coarse[l - 1].tg.nvec : 0;
-        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, sp);
+        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, (long long)C.g.V * C.N, sp);
         if (persistent) {
           pplan = persist_plan(C.g, C.N, ns, nvec_next, sp);
           pbuf.alloc(persist_buffer_bytes(pplan, nvec_next));
@@ -345,9 +355,7 @@ struct Engine {
   DslashParams dparams(Store s, int dagger) const {
     DslashParams p;
     p.g = c.g;
-    p.fat = c.fat_of(s);
-    if (c.has_naik) p.naik = c.naik_of(s);
-    p.c_naik = c.c_naik;
+    c.link_params(s, p);
     p.mass = mass_dev.as<double>();
     p.dagger = dagger;
     p.nsys = nsys;
@@ -500,15 +508,35 @@ struct Engine {
     for (int k = 0; k < G.K; ++k) { a.z[k] = (float2*)G.z[k].p; a.w[k] = (float2*)G.w[k].p; }
     if (!coarsest)
       for (int i = 0; i <= a.s; ++i) a.V[i] = (float2*)sm_c[l].V[i].p;
-    const size_t part = ((size_t)pplan.grid * kPersistMaxSys * kPersistSums * sizeof(double2) + 15) & ~(size_t)15;
-    a.partial = pbuf.as<double2>();
+    const size_t part = ((size_t)pplan.grid * kPersistMaxSys * kPersistSums * sizeof(float2) + 15) & ~(size_t)15;
+    a.partial = pbuf.as<float2>();
     a.rpart = (float2*)((char*)pbuf.p + part);
     a.plan = pplan;
     a.bar = (unsigned long long*)((char*)pbuf.p + pbuf.bytes - 64);
     a.exitc = (unsigned*)((char*)pbuf.p + pbuf.bytes - 64 + 8);
     a.err = (int*)((char*)pbuf.p + pbuf.bytes - 64 + 16);
     a.run = run;
+    a.trace = nullptr;
+    a.trace_cap = 0;
+    if (prof) {
+      // per-phase trace of this launch (CTA 0's barrier exits)
+      const int cap = 4096;
+      if (trace_buf.p == nullptr) trace_buf.alloc(sizeof(unsigned long long) * (1 + 2 * cap));
+      SMG_CUDA_OK(cudaMemsetAsync(trace_buf.p, 0, sizeof(unsigned long long), st()));
+      a.trace = trace_buf.as<unsigned long long>();
+      a.trace_cap = cap;
+    }
     persist_gcr(a, sp, st());
+    if (prof) {
+      std::vector<unsigned long long> h(1 + 2 * (size_t)a.trace_cap);
+      SMG_CUDA_OK(cudaMemcpyAsync(h.data(), trace_buf.p, h.size() * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, st()));
+      SMG_CUDA_OK(cudaStreamSynchronize(st()));
+      const size_t m = std::min<size_t>(h[0], (size_t)a.trace_cap);
+      for (size_t i = 1; i < m; ++i)
+        phases.add(persist_phase_name((int)h[1 + 2 * i], a.has_pre != 0),
+                   1e-6 * (double)(h[2 + 2 * i] - h[2 + 2 * (i - 1)]));
+    }
     return true;
   }
 
@@ -668,6 +696,17 @@ struct Engine {
 void EngineDeleter::operator()(Engine* e) const { delete e; }
 
 // ------------------------------------------------------------------ context
+void Context::link_params(Store s, DslashParams& p) const {
+  p.fat = fat_of(s);
+  if (has_naik) p.naik = naik_of(s);
+  p.c_naik = c_naik;
+  if (s == S16 || s == S32) {
+    p.hop = s == S16 ? hop16.st : hop32.st;
+    p.hop_kinds = has_naik ? 2 : 1;
+    p.hop_naik_scale = (s == S16 && has_naik) ? naik16.st.gscale : 1.0f;
+  }
+}
+
 void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik, int where) {
   const size_t nl = (size_t)4 * c.g.V * 9;
   c.engine.reset();
@@ -706,6 +745,16 @@ void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik,
   make_lp(c.fat64, c.fat32, c.fat16);
   if (c.has_naik) make_lp(c.naik64, c.naik32, c.naik16);
   else { c.naik32 = StoredBuf(); c.naik16 = StoredBuf(); }
+  {
+    const double2* n64 = c.has_naik ? c.naik64.as<double2>() : nullptr;
+    const float fs = c.fat16.st.gscale, ns = c.has_naik ? c.naik16.st.gscale : 1.0f;
+    c.hop16.alloc(S16, hop_link_entries(c.g, c.has_naik, S16), 0);
+    build_hop_links(c.hop16.v.p, S16, c.fat64.as<double2>(), n64, c.g, fs, ns, c.stream);
+    c.hop16.st.gscale = fs;
+    c.hop32.alloc(S32, hop_link_entries(c.g, c.has_naik, S32), 0);
+    build_hop_links(c.hop32.v.p, S32, c.fat64.as<double2>(), n64, c.g, 1.0f, 1.0f, c.stream);
+    c.hop32.st.gscale = 1.0f;
+  }
   c.gauge_set = true;
   c.kd_valid = false;
   c.setup_done = false;
@@ -777,9 +826,7 @@ struct SetupOp {
     if (l == 1) {
       DslashParams p;
       p.g = c.g;
-      p.fat = c.fat_of(sp);
-      if (c.has_naik) p.naik = c.naik_of(sp);
-      p.c_naik = c.c_naik;
+      c.link_params(sp, p);
       p.mass0 = c.mass;
       p.nsys = in.nsys;
       const Stored kd = c.kd_of(sp);
@@ -1083,9 +1130,7 @@ void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void
   Vec tmp = vin; tmp.p = s.t.p;
   DslashParams p;
   p.g = c.g;
-  p.fat = c.fat_of(sp);
-  if (c.has_naik) p.naik = c.naik_of(sp);
-  p.c_naik = c.c_naik;
+  c.link_params(sp, p);
   p.mass0 = c.mass;
   p.nsys = nsys;
   const Stored kd = c.kd_of(sp);
@@ -1266,9 +1311,7 @@ double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep) {
   }
   DslashParams dp;
   dp.g = c.g;
-  dp.fat = c.fat_of(sp);
-  if (c.has_naik) dp.naik = c.naik_of(sp);
-  dp.c_naik = c.c_naik;
+  c.link_params(sp, dp);
   dp.mass0 = c.mass;
   dp.nsys = nsys;
   const Stored kd = c.kd_of(sp);

@@ -94,6 +94,7 @@ struct Context {
   double c_naik = 0.0;
   DevBuf fat64, naik64;
   StoredBuf fat32, naik32, fat16, naik16;
+  StoredBuf hop32, hop16;     // hop-link copies (hop.cu)
   // mass and KD blocks
   double mass = 0.0;
   bool mass_set = false, kd_valid = false;
@@ -118,6 +119,8 @@ struct Context {
   const Stored& fat_of(Store s) const { return s == S64 ? fat64_st : (s == S32 ? fat32.st : fat16.st); }
   const Stored& naik_of(Store s) const { return s == S64 ? naik64_st : (s == S32 ? naik32.st : naik16.st); }
   const Stored& kd_of(Store s) const { return s == S64 ? kd64.st : (s == S32 ? kd32.st : kd16.st); }
+  // fat / Naik links (and their hop-link copy) of storage s into a dslash parameter block
+  void link_params(Store s, DslashParams& p) const;
   Stored fat64_st, naik64_st;
   void ensure_consts(int n);
 };
