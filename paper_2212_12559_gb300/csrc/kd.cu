@@ -14,17 +14,6 @@ namespace {
 
 constexpr int NB = 48;
 
-__device__ __forceinline__ int hyper_site(const Geom& g, int blk, int b) {
-  const int h0 = g.L[0] / 2, h1 = g.L[1] / 2, h2 = g.L[2] / 2;
-  int c[4];
-  c[0] = blk % h0; blk /= h0;
-  c[1] = blk % h1; blk /= h1;
-  c[2] = blk % h2; c[3] = blk / h2;
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu) c[mu] = 2 * c[mu] + ((b >> mu) & 1);
-  return g.index(c);
-}
-
 __global__ void __launch_bounds__(256) kd_build_kernel(double2* __restrict__ inv, const double2* __restrict__ fat,
                                                        double mass, Geom g) {
   extern __shared__ double2 aug[];   // [48][96]
@@ -47,7 +36,7 @@ __global__ void __launch_bounds__(256) kd_build_kernel(double2* __restrict__ inv
         if ((diff & (diff - 1)) == 0) {
           int mu = 0;
           while ((1 << mu) != diff) ++mu;
-          const int xb = hyper_site(g, blk, b);
+          const int xb = hypercube_site(g, blk, b);
           int c[4];
           g.coords(xb, c);
           int es = 0;
@@ -59,7 +48,7 @@ __global__ void __launch_bounds__(256) kd_build_kernel(double2* __restrict__ inv
             v = make_double2(eta * u.x, eta * u.y);
           } else {
             // backward hop: -1/2 eta conj(U_mu(x - mu)[a'][a])
-            const int xn = hyper_site(g, blk, bp);
+            const int xn = hypercube_site(g, blk, bp);
             const double2 u = fat[((size_t)mu * g.V + xn) * 9 + ap * 3 + a];
             v = make_double2(-eta * u.x, eta * u.y);
           }
@@ -169,7 +158,7 @@ __global__ void __launch_bounds__(192) kd_apply_kernel(typename cplx<R>::T* __re
   const float* sc = kd.scale[kidx];
   int site = 0;
   if (blk < nblk) {
-    site = hyper_site(g, (int)blk, r / 3);
+    site = hypercube_site(g, (int)blk, r / 3);
     vin[lb][r] = in[off + (size_t)site * 3 + (r % 3)];
   }
   __syncthreads();

@@ -41,8 +41,24 @@ void build_hop_links(void* H, Store s, const double2* fat, const double2* naik, 
                      float naik_scale, cudaStream_t st);
 bool hop_dslash_ok(const Vec& in, const DslashParams& p);
 void hop_dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run);
+// out = (B+m)^{-1} M in (or sub_from - that) in one kernel; needs hop_dslash_ok and dagger == 0.
+// kd[sys_map[s]] are the block inverses (storage of the link copy), see kd_apply.
+void apply_a_fused(const Vec& out, const Vec& in, const DslashParams& p, const Stored* kd, const int* sys_map, int nkd,
+                   cudaStream_t st, const int* run = nullptr, const void* sub_from = nullptr);
 
 // -------------------------------------------------------- Kahler-Dirac blocks
+// Site of position b = (x&1) + 2(y&1) + 4(z&1) + 8(t&1) in aligned hypercube blk
+// (hypercubes ordered lexicographically on the half-extent lattice).
+__device__ __forceinline__ int hypercube_site(const Geom& g, int blk, int b) {
+  const int h0 = g.L[0] / 2, h1 = g.L[1] / 2, h2 = g.L[2] / 2;
+  int c[4];
+  c[0] = blk % h0; blk /= h0;
+  c[1] = blk % h1; blk /= h1;
+  c[2] = blk % h2; c[3] = blk / h2;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) c[mu] = 2 * c[mu] + ((b >> mu) & 1);
+  return g.index(c);
+}
 // Section 3.1: one dense 48x48 block (B+m)^{-1} per 2^4 hypercube, rows and
 // columns ordered (position b in hypercube, colour a) -> 3b + a.
 // Build: FP64 into `inv64` [nblk][48][48] row-major.

@@ -206,6 +206,59 @@ __device__ __forceinline__ void resident_rows(const PersistArgs& a, const Own& o
   }
 }
 
+// One system, up to RW rows per warp at once (rows warp, warp + NW, ...):
+// the rows' loads and FMA chains interleave and their shuffle trees run side
+// by side, instead of one row's latency after another.
+template <typename SL, int RW>
+__device__ __forceinline__ void resident_rows_multi(const PersistArgs& a, const Own& o, const SL* Sres,
+                                                    const float* Ssc, const float2* stg, float2* out,
+                                                    const float2* sub, int s0, int warp, int lane) {
+  constexpr int C = Chunk<SL>::C;
+  const int N = a.N, W = 9 * N, nq = W / C;
+  const int nrows = o.r1 - o.r0;
+  for (int base = warp; base < nrows; base += NW * RW) {
+    int xl[RW];
+    float2 acc[RW];
+#pragma unroll
+    for (int u = 0; u < RW; ++u) {
+      const int lr = base + u * NW;
+      xl[u] = lr < nrows ? (o.r0 + lr) / N - o.xs0 : 0;
+      acc[u] = make_float2(0.f, 0.f);
+    }
+    for (int q = lane; q < nq; q += 32) {
+      const int e = q * C;
+#pragma unroll
+      for (int u = 0; u < RW; ++u) {
+        const int lr = base + u * NW;
+        if (lr < nrows) {
+          const uint4 raw = *reinterpret_cast<const uint4*>(Sres + (size_t)lr * W + e);
+          fma_chunk(acc[u], raw, Sres, stg + (size_t)xl[u] * W + e);
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int u = 0; u < RW; ++u) {
+        acc[u].x += __shfl_xor_sync(0xffffffffu, acc[u].x, off);
+        acc[u].y += __shfl_xor_sync(0xffffffffu, acc[u].y, off);
+      }
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < RW; ++u) {
+        const int lr = base + u * NW;
+        if (lr < nrows) {
+          const float sc = a.Srs != nullptr ? Ssc[lr] : 1.0f;
+          float2 v = make_float2(acc[u].x * sc, acc[u].y * sc);
+          const size_t oi = (size_t)s0 * a.n + o.r0 + lr;
+          if (sub != nullptr) v = csub(sub[oi], v);
+          out[oi] = v;
+        }
+      }
+    }
+  }
+}
+
 // out = A_hat in (or sub - A_hat in) on the CTA's own rows, stencil rows in
 // shared memory.  Inputs of the touched sites' nine neighbours are staged in
 // shared memory in the stencil's own [dir][col] order, so a row is one
@@ -230,7 +283,7 @@ __device__ void stencil_resident(const PersistArgs& a, Shared& sh, const Own& o,
     }
     __syncthreads();
     if (t == 0) trace_mark(a, 13);
-    if (ns == 1) resident_rows<SL, 1>(a, o, Sres, Ssc, stg, out, sub, s0, ns, warp, lane);
+    if (ns == 1) resident_rows_multi<SL, 6>(a, o, Sres, Ssc, stg, out, sub, s0, warp, lane);
     else if (ns == 2) resident_rows<SL, 2>(a, o, Sres, Ssc, stg, out, sub, s0, ns, warp, lane);
     else if (ns <= 4) resident_rows<SL, 4>(a, o, Sres, Ssc, stg, out, sub, s0, ns, warp, lane);
     else if (ns <= 8) resident_rows<SL, 8>(a, o, Sres, Ssc, stg, out, sub, s0, ns, warp, lane);
@@ -470,19 +523,37 @@ __device__ void dots_partial(const PersistArgs& a, Shared& sh, const Own& o, flo
 }
 
 // After a barrier: every CTA adds all CTAs' partials in the same order (one
-// warp per output, lanes over the CTAs, fixed shuffle tree).
+// warp per output, lanes over the CTAs, fixed shuffle tree).  A warp takes
+// four outputs at once so that their loads are in flight together.
 __device__ void dots_final(const PersistArgs& a, Shared& sh, int np) {
+  constexpr int U = 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = warp; e < a.nsys * np; e += NW) {
-    const int s = e / np, p = e % np;
-    float2 sum = make_float2(0.f, 0.f);
-    for (int b = lane; b < (int)gridDim.x; b += 32)
-      sum = cadd(sum, __ldcg(&a.partial[((size_t)b * kPersistMaxSys + s) * kPersistSums + p]));
-    for (int off = 16; off > 0; off >>= 1) {
-      sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
-      sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+  const int total = a.nsys * np;
+  for (int e0 = warp; e0 < total; e0 += NW * U) {
+    float2 sum[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      sum[u] = make_float2(0.f, 0.f);
+      const int e = e0 + u * NW;
+      if (e < total) {
+        const int s = e / np, p = e - (e / np) * np;
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+          sum[u] = cadd(sum[u], __ldcg(&a.partial[((size_t)b * kPersistMaxSys + s) * kPersistSums + p]));
+      }
     }
-    if (lane == 0) sh.sums[s][p] = sum;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        sum[u].x += __shfl_xor_sync(0xffffffffu, sum[u].x, off);
+        sum[u].y += __shfl_xor_sync(0xffffffffu, sum[u].y, off);
+      }
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NW;
+        if (e < total) sh.sums[e / np][e % np] = sum[u];
+      }
   }
   __syncthreads();
 }

@@ -375,6 +375,11 @@ struct Engine {
     kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run, sub ? sub->p : nullptr);
   }
   void As(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
+    DslashParams p = dparams(sp, 0);
+    if (hop_dslash_ok(in, p)) {
+      apply_a_fused(out, in, p, kd_s.data(), sys_map, nkd, st(), run, sub ? sub->p : nullptr);
+      return;
+    }
     Ms(tmpA, in, run);
     Binv(out, tmpA, run, sub);
   }
@@ -1139,7 +1144,14 @@ void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void
     case SMG_OP_MDAG: p.dagger = 1; dslash(vout, vin, p, c.stream); break;
     case SMG_OP_KD: kd_apply(vout, vin, c.g, &kd, nullptr, 1, 0, c.stream); break;
     case SMG_OP_KDDAG: kd_apply(vout, vin, c.g, &kd, nullptr, 1, 1, c.stream); break;
-    case SMG_OP_A: dslash(tmp, vin, p, c.stream); kd_apply(vout, tmp, c.g, &kd, nullptr, 1, 0, c.stream); break;
+    case SMG_OP_A:
+      if (hop_dslash_ok(vin, p)) {
+        apply_a_fused(vout, vin, p, &kd, nullptr, 1, c.stream);
+      } else {
+        dslash(tmp, vin, p, c.stream);
+        kd_apply(vout, tmp, c.g, &kd, nullptr, 1, 0, c.stream);
+      }
+      break;
     case SMG_OP_ADAG:
       kd_apply(tmp, vin, c.g, &kd, nullptr, 1, 1, c.stream);
       p.dagger = 1;

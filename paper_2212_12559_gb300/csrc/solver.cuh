@@ -94,7 +94,7 @@ struct Context {
   double c_naik = 0.0;
   DevBuf fat64, naik64;
   StoredBuf fat32, naik32, fat16, naik16;
-  StoredBuf hop32, hop16;     // hop-link copies (hop.cu)
+  StoredBuf hop32, hop16;     // phase-folded link copies (hop.cu)
   // mass and KD blocks
   double mass = 0.0;
   bool mass_set = false, kd_valid = false;
