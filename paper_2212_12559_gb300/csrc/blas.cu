@@ -7,8 +7,9 @@
 // lets a fixed launch sequence (and a CUDA graph of it) stop early once an
 // inner solve has converged.
 //
-// Reductions accumulate in FP64 whatever the vector precision and are
-// deterministic: per-CTA partial sums, then one finishing pass.
+// Reductions are deterministic: per-CTA partial sums, then one finishing pass
+// in a fixed order.  FP64 vectors reduce in FP64; FP32 vectors in FP32 (the
+// sums are returned as FP64 for the solvers' scalar steps).
 #include "blas.cuh"
 #include "ca_solve.cuh"
 
@@ -191,9 +192,10 @@ __device__ void epilogue_system(const Epilogue& e, int s, const double2* o) {
 
 // partial[s][block][p] = this CTA's share of conj(v[pi[p]]) * v[pj[p]]; the
 // last CTA to arrive adds the partials in a fixed order and runs the epilogue.
-// Accumulator type of a reduction: FP64 for FP64 vectors, FP32 per thread for
-// FP32 vectors (each thread sums at most a few hundred products; the CTA and
-// grid sums are FP64).  GB300's FP64 rate is a small fraction of its FP32 rate.
+// Accumulator type of a reduction: FP64 for FP64 vectors, FP32 for FP32
+// vectors (threads, CTA tree and grid sum; the inner solvers that use FP32
+// vectors only need their inner products to FP32 accuracy).  GB300's FP64
+// rate is a small fraction of its FP32 rate.
 template <typename C> struct AccOf;
 template <> struct AccOf<double2> { using T = double2; };
 template <> struct AccOf<float2> { using T = float2; };
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
   // one padding entry per vector row: the pairs of one row (same r, different
   // vectors) then fall in different shared-memory banks
   __shared__ __align__(16) C tile[kMaxVecs][TR + 1];
-  __shared__ double2 red[kThreads];
+  __shared__ A red[kThreads];
   __shared__ bool last;
   const int s = blockIdx.y;
   const int np = a.npairs;
@@ -254,9 +256,12 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
     }
     __syncthreads();
   }
-  red[t] = active ? make_double2(acc.x, acc.y) : make_double2(0, 0);
+  red[t] = active ? acc : A{0, 0};
   __syncthreads();
   const int nb = gridDim.x, nsys = gridDim.y;
+  // partial sums in the accumulator type (FP32 for FP32 vectors: this part
+  // runs FP64 at a small fraction of the FP32 rate)
+  A* part = reinterpret_cast<A*>(partial);
   // fixed-order tree over the row groups
   for (int gc = groups; gc > 1;) {
     const int half = (gc + 1) / 2;
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
     gc = half;
     __syncthreads();
   }
-  if (t < np) partial[((long long)s * nb + blockIdx.x) * np + t] = red[t];
+  if (t < np) part[((long long)s * nb + blockIdx.x) * np + t] = red[t];
   __threadfence();
   __syncthreads();
   if (t == 0) {
@@ -280,13 +285,13 @@ __global__ void __launch_bounds__(kThreads) pair_dot_kernel(PairDotArgs a, doubl
     const int warp = t >> 5, lane = t & 31;
     for (int o = warp; o < nsys * np; o += kThreads / 32) {
       const int ss = o / np, pp = o % np;
-      double2 sum = make_double2(0, 0);
-      for (int b = lane; b < nb; b += 32) sum = cadd(sum, __ldcg(&partial[((long long)ss * nb + b) * np + pp]));
+      A sum = A{0, 0};
+      for (int b = lane; b < nb; b += 32) sum = cadd(sum, __ldcg(&part[((long long)ss * nb + b) * np + pp]));
       for (int off = 16; off > 0; off >>= 1) {
         sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
         sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
       }
-      if (lane == 0) out[(long long)ss * ldo + pp] = sum;
+      if (lane == 0) out[(long long)ss * ldo + pp] = make_double2(sum.x, sum.y);
     }
   }
   if (t == 0) *counter = 0;
@@ -399,20 +404,20 @@ void blas_copy(const Vec& dst, const Vec& src, cudaStream_t st, const int* run) 
   SMG_REQUIRE(dst.n == src.n && dst.nsys == src.nsys, "copy: shape mismatch");
   dim3 grid(grid_for(dst.n), dst.nsys);
   if (dst.prec == P64 && src.prec == P64)
-    copy_kernel<<<grid, kThreads, 0, st>>>((double2*)dst.p, (const double2*)src.p, dst.n, dst.n, src.n, run);
+    launch_k(copy_kernel<double2, double2>, dim3(grid), dim3(kThreads), 0, st, (double2*)dst.p, (const double2*)src.p, dst.n, dst.n, src.n, run);
   else if (dst.prec == P64)
-    copy_kernel<<<grid, kThreads, 0, st>>>((double2*)dst.p, (const float2*)src.p, dst.n, dst.n, src.n, run);
+    launch_k(copy_kernel<double2, float2>, dim3(grid), dim3(kThreads), 0, st, (double2*)dst.p, (const float2*)src.p, dst.n, dst.n, src.n, run);
   else if (src.prec == P64)
-    copy_kernel<<<grid, kThreads, 0, st>>>((float2*)dst.p, (const double2*)src.p, dst.n, dst.n, src.n, run);
+    launch_k(copy_kernel<float2, double2>, dim3(grid), dim3(kThreads), 0, st, (float2*)dst.p, (const double2*)src.p, dst.n, dst.n, src.n, run);
   else
-    copy_kernel<<<grid, kThreads, 0, st>>>((float2*)dst.p, (const float2*)src.p, dst.n, dst.n, src.n, run);
+    launch_k(copy_kernel<float2, float2>, dim3(grid), dim3(kThreads), 0, st, (float2*)dst.p, (const float2*)src.p, dst.n, dst.n, src.n, run);
   SMG_LAUNCH_OK();
 }
 
 void blas_zero(const Vec& x, cudaStream_t st, const int* run) {
   dim3 grid(grid_for(x.n), x.nsys);
-  if (x.prec == P64) zero_kernel<<<grid, kThreads, 0, st>>>((double2*)x.p, x.n, run);
-  else zero_kernel<<<grid, kThreads, 0, st>>>((float2*)x.p, x.n, run);
+  if (x.prec == P64) launch_k(zero_kernel<double2>, dim3(grid), dim3(kThreads), 0, st, (double2*)x.p, x.n, run);
+  else launch_k(zero_kernel<float2>, dim3(grid), dim3(kThreads), 0, st, (float2*)x.p, x.n, run);
   SMG_LAUNCH_OK();
 }
 
@@ -427,16 +432,16 @@ void blas_maxpy(const Vec& y, const Vec* xs, int nx, const double2* c, int ldc, 
   }
   dim3 grid(grid_for(y.n), y.nsys);
   if (y.prec == P64)
-    maxpy_kernel<<<grid, kThreads, 0, st>>>((double2*)y.p, mp, nx, c, ldc, sign, accumulate ? 1 : 0, y.n, run);
+    launch_k(maxpy_kernel<double2>, dim3(grid), dim3(kThreads), 0, st, (double2*)y.p, mp, nx, c, ldc, sign, accumulate ? 1 : 0, y.n, run);
   else
-    maxpy_kernel<<<grid, kThreads, 0, st>>>((float2*)y.p, mp, nx, c, ldc, sign, accumulate ? 1 : 0, y.n, run);
+    launch_k(maxpy_kernel<float2>, dim3(grid), dim3(kThreads), 0, st, (float2*)y.p, mp, nx, c, ldc, sign, accumulate ? 1 : 0, y.n, run);
   SMG_LAUNCH_OK();
 }
 
 void blas_scale(const Vec& x, const double2* c, bool inv_real, cudaStream_t st, const int* run) {
   dim3 grid(grid_for(x.n), x.nsys);
-  if (x.prec == P64) scale_kernel<<<grid, kThreads, 0, st>>>((double2*)x.p, c, inv_real ? 1 : 0, x.n, run);
-  else scale_kernel<<<grid, kThreads, 0, st>>>((float2*)x.p, c, inv_real ? 1 : 0, x.n, run);
+  if (x.prec == P64) launch_k(scale_kernel<double2>, dim3(grid), dim3(kThreads), 0, st, (double2*)x.p, c, inv_real ? 1 : 0, x.n, run);
+  else launch_k(scale_kernel<float2>, dim3(grid), dim3(kThreads), 0, st, (float2*)x.p, c, inv_real ? 1 : 0, x.n, run);
   SMG_LAUNCH_OK();
 }
 
@@ -444,9 +449,9 @@ void blas_sub(const Vec& z, const Vec& x, const Vec& y, cudaStream_t st, const i
   SMG_REQUIRE(z.n == x.n && x.n == y.n && z.prec == x.prec && x.prec == y.prec, "sub: shape mismatch");
   dim3 grid(grid_for(z.n), z.nsys);
   if (z.prec == P64)
-    sub_kernel<<<grid, kThreads, 0, st>>>((double2*)z.p, (const double2*)x.p, (const double2*)y.p, z.n, run);
+    launch_k(sub_kernel<double2>, dim3(grid), dim3(kThreads), 0, st, (double2*)z.p, (const double2*)x.p, (const double2*)y.p, z.n, run);
   else
-    sub_kernel<<<grid, kThreads, 0, st>>>((float2*)z.p, (const float2*)x.p, (const float2*)y.p, z.n, run);
+    launch_k(sub_kernel<float2>, dim3(grid), dim3(kThreads), 0, st, (float2*)z.p, (const float2*)x.p, (const float2*)y.p, z.n, run);
   SMG_LAUNCH_OK();
 }
 
@@ -468,9 +473,9 @@ void blas_pair_dots(const Vec* vs, int nv, const int* pi, const int* pj, int np,
   double2* partial = (double2*)ws.get(sizeof(double2) * (size_t)nb * np * nsys);
   dim3 grid((unsigned)nb, nsys);
   if (vs[0].prec == P64)
-    pair_dot_kernel<double2><<<grid, kThreads, 0, st>>>(a, partial, out, ldo, ws.counter, epi, run);
+    launch_k(pair_dot_kernel<double2>, dim3(grid), dim3(kThreads), 0, st, a, partial, out, ldo, ws.counter, epi, run);
   else
-    pair_dot_kernel<float2><<<grid, kThreads, 0, st>>>(a, partial, out, ldo, ws.counter, epi, run);
+    launch_k(pair_dot_kernel<float2>, dim3(grid), dim3(kThreads), 0, st, a, partial, out, ldo, ws.counter, epi, run);
   SMG_LAUNCH_OK();
 }
 
@@ -484,9 +489,9 @@ void blas_gcr_update(const Vec* W, int k, const double2* c, int ldc, const doubl
   }
   dim3 grid(grid_for(r.n), r.nsys);
   if (r.prec == P64)
-    gcr_update_kernel<<<grid, kThreads, 0, st>>>(mp, k, c, ldc, ginv, (double2*)r.p, na, r.n, run);
+    launch_k(gcr_update_kernel<double2>, dim3(grid), dim3(kThreads), 0, st, mp, k, c, ldc, ginv, (double2*)r.p, na, r.n, run);
   else
-    gcr_update_kernel<<<grid, kThreads, 0, st>>>(mp, k, c, ldc, ginv, (float2*)r.p, na, r.n, run);
+    launch_k(gcr_update_kernel<float2>, dim3(grid), dim3(kThreads), 0, st, mp, k, c, ldc, ginv, (float2*)r.p, na, r.n, run);
   SMG_LAUNCH_OK();
 }
 
@@ -497,9 +502,9 @@ void blas_gcr_finish(const Vec& x, const Vec* Z, int K, const double2* alpha, co
   for (int j = 0; j < K; ++j) mp.p[j] = Z[j].p;
   dim3 grid(grid_for(x.n), x.nsys);
   if (x.prec == P64)
-    gcr_finish_kernel<<<grid, kThreads, 0, st>>>((double2*)x.p, mp, K, alpha, gamma, beta, nk, x.n, run);
+    launch_k(gcr_finish_kernel<double2>, dim3(grid), dim3(kThreads), 0, st, (double2*)x.p, mp, K, alpha, gamma, beta, nk, x.n, run);
   else
-    gcr_finish_kernel<<<grid, kThreads, 0, st>>>((float2*)x.p, mp, K, alpha, gamma, beta, nk, x.n, run);
+    launch_k(gcr_finish_kernel<float2>, dim3(grid), dim3(kThreads), 0, st, (float2*)x.p, mp, K, alpha, gamma, beta, nk, x.n, run);
   SMG_LAUNCH_OK();
 }
 

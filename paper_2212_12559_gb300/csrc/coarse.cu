@@ -453,7 +453,7 @@ void launch_mma(const Vec& out, const Vec& in, const CoarseParams& p, const Stor
     set = smem;
   }
   const int threads = 32 * (p.N / 16);
-  coarse_apply_mma_kernel<NT><<<p.g.V, threads, smem, st>>>((float2*)out.p, (const float2*)in.p,
+  launch_k(coarse_apply_mma_kernel<NT>, dim3(p.g.V), dim3(threads), smem, st, (float2*)out.p, (const float2*)in.p,
                                                             (const __half2*)S.p, S.scale, p.g, p.N, in.nsys, s0,
                                                             in.n, (const float2*)p.sub_from, run);
   SMG_LAUNCH_OK();
@@ -498,16 +498,16 @@ void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const St
   int4 agg = make_int4(p.agg[0], p.agg[1], p.agg[2], p.agg[3]);
   if (in.prec == P64) {
     SMG_REQUIRE(S.s == S64, "coarse_apply: FP64 vectors need FP64 stencil");
-    coarse_apply_kernel<double, double2><<<grid, 256, smem, st>>>((double2*)out.p, (const double2*)in.p,
+    launch_k(coarse_apply_kernel<double, double2>, dim3(grid), dim3(256), smem, st, (double2*)out.p, (const double2*)in.p,
                                                                   (const double2*)S.p, nullptr, p.g, p.N, p.part,
                                                                   agg, (const double2*)p.sub_from, run);
   } else if (S.s == S32) {
-    coarse_apply_kernel<float, float2><<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p,
+    launch_k(coarse_apply_kernel<float, float2>, dim3(grid), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p,
                                                                 (const float2*)S.p, nullptr, p.g, p.N, p.part,
                                                                 agg, (const float2*)p.sub_from, run);
   } else {
     SMG_REQUIRE(S.s == S16, "coarse_apply: unsupported storage");
-    coarse_apply_kernel<float, __half2><<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p,
+    launch_k(coarse_apply_kernel<float, __half2>, dim3(grid), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p,
                                                                  (const __half2*)S.p, S.scale, p.g, p.N, p.part,
                                                                  agg, (const float2*)p.sub_from, run);
   }
@@ -569,11 +569,11 @@ void dense_apply(const Vec& out, const Vec& in, const void* Dinv, Prec dprec, in
   dim3 grid(ceil_div(n, 8), in.nsys);
   if (in.prec == P64) {
     SMG_REQUIRE(dprec == P64, "dense_apply: FP64 vectors need the FP64 inverse");
-    dense_apply_kernel<double, double2><<<grid, 256, 0, st>>>((double2*)out.p, (const double2*)in.p,
+    launch_k(dense_apply_kernel<double, double2>, dim3(grid), dim3(256), 0, st, (double2*)out.p, (const double2*)in.p,
                                                               (const double2*)Dinv, n, run);
   } else {
     SMG_REQUIRE(dprec == P32, "dense_apply: FP32 vectors need the FP32 inverse");
-    dense_apply_kernel<float, float2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p,
+    launch_k(dense_apply_kernel<float, float2>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p,
                                                             (const float2*)Dinv, n, run);
   }
   SMG_LAUNCH_OK();

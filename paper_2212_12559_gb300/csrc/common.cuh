@@ -13,6 +13,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace smg {
@@ -84,11 +85,15 @@ struct Geom {
   __host__ __device__ __forceinline__ int index(const int c[4]) const {
     return c[0] + L[0] * (c[1] + L[1] * (c[2] + L[2] * c[3]));
   }
-  // site index of c + k*mu_hat (periodic), for |k| < L[mu] + ...
+  // site index of c + k*mu_hat (periodic); one conditional wrap when
+  // |k| <= L[mu] (every hop of the method), a modulo otherwise
   __host__ __device__ __forceinline__ int shift(const int c[4], int mu, int k) const {
     int d[4] = {c[0], c[1], c[2], c[3]};
+    const int l = L[mu];
     int v = d[mu] + k;
-    v %= L[mu]; if (v < 0) v += L[mu];
+    if (v >= l) v -= l;
+    else if (v < 0) v += l;
+    if (v < 0 || v >= l) { v %= l; if (v < 0) v += l; }
     d[mu] = v;
     return index(d);
   }
@@ -133,4 +138,19 @@ struct ArgError {
 #define SMG_REQUIRE(cond, msg) do { if (!(cond)) throw smg::ArgError(msg); } while (0)
 
 inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// Kernel launch with explicit configuration (arguments converted to the
+// kernel's parameter types).  Programmatic dependent launch was measured on
+// the solver's kernel chain and made it slower (dependent CTAs waiting on
+// SMs while the previous kernel drains), so launches are plain stream-ordered.
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  SMG_CUDA_OK(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 }  // namespace smg

@@ -111,7 +111,7 @@ void launch(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t s
   using C = typename cplx<R>::T;
   dim3 grid(ceil_div((long long)p.g.V * 3, 192), p.nsys);
   int4 agg = make_int4(p.agg[0], p.agg[1], p.agg[2], p.agg[3]);
-  dslash_kernel<R, SL><<<grid, 192, 0, st>>>((C*)out.p, (const C*)in.p, (const SL*)p.fat.p, (const SL*)p.naik.p,
+  launch_k(dslash_kernel<R, SL>, dim3(grid), dim3(192), 0, st, (C*)out.p, (const C*)in.p, (const SL*)p.fat.p, (const SL*)p.naik.p,
                                              (R)p.fat.gscale, (R)p.naik.gscale, (R)(0.5 * p.c_naik), p.mass,
                                              p.mass0, p.dagger, p.part, agg, p.g, (const C*)p.sub_from, run);
   SMG_LAUNCH_OK();

@@ -215,10 +215,13 @@ __global__ void __launch_bounds__(256) fused_a_kernel(float2* __restrict__ out, 
     const int ls = t >> 2, mu = t & 3;
     const int hc = ls >> 4, b = ls & 15;
     const int blk = blk0 + hc;
-    const int x = hypercube_site(g, blk < nblk ? blk : nblk - 1, b);
-    const float2* vin = in + (size_t)s * g.V * 3;
+    // coordinates straight from the hypercube index (no division per hop)
     int c[4];
-    g.coords(x, c);
+    hypercube_coords(g, blk < nblk ? blk : nblk - 1, c);
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) c[nu] += (b >> nu) & 1;
+    const int x = g.index(c);
+    const float2* vin = in + (size_t)s * g.V * 3;
     float2 acc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) acc[a] = make_float2(0.f, 0.f);
@@ -265,12 +268,18 @@ __global__ void __launch_bounds__(256) fused_a_kernel(float2* __restrict__ out, 
     }
   if (!ok || cg != 0) return;
   const float* sc = kd.scale[kidx];
+  int hcoord[4];
+  hypercube_coords(g, blk2, hcoord);
 #pragma unroll
   for (int u = 0; u < VPC; ++u) {
     const int r = rg * VPC + u;
     float2 v = o[u];
     if (sc != nullptr) v = cscale(v, sc[(size_t)blk2 * NB + r]);
-    const size_t oi = (size_t)s * g.V * 3 + (size_t)hypercube_site(g, blk2, r / 3) * 3 + (r % 3);
+    const int bb = r / 3;
+    int cc[4];
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) cc[nu] = hcoord[nu] + ((bb >> nu) & 1);
+    const size_t oi = (size_t)s * g.V * 3 + (size_t)g.index(cc) * 3 + (r - 3 * bb);
     if (sub_from != nullptr) v = csub(sub_from[oi], v);
     out[oi] = v;
   }
@@ -281,7 +290,7 @@ void launch_hop(const Vec& out, const Vec& in, const DslashParams& p, cudaStream
   dim3 grid(ceil_div((long long)p.g.V * 4, 256), p.nsys);
   const float cf = 0.5f * p.hop.gscale;
   const float cn = (float)(0.5 * p.c_naik) * p.hop_naik_scale;
-  hop_dslash_kernel<SL, K><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p, (const SL*)p.hop.p, cf, cn,
+  launch_k(hop_dslash_kernel<SL, K>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p, (const SL*)p.hop.p, cf, cn,
                                                  p.mass, p.mass0, p.dagger, p.g, (const float2*)p.sub_from, run);
   SMG_LAUNCH_OK();
 }
@@ -293,7 +302,7 @@ void launch_fused(const Vec& out, const Vec& in, const DslashParams& p, const Kd
   dim3 grid(ceil_div(nblk, 4), p.nsys);
   const float cf = 0.5f * p.hop.gscale;
   const float cn = (float)(0.5 * p.c_naik) * p.hop_naik_scale;
-  fused_a_kernel<SL, K><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p, (const SL*)p.hop.p, cf, cn, p.mass,
+  launch_k(fused_a_kernel<SL, K>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p, (const SL*)p.hop.p, cf, cn, p.mass,
                                               p.mass0, p.g, kd, sys_map, nblk, (const float2*)sub_from, run);
   SMG_LAUNCH_OK();
 }

@@ -218,13 +218,13 @@ void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, co
   dim3 grid(ceil_div(nblk, 4), in.nsys);
   if (in.prec == P64) {
     SMG_REQUIRE(kd[0].s == S64, "kd_apply: FP64 vectors need FP64 blocks");
-    kd_apply_kernel<double, double2><<<grid, 192, 0, st>>>((double2*)out.p, (const double2*)in.p, set, sys_map,
+    launch_k(kd_apply_kernel<double, double2>, dim3(grid), dim3(192), 0, st, (double2*)out.p, (const double2*)in.p, set, sys_map,
                                                            dagger, nblk, g, (const double2*)sub_from, run);
   } else if (kd[0].s == S32) {
-    kd_apply_kernel<float, float2><<<grid, 192, 0, st>>>((float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
+    launch_k(kd_apply_kernel<float, float2>, dim3(grid), dim3(192), 0, st, (float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
                                                          nblk, g, (const float2*)sub_from, run);
   } else if (kd[0].s == S16) {
-    kd_apply_kernel<float, __half2><<<grid, 192, 0, st>>>((float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
+    launch_k(kd_apply_kernel<float, __half2>, dim3(grid), dim3(192), 0, st, (float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
                                                           nblk, g, (const float2*)sub_from, run);
   } else {
     SMG_REQUIRE(false, "kd_apply: unsupported precision pair");

@@ -49,14 +49,20 @@ void apply_a_fused(const Vec& out, const Vec& in, const DslashParams& p, const S
 // -------------------------------------------------------- Kahler-Dirac blocks
 // Site of position b = (x&1) + 2(y&1) + 4(z&1) + 8(t&1) in aligned hypercube blk
 // (hypercubes ordered lexicographically on the half-extent lattice).
-__device__ __forceinline__ int hypercube_site(const Geom& g, int blk, int b) {
+// Base (even) coordinates of aligned hypercube blk.
+__device__ __forceinline__ void hypercube_coords(const Geom& g, int blk, int c[4]) {
   const int h0 = g.L[0] / 2, h1 = g.L[1] / 2, h2 = g.L[2] / 2;
-  int c[4];
   c[0] = blk % h0; blk /= h0;
   c[1] = blk % h1; blk /= h1;
   c[2] = blk % h2; c[3] = blk / h2;
 #pragma unroll
-  for (int mu = 0; mu < 4; ++mu) c[mu] = 2 * c[mu] + ((b >> mu) & 1);
+  for (int mu = 0; mu < 4; ++mu) c[mu] *= 2;
+}
+__device__ __forceinline__ int hypercube_site(const Geom& g, int blk, int b) {
+  int c[4];
+  hypercube_coords(g, blk, c);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) c[mu] += (b >> mu) & 1;
   return g.index(c);
 }
 // Section 3.1: one dense 48x48 block (B+m)^{-1} per 2^4 hypercube, rows and

@@ -349,17 +349,17 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
         SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
         auto k = restrict_vec_kernel<double, double2>;
         ensure_smem(k, smem);
-        k<<<grid, 512, smem, st>>>((double2*)out.p, (const double2*)in.p, (const double2*)P.p, (double)P.gscale,
+        launch_k(k, dim3(grid), dim3(512), smem, st, (double2*)out.p, (const double2*)in.p, (const double2*)P.p, (double)P.gscale,
                                    t, run);
       } else if (P.s == S32) {
         auto k = restrict_vec_kernel<float, float2>;
         ensure_smem(k, smem);
-        k<<<grid, 512, smem, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t, run);
+        launch_k(k, dim3(grid), dim3(512), smem, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t, run);
       } else {
         SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
         auto k = restrict_vec_kernel<float, __half2>;
         ensure_smem(k, smem);
-        k<<<grid, 512, smem, st>>>((float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t, run);
+        launch_k(k, dim3(grid), dim3(512), smem, st, (float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t, run);
       }
       SMG_LAUNCH_OK();
       return;
@@ -371,16 +371,16 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
     SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
     auto k = restrict_kernel<double, double2>;
     ensure_smem(k, smem);
-    k<<<grid, 256, smem, st>>>((double2*)out.p, (const double2*)in.p, (const double2*)P.p, (double)P.gscale, t, run);
+    launch_k(k, dim3(grid), dim3(256), smem, st, (double2*)out.p, (const double2*)in.p, (const double2*)P.p, (double)P.gscale, t, run);
   } else if (P.s == S32) {
     auto k = restrict_kernel<float, float2>;
     ensure_smem(k, smem);
-    k<<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t, run);
+    launch_k(k, dim3(grid), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t, run);
   } else {
     SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
     auto k = restrict_kernel<float, __half2>;
     ensure_smem(k, smem);
-    k<<<grid, 256, smem, st>>>((float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t, run);
+    launch_k(k, dim3(grid), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t, run);
   }
   SMG_LAUNCH_OK();
 }
@@ -393,14 +393,14 @@ void prolong_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stor
   dim3 grid(ceil_div(out.n, 256), in.nsys);
   if (in.prec == P64) {
     SMG_REQUIRE(P.s == S64, "prolong: FP64 vectors need FP64 prolongator");
-    prolong_kernel<double, double2><<<grid, 256, 0, st>>>((double2*)out.p, (const double2*)in.p,
+    launch_k(prolong_kernel<double, double2>, dim3(grid), dim3(256), 0, st, (double2*)out.p, (const double2*)in.p,
                                                           (const double2*)P.p, (double)P.gscale, t, run);
   } else if (P.s == S32) {
-    prolong_kernel<float, float2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p, (const float2*)P.p,
+    launch_k(prolong_kernel<float, float2>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p,
                                                         P.gscale, t, run);
   } else {
     SMG_REQUIRE(P.s == S16, "prolong: unsupported storage");
-    prolong_kernel<float, __half2><<<grid, 256, 0, st>>>((float2*)out.p, (const float2*)in.p,
+    launch_k(prolong_kernel<float, __half2>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p,
                                                          (const __half2*)P.p, P.gscale, t, run);
   }
   SMG_LAUNCH_OK();
