@@ -51,7 +51,7 @@ REF_OUTER_ITERS = {2: 62, 1: 10}
 # dram__bytes_read.sum + dram__bytes_write.sum of one coarse_apply_kernel launch
 # on the 4096-site, N=128 FP16 stencil (ncu, see profiles/); None once the
 # kernel changes until it is captured again.
-NCU_TRAFFIC_COARSE_CFG3 = 2.428485e9 + 0.078377e9
+NCU_TRAFFIC_COARSE_CFG3 = 2.428274e9 + 0.078370e9
 
 
 # ------------------------------------------------------------------ helpers
@@ -228,6 +228,13 @@ def kd_bytes(nsys, store_bytes=4):
     """Per fine site: 48^2/16 = 144 complex block entries, 3 FP32 row scales,
     input and output colour vectors."""
     return 144 * store_bytes + 3 * 4 + 2 * 3 * 8 * nsys
+
+
+def a_bytes(hisq, nsys, store_bytes=4):
+    """Per fine site for A = (B+m)^{-1} M: the links and the block entries
+    (each read once), input and output colour vectors."""
+    nl = 8 if hisq else 4
+    return nl * 9 * store_bytes + 144 * store_bytes + 3 * 4 + 2 * 3 * 8 * nsys
 
 
 # ------------------------------------------------------ coarse apply alone
@@ -503,12 +510,16 @@ def run_ours(args):
         N = 2 * c["nvec"][0]
         ms_d = s.time_kernel(binding.K_DSLASH, 0, 1, 200)
         ms_k = s.time_kernel(binding.K_KD, 0, 1, 200)
+        ms_a = s.time_kernel(binding.K_A, 0, 1, 200)
         roof["others"] = {
             "coarse_apply_this_workload_L2_resident": {"ms": ms, "GB/s": coarse_bytes(N, 1) * Vc / (ms * 1e-3) / 1e9},
             "coarse_apply_cfg3_12rhs": coarse_roofline(binding, s, "cfg3", 12, 3, hbm),
             "coarse_apply_cfg4_1rhs": coarse_roofline(binding, s, "cfg4", 1, 20, hbm),
             "dslash_hisq_fp16": {"ms": ms_d, "GB/s": dslash_bytes(True, 1) * V / (ms_d * 1e-3) / 1e9},
             "kd_apply_fp16": {"ms": ms_k, "GB/s": kd_bytes(1) * V / (ms_k * 1e-3) / 1e9},
+            # the solve's most-applied operator (ten applies per level-1 iteration), dslash + block kernels,
+            # back-to-back applies (its ~60 MB of links and blocks stay in L2)
+            "A_apply_fp16": {"ms": ms_a, "GB/s": a_bytes(c["naik"] is not None, 1) * V / (ms_a * 1e-3) / 1e9},
         }
 
     # plain FP64 GPU MG-GCR on the same problem (the comparison the metric names)

@@ -180,7 +180,9 @@ enum {
   SMG_KERNEL_KD = 1,        /* (B+m)^{-1} per hypercube                     */
   SMG_KERNEL_RESTRICT = 2,  /* R of coarsening l                            */
   SMG_KERNEL_PROLONG = 3,   /* P of coarsening l                            */
-  SMG_KERNEL_COARSE = 4     /* 9-point coarse operator of coarsening l      */
+  SMG_KERNEL_COARSE = 4,    /* 9-point coarse operator of coarsening l      */
+  SMG_KERNEL_A = 5          /* A = (B+m)^{-1} M on the fine lattice (Eq. 2):  */
+                            /* the dslash and block launches of one apply   */
 };
 /* Average device milliseconds of one launch of `kernel` on nsys systems, in
  * the setup's preconditioner precision (FP64 before mg_setup), timed with

@@ -183,108 +183,6 @@ __global__ void __launch_bounds__(256) hop_dslash_kernel(float2* __restrict__ ou
   out[oi] = v;
 }
 
-struct KdPtrs {
-  const void* p[16];
-  const float* scale[16];
-};
-
-// A = (B + m)^{-1} M in one pass (Sec. 3.1): a CTA takes four aligned 2^4
-// hypercubes, computes M in on their 64 sites (four threads per site, as
-// above) into shared memory in the block order 3b + a, then multiplies each
-// hypercube by its 48x48 inverse block (column-major, FP16 with one scale per
-// row, or FP32).  The block product uses 16-byte loads: thread (r4, cg) of a
-// hypercube takes rows 4 r4 .. 4 r4 + 3 and columns 12 cg .. 12 cg + 11
-// (all twelve loads in flight), and a two-step shuffle adds the four column
-// groups.  out = A in, or sub_from - A in.
-template <typename SL, int K>
-__global__ void __launch_bounds__(256) fused_a_kernel(float2* __restrict__ out, const float2* __restrict__ in,
-                                                      const SL* __restrict__ H, float cf, float cn,
-                                                      const double* __restrict__ mass, double mass0, Geom g,
-                                                      KdPtrs kd, const int* __restrict__ sys_map, int nblk,
-                                                      const float2* __restrict__ sub_from, const int* run) {
-  constexpr int NB = 48;
-  constexpr int VPC = 16 / (int)sizeof(SL);   // rows per 16-byte load (4 FP16, 2 FP32)
-  constexpr int RG = NB / VPC;                // row groups per column
-  constexpr int CG = 192 / (4 * RG);          // column groups (4 for FP16, 2 for FP32)
-  constexpr int CPG = NB / CG;                // columns per group
-  __shared__ float2 mv[4][NB];
-  if (run != nullptr && *run == 0) return;
-  const int s = blockIdx.y, t = threadIdx.x;
-  const int blk0 = blockIdx.x * 4;
-  {
-    const int ls = t >> 2, mu = t & 3;
-    const int hc = ls >> 4, b = ls & 15;
-    const int blk = blk0 + hc;
-    // coordinates straight from the hypercube index (no division per hop)
-    int c[4];
-    hypercube_coords(g, blk < nblk ? blk : nblk - 1, c);
-#pragma unroll
-    for (int nu = 0; nu < 4; ++nu) c[nu] += (b >> nu) & 1;
-    const int x = g.index(c);
-    const float2* vin = in + (size_t)s * g.V * 3;
-    float2 acc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) acc[a] = make_float2(0.f, 0.f);
-    hop_dir_eager<SL, K>(acc, reinterpret_cast<const uint4*>(H), vin, g, x, mu, c, cf, cn);
-    sum_quad(acc);
-    if (mu < 3) {
-      float2 v = mu == 0 ? acc[0] : (mu == 1 ? acc[1] : acc[2]);
-      const float m = (float)(mass != nullptr ? mass[s] : mass0);
-      const float2 self = vin[(size_t)x * 3 + mu];
-      v.x = fmaf(m, self.x, v.x);
-      v.y = fmaf(m, self.y, v.y);
-      mv[hc][3 * b + mu] = v;
-    }
-  }
-  __syncthreads();
-  if (t >= 192) return;   // warps 0..5 (whole warps: 192 = 6 x 32)
-  const int lb = t / (RG * CG), q = t - lb * (RG * CG);
-  const int rg = q / CG, cg = q - rg * CG;
-  const int blk2 = blk0 + lb;
-  const bool ok = blk2 < nblk;
-  const int kidx = sys_map != nullptr ? sys_map[s] : 0;
-  const SL* Kb = reinterpret_cast<const SL*>(kd.p[kidx]) + (size_t)(ok ? blk2 : blk0) * NB * NB;
-  uint4 raw[CPG];
-#pragma unroll
-  for (int j = 0; j < CPG; ++j)
-    raw[j] = __ldg(reinterpret_cast<const uint4*>(Kb + (size_t)(cg * CPG + j) * NB + rg * VPC));
-  asm volatile("" ::: "memory");   // all block loads in flight before the products
-  float2 o[VPC];
-#pragma unroll
-  for (int u = 0; u < VPC; ++u) o[u] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int j = 0; j < CPG; ++j) {
-    const SL* kv = reinterpret_cast<const SL*>(&raw[j]);
-    const float2 vv = mv[lb][cg * CPG + j];
-#pragma unroll
-    for (int u = 0; u < VPC; ++u) cfma(o[u], to_f2(kv[u]), vv);
-  }
-#pragma unroll
-  for (int off = 1; off < CG; off <<= 1)
-#pragma unroll
-    for (int u = 0; u < VPC; ++u) {
-      o[u].x += __shfl_xor_sync(0xffffffffu, o[u].x, off);
-      o[u].y += __shfl_xor_sync(0xffffffffu, o[u].y, off);
-    }
-  if (!ok || cg != 0) return;
-  const float* sc = kd.scale[kidx];
-  int hcoord[4];
-  hypercube_coords(g, blk2, hcoord);
-#pragma unroll
-  for (int u = 0; u < VPC; ++u) {
-    const int r = rg * VPC + u;
-    float2 v = o[u];
-    if (sc != nullptr) v = cscale(v, sc[(size_t)blk2 * NB + r]);
-    const int bb = r / 3;
-    int cc[4];
-#pragma unroll
-    for (int nu = 0; nu < 4; ++nu) cc[nu] = hcoord[nu] + ((bb >> nu) & 1);
-    const size_t oi = (size_t)s * g.V * 3 + (size_t)g.index(cc) * 3 + (r - 3 * bb);
-    if (sub_from != nullptr) v = csub(sub_from[oi], v);
-    out[oi] = v;
-  }
-}
-
 template <typename SL, int K>
 void launch_hop(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
   dim3 grid(ceil_div((long long)p.g.V * 4, 256), p.nsys);
@@ -292,18 +190,6 @@ void launch_hop(const Vec& out, const Vec& in, const DslashParams& p, cudaStream
   const float cn = (float)(0.5 * p.c_naik) * p.hop_naik_scale;
   launch_k(hop_dslash_kernel<SL, K>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p, (const SL*)p.hop.p, cf, cn,
                                                  p.mass, p.mass0, p.dagger, p.g, (const float2*)p.sub_from, run);
-  SMG_LAUNCH_OK();
-}
-
-template <typename SL, int K>
-void launch_fused(const Vec& out, const Vec& in, const DslashParams& p, const KdPtrs& kd, const int* sys_map,
-                  cudaStream_t st, const int* run, const void* sub_from) {
-  const int nblk = p.g.V / 16;
-  dim3 grid(ceil_div(nblk, 4), p.nsys);
-  const float cf = 0.5f * p.hop.gscale;
-  const float cn = (float)(0.5 * p.c_naik) * p.hop_naik_scale;
-  launch_k(fused_a_kernel<SL, K>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p, (const SL*)p.hop.p, cf, cn, p.mass,
-                                              p.mass0, p.g, kd, sys_map, nblk, (const float2*)sub_from, run);
   SMG_LAUNCH_OK();
 }
 
@@ -349,27 +235,6 @@ void hop_dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream
   } else {
     if (p.hop_kinds == 2) launch_hop<float2, 2>(out, in, p, st, run);
     else launch_hop<float2, 1>(out, in, p, st, run);
-  }
-}
-
-void apply_a_fused(const Vec& out, const Vec& in, const DslashParams& p, const Stored* kd, const int* sys_map, int nkd,
-                   cudaStream_t st, const int* run, const void* sub_from) {
-  SMG_REQUIRE(hop_dslash_ok(in, p) && p.dagger == 0, "fused A: FP32 vectors with a phase-folded link copy");
-  SMG_REQUIRE(in.n == (long long)p.g.V * 3 && out.n == in.n && in.nsys == p.nsys && out.nsys == p.nsys &&
-                  out.prec == P32, "fused A: shape mismatch");
-  SMG_REQUIRE(nkd >= 1 && nkd <= 16, "fused A: 1..16 block inverses");
-  KdPtrs set{};
-  for (int i = 0; i < nkd; ++i) {
-    SMG_REQUIRE(kd[i].s == p.hop.s, "fused A: blocks and links must share the storage");
-    set.p[i] = kd[i].p;
-    set.scale[i] = kd[i].s == S16 ? kd[i].scale : nullptr;
-  }
-  if (p.hop.s == S16) {
-    if (p.hop_kinds == 2) launch_fused<__half2, 2>(out, in, p, set, sys_map, st, run, sub_from);
-    else launch_fused<__half2, 1>(out, in, p, set, sys_map, st, run, sub_from);
-  } else {
-    if (p.hop_kinds == 2) launch_fused<float2, 2>(out, in, p, set, sys_map, st, run, sub_from);
-    else launch_fused<float2, 1>(out, in, p, set, sys_map, st, run, sub_from);
   }
 }
 

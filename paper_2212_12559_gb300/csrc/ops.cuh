@@ -41,10 +41,6 @@ void build_hop_links(void* H, Store s, const double2* fat, const double2* naik, 
                      float naik_scale, cudaStream_t st);
 bool hop_dslash_ok(const Vec& in, const DslashParams& p);
 void hop_dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run);
-// out = (B+m)^{-1} M in (or sub_from - that) in one kernel; needs hop_dslash_ok and dagger == 0.
-// kd[sys_map[s]] are the block inverses (storage of the link copy), see kd_apply.
-void apply_a_fused(const Vec& out, const Vec& in, const DslashParams& p, const Stored* kd, const int* sys_map, int nkd,
-                   cudaStream_t st, const int* run = nullptr, const void* sub_from = nullptr);
 
 // -------------------------------------------------------- Kahler-Dirac blocks
 // Site of position b = (x&1) + 2(y&1) + 4(z&1) + 8(t&1) in aligned hypercube blk

@@ -375,11 +375,6 @@ struct Engine {
     kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run, sub ? sub->p : nullptr);
   }
   void As(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
-    DslashParams p = dparams(sp, 0);
-    if (hop_dslash_ok(in, p)) {
-      apply_a_fused(out, in, p, kd_s.data(), sys_map, nkd, st(), run, sub ? sub->p : nullptr);
-      return;
-    }
     Ms(tmpA, in, run);
     Binv(out, tmpA, run, sub);
   }
@@ -1144,14 +1139,7 @@ void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void
     case SMG_OP_MDAG: p.dagger = 1; dslash(vout, vin, p, c.stream); break;
     case SMG_OP_KD: kd_apply(vout, vin, c.g, &kd, nullptr, 1, 0, c.stream); break;
     case SMG_OP_KDDAG: kd_apply(vout, vin, c.g, &kd, nullptr, 1, 1, c.stream); break;
-    case SMG_OP_A:
-      if (hop_dslash_ok(vin, p)) {
-        apply_a_fused(vout, vin, p, &kd, nullptr, 1, c.stream);
-      } else {
-        dslash(tmp, vin, p, c.stream);
-        kd_apply(vout, tmp, c.g, &kd, nullptr, 1, 0, c.stream);
-      }
-      break;
+    case SMG_OP_A: dslash(tmp, vin, p, c.stream); kd_apply(vout, tmp, c.g, &kd, nullptr, 1, 0, c.stream); break;
     case SMG_OP_ADAG:
       kd_apply(tmp, vin, c.g, &kd, nullptr, 1, 1, c.stream);
       p.dagger = 1;
@@ -1299,7 +1287,8 @@ double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep) {
   if (!c.kd_valid) ctx_build_kd(c);
   long long nin = (long long)c.g.V * 3, nout = nin;
   const CoarseLevel* C = nullptr;
-  if (kernel >= SMG_KERNEL_RESTRICT) {
+  SMG_REQUIRE(kernel >= SMG_KERNEL_DSLASH && kernel <= SMG_KERNEL_A, "time_kernel: unknown kernel");
+  if (kernel >= SMG_KERNEL_RESTRICT && kernel <= SMG_KERNEL_COARSE) {
     SMG_REQUIRE(c.setup_done && l >= 0 && l < (int)c.coarse.size(), "time_kernel: bad level");
     C = &c.coarse[l];
     const long long nf = (long long)C->tg.fine.V * C->tg.ndof, nc = (long long)C->g.V * C->N;
@@ -1338,6 +1327,10 @@ double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep) {
         coarse_apply(out, in, p, C->Ss.st, c.stream);
         break;
       }
+      case SMG_KERNEL_A:
+        dslash(tmp, in, dp, c.stream);
+        kd_apply(out, tmp, c.g, &kd, nullptr, 1, 0, c.stream);
+        break;
       default: SMG_REQUIRE(false, "time_kernel: unknown kernel");
     }
   };
