@@ -44,10 +44,11 @@ WORKLOADS = {
     4: "24^3x48 HISQ-shaped, 8 masses log-spaced 0.001-0.05 x 4 sources = 32 systems in one batch, 3-level KD-MG "
        "(4^4/2^4 aggregates, 24/32 vectors, operators of the lightest mass), FP32 + FP16 storage, FP64 outer GCR",
 }
-# Outer GCR iterations a solve of the default workload takes with this
-# algorithm and these parameters (measured by the GPU path); scales the
+# Outer GCR iterations a solve of the workload takes with this
+# algorithm, keyed by (workload, truncated level-1 operator), measured by the
+# GPU path with the same parameters; scales the
 # oracle's per-iteration time in --impl reference, where no GPU runs.
-REF_OUTER_ITERS = {2: 62, 1: 10}
+REF_OUTER_ITERS = {(2, 0): 64, (2, 1): 31, (1, 0): 10, (1, 1): 10}
 # dram__bytes_read.sum + dram__bytes_write.sum of one coarse_apply_kernel launch
 # on the 4096-site, N=128 FP16 stencil (ncu, see profiles/); None once the
 # kernel changes until it is captured again.
@@ -173,10 +174,11 @@ def build_problem(cfg, torch, dev, seed_offset=0, dims=None):
     return c, s, phi0, src
 
 
-def setup(binding, s, c, phi0, precision, use_graph, setup_maxiter=2000, max_outer=500):
+def setup(binding, s, c, phi0, precision, use_graph, setup_maxiter=2000, max_outer=500, truncate_naik=0):
     prec = {"double": binding.PREC_DOUBLE, "single": binding.PREC_SINGLE, "mixed": binding.PREC_HALF}[precision]
     p = binding.default_params(n_coarse=len(c["nvec"]), agg=c["agg"], nvec=c["nvec"], precision=prec,
-                               use_graph=use_graph, setup_maxiter=setup_maxiter, max_outer=max_outer)
+                               use_graph=use_graph, setup_maxiter=setup_maxiter, max_outer=max_outer,
+                               truncate_naik=truncate_naik)
     t0 = time.perf_counter()
     s.mg_setup(p, phi0)
     return time.perf_counter() - t0
@@ -277,7 +279,7 @@ def run_coarse_only(args):
 
 
 # --------------------------------------------------------- oracle sample
-def oracle_sample(cfg, n_iter, out_path, sub=0):
+def oracle_sample(cfg, n_iter, out_path, sub=0, truncate_naik=0):
     """Runs in a child process with one BLAS thread: times the oracle's outer
     GCR iterations of the workload (setup with unrefined random near-null
     vectors, excluded from the timing).  With sub > 0 the lattice extents are
@@ -302,7 +304,8 @@ def oracle_sample(cfg, n_iter, out_path, sub=0):
         ndof = 2 * nv[l - 1]
         phi0.append(inputs.gaussian_fields(nv[l], int(np.prod(cdims)), ndof, c["nullvec_seed"] + 10 * l))
     t0 = time.perf_counter()
-    mg = MultigridSolver(op, MGParams(agg=c["agg"], nvec=nv, setup_maxiter=0), phi0)
+    mg = MultigridSolver(op, MGParams(agg=c["agg"], nvec=nv, setup_maxiter=0, truncate_naik=bool(truncate_naik)),
+                         phi0)
     t_setup = time.perf_counter() - t0
     b = c["sources"][0]
     times = []
@@ -315,13 +318,14 @@ def oracle_sample(cfg, n_iter, out_path, sub=0):
         json.dump({"iter_times": times, "setup_s": t_setup, "V": V}, f)
 
 
-def run_oracle_sample(cfg, n_iter, timeout=600, sub=0):
+def run_oracle_sample(cfg, n_iter, timeout=600, sub=0, truncate_naik=0):
     out = os.path.join(ROOT, f".oracle_sample_{os.getpid()}.json")
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
         env.pop(k, None)
-    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-sample", str(cfg), str(n_iter), out, str(sub)]
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-sample", str(cfg), str(n_iter), out, str(sub),
+           str(truncate_naik)]
     r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
@@ -337,9 +341,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = args.config
-    iters = REF_OUTER_ITERS[cfg]
+    iters = REF_OUTER_ITERS[(cfg, args.truncate_naik)]
     n = args.steps + args.warmup
-    d = run_oracle_sample(cfg, n, timeout=3600)
+    d = run_oracle_sample(cfg, n, timeout=3600, truncate_naik=args.truncate_naik)
     per_iter = d["iter_times"][args.warmup:]
     per_solve = [t * iters for t in per_iter]
     value = statistics.mean(per_solve)
@@ -347,7 +351,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[cfg], "oracle_setup_s": d["setup_s"]},
+        "config": {"workload": WORKLOADS[cfg], "oracle_setup_s": d["setup_s"],
+                   "level1_operator": "truncated (Naik dropped)" if args.truncate_naik else "KD-preconditioned HISQ"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} oracle outer-GCR iterations (K-cycle + M), each scaled by "
                                    f"{iters} iterations per solve; setup with unrefined near-null vectors excluded"},
@@ -371,7 +376,8 @@ def run_batched(args):
     V = int(np.prod(c["dims"]))
     masses = np.array([c["mass"]]) if c["masses"] is None else inputs.log_masses(0.001, 0.05, 8)
     log(f"inputs ready (dims {c['dims']}); setup")
-    t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer)
+    t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer,
+                    args.truncate_naik)
     setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
     log(f"setup {t_setup:.1f} s, CGNE iterations {setup_iters}")
     b = torch.from_numpy(c["sources"]).to(dev)
@@ -447,7 +453,8 @@ def run_ours(args):
     c, s, phi0, src = build_problem(cfg, torch, dev, seed_offset=rank)
     V = int(np.prod(c["dims"]))
     log("setup")
-    t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer)
+    t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer,
+                    args.truncate_naik)
     log(f"setup {t_setup:.1f} s")
     setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
     b_dev = torch.from_numpy(src).to(dev)
@@ -530,7 +537,7 @@ def run_ours(args):
         s64.set_gauge(torch.from_numpy(c["fat"]).to(dev),
                       None if c["naik"] is None else torch.from_numpy(c["naik"]).to(dev), c["c_naik"])
         s64.set_mass(c["mass"])
-        t64_setup = setup(binding, s64, c, phi0, "double", 0)
+        t64_setup = setup(binding, s64, c, phi0, "double", 0, truncate_naik=args.truncate_naik)
         t64, inf64, _ = timed_solves(torch, s64, b_dev, max(1, args.steps // 2), 1, flush)
         fp64 = {"s_per_solve": statistics.mean(t64), "setup_s": t64_setup,
                 "outer_iters": [i.iterations for i in inf64[1:]],
@@ -541,7 +548,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
             n_it = args.cpu_iters
-            d = run_oracle_sample(cfg, n_it, sub=2)
+            d = run_oracle_sample(cfg, n_it, sub=2, truncate_naik=args.truncate_naik)
             vol = V / d["V"]
             per_iter = statistics.mean(d["iter_times"]) * vol
             it_per_solve = statistics.mean(iters)
@@ -563,6 +570,7 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[cfg], "dims": list(c["dims"]), "mass": c["mass"],
                        "nvec": c["nvec"], "agg": [list(a) for a in c["agg"]], "precision": c["precision"],
                        "cuda_graph": bool(args.graph), "l2": "flushed (512 MB write) before every timed solve",
+                       "level1_operator": "truncated (Naik dropped)" if args.truncate_naik else "KD-preconditioned HISQ",
                        "setup_s": t_setup, "setup_cgne_iters": setup_iters, "outer_iters": iters, "all_converged": conv,
                        "max_true_residual": res, "timed_wall_s": t_wall, "parallelism": f"replicas x{ws}"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
@@ -581,7 +589,7 @@ def run_ours(args):
 
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--_oracle-sample":
-        oracle_sample(int(sys.argv[2]), int(sys.argv[3]), sys.argv[4], int(sys.argv[5]))
+        oracle_sample(int(sys.argv[2]), int(sys.argv[3]), sys.argv[4], int(sys.argv[5]), int(sys.argv[6]))
         return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -591,6 +599,9 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--compare-fp64", type=int, default=1)
+    ap.add_argument("--truncate-naik", type=int, default=1,
+                    help="Table 1 level-1 operator: 1 = truncated (Naik hops dropped from the pseudo-fine "
+                         "operator), 0 = KD-preconditioned HISQ; the outer operator is the full M either way")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--setup-maxiter", type=int, default=2000,

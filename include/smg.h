@@ -79,6 +79,10 @@ typedef struct smg_mg_params {
   int use_graph;                   /* 1: replay the K-cycle from a captured CUDA graph */
   int persistent;                  /* 1: run the last coarse GCR level as one cooperative launch
                                       (FP32 preconditioner, at most 16 systems) */
+  int truncate_naik;               /* Table 1 level-1 operator: 0 = KD-preconditioned HISQ
+                                      A = (B+m)^{-1} M; 1 = truncated A' = (B+m)^{-1}(m + D_fat),
+                                      the Naik hops dropped from the pseudo-fine operator only
+                                      (Sec. 3.1); the outer GCR keeps the full M.  Default 0. */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */

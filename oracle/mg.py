@@ -17,6 +17,13 @@ prolongate and correct, post-smooth); Sec. 2.3 and Table 1 fix the levels:
   (when it has at most ``dense_max`` unknowns) or GCR to 0.25 / 8
   iterations.
 
+Table 1 offers two level-1 operators: the KD-preconditioned HISQ operator
+above, or the "truncated" one, which drops the distance-three Naik hops from
+the pseudo-fine operator (Sec. 3.1): A' = (B+m)^{-1} (m + D_fat).  The outer
+level keeps the full M, so the truncation only changes the preconditioner
+(the outer GCR is flexible); B holds distance-one hops only, so (B+m)^{-1} is
+the same block inverse.  ``truncate_naik`` selects it.
+
 Readings taken where the paper is silent: no pre-smoothing anywhere (Table 1
 lists none), "0.25 or 8 iterations" stops at whichever comes first, the
 coarse levels use the un-preconditioned Galerkin operator (the Schur form of
@@ -47,6 +54,7 @@ class MGParams:
     smoother_s: int = 8
     dense_max: int = 4096
     nkrylov: int = 16
+    truncate_naik: bool = False
 
 
 class MultigridSolver:
@@ -54,8 +62,11 @@ class MultigridSolver:
         """op: M at level 0; phi0[l]: (nvec[l], V_l, n_l) random starts."""
         self.op = op
         self.p = params
-        self.kd = KahlerDirac(op)
-        self.levels = [FineLevelOp(self.kd)]      # level 1 operator
+        op1 = op
+        if params.truncate_naik and op.naik is not None:
+            op1 = Staggered(op.lat, op.fat, None, 0.0, op.mass)
+        self.kd = KahlerDirac(op1)                # (B+m)^{-1}: distance-one hops only
+        self.levels = [FineLevelOp(self.kd)]      # level 1 operator A (or A')
         self.transfers = []
         self.setup_iters = []
         for l, (agg, nv) in enumerate(zip(params.agg, params.nvec)):

@@ -47,6 +47,7 @@ class MGParams(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("persistent", ctypes.c_int),
+        ("truncate_naik", ctypes.c_int),
     ]
 
 

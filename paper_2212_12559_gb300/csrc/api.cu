@@ -66,6 +66,7 @@ void smg_default_params(smg_mg_params* p) {
   p->precision = SMG_PREC_DOUBLE;
   p->use_graph = 0;
   p->persistent = 1;
+  p->truncate_naik = 0;
 }
 
 int smg_create(const int dims[4], smg_ctx** out) {

@@ -374,8 +374,11 @@ struct Engine {
   void Binv(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
     kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run, sub ? sub->p : nullptr);
   }
+  // A_1 = (B+m)^{-1} M_1; M_1 = M, or m + D_fat for the truncated operator
   void As(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
-    Ms(tmpA, in, run);
+    DslashParams p = dparams(sp, 0);
+    if (c.trunc1()) c.link_params(sp, p, true);
+    dslash(tmpA, in, p, st(), run);
     Binv(out, tmpA, run, sub);
   }
   // out = A_l in, or out = sub - A_l in
@@ -696,14 +699,16 @@ struct Engine {
 void EngineDeleter::operator()(Engine* e) const { delete e; }
 
 // ------------------------------------------------------------------ context
-void Context::link_params(Store s, DslashParams& p) const {
+void Context::link_params(Store s, DslashParams& p, bool truncate) const {
+  const bool naik = has_naik && !truncate;
   p.fat = fat_of(s);
-  if (has_naik) p.naik = naik_of(s);
-  p.c_naik = c_naik;
+  p.naik = naik ? naik_of(s) : Stored{};
+  p.c_naik = naik ? c_naik : 0.0;
   if (s == S16 || s == S32) {
-    p.hop = s == S16 ? hop16.st : hop32.st;
-    p.hop_kinds = has_naik ? 2 : 1;
-    p.hop_naik_scale = (s == S16 && has_naik) ? naik16.st.gscale : 1.0f;
+    if (has_naik && truncate) p.hop = s == S16 ? hop16f.st : hop32f.st;
+    else p.hop = s == S16 ? hop16.st : hop32.st;
+    p.hop_kinds = naik ? 2 : 1;
+    p.hop_naik_scale = (s == S16 && naik) ? naik16.st.gscale : 1.0f;
   }
 }
 
@@ -754,6 +759,17 @@ void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik,
     c.hop32.alloc(S32, hop_link_entries(c.g, c.has_naik, S32), 0);
     build_hop_links(c.hop32.v.p, S32, c.fat64.as<double2>(), n64, c.g, 1.0f, 1.0f, c.stream);
     c.hop32.st.gscale = 1.0f;
+    if (c.has_naik) {   // fat-only records for the truncated level-1 operator
+      c.hop16f.alloc(S16, hop_link_entries(c.g, false, S16), 0);
+      build_hop_links(c.hop16f.v.p, S16, c.fat64.as<double2>(), nullptr, c.g, fs, 1.0f, c.stream);
+      c.hop16f.st.gscale = fs;
+      c.hop32f.alloc(S32, hop_link_entries(c.g, false, S32), 0);
+      build_hop_links(c.hop32f.v.p, S32, c.fat64.as<double2>(), nullptr, c.g, 1.0f, 1.0f, c.stream);
+      c.hop32f.st.gscale = 1.0f;
+    } else {
+      c.hop16f = StoredBuf();
+      c.hop32f = StoredBuf();
+    }
   }
   c.gauge_set = true;
   c.kd_valid = false;
@@ -796,8 +812,10 @@ void op_part64(Context& c, int l, const Vec& out, const Vec& in, Vec& tmp, int p
     DslashParams p;
     p.g = c.g;
     p.fat = c.fat64_st;
-    if (c.has_naik) p.naik = c.naik64_st;
-    p.c_naik = c.c_naik;
+    if (c.has_naik && !c.trunc1()) {
+      p.naik = c.naik64_st;
+      p.c_naik = c.c_naik;
+    }
     p.mass0 = c.mass;
     p.part = part;
     for (int mu = 0; mu < 4; ++mu) p.agg[mu] = agg[mu];
@@ -826,7 +844,7 @@ struct SetupOp {
     if (l == 1) {
       DslashParams p;
       p.g = c.g;
-      c.link_params(sp, p);
+      c.link_params(sp, p, c.trunc1());
       p.mass0 = c.mass;
       p.nsys = in.nsys;
       const Stored kd = c.kd_of(sp);

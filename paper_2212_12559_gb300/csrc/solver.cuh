@@ -95,6 +95,7 @@ struct Context {
   DevBuf fat64, naik64;
   StoredBuf fat32, naik32, fat16, naik16;
   StoredBuf hop32, hop16;     // phase-folded link copies (hop.cu)
+  StoredBuf hop32f, hop16f;   // the same without the Naik links (truncated level-1 operator)
   // mass and KD blocks
   double mass = 0.0;
   bool mass_set = false, kd_valid = false;
@@ -119,8 +120,11 @@ struct Context {
   const Stored& fat_of(Store s) const { return s == S64 ? fat64_st : (s == S32 ? fat32.st : fat16.st); }
   const Stored& naik_of(Store s) const { return s == S64 ? naik64_st : (s == S32 ? naik32.st : naik16.st); }
   const Stored& kd_of(Store s) const { return s == S64 ? kd64.st : (s == S32 ? kd32.st : kd16.st); }
-  // fat / Naik links (and their hop-link copy) of storage s into a dslash parameter block
-  void link_params(Store s, DslashParams& p) const;
+  // fat / Naik links (and their phase-folded copy) of storage s into a dslash
+  // parameter block; `truncate` leaves the Naik hops out
+  void link_params(Store s, DslashParams& p, bool truncate = false) const;
+  // the level-1 (pseudo-fine) operator drops the Naik hops (Table 1, truncated operator)
+  bool trunc1() const { return has_naik && params.truncate_naik != 0; }
   Stored fat64_st, naik64_st;
   void ensure_consts(int n);
 };

@@ -220,3 +220,54 @@ def test_persistent_coarse_solver_matches_launch_path(binding, nrhs):
             assert infos[r].converged == 1
             assert np.linalg.norm(b[r] - op.M(xs[r])) <= 1e-10 * np.linalg.norm(b[r])
     assert abs(its[0] - its[1]) <= max(2, 0.25 * max(its.values())), its
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_truncated_pseudo_fine_operator(binding, prec):
+    """Table 1's truncated level-1 operator (Naik hops dropped from the
+    pseudo-fine operator only, Sec. 3.1): the outer solve on the full HISQ M
+    still meets 1e-10 and the dense solution; in FP64 the iteration count
+    follows the oracle's solve with the same option."""
+    from oracle.mg import MGParams, MultigridSolver
+    dims = (8, 4, 4, 4)
+    fat, naik, c, op = problem(dims, True, 0.1, seed=1011)
+    phi = inputs.gaussian_fields(4, op.lat.V, 3, 3011)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(0.1)
+    s.mg_setup(binding.default_params(nvec=[4], setup_maxiter=50, precision=prec, truncate_naik=1), [phi])
+    b = inputs.gaussian_field(op.lat.V, 3, 2011)
+    x, info = s.solve(b, 1e-10)
+    assert info.converged == 1 and info.true_residual <= 1e-10
+    check_solution(op, b, x, dense_solution(op, b), 1e-13)
+    if prec == 0:
+        mg = MultigridSolver(op, MGParams(nvec=[4], setup_maxiter=50, truncate_naik=True), [phi])
+        _, it_ref, _ = mg.solve(b, tol=1e-10)
+        assert abs(info.iterations - it_ref) <= max(2, 0.15 * it_ref), (info.iterations, it_ref)
+
+
+def test_truncated_coarse_operator(binding):
+    """With the truncated option the Galerkin stencil is R A' P with
+    A' = (B+m)^{-1}(m + D_fat): same raw near-null vectors on both sides."""
+    from oracle.coarse import FineLevelOp, Transfer, galerkin
+    from oracle.dirac import KahlerDirac
+    dims = (8, 8, 8, 8)
+    fat, naik, c, op = problem(dims, True, 0.1, seed=1012)
+    op_fat = Staggered(op.lat, fat, None, 0.0, 0.1)
+    phi = inputs.gaussian_fields(4, op.lat.V, 3, 3012)
+    lop = FineLevelOp(KahlerDirac(op_fat))
+    T = Transfer(op.lat, 3, lop.chirality(), (4, 4, 4, 4), phi)
+    S = galerkin(lop, T)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(0.1)
+    s.mg_setup(binding.default_params(nvec=[4], setup_maxiter=0, precision=binding.PREC_HALF,
+                                      truncate_naik=1), [phi])
+    got = s.coarse_op(0)
+    Vc, N = S.X.shape[0], S.X.shape[1]
+    ref = np.empty((Vc, N, 9, N), dtype=np.complex128)
+    ref[:, :, 0, :] = S.X
+    for mu in range(4):
+        ref[:, :, 1 + 2 * mu, :] = S.Yf[mu]
+        ref[:, :, 2 + 2 * mu, :] = S.Yb[mu]
+    assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)

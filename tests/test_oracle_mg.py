@@ -55,3 +55,33 @@ def test_three_level_solve():
     x, it, res = mg.solve(b, tol=1e-10)
     assert res <= 1e-10
     assert np.linalg.norm(b - op.M(x)) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_truncated_pseudo_fine_operator():
+    """Table 1's truncated level-1 operator (Sec. 3.1): the Naik hops are
+    dropped from the pseudo-fine operator only.  (B+m)^{-1} is unchanged
+    (the Naik reach of three never stays inside a 2^4 hypercube), A' differs
+    from A by exactly (B+m)^{-1} applied to the Naik part of D, and the outer
+    solve on the full HISQ M still reaches 1e-10 and the dense solution."""
+    from oracle.dirac import KahlerDirac
+    dims = (8, 4, 4, 4)
+    lat = Lattice(dims)
+    thin = inputs.random_su3_links(dims, 1011)
+    fat, naik = inputs.fat_links(thin, dims), inputs.naik_links(thin, dims)
+    op = Staggered(lat, fat, naik, -1 / 24, 0.1)
+    op_fat = Staggered(lat, fat, None, 0.0, 0.1)
+    kd, kd_fat = KahlerDirac(op), KahlerDirac(op_fat)
+    assert np.array_equal(kd.blocks, kd_fat.blocks)
+    v = inputs.gaussian_field(lat.V, 3, 7)
+    naik_only = Staggered(lat, np.zeros_like(fat), naik, -1 / 24, 0.0)
+    np.testing.assert_allclose(kd.A(v) - kd_fat.A(v), kd.apply_inv(naik_only.M(v)), rtol=0, atol=1e-12)
+    p = MGParams(agg=[(4, 4, 4, 4)], nvec=[4], setup_maxiter=50, truncate_naik=True)
+    mg = MultigridSolver(op, p, [inputs.gaussian_fields(4, lat.V, 3, 3011)])
+    w = inputs.gaussian_field(lat.V, 3, 8)
+    np.testing.assert_allclose(mg.levels[0].apply(w), kd_fat.A(w), rtol=0, atol=1e-13)
+    b = inputs.gaussian_field(lat.V, 3, 2011)
+    x, it, res = mg.solve(b, tol=1e-10)
+    assert res <= 1e-10
+    xs = scipy.linalg.solve(dense_M(op), b.ravel())
+    bound = 1e-10 * (op.mass + 4 * (1 + abs(op.c_naik))) / op.mass
+    assert np.linalg.norm(x.ravel() - xs) <= bound * np.linalg.norm(xs)
