@@ -135,6 +135,25 @@ SMG_API int smg_solve(smg_ctx* ctx, const void* b, void* x, double tol, int wher
 SMG_API int smg_multi_solve(smg_ctx* ctx, int nrhs, const void* b, int nshift, const double* masses, void* x,
                     double tol, int where, smg_solve_info* info);
 
+/* Sec. 4 (propagator workflow): M(m_i) x_i = b for nshift masses by
+ * conjugate gradients on M^dag M = m^2 + D^dag D with every shift in one
+ * Krylov space (one product by D^dag D per iteration for all of them), then
+ * x_i = M(m_i)^dag y_i.  FP64 on the full operator (Naik included); needs
+ * set_gauge only (no mass, no setup).  b: V*3 complex FP64; x: [nshift][V][3];
+ * masses > 0, any order; info: nshift entries with the recomputed
+ * ||b - M(m_i) x_i|| / ||b|| and the shared iteration count (may be NULL).
+ * Returns SMG_ERR_NOT_CONVERGED when a residual misses tol after maxiter. */
+SMG_API int smg_multishift_cg(smg_ctx* ctx, const void* b, int nshift, const double* masses, void* x, double tol,
+                              int maxiter, int where, smg_solve_info* info);
+
+/* Sec. 4: the propagator workflow's split: the n_mg lightest masses by the MG
+ * solver of the current setup (as smg_multi_solve: near-null vectors and
+ * coarse operators of the setup mass serve every mass), the others by
+ * smg_multishift_cg (at most cg_maxiter iterations).  b: V*3; x: [nmass][V][3]
+ * in the order of `masses`; info: nmass entries in that order (may be NULL). */
+SMG_API int smg_propagators(smg_ctx* ctx, const void* b, int nmass, const double* masses, int n_mg, void* x,
+                            double tol, int cg_maxiter, int where, smg_solve_info* info);
+
 /* ------------------------------------------------------ test / bench hooks */
 /* Operators applied to nsys FP64 fields (in/out [nsys][V][3]) in precision
  * `prec` (SMG_PREC_*; inputs are rounded to it, outputs widened to FP64). */

@@ -110,3 +110,76 @@ def cgne(apply, apply_dag, b, x0, tol: float, maxiter: int):
         p = apply_dag(r) + beta * p
         it += 1
     return x, it, float(np.sqrt(rr) / r0)
+
+
+def multishift_cg(apply, b, shifts, tol: float = 1e-10, maxiter: int = 10000):
+    """Conjugate gradients for (A + sigma_i) x_i = b, all shifts at once.
+
+    A is Hermitian positive (semi)definite and every sigma_i >= 0.  The
+    shifted systems share one Krylov space: CG runs on the base system
+    A + sigma_0 (sigma_0 = min sigma) with one product by A per iteration, and
+    shift i carries a scalar zeta_i with its residual r_i = zeta_i r.  From the
+    three-term recurrence of the Lanczos polynomials (Jegerlehner 1996,
+    "Krylov space solvers for shifted linear systems"), with d_i = sigma_i -
+    sigma_0, base step alpha and base beta:
+
+      zeta_i' = zeta_i zeta_i^- a^- / (a b^- (zeta_i^- - zeta_i)
+                                        + zeta_i^- a^- (1 + d_i a)),
+      alpha_i = a zeta_i' / zeta_i,   beta_i = b (zeta_i' / zeta_i)^2,
+      x_i += alpha_i p_i,             p_i = zeta_i' r' + beta_i p_i.
+
+    Shift i stops updating x_i once |zeta_i| ||r|| <= tol ||b||; the loop stops
+    when every shift has.  Returns (xs, iterations, residuals) with xs[i]
+    the solution of shift i and residuals[i] = ||b - (A + sigma_i) x_i|| / ||b||
+    recomputed.
+    """
+    shifts = np.asarray(shifts, dtype=np.float64)
+    ns = len(shifts)
+    s0 = float(shifts.min())
+    d = shifts - s0
+    bn = norm(b)
+    xs = np.zeros((ns,) + b.shape, dtype=np.complex128)
+    ps = np.repeat(b[None].astype(np.complex128), ns, axis=0)
+    r = b.astype(np.complex128).copy()
+    rr = dot(r, r).real
+    zeta = np.ones(ns)
+    zeta_prev = np.ones(ns)
+    a_prev, b_prev = 1.0, 0.0
+    active = np.ones(ns, dtype=bool)
+    base = int(np.argmin(shifts))
+    it = 0
+    while it < maxiter and active.any() and bn > 0:
+        w = apply(ps[base]) + s0 * ps[base]
+        a = rr / dot(ps[base], w).real
+        zeta_new = np.empty(ns)
+        for i in range(ns):
+            den = a * b_prev * (zeta_prev[i] - zeta[i]) + zeta_prev[i] * a_prev * (1.0 + d[i] * a)
+            zeta_new[i] = zeta[i] * zeta_prev[i] * a_prev / den if den != 0 else 0.0
+            if active[i]:
+                xs[i] += (a * zeta_new[i] / zeta[i]) * ps[i]
+        r = r - a * w
+        rr_new = dot(r, r).real
+        beta = rr_new / rr
+        for i in range(ns):
+            bi = beta * (zeta_new[i] / zeta[i]) ** 2 if zeta[i] != 0 else 0.0
+            ps[i] = zeta_new[i] * r + bi * ps[i]
+        zeta_prev, zeta = zeta, zeta_new
+        a_prev, b_prev, rr = a, beta, rr_new
+        it += 1
+        active &= np.abs(zeta) * np.sqrt(rr) > tol * bn
+    res = [norm(b - (apply(xs[i]) + shifts[i] * xs[i])) / bn if bn > 0 else 0.0 for i in range(ns)]
+    return xs, it, res
+
+
+def staggered_multishift(op, b, masses, tol: float = 1e-10, maxiter: int = 10000):
+    """M(m_i) x_i = b for several masses with one Krylov space (the paper's
+    multi-shift CG for the heavier masses of a propagator workflow, Sec. 4):
+    M(m) = m + D with D anti-Hermitian is normal, M(m)^dag M(m) = m^2 + D^dag D,
+    so CG on (D^dag D + m_i^2) y_i = b with shifts m_i^2, then x_i = M(m_i)^dag y_i
+    = m_i y_i - D y_i.  `op` supplies D (its own mass is not used).
+    Returns (xs, iterations, residuals ||b - M(m_i) x_i|| / ||b||)."""
+    ys, it, _ = multishift_cg(lambda v: -op.D(op.D(v)), b, [m * m for m in masses], tol, maxiter)
+    xs = np.stack([m * y - op.D(y) for m, y in zip(masses, ys)])
+    bn = norm(b)
+    res = [norm(b - (m * x + op.D(x))) / bn for m, x in zip(masses, xs)]
+    return xs, it, res

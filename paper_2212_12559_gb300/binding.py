@@ -28,7 +28,7 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
            "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc",
-           "smg_bench_coarse_apply"]
+           "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators"]
 
 
 class MGParams(ctypes.Structure):
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
         "smg_mg_setup": (i, [vp, ctypes.POINTER(MGParams), ctypes.POINTER(vp), i]),
         "smg_solve": (i, [vp, vp, vp, d, i, ctypes.POINTER(SolveInfo)]),
         "smg_multi_solve": (i, [vp, i, vp, i, ctypes.POINTER(d), vp, d, i, ctypes.POINTER(SolveInfo)]),
+        "smg_multishift_cg": (i, [vp, vp, i, ctypes.POINTER(d), vp, d, i, i, ctypes.POINTER(SolveInfo)]),
+        "smg_propagators": (i, [vp, vp, i, ctypes.POINTER(d), i, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
         "smg_apply_fine": (i, [vp, i, i, i, vp, vp, i]),
         "smg_get_maps": (i, [vp, ip, ip, ip, ip, ip, ip, i]),
         "smg_get_kd_inverse": (i, [vp, vp, i]),
@@ -227,6 +229,35 @@ class Solver:
         mp = masses.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self._check(self.lib.smg_multi_solve(self.ctx, nrhs, pb, nshift, mp, px, float(tol), where, infos),
                     allow=(-5,))
+        return x, list(infos)
+
+    def multishift_cg(self, b, masses, tol=1e-10, maxiter=10000):
+        """M(m_i) x_i = b for every mass with one multi-shift CG; b: (V, 3);
+        returns x: (nshift, V, 3) and a list of infos."""
+        b = _prep(b)
+        masses = np.ascontiguousarray(masses, dtype=np.float64)
+        x = _like(b, (masses.size,) + tuple(b.shape))
+        pb, where = _ptr(b)
+        px, _ = _ptr(x)
+        infos = (SolveInfo * masses.size)()
+        mp = masses.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(self.lib.smg_multishift_cg(self.ctx, pb, masses.size, mp, px, float(tol), int(maxiter), where,
+                                               infos), allow=(-5,))
+        return x, list(infos)
+
+    def propagators(self, b, masses, n_mg, tol=1e-10, cg_maxiter=10000):
+        """The workflow split: the n_mg lightest masses by MG, the rest by
+        multi-shift CG; b: (V, 3); returns x: (nmass, V, 3) in the order of
+        `masses` and a list of infos."""
+        b = _prep(b)
+        masses = np.ascontiguousarray(masses, dtype=np.float64)
+        x = _like(b, (masses.size,) + tuple(b.shape))
+        pb, where = _ptr(b)
+        px, _ = _ptr(x)
+        infos = (SolveInfo * masses.size)()
+        mp = masses.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(self.lib.smg_propagators(self.ctx, pb, masses.size, mp, int(n_mg), px, float(tol),
+                                             int(cg_maxiter), where, infos), allow=(-5,))
         return x, list(infos)
 
     # -- hooks -------------------------------------------------------------------

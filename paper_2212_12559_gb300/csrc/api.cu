@@ -156,6 +156,27 @@ int smg_multi_solve(smg_ctx* ctx, int nrhs, const void* b, int nshift, const dou
   });
 }
 
+int smg_multishift_cg(smg_ctx* ctx, const void* b, int nshift, const double* masses, void* x, double tol, int maxiter,
+                      int where, smg_solve_info* info) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(b != nullptr && x != nullptr && masses != nullptr && valid_where(where),
+                "multishift_cg: null buffer or bad `where`");
+    if (!c.gauge_set) throw smg::StateError("multishift_cg needs set_gauge first");
+    return smg::ctx_multishift_cg(c, b, nshift, masses, x, tol, maxiter, where, info);
+  });
+}
+
+int smg_propagators(smg_ctx* ctx, const void* b, int nmass, const double* masses, int n_mg, void* x, double tol,
+                    int cg_maxiter, int where, smg_solve_info* info) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(b != nullptr && x != nullptr && masses != nullptr && valid_where(where),
+                "propagators: null buffer or bad `where`");
+    if (!c.gauge_set) throw smg::StateError("propagators needs set_gauge first");
+    if (n_mg > 0 && !c.setup_done) throw smg::StateError("propagators: MG masses need mg_setup first");
+    return smg::ctx_propagators(c, b, nmass, masses, n_mg, x, tol, cg_maxiter, where, info);
+  });
+}
+
 int smg_apply_fine(smg_ctx* ctx, int op, int prec, int nsys, const void* in, void* out, int where) {
   return guarded(ctx, [&](smg::Context& c) {
     SMG_REQUIRE(in != nullptr && out != nullptr && valid_where(where), "apply_fine: null buffer or bad `where`");

@@ -399,6 +399,28 @@ unsigned grid_for(long long n) {
 
 }  // namespace
 
+// Multi-shift CG step for shift s (coef = [alpha | zeta | beta] per shift,
+// real): x[s] += alpha[s] p[s] (skipped when alpha is 0), then
+// p[s] = zeta[s] r + beta[s] p[s] with one base residual r for every shift.
+__global__ void shift_update_kernel(double2* __restrict__ x, double2* __restrict__ p, const double2* __restrict__ r,
+                                    const double* __restrict__ coef, int nshift, long long n) {
+  const int s = blockIdx.y;
+  const double a = coef[s], z = coef[nshift + s], b = coef[2 * nshift + s];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)s * n + i;
+    const double2 pv = p[o];
+    if (a != 0.0) {
+      double2 xv = x[o];
+      xv.x = fma(a, pv.x, xv.x);
+      xv.y = fma(a, pv.y, xv.y);
+      x[o] = xv;
+    }
+    const double2 rv = r[i];
+    p[o] = make_double2(fma(z, rv.x, b * pv.x), fma(z, rv.y, b * pv.y));
+  }
+}
+
 // ------------------------------------------------------------------- host API
 void blas_copy(const Vec& dst, const Vec& src, cudaStream_t st, const int* run) {
   SMG_REQUIRE(dst.n == src.n && dst.nsys == src.nsys, "copy: shape mismatch");
@@ -527,6 +549,16 @@ void* Workspace::get(size_t bytes) {
 Workspace::~Workspace() {
   if (ptr) cudaFree(ptr);
   if (counter) cudaFree(counter);
+}
+
+void blas_shift_update(const Vec& X, const Vec& P, const Vec& r, const double* coef, cudaStream_t st) {
+  SMG_REQUIRE(X.prec == P64 && P.prec == P64 && r.prec == P64 && X.n == r.n && P.n == r.n && X.nsys == P.nsys &&
+                  r.nsys == 1,
+              "shift_update: FP64 batch with one base residual");
+  dim3 grid(grid_for(r.n), X.nsys);
+  launch_k(shift_update_kernel, grid, dim3(kThreads), 0, st, (double2*)X.p, (double2*)P.p, (const double2*)r.p, coef,
+           X.nsys, r.n);
+  SMG_LAUNCH_OK();
 }
 
 }  // namespace smg

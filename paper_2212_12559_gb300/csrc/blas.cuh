@@ -81,4 +81,7 @@ void blas_gcr_update(const Vec* W, int k, const double2* c, int ldc, const doubl
 void blas_gcr_finish(const Vec& x, const Vec* Z, int K, const double2* alpha, const double2* gamma,
                      const double2* beta, const int* nk, cudaStream_t st, const int* run);
 
+// Multi-shift CG update (FP64): X[s] += coef[s] P[s]; P[s] = coef[nshift+s] r + coef[2 nshift+s] P[s]
+void blas_shift_update(const Vec& X, const Vec& P, const Vec& r, const double* coef, cudaStream_t st);
+
 }  // namespace smg

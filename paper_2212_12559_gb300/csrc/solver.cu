@@ -16,6 +16,7 @@
 // No pre-smoothing (Table 1).  Inner loops launch a fixed kernel sequence;
 // a device flag per loop makes the remaining launches return at once after
 // convergence, so no host synchronisation happens inside K_0.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -1101,6 +1102,176 @@ int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* mas
     }
   }
   return all ? SMG_OK : SMG_ERR_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------- multi-shift CG
+// M(m_i) x_i = b for several masses in one Krylov space (Sec. 4, the
+// propagator workflow's multi-shift CG): CG on the base system
+// M(m_0)^dag M(m_0) = m_0^2 + D^dag D with m_0 the lightest mass (one dslash
+// pair per iteration), shift i = m_i^2 - m_0^2 carried by the scalar zeta_i
+// of the three-term Lanczos recurrence (Jegerlehner 1996); then
+// x_i = M(m_i)^dag y_i.  FP64 on the full operator.  The scalar recurrences run
+// on the host from two device reductions per iteration; a shift stops moving
+// once |zeta_i| ||r|| <= tol ||b|| / 2 (margin for the recomputed residual).
+int ctx_multishift_cg(Context& c, const void* b, int nshift, const double* masses, void* x, double tol, int maxiter,
+                      int where, smg_solve_info* info) {
+  SMG_REQUIRE(c.gauge_set, "multishift_cg needs set_gauge first");
+  SMG_REQUIRE(nshift >= 1 && nshift <= 64, "multishift_cg: 1 <= nshift <= 64");
+  SMG_REQUIRE(tol > 0 && tol < 1 && maxiter >= 1, "multishift_cg: tol in (0, 1), maxiter >= 1");
+  std::vector<double> ms(masses, masses + nshift);
+  for (double m : ms) SMG_REQUIRE(std::isfinite(m) && m > 0, "multishift_cg: masses must be positive");
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = c.stream;
+  const long long n = (long long)c.g.V * 3;
+  const size_t vb = (size_t)n * sizeof(double2);
+  DevBuf buf;
+  buf.alloc(vb * (4 + 2 * (size_t)nshift));
+  auto vec = [&](size_t slot, int nsys) {
+    Vec v; v.p = (char*)buf.p + vb * slot; v.n = n; v.nsys = nsys; v.prec = P64;
+    return v;
+  };
+  Vec bb = vec(0, 1), r = vec(1, 1), t = vec(2, 1), w = vec(3, 1);
+  Vec X = vec(4, nshift), P = vec(4 + (size_t)nshift, nshift);
+  // reduction outputs (nshift + 8 entries; entry 4 holds -alpha during the
+  // iteration), then coef[3][nshift] and the masses
+  const size_t nred = (size_t)nshift + 8;
+  DevBuf sc;
+  sc.alloc(sizeof(double2) * nred + sizeof(double) * 4 * (size_t)nshift);
+  double2* red = sc.as<double2>();
+  double* coef = (double*)((char*)sc.p + sizeof(double2) * nred);
+  double* mdev = coef + 3 * (size_t)nshift;
+  upload(bb.p, b, vb, where, st);
+  SMG_CUDA_OK(cudaMemcpyAsync(r.p, bb.p, vb, cudaMemcpyDeviceToDevice, st));
+  for (int i = 0; i < nshift; ++i) SMG_CUDA_OK(cudaMemcpyAsync(P.sys(i), bb.p, vb, cudaMemcpyDeviceToDevice, st));
+  SMG_CUDA_OK(cudaMemsetAsync(X.p, 0, vb * nshift, st));
+  const int p00[1] = {0};
+  auto dot1 = [&](const Vec& a, const Vec& bv) {
+    Vec vv[2] = {a, bv};
+    const int pj[1] = {1};
+    blas_pair_dots(vv, 2, p00, pj, 1, red, 1, c.ws, st);
+    double2 h;
+    SMG_CUDA_OK(cudaMemcpyAsync(&h, red, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    SMG_CUDA_OK(cudaStreamSynchronize(st));
+    return h.x;
+  };
+  int base = 0;
+  for (int i = 1; i < nshift; ++i) if (ms[i] < ms[base]) base = i;
+  const double mb = ms[base];
+  DslashParams dp;
+  dp.g = c.g;
+  c.link_params(S64, dp);
+  dp.nsys = 1;
+  dp.mass0 = mb;
+  double rr = dot1(r, r);
+  const double bn = std::sqrt(rr);
+  std::vector<double> zeta(nshift, 1.0), zprev(nshift, 1.0), zn(nshift), hcoef(3 * (size_t)nshift);
+  std::vector<char> active(nshift, bn > 0 ? 1 : 0);
+  double a_prev = 1.0, b_prev = 0.0;
+  int it = 0;
+  auto any_active = [&]() { for (char a : active) if (a) return true; return false; };
+  while (it < maxiter && any_active()) {
+    Vec pb = P; pb.p = P.sys(base); pb.nsys = 1;
+    dp.dagger = 0;
+    dslash(t, pb, dp, st);
+    dp.dagger = 1;
+    dslash(w, t, dp, st);                        // w = (m_0^2 + D^dag D) p_0
+    const double pw = dot1(pb, w);
+    SMG_REQUIRE(pw > 0 && std::isfinite(pw), "multishift_cg: breakdown (p^dag A p <= 0)");
+    const double a = rr / pw;
+    for (int i = 0; i < nshift; ++i) {
+      const double d = ms[i] * ms[i] - mb * mb;
+      const double den = a * b_prev * (zprev[i] - zeta[i]) + zprev[i] * a_prev * (1.0 + d * a);
+      zn[i] = den != 0.0 ? zeta[i] * zprev[i] * a_prev / den : 0.0;
+      hcoef[i] = (active[i] && zeta[i] != 0.0) ? a * zn[i] / zeta[i] : 0.0;
+    }
+    const double2 na = make_double2(-a, 0.0);
+    SMG_CUDA_OK(cudaMemcpyAsync(red + 4, &na, sizeof(double2), cudaMemcpyHostToDevice, st));
+    blas_maxpy(r, &w, 1, red + 4, 1, 1.0, true, st);   // r -= a w
+    const double rr_new = dot1(r, r);
+    const double beta = rr_new / rr;
+    for (int i = 0; i < nshift; ++i) {
+      hcoef[nshift + i] = zn[i];
+      hcoef[2 * nshift + i] = zeta[i] != 0.0 ? beta * (zn[i] / zeta[i]) * (zn[i] / zeta[i]) : 0.0;
+    }
+    SMG_CUDA_OK(cudaMemcpyAsync(coef, hcoef.data(), sizeof(double) * 3 * nshift, cudaMemcpyHostToDevice, st));
+    blas_shift_update(X, P, r, coef, st);
+    zprev = zeta;
+    zeta = zn;
+    a_prev = a;
+    b_prev = beta;
+    rr = rr_new;
+    ++it;
+    for (int i = 0; i < nshift; ++i)
+      if (active[i] && !(std::fabs(zeta[i]) * std::sqrt(rr) > 0.5 * tol * bn)) active[i] = 0;
+  }
+  // x_i = M(m_i)^dag y_i into P, then b - M(m_i) x_i into X for the residuals
+  SMG_CUDA_OK(cudaMemcpyAsync(mdev, ms.data(), sizeof(double) * nshift, cudaMemcpyHostToDevice, st));
+  DslashParams q = dp;
+  q.nsys = nshift;
+  q.mass = mdev;
+  q.dagger = 1;
+  dslash(P, X, q, st);
+  for (int i = 0; i < nshift; ++i) SMG_CUDA_OK(cudaMemcpyAsync(X.sys(i), bb.p, vb, cudaMemcpyDeviceToDevice, st));
+  q.dagger = 0;
+  q.sub_from = X.p;
+  dslash(X, P, q, st);
+  blas_pair_dots(&X, 1, p00, p00, 1, red, 1, c.ws, st);
+  std::vector<double2> rn(nshift);
+  SMG_CUDA_OK(cudaMemcpyAsync(rn.data(), red, sizeof(double2) * nshift, cudaMemcpyDeviceToHost, st));
+  download(x, P.p, vb * nshift, where, st);
+  SMG_CUDA_OK(cudaStreamSynchronize(st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  bool all = true;
+  for (int i = 0; i < nshift; ++i) {
+    const double res = bn > 0 ? std::sqrt(std::fmax(rn[i].x, 0.0)) / bn : 0.0;
+    const bool conv = res <= tol;
+    all = all && conv;
+    if (info) {
+      info[i].converged = conv ? 1 : 0;
+      info[i].iterations = it;
+      info[i].restarts = 0;
+      info[i].true_residual = res;
+      info[i].seconds = secs;
+    }
+  }
+  return all ? SMG_OK : SMG_ERR_NOT_CONVERGED;
+}
+
+// The propagator workflow's split (Sec. 4): the n_mg lightest masses by the
+// MG solver of the current setup (coarse operators of the setup mass
+// reused), the others by multi-shift CG.
+int ctx_propagators(Context& c, const void* b, int nmass, const double* masses, int n_mg, void* x, double tol,
+                    int cg_maxiter, int where, smg_solve_info* info) {
+  SMG_REQUIRE(nmass >= 1 && nmass <= 64 && n_mg >= 0 && n_mg <= nmass, "propagators: 0 <= n_mg <= nmass <= 64");
+  SMG_REQUIRE(n_mg == 0 || c.setup_done, "propagators: MG masses need mg_setup first");
+  std::vector<int> order(nmass);
+  for (int i = 0; i < nmass; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return masses[i] < masses[j]; });
+  const long long n = (long long)c.g.V * 3;
+  const size_t vb = (size_t)n * sizeof(double2);
+  DevBuf bd, xd;
+  bd.alloc(vb);
+  xd.alloc(vb * (size_t)nmass);
+  upload(bd.p, b, vb, where, c.stream);
+  std::vector<smg_solve_info> inf(nmass);
+  int rc_mg = SMG_OK, rc_cg = SMG_OK;
+  if (n_mg > 0) {
+    std::vector<double> ml(n_mg);
+    for (int k = 0; k < n_mg; ++k) ml[k] = masses[order[k]];
+    rc_mg = ctx_solve(c, 1, bd.p, n_mg, ml.data(), xd.p, tol, SMG_DEVICE, inf.data());
+  }
+  if (n_mg < nmass) {
+    std::vector<double> mh(nmass - n_mg);
+    for (int k = n_mg; k < nmass; ++k) mh[k - n_mg] = masses[order[k]];
+    rc_cg = ctx_multishift_cg(c, bd.p, nmass - n_mg, mh.data(), (char*)xd.p + vb * n_mg, tol, cg_maxiter,
+                              SMG_DEVICE, inf.data() + n_mg);
+  }
+  for (int k = 0; k < nmass; ++k) {
+    download((char*)x + vb * order[k], (char*)xd.p + vb * k, vb, where, c.stream);
+    if (info) info[order[k]] = inf[k];
+  }
+  SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+  return (rc_mg == SMG_OK && rc_cg == SMG_OK) ? SMG_OK : SMG_ERR_NOT_CONVERGED;
 }
 
 // ---------------------------------------------------------------- test hooks

@@ -133,6 +133,10 @@ struct Context {
 void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik, int where);
 void ctx_set_mass(Context& c, double m);
 void ctx_mg_setup(Context& c, const smg_mg_params& p, const void* const* phi0, int where);
+int ctx_multishift_cg(Context& c, const void* b, int nshift, const double* masses, void* x, double tol, int maxiter,
+                      int where, smg_solve_info* info);
+int ctx_propagators(Context& c, const void* b, int nmass, const double* masses, int n_mg, void* x, double tol,
+                    int cg_maxiter, int where, smg_solve_info* info);
 int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* masses, void* x, double tol, int where,
               smg_solve_info* info);
 void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void* out, int where);

@@ -271,3 +271,45 @@ def test_truncated_coarse_operator(binding):
         ref[:, :, 1 + 2 * mu, :] = S.Yf[mu]
         ref[:, :, 2 + 2 * mu, :] = S.Yb[mu]
     assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_multishift_cg(binding):
+    """Sec. 4's multi-shift CG: every mass of an unsorted list is solved to
+    1e-10 on the full HISQ-shaped M (recomputed by the oracle) and matches the
+    dense solution; the shared iteration count follows the oracle's
+    multi-shift CG run to the same stopping rule."""
+    from oracle.solvers import staggered_multishift
+    dims = (8, 4, 4, 4)
+    fat, naik, c, op = problem(dims, True, 0.1, seed=1021)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    b = inputs.gaussian_field(op.lat.V, 3, 2021)
+    masses = [0.4, 0.05, 0.1, 0.2]
+    x, infos = s.multishift_cg(b, masses, 1e-10)
+    for m, xi, inf in zip(masses, x, infos):
+        assert inf.converged == 1 and inf.true_residual <= 1e-10
+        op_m = Staggered(op.lat, fat, naik, c, m)
+        check_solution(op_m, b, xi, dense_solution(op_m, b), 1e-13)
+    _, it_ref, res_ref = staggered_multishift(op, b, masses, tol=0.5e-10)
+    assert max(res_ref) <= 1e-10
+    assert abs(infos[0].iterations - it_ref) <= 2, (infos[0].iterations, it_ref)
+
+
+def test_propagator_split(binding):
+    """The workflow split of Sec. 4: the two lightest masses by MG (setup at
+    the lightest mass, coarse operators reused), the rest by multi-shift CG;
+    every result in the caller's mass order solves its own M to 1e-10."""
+    dims = (8, 4, 4, 4)
+    fat, naik, c, op = problem(dims, True, 0.02, seed=1022)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(0.02)
+    s.mg_setup(binding.default_params(nvec=[4], setup_maxiter=50, precision=binding.PREC_HALF),
+               [inputs.gaussian_fields(4, op.lat.V, 3, 3022)])
+    b = inputs.gaussian_field(op.lat.V, 3, 2022)
+    masses = [0.2, 0.02, 0.1, 0.03, 0.4, 0.05]
+    x, infos = s.propagators(b, masses, n_mg=2)
+    for m, xi, inf in zip(masses, x, infos):
+        assert inf.converged == 1 and inf.true_residual <= 1e-10, (m, inf.true_residual)
+        op_m = Staggered(op.lat, fat, naik, c, m)
+        check_solution(op_m, b, xi, dense_solution(op_m, b), 1e-13)
