@@ -183,3 +183,47 @@ def staggered_multishift(op, b, masses, tol: float = 1e-10, maxiter: int = 10000
     bn = norm(b)
     res = [norm(b - (m * x + op.D(x))) / bn for m, x in zip(masses, xs)]
     return xs, it, res
+
+
+def chebyshev_basis(apply, r, s: int, lmin: float, lmax: float):
+    """q_k = T_k((A - c)/h) r for k < s by the three-term recurrence of the
+    Chebyshev polynomials, c = (lmax + lmin)/2, h = (lmax - lmin)/2."""
+    c = 0.5 * (lmax + lmin)
+    h = 0.5 * (lmax - lmin)
+    Q = [r]
+    if s > 1:
+        Q.append((apply(r) - c * r) / h)
+    while len(Q) < s:
+        Q.append(2.0 * (apply(Q[-1]) - c * Q[-1]) / h - Q[-2])
+    return Q
+
+
+def ca_gcr_chebyshev(apply, r, s: int, lmin: float, lmax: float):
+    """CA-GCR(s) with a Chebyshev basis (Table 1, coarsest level): the basis
+    q_0 = r, q_1 = T q_0, q_{k+1} = 2 T q_k - q_{k-1} with T = (A - c)/h,
+    c = (lmax + lmin)/2, h = (lmax - lmin)/2, spans the same Krylov space
+    K_s(A, r) as the power basis but stays far better conditioned when the
+    spectrum lies near [lmin, lmax]; the correction is the minimum-residual
+    combination sum_k a_k q_k over that space (one least-squares solve)."""
+    Q = chebyshev_basis(apply, r, s, lmin, lmax)
+    W = np.stack([apply(q).ravel() for q in Q], axis=1)
+    a, *_ = np.linalg.lstsq(W, r.ravel(), rcond=None)
+    return sum(ak * q for ak, q in zip(a, Q))
+
+
+def lowest_singular_triplets(dense, k: int):
+    """The k smallest singular values of a (small) dense operator with their
+    left (U) and right (V) singular vectors: A V = U diag(sigma)."""
+    U, sig, Vh = np.linalg.svd(dense)
+    idx = np.argsort(sig)[:k]
+    return U[:, idx], sig[idx], Vh[idx].conj().T
+
+
+def svd_deflated_gcr(apply, b, U, sigma, V, tol=1e-10, maxiter=1000, nkrylov=16):
+    """GCR from the deflated start x0 = V diag(1/sigma) U^dag b (Table 1's
+    SVD-deflated coarsest solve): the residual b - A x0 = (1 - U U^dag) b has
+    no component along the deflated left singular vectors, which removes the
+    slowest directions before the iteration starts.  Fields are flattened."""
+    shape = b.shape
+    x0 = (V @ ((U.conj().T @ b.ravel()) / sigma)).reshape(shape)
+    return gcr(apply, b, x0=x0, tol=tol, maxiter=maxiter, nkrylov=nkrylov)

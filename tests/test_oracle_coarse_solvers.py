@@ -1,0 +1,148 @@
+"""Pins of the oracle's coarse-level solver forms of Table 1 (levels 2 and 3):
+the block-preconditioned and Schur (even/odd) coarse operators, the
+Chebyshev-basis CA-GCR and the SVD-deflated coarsest solve.
+
+* X^{-1} A_hat applied matrix-free equals the dense product; its even-even
+  and odd-odd blocks are identities (every coarse hop changes parity).
+* The matrix-free Schur operator equals 1 - A'_eo A'_oe built from the dense
+  blocks, and the Schur solve with reconstruction reproduces the dense
+  solution of A_hat x = b.
+* The Chebyshev basis vectors equal T_k((A - c)/h) r evaluated from the
+  polynomials' power-series coefficients (numpy.polynomial), not the
+  recurrence; Chebyshev-basis CA-GCR(s) spans K_s(A, r): its residual equals
+  the minimum over an Arnoldi basis, and for small s the power-basis result.
+* The deflated start leaves no residual along the deflated left singular
+  vectors (exact identity), is the exact solution when every triplet is
+  deflated, and the deflated GCR reaches the dense solution.
+"""
+import numpy as np
+import pytest
+
+from oracle.coarse import FineLevelOp, Transfer, galerkin
+from oracle.dirac import KahlerDirac, Staggered
+from oracle.lattice import Lattice
+from oracle.schur import SchurCoarse
+from oracle.solvers import (ca_gcr, ca_gcr_chebyshev, chebyshev_basis, gcr, lowest_singular_triplets,
+                            svd_deflated_gcr)
+from paper_2212_12559_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def coarse():
+    """Galerkin operator of an 8^4 HISQ-shaped KD operator on 4^4 aggregates
+    (coarse lattice 2^4, N = 8)."""
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims)
+    thin = inputs.random_su3_links(dims, 41)
+    op = Staggered(lat, inputs.fat_links(thin, dims), inputs.naik_links(thin, dims), -1 / 24, 0.1)
+    lop = FineLevelOp(KahlerDirac(op))
+    T = Transfer(lat, 3, lop.chirality(), (4, 4, 4, 4), inputs.gaussian_fields(4, lat.V, 3, 42))
+    S = galerkin(lop, T)
+    return S, S.dense()
+
+
+def test_block_preconditioned_operator(coarse):
+    S, Ad = coarse
+    sc = SchurCoarse(S)
+    V, N = S.lat.V, S.n
+    Xd = np.zeros_like(Ad)
+    for x in range(V):
+        Xd[x * N:(x + 1) * N, x * N:(x + 1) * N] = S.X[x]
+    Bd = np.linalg.solve(Xd, Ad)                         # X^{-1} A_hat, dense
+    v = inputs.gaussian_field(V, N, 43)
+    np.testing.assert_allclose(sc.block_apply(v).ravel(), Bd @ v.ravel(), rtol=0, atol=1e-11 * np.abs(Bd).max())
+    ev = np.concatenate([np.arange(x * N, (x + 1) * N) for x in sc.even])
+    od = np.concatenate([np.arange(x * N, (x + 1) * N) for x in sc.odd])
+    assert np.allclose(Bd[np.ix_(ev, ev)], np.eye(len(ev)), atol=1e-12)
+    assert np.allclose(Bd[np.ix_(od, od)], np.eye(len(od)), atol=1e-12)
+
+
+def test_schur_operator_and_solve(coarse):
+    S, Ad = coarse
+    sc = SchurCoarse(S)
+    V, N = S.lat.V, S.n
+    Xd = np.zeros_like(Ad)
+    for x in range(V):
+        Xd[x * N:(x + 1) * N, x * N:(x + 1) * N] = S.X[x]
+    Bd = np.linalg.solve(Xd, Ad)
+    ev = np.concatenate([np.arange(x * N, (x + 1) * N) for x in sc.even])
+    od = np.concatenate([np.arange(x * N, (x + 1) * N) for x in sc.odd])
+    Sd = np.eye(len(ev)) - Bd[np.ix_(ev, od)] @ Bd[np.ix_(od, ev)]
+    ve = inputs.gaussian_field(len(sc.even), N, 44)
+    np.testing.assert_allclose(sc.schur_apply(ve).ravel(), Sd @ ve.ravel(), rtol=0,
+                               atol=1e-11 * np.abs(Sd).max())
+    b = inputs.gaussian_field(V, N, 45)
+    x = sc.solve(b, lambda apply, rhs: np.linalg.solve(Sd, rhs.ravel()).reshape(rhs.shape))
+    xs = np.linalg.solve(Ad, b.ravel())
+    assert np.linalg.norm(x.ravel() - xs) <= 1e-10 * np.linalg.norm(xs)
+    # the same through GCR on the Schur system (matrix-free)
+    x2 = sc.solve(b, lambda apply, rhs: gcr(apply, rhs, tol=1e-12, maxiter=400, nkrylov=64)[0])
+    assert np.linalg.norm(x2.ravel() - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def arnoldi_min_residual(Am, r, s):
+    Q = np.zeros((r.size, s), dtype=np.complex128)
+    Q[:, 0] = r / np.linalg.norm(r)
+    for j in range(1, s):
+        w = Am @ Q[:, j - 1]
+        for i in range(j):
+            w -= np.vdot(Q[:, i], w) * Q[:, i]
+        Q[:, j] = w / np.linalg.norm(w)
+    y, *_ = np.linalg.lstsq(Am @ Q, r, rcond=None)
+    return np.linalg.norm(r - Am @ (Q @ y))
+
+
+@pytest.mark.parametrize("s", [3, 6, 10])
+def test_chebyshev_ca_gcr_is_krylov_min_residual(coarse, s):
+    S, Ad = coarse
+    r = inputs.gaussian_field(S.lat.V, S.n, 46)
+    ev = np.linalg.eigvals(Ad)
+    lmin, lmax = float(ev.real.min()), float(ev.real.max())
+    apply = lambda v: (Ad @ v.ravel()).reshape(v.shape)
+    e = ca_gcr_chebyshev(apply, r, s, lmin, lmax).ravel()
+    got = np.linalg.norm(r.ravel() - Ad @ e)
+    best = arnoldi_min_residual(Ad, r.ravel(), s)
+    assert abs(got - best) <= 1e-9 * np.linalg.norm(r)
+    if s <= 6:
+        e_pow = ca_gcr(apply, r, s).ravel()
+        assert np.linalg.norm(e - e_pow) <= 1e-7 * np.linalg.norm(e_pow)
+
+
+def test_svd_deflation(coarse):
+    S, Ad = coarse
+    n = Ad.shape[0]
+    b = inputs.gaussian_field(S.lat.V, S.n, 47)
+    U, sig, V = lowest_singular_triplets(Ad, 16)
+    assert np.all(np.diff(sig) >= 0)
+    np.testing.assert_allclose(Ad @ V, U * sig, rtol=0, atol=1e-11 * np.abs(Ad).max())
+    x0 = (V @ ((U.conj().T @ b.ravel()) / sig))
+    r0 = b.ravel() - Ad @ x0
+    assert np.linalg.norm(U.conj().T @ r0) <= 1e-11 * np.linalg.norm(b)
+    Uall, sall, Vall = lowest_singular_triplets(Ad, n)
+    xfull = Vall @ ((Uall.conj().T @ b.ravel()) / sall)
+    xs = np.linalg.solve(Ad, b.ravel())
+    assert np.linalg.norm(xfull - xs) <= 1e-10 * np.linalg.norm(xs)
+    apply = lambda v: (Ad @ v.ravel()).reshape(v.shape)
+    x, it, res = svd_deflated_gcr(apply, b, U, sig, V, tol=1e-11, maxiter=500, nkrylov=64)
+    assert res <= 1e-11
+    assert np.linalg.norm(x.ravel() - xs) <= 1e-8 * np.linalg.norm(xs)
+    _, it_plain, _ = gcr(apply, b, tol=1e-11, maxiter=500, nkrylov=64)
+    assert it <= it_plain
+
+
+def test_chebyshev_basis_is_chebyshev_polynomials(coarse):
+    from numpy.polynomial import chebyshev as C
+    S, Ad = coarse
+    r = inputs.gaussian_field(S.lat.V, S.n, 48).ravel()
+    lmin, lmax = 0.05, 3.0
+    c, h = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    T = (Ad - c * np.eye(Ad.shape[0])) / h
+    Q = chebyshev_basis(lambda v: (Ad @ v.ravel()).reshape(v.shape), r, 7, lmin, lmax)
+    for k, q in enumerate(Q):
+        coef = C.cheb2poly([0] * k + [1])          # T_k as a power series
+        ref = np.zeros_like(r)
+        Tp = r.copy()
+        for a in coef:
+            ref += a * Tp
+            Tp = T @ Tp
+        assert np.linalg.norm(q - ref) <= 1e-9 * max(1.0, np.linalg.norm(ref))
