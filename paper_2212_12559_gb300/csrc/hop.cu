@@ -104,9 +104,10 @@ __device__ __forceinline__ void hop3(float2 (&acc)[3], const uint4 (&raw)[NCH], 
   }
 }
 
-// All loads of the hops of direction mu out of site x are issued before any
-// arithmetic (records of x, x - mu and x - 3mu; the neighbour spinors), so a
-// thread keeps ~11 16-byte and 12 8-byte loads in flight.
+// The hops of direction mu out of site x.  All their loads (the records of
+// x, x - mu and x - 3mu; the neighbour spinors) come first and are
+// independent of each other, so a thread has ~11 16-byte and 12 8-byte loads
+// available to be in flight together before its arithmetic.
 template <typename SL, int K>
 __device__ __forceinline__ void hop_dir_eager(float2 (&acc)[3], const uint4* __restrict__ base,
                                               const float2* __restrict__ vin, const Geom& g, int x, int mu,
@@ -130,7 +131,6 @@ __device__ __forceinline__ void hop_dir_eager(float2 (&acc)[3], const uint4* __r
       pb3[b] = vin[(size_t)xb3 * 3 + b];
     }
   }
-  asm volatile("" ::: "memory");   // keep every load above the arithmetic
   hop3<SL, NCH, false>(acc, own, 0, pf1, cf);
   hop3<SL, NCH, true>(acc, bf, 0, pb1, cf);
   if constexpr (K == 2) {
