@@ -108,6 +108,16 @@ class CoarseStencil:
         return out
 
 
+def block_preconditioned(S: CoarseStencil) -> CoarseStencil:
+    """X^{-1} A_hat as a 9-point stencil (Sec. 2.3, the block-preconditioned
+    coarse operator): identity self blocks, hops X(x)^{-1} Y_{+-mu}(x)."""
+    xinv = np.linalg.inv(S.X)
+    eye = np.broadcast_to(np.eye(S.n, dtype=np.complex128), S.X.shape).copy()
+    Yf = np.einsum("xij,mxjk->mxik", xinv, S.Yf)
+    Yb = np.einsum("xij,mxjk->mxik", xinv, S.Yb)
+    return CoarseStencil(S.lat, eye, Yf, Yb)
+
+
 def near_null_vectors(op, phi0, tol=1e-6, maxiter=2000):
     """CGNE on op.apply(phi) = 0 from each start phi0[k] (Table 1, Sec. 2.1).
 

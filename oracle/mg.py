@@ -24,6 +24,13 @@ level keeps the full M, so the truncation only changes the preconditioner
 (the outer GCR is flexible); B holds distance-one hops only, so (B+m)^{-1} is
 the same block inverse.  ``truncate_naik`` selects it.
 
+Sec. 2.3 generates the near-null vectors of each coarse level with its
+coarse operator A_hat and then coarsens the block-preconditioned operator
+X^{-1} A_hat (X the self blocks), the coarse analogue of the KD
+preconditioning of level 1.  ``block_coarse`` selects this: the level's GCR,
+smoother and Galerkin product use X^{-1} A_hat, the right-hand side handed
+down is X^{-1} R r, and the near-null CGNE runs on A_hat.
+
 Readings taken where the paper is silent: no pre-smoothing anywhere (Table 1
 lists none), "0.25 or 8 iterations" stops at whichever comes first, the
 coarse levels use the un-preconditioned Galerkin operator (the Schur form of
@@ -37,7 +44,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg
 
-from .coarse import FineLevelOp, Transfer, galerkin, near_null_vectors
+from .coarse import FineLevelOp, Transfer, block_preconditioned, galerkin, near_null_vectors
 from .dirac import KahlerDirac, Staggered
 from .lattice import Lattice
 from .solvers import ca_gcr, gcr
@@ -55,6 +62,7 @@ class MGParams:
     dense_max: int = 4096
     nkrylov: int = 16
     truncate_naik: bool = False
+    block_coarse: bool = False
 
 
 class MultigridSolver:
@@ -67,16 +75,25 @@ class MultigridSolver:
             op1 = Staggered(op.lat, op.fat, None, 0.0, op.mass)
         self.kd = KahlerDirac(op1)                # (B+m)^{-1}: distance-one hops only
         self.levels = [FineLevelOp(self.kd)]      # level 1 operator A (or A')
+        self.raw = [self.levels[0]]              # operator the near-null CGNE uses, per level
+        self.xinv = [None]                       # X^{-1} of each block-preconditioned level
         self.transfers = []
         self.setup_iters = []
         for l, (agg, nv) in enumerate(zip(params.agg, params.nvec)):
             lop = self.levels[-1]
-            vecs, its = near_null_vectors(lop, np.asarray(phi0[l]), params.setup_tol,
+            vecs, its = near_null_vectors(self.raw[-1], np.asarray(phi0[l]), params.setup_tol,
                                           params.setup_maxiter)
             self.setup_iters.append(its)
             T = Transfer(lop.lat, lop.n, lop.chirality(), agg, vecs)
             self.transfers.append(T)
-            self.levels.append(galerkin(lop, T))
+            S = galerkin(lop, T)
+            self.raw.append(S)
+            if params.block_coarse:
+                self.levels.append(block_preconditioned(S))
+                self.xinv.append(np.linalg.inv(S.X))
+            else:
+                self.levels.append(S)
+                self.xinv.append(None)
         coarsest = self.levels[-1]
         self.dense_lu = None
         if coarsest.lat.V * coarsest.n <= params.dense_max:
@@ -86,6 +103,8 @@ class MultigridSolver:
     def coarse_solve(self, l, rc):
         """Approximate solve on level l >= 2 (index into self.levels is l-1)."""
         lop = self.levels[l - 1]
+        if self.xinv[l - 1] is not None:          # X^{-1} A_hat e = X^{-1} rc
+            rc = np.einsum("xij,xj->xi", self.xinv[l - 1], rc)
         if l - 1 == len(self.levels) - 1:
             if self.dense_lu is not None:
                 x = scipy.linalg.lu_solve(self.dense_lu, rc.ravel())

@@ -146,3 +146,32 @@ def test_chebyshev_basis_is_chebyshev_polynomials(coarse):
             ref += a * Tp
             Tp = T @ Tp
         assert np.linalg.norm(q - ref) <= 1e-9 * max(1.0, np.linalg.norm(ref))
+
+
+def test_block_preconditioned_stencil(coarse):
+    """block_preconditioned(S) is the stencil of X^{-1} A_hat: identity self
+    blocks, and it applies like the matrix-free block-preconditioned operator."""
+    from oracle.coarse import block_preconditioned
+    S, _ = coarse
+    B = block_preconditioned(S)
+    assert np.allclose(B.X, np.eye(S.n)[None], atol=1e-13)
+    v = inputs.gaussian_field(S.lat.V, S.n, 49)
+    np.testing.assert_allclose(B.apply(v), SchurCoarse(S).block_apply(v), rtol=0, atol=1e-11)
+
+
+def test_block_coarse_three_level_solve():
+    """Sec. 2.3's coarsening of X^{-1} A_hat (near-null vectors from A_hat)
+    inside the K-cycle: the outer solve still reaches 1e-10 on M."""
+    from oracle.mg import MGParams, MultigridSolver
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims)
+    thin = inputs.random_su3_links(dims, 1002)
+    op = Staggered(lat, inputs.fat_links(thin, dims), inputs.naik_links(thin, dims), -1 / 24, 0.05)
+    p = MGParams(agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[4, 4], setup_maxiter=40, block_coarse=True)
+    phi0 = [inputs.gaussian_fields(4, lat.V, 3, 3002), inputs.gaussian_fields(4, 16, 8, 3003)]
+    mg = MultigridSolver(op, p, phi0)
+    assert np.allclose(mg.levels[1].X, np.eye(8)[None], atol=1e-12)
+    b = inputs.gaussian_field(lat.V, 3, 2002)
+    x, it, res = mg.solve(b, tol=1e-10)
+    assert res <= 1e-10
+    assert np.linalg.norm(b - op.M(x)) <= 1e-10 * np.linalg.norm(b)
