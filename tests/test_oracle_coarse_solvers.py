@@ -175,3 +175,25 @@ def test_block_coarse_three_level_solve():
     x, it, res = mg.solve(b, tol=1e-10)
     assert res <= 1e-10
     assert np.linalg.norm(b - op.M(x)) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_deflated_coarsest_in_kcycle():
+    """Table 1's coarsest solver inside the K-cycle (two levels, coarsest not
+    dense): the outer solve reaches 1e-10 on M, and one coarsest solve meets
+    the level's 0.25 rule or uses at most inner_maxiter CA-GCR steps."""
+    from oracle.mg import MGParams, MultigridSolver
+    from oracle.solvers import norm
+    dims = (8, 8, 4, 4)
+    lat = Lattice(dims)
+    thin = inputs.random_su3_links(dims, 1003)
+    op = Staggered(lat, thin, None, 0.0, 0.1)
+    p = MGParams(agg=[(4, 4, 4, 4)], nvec=[4], setup_maxiter=50, dense_max=0, coarsest_deflate=8,
+                 coarsest_cheb_s=8)
+    mg = MultigridSolver(op, p, [inputs.gaussian_fields(4, lat.V, 3, 3004)])
+    assert mg.dense_lu is None and mg.defl is not None
+    rc = inputs.gaussian_field(mg.levels[-1].lat.V, mg.levels[-1].n, 5)
+    x = mg.deflated_coarsest(mg.levels[-1], rc)
+    assert norm(rc - mg.levels[-1].apply(x)) < norm(rc)
+    b = inputs.gaussian_field(lat.V, 3, 2003)
+    xs, it, res = mg.solve(b, tol=1e-10)
+    assert res <= 1e-10
