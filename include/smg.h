@@ -219,6 +219,17 @@ SMG_API int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep,
  * context's stream).  Allocates and frees its own stencil and fields. */
 SMG_API int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int nsys, int prec, int nrep,
                                    double* ms_per_launch);
+/* Launch plan of the persistent coarse-level solver (host only, no device
+ * needed): a level of V sites with N components, nsys systems, nvec_next
+ * near-null vectors of the next level (0: coarsest, no restriction), storage
+ * SMG_PREC_SINGLE or SMG_PREC_HALF, on a device with `sms` SMs and `smem_cap`
+ * bytes of shared memory per block.  out: grid, rows per CTA, site slots per
+ * CTA, resident (1/0), systems per staging round, dynamic shared bytes, and
+ * the shared-memory offsets of the stencil rows, row scales, prolongator rows
+ * and staging area.  Returns SMG_ERR_ARG on a bad shape. */
+SMG_API int smg_persist_plan(int V, int N, int nsys, int nvec_next, int prec, int sms, long long smem_cap,
+                             long long out[10]);
+
 /* Total kernels launched by the library in this process (a CUDA-graph replay
  * counts every kernel node it runs). */
 SMG_API long long smg_kernel_launches(void);

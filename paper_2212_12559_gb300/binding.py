@@ -28,7 +28,7 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
            "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc",
-           "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators"]
+           "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators", "smg_persist_plan"]
 
 
 class MGParams(ctypes.Structure):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "smg_solve": (i, [vp, vp, vp, d, i, ctypes.POINTER(SolveInfo)]),
         "smg_multi_solve": (i, [vp, i, vp, i, ctypes.POINTER(d), vp, d, i, ctypes.POINTER(SolveInfo)]),
         "smg_multishift_cg": (i, [vp, vp, i, ctypes.POINTER(d), vp, d, i, i, ctypes.POINTER(SolveInfo)]),
+        "smg_persist_plan": (i, [i, i, i, i, i, i, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
         "smg_propagators": (i, [vp, vp, i, ctypes.POINTER(d), i, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
         "smg_apply_fine": (i, [vp, i, i, i, vp, vp, i]),
         "smg_get_maps": (i, [vp, ip, ip, ip, ip, ip, ip, i]),
@@ -115,6 +116,17 @@ def load(path: str = LIB_PATH):
 
 def kernel_launches() -> int:
     return int(load().smg_kernel_launches())
+
+
+def persist_plan(V, N, nsys, nvec_next, prec, sms, smem_cap):
+    """Launch plan of the persistent coarse solver (host only): dict of grid,
+    per, nslot, resident, sg, smem, off_S, off_sc, off_P, off_stg."""
+    out = (ctypes.c_longlong * 10)()
+    rc = load().smg_persist_plan(V, N, nsys, nvec_next, prec, sms, smem_cap, out)
+    if rc != 0:
+        raise SmgError(rc, "persist_plan: bad shape")
+    keys = ("grid", "per", "nslot", "resident", "sg", "smem", "off_S", "off_sc", "off_P", "off_stg")
+    return dict(zip(keys, list(out)))
 
 
 def default_params(**kw) -> MGParams:

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "persist.cuh"
 #include "solver.cuh"
 
 namespace smg {
@@ -46,6 +47,27 @@ bool valid_where(int w) { return w == SMG_HOST || w == SMG_DEVICE; }
 }  // namespace
 
 extern "C" {
+
+int smg_persist_plan(int V, int N, int nsys, int nvec_next, int prec, int sms, long long smem_cap, long long out[10]) {
+  if (out == nullptr || smem_cap <= 0 || (prec != SMG_PREC_SINGLE && prec != SMG_PREC_HALF)) return SMG_ERR_ARG;
+  try {
+    const smg::PersistPlan p = smg::persist_plan_for(V, N, nsys, nvec_next, prec == SMG_PREC_HALF ? smg::S16 : smg::S32,
+                                                      sms, (size_t)smem_cap);
+    out[0] = p.grid;
+    out[1] = p.per;
+    out[2] = p.nslot;
+    out[3] = p.resident;
+    out[4] = p.sg;
+    out[5] = (long long)p.smem;
+    out[6] = (long long)p.off_S;
+    out[7] = (long long)p.off_sc;
+    out[8] = (long long)p.off_P;
+    out[9] = (long long)p.off_stg;
+    return SMG_OK;
+  } catch (...) {
+    return SMG_ERR_ARG;
+  }
+}
 
 void smg_default_params(smg_mg_params* p) {
   if (!p) return;

@@ -927,9 +927,14 @@ bool persist_supported(int nsys, int K, int s, int N, long long n, Store st) {
 }
 
 PersistPlan persist_plan(const Geom& g, int N, int nsys, int nvec_next, Store st) {
+  return persist_plan_for(g.V, N, nsys, nvec_next, st, device_sms(), (size_t)smem_optin());
+}
+
+PersistPlan persist_plan_for(int V, int N, int nsys, int nvec_next, Store st, int sms, size_t cap) {
+  SMG_REQUIRE(V >= 1 && N >= 2 && nsys >= 1 && nvec_next >= 0 && sms >= 1, "persist plan: bad shape");
   PersistPlan p;
-  const long long n = (long long)g.V * N;
-  p.grid = std::min(device_sms(), g.V);
+  const long long n = (long long)V * N;
+  p.grid = std::min(sms, V);
   p.per = (n + p.grid - 1) / p.grid;
   p.nslot = (int)((p.per - 1 + N - 1) / N) + 1;
   const size_t sl = store_bytes(st);
@@ -943,7 +948,6 @@ PersistPlan persist_plan(const Geom& g, int N, int nsys, int nvec_next, Store st
     const size_t pres = nvec_next > 0 ? align16((size_t)p.per * nvec_next * sl) : 0;
     const size_t stage1 = (size_t)p.nslot * 9 * N * sizeof(float2);
     const size_t fixed = base + sres + scl + pres;
-    const size_t cap = (size_t)smem_optin();
     if (fixed + stage1 <= cap) {
       p.resident = 1;
       p.sg = (int)std::min<size_t>((size_t)nsys, (cap - fixed) / stage1);

@@ -61,6 +61,8 @@ const char* persist_phase_name(int id, bool has_pre);
 bool persist_supported(int nsys, int K, int s, int N, long long n, Store st);
 // nvec_next: null vectors of the next level (0 for the coarsest GCR level, no preconditioner)
 PersistPlan persist_plan(const Geom& g, int N, int nsys, int nvec_next, Store st);
+// The same for a device of `sms` SMs with `cap` bytes of shared memory per block (host only)
+PersistPlan persist_plan_for(int V, int N, int nsys, int nvec_next, Store st, int sms, size_t cap);
 // bytes of the device buffer behind partial, rpart and the barrier words
 size_t persist_buffer_bytes(const PersistPlan& p, int nvec_next);
 void persist_gcr(const PersistArgs& a, Store st, cudaStream_t stream);
