@@ -83,6 +83,12 @@ typedef struct smg_mg_params {
                                       A = (B+m)^{-1} M; 1 = truncated A' = (B+m)^{-1}(m + D_fat),
                                       the Naik hops dropped from the pseudo-fine operator only
                                       (Sec. 3.1); the outer GCR keeps the full M.  Default 0. */
+  int block_coarse;                /* Sec. 2.3: 1 = every coarse level uses the block-preconditioned
+                                      operator X^{-1} A_hat (X its self blocks) in its GCR, smoother
+                                      and the next Galerkin product, with the right-hand side
+                                      X^{-1} R r; the near-null CGNE runs on A_hat.  A dense
+                                      coarsest level is inverted from A_hat, which gives the same
+                                      solution.  Default 0 (un-preconditioned A_hat). */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */
@@ -174,8 +180,12 @@ SMG_API int smg_get_maps(smg_ctx* ctx, const int agg[4], int* parity, int* kd_bl
 SMG_API int smg_get_kd_inverse(smg_ctx* ctx, void* out, int where);
 /* Block-orthonormal near-null vectors of coarsening l: [nvec][sites][dof] FP64. */
 SMG_API int smg_get_null_vectors(smg_ctx* ctx, int l, void* out, int where);
-/* Coarse operator produced by coarsening l: [Vc][N][9][N] FP64 (Sec. 2.1). */
+/* Coarse operator produced by coarsening l, as the level uses it: A_hat, or
+ * X^{-1} A_hat with block_coarse; [Vc][N][9][N] FP64 (Sec. 2.1, 2.3). */
 SMG_API int smg_get_coarse_op(smg_ctx* ctx, int l, void* out, int where);
+/* X^{-1} of the self blocks of coarsening l's A_hat, [Vc][N][N] FP64 row-major
+ * (Sec. 2.3).  SMG_ERR_STATE unless the setup used block_coarse. */
+SMG_API int smg_get_coarse_xinv(smg_ctx* ctx, int l, void* out, int where);
 /* Restriction / prolongation of coarsening l and the coarse operator of
  * level l in precision `prec`, on nsys FP64 fields. */
 SMG_API int smg_restrict(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where);

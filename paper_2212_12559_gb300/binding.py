@@ -28,7 +28,8 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_apply_fine", "smg_get_maps", "smg_get_kd_inverse", "smg_get_null_vectors",
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
            "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc",
-           "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators", "smg_persist_plan"]
+           "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators", "smg_persist_plan",
+           "smg_get_coarse_xinv"]
 
 
 class MGParams(ctypes.Structure):
@@ -48,6 +49,7 @@ class MGParams(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("persistent", ctypes.c_int),
         ("truncate_naik", ctypes.c_int),
+        ("block_coarse", ctypes.c_int),
     ]
 
 
@@ -94,6 +96,7 @@ def load(path: str = LIB_PATH):
         "smg_get_kd_inverse": (i, [vp, vp, i]),
         "smg_get_null_vectors": (i, [vp, i, vp, i]),
         "smg_get_coarse_op": (i, [vp, i, vp, i]),
+        "smg_get_coarse_xinv": (i, [vp, i, vp, i]),
         "smg_restrict": (i, [vp, i, i, i, vp, vp, i]),
         "smg_prolong": (i, [vp, i, i, i, vp, vp, i]),
         "smg_coarse_apply": (i, [vp, i, i, i, vp, vp, i]),
@@ -314,6 +317,12 @@ class Solver:
         _, _, Vc, N = self._level_shape(l)
         out = np.empty((Vc, N, 9, N), dtype=np.complex128)
         self._check(self.lib.smg_get_coarse_op(self.ctx, l, ctypes.c_void_p(out.ctypes.data), SMG_HOST))
+        return out
+
+    def coarse_xinv(self, l):
+        _, _, Vc, N = self._level_shape(l)
+        out = np.empty((Vc, N, N), dtype=np.complex128)
+        self._check(self.lib.smg_get_coarse_xinv(self.ctx, l, ctypes.c_void_p(out.ctypes.data), SMG_HOST))
         return out
 
     def _xfer(self, fn, l, v, prec, out_shape):

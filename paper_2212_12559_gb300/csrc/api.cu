@@ -89,6 +89,7 @@ void smg_default_params(smg_mg_params* p) {
   p->use_graph = 0;
   p->persistent = 1;
   p->truncate_naik = 0;
+  p->block_coarse = 0;
 }
 
 int smg_create(const int dims[4], smg_ctx** out) {
@@ -255,6 +256,18 @@ int smg_get_coarse_op(smg_ctx* ctx, int l, void* out, int where) {
     if (!c.setup_done) throw smg::StateError("get_coarse_op needs mg_setup");
     SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "get_coarse_op: bad level");
     smg::download(out, c.coarse[l].S64.p, c.coarse[l].S64.bytes, where, c.stream);
+    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    return SMG_OK;
+  });
+}
+
+int smg_get_coarse_xinv(smg_ctx* ctx, int l, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(out != nullptr && valid_where(where), "get_coarse_xinv: null buffer");
+    if (!c.setup_done) throw smg::StateError("get_coarse_xinv needs mg_setup");
+    SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "get_coarse_xinv: bad level");
+    if (!c.coarse[l].block) throw smg::StateError("get_coarse_xinv needs a block_coarse setup");
+    smg::download(out, c.coarse[l].Xinv64.p, c.coarse[l].Xinv64.bytes, where, c.stream);
     SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
     return SMG_OK;
   });

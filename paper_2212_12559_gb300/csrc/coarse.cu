@@ -248,6 +248,123 @@ __global__ void gj_unpermute_kernel(double2* __restrict__ A, int n, const int* _
   }
 }
 
+// ------------------------------------------------ block-preconditioned stencil
+// X^{-1} A_hat (Sec. 2.3) by Gauss-Jordan elimination with partial pivoting
+// on the augmented rows [X | Y_1 .. Y_8 | 1] of one coarse site, one CTA per
+// site, in place in global memory.  A super-row of the stencil layout is an
+// augmented row without its identity part, which is kept in Xinv; the
+// elimination leaves [1 | X^{-1} Y_1 .. X^{-1} Y_8 | X^{-1}].  Row swaps act
+// on whole augmented rows, so no column unpermutation is needed.
+constexpr int kBlockPrecThreads = 256;
+
+__global__ void __launch_bounds__(kBlockPrecThreads) block_precondition_kernel(double2* __restrict__ S,
+                                                                               double2* __restrict__ Xinv, int N,
+                                                                               int* __restrict__ err) {
+  constexpr int NW = kBlockPrecThreads / 32;
+  __shared__ double bm[NW];
+  __shared__ int bi[NW];
+  __shared__ int prow;
+  __shared__ double2 ipiv;
+  extern __shared__ double2 fac[];          // elimination factors, N
+  const int t = threadIdx.x;
+  const int W = 10 * N;                     // augmented row length
+  double2* Sx = S + (size_t)blockIdx.x * N * 9 * N;
+  double2* Ix = Xinv + (size_t)blockIdx.x * N * N;
+  auto at = [&](int i, int j) -> double2& {
+    return j < 9 * N ? Sx[(size_t)i * 9 * N + j] : Ix[(size_t)i * N + (j - 9 * N)];
+  };
+  for (int e = t; e < N * N; e += kBlockPrecThreads) Ix[e] = make_double2(e / N == e % N ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    // pivot: the largest |X_ik| over rows i >= k (the first one on ties)
+    double best = -1.0;
+    int idx = k;
+    for (int i = k + t; i < N; i += kBlockPrecThreads) {
+      const double2 v = Sx[(size_t)i * 9 * N + k];
+      const double m2 = v.x * v.x + v.y * v.y;
+      if (m2 > best) { best = m2; idx = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, idx, o);
+      if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+    }
+    if ((t & 31) == 0) { bm[t >> 5] = best; bi[t >> 5] = idx; }
+    __syncthreads();
+    if (t == 0) {
+      double b = -1.0;
+      int p = k;
+      for (int w = 0; w < NW; ++w)
+        if (bm[w] > b || (bm[w] == b && bi[w] < p)) { b = bm[w]; p = bi[w]; }
+      prow = p;
+      const double2 pv = Sx[(size_t)p * 9 * N + k];
+      const double d = pv.x * pv.x + pv.y * pv.y;
+      if (d > 0.0) {
+        ipiv = make_double2(pv.x / d, -pv.y / d);
+      } else {
+        ipiv = make_double2(0.0, 0.0);
+        atomicExch(err, 1);                 // singular self block
+      }
+    }
+    __syncthreads();
+    const int p = prow;
+    if (p != k)
+      for (int j = t; j < W; j += kBlockPrecThreads) {
+        const double2 tmp = at(k, j);
+        at(k, j) = at(p, j);
+        at(p, j) = tmp;
+      }
+    __syncthreads();
+    const double2 ip = ipiv;
+    for (int j = t; j < W; j += kBlockPrecThreads) at(k, j) = (j == k) ? make_double2(1.0, 0.0) : cmul(at(k, j), ip);
+    for (int i = t; i < N; i += kBlockPrecThreads) fac[i] = (i == k) ? make_double2(0.0, 0.0) : at(i, k);
+    __syncthreads();
+    // eliminate column k from the other rows; the X columns j < k are unit
+    // columns already (row k is zero there), so the row update starts at k
+    const int Wk = W - k;
+    for (int e = t; e < N * Wk; e += kBlockPrecThreads) {
+      const int i = e / Wk, j = k + e % Wk;
+      if (i == k) continue;
+      const double2 f = fac[i];
+      if (j == k) { at(i, j) = make_double2(0.0, 0.0); continue; }
+      double2 v = at(i, j);
+      const double2 w = at(k, j);
+      v.x -= f.x * w.x - f.y * w.y;
+      v.y -= f.x * w.y + f.y * w.x;
+      at(i, j) = v;
+    }
+    __syncthreads();
+  }
+}
+
+// v[s](X) <- Xinv(X) v[s](X) in place, one CTA per (site, system): the site's
+// N entries are staged in shared memory, each warp takes rows with its lanes
+// on consecutive columns of X^{-1}.
+template <typename C>
+__global__ void __launch_bounds__(128) block_diag_kernel(C* __restrict__ v, const C* __restrict__ Xinv, int V, int N,
+                                                         const int* __restrict__ run) {
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ unsigned char bd_smem[];
+  C* vin = reinterpret_cast<C*>(bd_smem);
+  C* vx = v + ((size_t)blockIdx.y * V + blockIdx.x) * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) vin[j] = vx[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  const C* Xr = Xinv + (size_t)blockIdx.x * N * N;
+  for (int i = threadIdx.x >> 5; i < N; i += nw) {
+    C acc;
+    acc.x = 0;
+    acc.y = 0;
+    for (int j = lane; j < N; j += 32) cfma(acc, Xr[(size_t)i * N + j], vin[j]);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) vx[i] = acc;
+  }
+}
+
 template <typename R, typename DT>
 __global__ void __launch_bounds__(256) dense_apply_kernel(typename cplx<R>::T* __restrict__ out,
                                                           const typename cplx<R>::T* __restrict__ in,
@@ -560,6 +677,26 @@ void dense_invert(double2* Dn, int n, double2* fac, int* perm, cudaStream_t st) 
     gj_eliminate_kernel<<<grid_cap((long long)n * n, 256), 256, 0, st>>>(Dn, n, k, fac);
   }
   gj_unpermute_kernel<<<ceil_div(n, 128), 128, 0, st>>>(Dn, n, perm);
+  SMG_LAUNCH_OK();
+}
+
+void block_precondition(double2* S64, double2* Xinv, const Geom& g, int N, int* err, cudaStream_t st) {
+  SMG_REQUIRE(N >= 1 && N <= 256, "block_precondition: N out of range");
+  block_precondition_kernel<<<(unsigned)g.V, kBlockPrecThreads, sizeof(double2) * N, st>>>(S64, Xinv, N, err);
+  SMG_LAUNCH_OK();
+}
+
+void block_diag_apply(const Vec& v, const void* Xinv, Prec xprec, int N, cudaStream_t st, const int* run) {
+  SMG_REQUIRE(N >= 1 && N <= 1024 && v.n % N == 0 && v.nsys >= 1 && v.nsys <= 65535 && xprec == v.prec,
+              "block_diag_apply: shape or precision mismatch");
+  const int V = (int)(v.n / N);
+  const dim3 grid(V, v.nsys);
+  if (v.prec == P64)
+    launch_k(block_diag_kernel<double2>, grid, dim3(128), sizeof(double2) * N, st, (double2*)v.p,
+             (const double2*)Xinv, V, N, run);
+  else
+    launch_k(block_diag_kernel<float2>, grid, dim3(128), sizeof(float2) * N, st, (float2*)v.p,
+             (const float2*)Xinv, V, N, run);
   SMG_LAUNCH_OK();
 }
 

@@ -128,6 +128,13 @@ void galerkin_scatter(double2* S64, const double2* C, const Geom& g, int N, int 
 // Unit coarse probes: E[s][X][i] = (i == j0 + s)
 void unit_probes(double2* E, long long Vc, int N, int j0, int ncol, cudaStream_t st);
 
+// Block-preconditioned stencil X^{-1} A_hat (Sec. 2.3), in place on the FP64
+// stencil: self blocks become 1, hops X^{-1} Y_{+-mu}; X^{-1} goes to Xinv
+// [Vc][N][N].  Sets *err (device int) when a self block is singular.
+void block_precondition(double2* S64, double2* Xinv, const Geom& g, int N, int* err, cudaStream_t st);
+// v[s](X) <- Xinv(X) v[s](X) on a coarse batch; Xinv in v's precision
+void block_diag_apply(const Vec& v, const void* Xinv, Prec xprec, int N, cudaStream_t st, const int* run = nullptr);
+
 // ------------------------------------------------------- dense coarsest op
 void dense_from_stencil(double2* Dn, const double2* S64, const Geom& g, int N, cudaStream_t st);
 // In-place Gauss-Jordan inverse with partial pivoting (FP64); returns false if singular.

@@ -585,6 +585,9 @@ struct Engine {
     dbg("K.r", r);
     if (l == 1) pb("K1.restrict");
     restrict_op(lev[l + 1].b, r, C.tg, C.Ps.st, st(), run);
+    // X^{-1} A_hat e = X^{-1} R r on a block-preconditioned level (Sec. 2.3)
+    if (C.block && !C.dense)
+      block_diag_apply(lev[l + 1].b, vp == P64 ? C.Xinv64.p : C.Xinv32.p, vp, C.N, st(), run);
     if (l == 1) { pe(); pb("K1.coarse_solve"); }
     dbg("K.rc", lev[l + 1].b);
     coarse_solve(l + 1, run);
@@ -864,7 +867,9 @@ struct SetupOp {
       p.g = C.g; p.N = C.N;
       p.allow_tc = 0;   // near-null iterations keep FP32 inputs (CGNE's recursive residual would
                         // otherwise run below the FP16 input rounding)
-      coarse_apply(out, in, p, dagger ? C.Sdags.st : C.Ss.st, c.stream, run);
+      // the near-null CGNE runs on A_hat also when the level uses X^{-1} A_hat (Sec. 2.3)
+      const Stored& S = dagger ? C.Sdags.st : (C.block ? C.Sraws.st : C.Ss.st);
+      coarse_apply(out, in, p, S, c.stream, run);
     }
   }
 };
@@ -1024,21 +1029,47 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
     }
     C.Sdag64.alloc(C.S64.bytes);
     coarse_dagger(C.Sdag64.as<double2>(), C.S64.as<double2>(), cg, N, st);
+    // ---- block-preconditioned operator X^{-1} A_hat (Sec. 2.3): the level's GCR,
+    // smoother and the next Galerkin product use it, the near-null CGNE keeps A_hat
+    C.block = P.block_coarse != 0;
+    if (C.block) {
+      C.Sraw64.alloc(C.S64.bytes);
+      SMG_CUDA_OK(cudaMemcpyAsync(C.Sraw64.p, C.S64.p, C.S64.bytes, cudaMemcpyDeviceToDevice, st));
+      C.Xinv64.alloc((size_t)cg.V * N * N * sizeof(double2));
+      DevBuf eb;
+      eb.alloc(sizeof(int));
+      SMG_CUDA_OK(cudaMemsetAsync(eb.p, 0, sizeof(int), st));
+      block_precondition(C.S64.as<double2>(), C.Xinv64.as<double2>(), cg, N, eb.as<int>(), st);
+      int sing = 0;
+      SMG_CUDA_OK(cudaMemcpyAsync(&sing, eb.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SMG_CUDA_OK(cudaStreamSynchronize(st));
+      SMG_REQUIRE(!sing, "a coarse self block X is singular (block_coarse)");
+      C.Xinv32.alloc((size_t)cg.V * N * N * sizeof(float2));
+      Vec a; a.p = C.Xinv64.p; a.n = (long long)cg.V * N * N; a.prec = P64;
+      Vec b; b.p = C.Xinv32.p; b.n = a.n; b.prec = P32;
+      blas_copy(b, a, st);
+    }
     if (sp != S64) {
       C.Ss.alloc(sp, (size_t)nc * 9 * N, (size_t)nc);
       coarse_pack(C.Ss.st, C.S64.as<double2>(), cg, N, st);
       C.Sdags.alloc(sp, (size_t)nc * 9 * N, (size_t)nc);
       coarse_pack(C.Sdags.st, C.Sdag64.as<double2>(), cg, N, st);
+      if (C.block) {
+        C.Sraws.alloc(sp, (size_t)nc * 9 * N, (size_t)nc);
+        coarse_pack(C.Sraws.st, C.Sraw64.as<double2>(), cg, N, st);
+      }
     } else {
       C.Ss.st = Stored{C.S64.p, nullptr, 1.0f, S64};
       C.Sdags.st = Stored{C.Sdag64.p, nullptr, 1.0f, S64};
+      if (C.block) C.Sraws.st = Stored{C.Sraw64.p, nullptr, 1.0f, S64};
     }
-    // ---- dense coarsest inverse
+    // ---- dense coarsest inverse; in block mode that of A_hat, since
+    // (X^{-1} A_hat)^{-1} X^{-1} = A_hat^{-1} (the right-hand side then needs no X^{-1})
     C.dense = false;
     if (l == P.n_coarse - 1 && nc <= P.dense_max) {
       C.nd = (int)nc;
       C.D64.alloc((size_t)nc * nc * sizeof(double2));
-      dense_from_stencil(C.D64.as<double2>(), C.S64.as<double2>(), cg, N, st);
+      dense_from_stencil(C.D64.as<double2>(), (C.block ? C.Sraw64 : C.S64).as<double2>(), cg, N, st);
       DevBuf fac, perm;
       fac.alloc(sizeof(double2) * nc);
       perm.alloc(sizeof(int) * (nc + 1));

@@ -50,8 +50,11 @@ struct CoarseLevel {
   DevBuf raw64;             // block-orthonormal vectors, FP64 [nvec][V][ndof]
   Geom g;                   // coarse lattice
   int N = 0;                // coarse dof per site
-  DevBuf S64, Sdag64;       // FP64 stencil and its adjoint
+  DevBuf S64, Sdag64;       // FP64 stencil of the level's operator, adjoint of A_hat
   StoredBuf Ss, Sdags;      // preconditioner-precision copies
+  bool block = false;       // the level's operator is X^{-1} A_hat (Sec. 2.3)
+  DevBuf Sraw64, Xinv64, Xinv32;   // block mode: A_hat (near-null CGNE) and X^{-1} [Vc][N][N]
+  StoredBuf Sraws;          // block mode: A_hat in preconditioner precision
   bool dense = false;       // exact coarsest solve
   DevBuf D64, D32;          // dense inverse
   int nd = 0;
