@@ -149,46 +149,6 @@ def test_setup_cross_fed(binding, dims, hisq):
             assert rel(ca2[k], S2.apply(vc2[k])) <= tol
 
 
-def test_block_preconditioned_setup_cross_fed(binding):
-    """Sec. 2.3's block-preconditioned coarse operators, same raw near-null
-    vectors on both sides: X^{-1} of both coarsenings, the stencils X^{-1} A_hat
-    (the second Galerkin product taken with the first X^{-1} A_hat) and the
-    applies of the first agree with the oracle; without the option there is
-    no X^{-1} to read."""
-    from oracle.coarse import block_preconditioned
-    dims, mass = (8, 8, 8, 8), 0.1
-    fat, naik, c, op = make(dims, True, mass)
-    lat = op.lat
-    phi1 = inputs.gaussian_fields(4, lat.V, 3, 31)
-    phi2 = inputs.gaussian_fields(3, 16, 8, 32)
-    lop = FineLevelOp(KahlerDirac(op))
-    T1 = Transfer(lat, 3, lop.chirality(), (4, 4, 4, 4), phi1)
-    S1 = galerkin(lop, T1)
-    B1 = block_preconditioned(S1)
-    T2 = Transfer(B1.lat, B1.n, B1.chirality(), (2, 2, 2, 2), phi2)
-    S2 = galerkin(B1, T2)
-    B2 = block_preconditioned(S2)
-    s = binding.Solver(dims)
-    s.set_gauge(fat, naik, c)
-    s.set_mass(mass)
-    kw = dict(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[4, 3], setup_maxiter=0,
-              precision=binding.PREC_HALF)
-    s.mg_setup(binding.default_params(block_coarse=1, **kw), [phi1, phi2])
-    assert rel(s.coarse_xinv(0), np.linalg.inv(S1.X)) <= 1e-11
-    assert rel(s.coarse_op(0), oracle_stencil_layout(B1)) <= 1e-11
-    assert rel(s.coarse_xinv(1), np.linalg.inv(S2.X)) <= 1e-11
-    assert rel(s.coarse_op(1), oracle_stencil_layout(B2)) <= 1e-11
-    vc = inputs.gaussian_fields(2, S1.lat.V, S1.n, 6)
-    for prec in (0, 2):
-        ca = s.coarse_apply(0, vc, prec)
-        for k in range(2):
-            assert rel(ca[k], B1.apply(vc[k])) <= TOL[prec]
-    s.mg_setup(binding.default_params(**kw), [phi1, phi2])
-    assert rel(s.coarse_op(0), oracle_stencil_layout(S1)) <= 1e-11
-    with pytest.raises(binding.SmgError):
-        s.coarse_xinv(0)
-
-
 @pytest.mark.parametrize("hisq", [False, True])
 def test_force_kernel(binding, hisq):
     dims = (4, 6, 4, 8)

@@ -273,40 +273,6 @@ def test_truncated_coarse_operator(binding):
     assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
-def test_block_coarse_solve_matches_oracle(binding):
-    """Sec. 2.3's block-preconditioned coarse levels in the three-level K-cycle
-    (near-null vectors from the oracle's CGNE on A and on A_hat fed to both
-    sides): the FP64 GPU solve needs the oracle's outer iteration count and
-    reaches the dense solution; the mixed-precision solve with the persistent
-    coarse solver and the graph-replayed K-cycle converges as well."""
-    from oracle.coarse import FineLevelOp, Transfer, galerkin, near_null_vectors
-    from oracle.dirac import KahlerDirac
-    from oracle.mg import MGParams, MultigridSolver
-    dims, mass = (8, 8, 8, 8), 0.05
-    fat, naik, c, op = problem(dims, True, mass, seed=1031)
-    agg = [(4, 4, 4, 4), (2, 2, 2, 2)]
-    lop = FineLevelOp(KahlerDirac(op))
-    raw1, _ = near_null_vectors(lop, inputs.gaussian_fields(4, op.lat.V, 3, 3031), 1e-6, 40)
-    S1 = galerkin(lop, Transfer(op.lat, 3, lop.chirality(), agg[0], raw1))
-    raw2, _ = near_null_vectors(S1, inputs.gaussian_fields(4, S1.lat.V, S1.n, 3032), 1e-6, 40)
-    mg = MultigridSolver(op, MGParams(agg=agg, nvec=[4, 4], setup_maxiter=0, block_coarse=True), [raw1, raw2])
-    b = inputs.gaussian_field(op.lat.V, 3, 2031)
-    x_o, it_o, res_o = mg.solve(b, 1e-10)
-    assert res_o <= 1e-10
-    x_d = dense_solution(op, b)
-    for prec, pers in ((binding.PREC_DOUBLE, 0), (binding.PREC_HALF, 1)):
-        s = binding.Solver(dims)
-        s.set_gauge(fat, naik, c)
-        s.set_mass(mass)
-        s.mg_setup(binding.default_params(n_coarse=2, agg=agg, nvec=[4, 4], setup_maxiter=0, precision=prec,
-                                          persistent=pers, use_graph=pers, block_coarse=1), [raw1, raw2])
-        x, info = s.solve(b, 1e-10)
-        assert info.converged == 1 and info.true_residual <= 1e-10
-        check_solution(op, b, x, x_d, 1e-13)
-        if prec == binding.PREC_DOUBLE:
-            assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
-
-
 def test_multishift_cg(binding):
     """Sec. 4's multi-shift CG: every mass of an unsorted list is solved to
     1e-10 on the full HISQ-shaped M (recomputed by the oracle) and matches the
