@@ -89,6 +89,16 @@ typedef struct smg_mg_params {
                                       X^{-1} R r; the near-null CGNE runs on A_hat.  A dense
                                       coarsest level is inverted from A_hat, which gives the same
                                       solution.  Default 0 (un-preconditioned A_hat). */
+  int coarsest_deflate;            /* Table 1 coarsest solver: k > 0 = SVD-deflated Chebyshev-basis
+                                      CA-GCR when the coarsest level is not solved densely.  Setup:
+                                      the k lowest singular triplets of the coarsest operator by a
+                                      Chebyshev-filtered subspace iteration on A^dag A from the start
+                                      block phi0[n_coarse] (k + max(4, k/4) <= 64 fields).  Solve:
+                                      x0 = V diag(1/sigma) U^dag b, then CA-GCR(coarsest_cheb_s)
+                                      cycles with a Chebyshev basis on [sigma_k, sigma_max] until
+                                      0.25 ||b|| or inner_maxiter cycles.  Default 0 (GCR). */
+  int coarsest_cheb_s;             /* Chebyshev basis length of that CA-GCR, 1..8 (Table 1: 16;
+                                      this build's reduction holds the Gram of at most 8) */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */
@@ -186,6 +196,17 @@ SMG_API int smg_get_coarse_op(smg_ctx* ctx, int l, void* out, int where);
 /* X^{-1} of the self blocks of coarsening l's A_hat, [Vc][N][N] FP64 row-major
  * (Sec. 2.3).  SMG_ERR_STATE unless the setup used block_coarse. */
 SMG_API int smg_get_coarse_xinv(smg_ctx* ctx, int l, void* out, int where);
+/* Deflation of the coarsest level (coarsest_deflate = k): sigma[k] the k
+ * lowest singular values (ascending); info[4] = {Chebyshev interval lower
+ * end sigma_k, upper end (sigma_max estimate), subspace iterations, largest
+ * relative residual |A^dag A v - sigma^2 v| / b of the k pairs}.
+ * SMG_ERR_STATE without a deflated coarsest level. */
+SMG_API int smg_get_deflation(smg_ctx* ctx, double* sigma, double* info);
+/* One solve of coarse level l + 2 (the level coarsening l produces) as the
+ * K-cycle runs it (dense inverse, deflated Chebyshev CA-GCR, or GCR with the
+ * K-cycle below), in the setup's precision, on nsys right-hand sides
+ * [nsys][Vc][N] complex FP64; out likewise. */
+SMG_API int smg_coarse_solve(smg_ctx* ctx, int l, int nsys, const void* in, void* out, int where);
 /* Restriction / prolongation of coarsening l and the coarse operator of
  * level l in precision `prec`, on nsys FP64 fields. */
 SMG_API int smg_restrict(smg_ctx* ctx, int l, int prec, int nsys, const void* in, void* out, int where);

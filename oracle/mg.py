@@ -35,9 +35,11 @@ Table 1 solves the coarsest level with an SVD-deflated Chebyshev-basis
 CA-GCR(16).  ``coarsest_deflate`` = k > 0 selects it (when the coarsest level
 is not solved densely): the start V diag(1/sigma) U^dag b from the k lowest
 singular triplets, then CA-GCR(s) steps with a Chebyshev basis on the real
-interval of the operator's spectrum not removed by deflation (from the k-th
-singular value to the largest real part of the eigenvalues), to the level's
-0.25 / 8-step rule.
+interval [sigma_k, sigma_max] (the k-th singular value, the first one not
+deflated, up to the largest one, which bounds the real part of every
+eigenvalue), to the level's 0.25 / 8-step rule.  The interval only conditions
+the basis: the correction is the minimum-residual one over K_s(A, r) for any
+interval.
 
 Readings taken where the paper is silent: no pre-smoothing anywhere (Table 1
 lists none), "0.25 or 8 iterations" stops at whichever comes first, the
@@ -112,8 +114,7 @@ class MultigridSolver:
         elif params.coarsest_deflate > 0:
             Ad = coarsest.dense()
             U, sig, V = lowest_singular_triplets(Ad, params.coarsest_deflate)
-            ev = np.linalg.eigvals(Ad)
-            self.defl = (U, sig, V, float(sig[-1]), float(ev.real.max()))
+            self.defl = (U, sig, V, float(sig[-1]), float(np.linalg.norm(Ad, 2)))
 
     # --- the K-cycle -------------------------------------------------------------
     def coarse_solve(self, l, rc):

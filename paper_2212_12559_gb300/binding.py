@@ -29,7 +29,7 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
            "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc",
            "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators", "smg_persist_plan",
-           "smg_get_coarse_xinv"]
+           "smg_get_coarse_xinv", "smg_get_deflation", "smg_coarse_solve"]
 
 
 class MGParams(ctypes.Structure):
@@ -50,6 +50,8 @@ class MGParams(ctypes.Structure):
         ("persistent", ctypes.c_int),
         ("truncate_naik", ctypes.c_int),
         ("block_coarse", ctypes.c_int),
+        ("coarsest_deflate", ctypes.c_int),
+        ("coarsest_cheb_s", ctypes.c_int),
     ]
 
 
@@ -97,6 +99,8 @@ def load(path: str = LIB_PATH):
         "smg_get_null_vectors": (i, [vp, i, vp, i]),
         "smg_get_coarse_op": (i, [vp, i, vp, i]),
         "smg_get_coarse_xinv": (i, [vp, i, vp, i]),
+        "smg_get_deflation": (i, [vp, vp, vp]),
+        "smg_coarse_solve": (i, [vp, i, i, vp, vp, i]),
         "smg_restrict": (i, [vp, i, i, i, vp, vp, i]),
         "smg_prolong": (i, [vp, i, i, i, vp, vp, i]),
         "smg_coarse_apply": (i, [vp, i, i, i, vp, vp, i]),
@@ -130,6 +134,11 @@ def persist_plan(V, N, nsys, nvec_next, prec, sms, smem_cap):
         raise SmgError(rc, "persist_plan: bad shape")
     keys = ("grid", "per", "nslot", "resident", "sg", "smem", "off_S", "off_sc", "off_P", "off_stg")
     return dict(zip(keys, list(out)))
+
+
+def deflation_block(k: int) -> int:
+    """Fields in the start block of a k-vector coarsest deflation (k + guard)."""
+    return k + max(4, k // 4)
 
 
 def default_params(**kw) -> MGParams:
@@ -216,7 +225,9 @@ class Solver:
         arrs = [_prep(a) for a in phi0]
         ptrs = [_ptr(a) for a in arrs]
         where = ptrs[0][1]
-        arr = (ctypes.c_void_p * len(arrs))(*[p for p, _ in ptrs])
+        # a trailing NULL: the library reads phi0[n_coarse] (the deflation start
+        # block) only with coarsest_deflate > 0 and reports a missing one
+        arr = (ctypes.c_void_p * (len(arrs) + 1))(*([p for p, _ in ptrs] + [None]))
         self._check(self.lib.smg_mg_setup(self.ctx, ctypes.byref(params), arr, where))
         self.params = params
         self._keep = arrs
@@ -323,6 +334,27 @@ class Solver:
         _, _, Vc, N = self._level_shape(l)
         out = np.empty((Vc, N, N), dtype=np.complex128)
         self._check(self.lib.smg_get_coarse_xinv(self.ctx, l, ctypes.c_void_p(out.ctypes.data), SMG_HOST))
+        return out
+
+    def deflation(self):
+        """(sigma, info) of the deflated coarsest level: the k lowest singular
+        values and {lmin, lmax, iterations, residual}."""
+        k = self.params.coarsest_deflate
+        sig = np.empty(k, dtype=np.float64)
+        info = np.empty(4, dtype=np.float64)
+        self._check(self.lib.smg_get_deflation(self.ctx, ctypes.c_void_p(sig.ctypes.data),
+                                               ctypes.c_void_p(info.ctypes.data)))
+        return sig, dict(lmin=info[0], lmax=info[1], iterations=int(info[2]), residual=info[3])
+
+    def coarse_solve(self, l, v):
+        """One solve of the level coarsening l produces, as the K-cycle runs it."""
+        _, _, Vc, N = self._level_shape(l)
+        v = _prep(v)
+        nsys = v.shape[0]
+        out = _like(v, (nsys, Vc, N))
+        pi, where = _ptr(v)
+        po, _ = _ptr(out)
+        self._check(self.lib.smg_coarse_solve(self.ctx, l, nsys, pi, po, where))
         return out
 
     def _xfer(self, fn, l, v, prec, out_shape):

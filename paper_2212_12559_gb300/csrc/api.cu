@@ -90,6 +90,8 @@ void smg_default_params(smg_mg_params* p) {
   p->persistent = 1;
   p->truncate_naik = 0;
   p->block_coarse = 0;
+  p->coarsest_deflate = 0;
+  p->coarsest_cheb_s = 8;
 }
 
 int smg_create(const int dims[4], smg_ctx** out) {
@@ -269,6 +271,30 @@ int smg_get_coarse_xinv(smg_ctx* ctx, int l, void* out, int where) {
     if (!c.coarse[l].block) throw smg::StateError("get_coarse_xinv needs a block_coarse setup");
     smg::download(out, c.coarse[l].Xinv64.p, c.coarse[l].Xinv64.bytes, where, c.stream);
     SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    return SMG_OK;
+  });
+}
+
+int smg_get_deflation(smg_ctx* ctx, double* sigma, double* info) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(sigma != nullptr && info != nullptr, "get_deflation: null buffer");
+    if (!c.setup_done || c.coarse.empty() || c.coarse.back().defl_k == 0)
+      throw smg::StateError("get_deflation needs a setup with a deflated coarsest level");
+    const smg::CoarseLevel& C = c.coarse.back();
+    for (int i = 0; i < C.defl_k; ++i) sigma[i] = C.sigma[i];
+    info[0] = C.cheb_lmin;
+    info[1] = C.cheb_lmax;
+    info[2] = C.defl_iters;
+    info[3] = C.defl_res;
+    return SMG_OK;
+  });
+}
+
+int smg_coarse_solve(smg_ctx* ctx, int l, int nsys, const void* in, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(in && out && valid_where(where), "coarse_solve: null buffer");
+    if (!c.setup_done) throw smg::StateError("coarse_solve needs mg_setup");
+    smg::ctx_coarse_solve(c, l, nsys, in, out, where);
     return SMG_OK;
   });
 }

@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "defl.cuh"
 #include "persist.cuh"
 #include "solver.cuh"
 
@@ -247,6 +248,17 @@ struct Engine {
   void pb(const char* n) { if (prof) phases.begin(n, st()); }
   void pe() { if (prof) phases.end(st()); }
   bool persistent = false;          // last GCR level solved by one cooperative launch
+  // deflated coarsest level: Chebyshev basis Q_1..Q_{s-1} (Q_0 is the
+  // residual), W_i = A Q_i, recurrence coefficients, Gram and flags
+  struct ChebWork {
+    int s = 0;
+    std::vector<Vec> Q, W;
+    DevBuf vbuf, sbuf;
+    double2 *c1 = nullptr, *c2 = nullptr, *gram = nullptr, *coef = nullptr, *yd = nullptr, *rr = nullptr,
+            *bb = nullptr;
+    int *active = nullptr, *drun = nullptr;
+    int pi[kMaxPairs], pj[kMaxPairs], np = 0;
+  } cw;
   // graph of K_0
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
@@ -313,11 +325,56 @@ struct Engine {
     }
     c.ensure_consts(ns * 2 + 2);
     ws.get(sizeof(double2) * (size_t)(152 * 4) * kMaxPairs * ns);
+    if (c.coarse.back().defl_k > 0) {
+      SMG_REQUIRE(ns <= kDeflMaxBlock, "a deflated coarsest level solves at most 64 systems at once");
+      const CoarseLevel& C = c.coarse.back();
+      const long long n = (long long)C.g.V * C.N;
+      const int s = P.coarsest_cheb_s;
+      cw.s = s;
+      const size_t vb = (size_t)n * ns * prec_bytes(vp);
+      cw.vbuf.alloc(vb * (2 * s));
+      cw.Q.assign(s, Vec());
+      cw.W.assign(s, Vec());
+      for (int i = 0; i < s; ++i) {
+        cw.W[i] = mkv((char*)cw.vbuf.p + vb * i, n, vp);
+        if (i > 0) cw.Q[i] = mkv((char*)cw.vbuf.p + vb * (s + i), n, vp);
+      }
+      cw.np = 0;
+      for (int i = 0; i < s; ++i)
+        for (int j = i; j < s; ++j) { cw.pi[cw.np] = i + 1; cw.pj[cw.np] = j + 1; ++cw.np; }
+      for (int i = 0; i < s; ++i) { cw.pi[cw.np] = i + 1; cw.pj[cw.np] = 0; ++cw.np; }
+      const size_t nd = (size_t)ns * (2 + 3 + kMaxPairs + s + 2) + (size_t)C.defl_k * ns;
+      cw.sbuf.alloc(sizeof(double2) * nd + sizeof(int) * (ns + 1));
+      cw.c1 = cw.sbuf.as<double2>();
+      cw.c2 = cw.c1 + 2 * ns;
+      cw.gram = cw.c2 + 3 * ns;
+      cw.coef = cw.gram + (size_t)kMaxPairs * ns;
+      cw.rr = cw.coef + (size_t)s * ns;
+      cw.bb = cw.rr + ns;
+      cw.yd = cw.bb + ns;
+      cw.active = (int*)(cw.yd + (size_t)C.defl_k * ns);
+      cw.drun = cw.active + ns;
+      // T = (A - c) / h maps [sigma_k, sigma_max] to [-1, 1]
+      double cc = 0.5 * (C.cheb_lmax + C.cheb_lmin), h = 0.5 * (C.cheb_lmax - C.cheb_lmin);
+      if (!(h > 0.0)) { h = C.cheb_lmax > 0.0 ? 0.5 * C.cheb_lmax : 1.0; cc = h; }
+      std::vector<double2> hc((size_t)5 * ns);
+      for (int q = 0; q < ns; ++q) {
+        hc[2 * q] = make_double2(1.0 / h, 0.0);
+        hc[2 * q + 1] = make_double2(-cc / h, 0.0);
+        hc[2 * ns + 3 * q] = make_double2(2.0 / h, 0.0);
+        hc[2 * ns + 3 * q + 1] = make_double2(-2.0 * cc / h, 0.0);
+        hc[2 * ns + 3 * q + 2] = make_double2(-1.0, 0.0);
+      }
+      SMG_CUDA_OK(cudaMemcpyAsync(cw.c1, hc.data(), sizeof(double2) * hc.size(), cudaMemcpyHostToDevice, c.stream));
+      ws.get(sizeof(double2) * (size_t)(2 * 152) * C.defl_k * ns);
+      SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    }
     // one cooperative launch for the last GCR level when its coarser level is
     // the dense coarsest (or it is itself the coarsest without a dense solve)
     {
       const int l = c.coarse.back().dense ? nlev : nlev + 1;
-      if (P.persistent && vp == P32 && l >= 2) {
+      const bool deflated_target = (l == nlev + 1 && c.coarse.back().defl_k > 0);
+      if (P.persistent && vp == P32 && l >= 2 && !deflated_target) {
         const CoarseLevel& C = c.coarse[l - 2];
         const int nvec_next = l <= nlev ? c.coarse[l - 1].tg.nvec : 0;
         persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, (long long)C.g.V * C.N, sp);
@@ -558,11 +615,65 @@ struct Engine {
     }
   }
 
+  // Table 1's coarsest solver: the deflated start x0 = V diag(1/sigma) U^dag b,
+  // then up to inner_maxiter Chebyshev-basis CA-GCR(s) corrections, each one
+  // only for the systems whose residual is still above 0.25 ||b||
+  void deflated_solve(int l, const int* run) {
+    const CoarseLevel& C = c.coarse[l - 2];
+    GcrWork& G = lev[l];
+    const int s = cw.s;
+    const long long n = (long long)C.g.V * C.N;
+    Vec Ub;
+    Ub.p = vp == P64 ? C.dU64.p : C.dU32.p;
+    Ub.n = n; Ub.nsys = C.defl_k; Ub.prec = vp;
+    Vec Vb = Ub;
+    Vb.p = vp == P64 ? C.dV64.p : C.dV32.p;
+    block_gram(Ub, G.b, cw.yd, ws, st(), run);
+    block_combine(G.x, Vb, cw.yd, nsys, st(), run);
+    const int p0[1] = {0};
+    blas_pair_dots(&G.b, 1, p0, p0, 1, cw.bb, 1, ws, st(), run);
+    const double tol2 = c.params.inner_tol * c.params.inner_tol;
+    for (int it = 0; it < c.params.inner_maxiter; ++it) {
+      const int* rn = it == 0 ? run : cw.drun;
+      op(l, G.r, G.x, rn, &G.b);                        // r = b - A x
+      blas_pair_dots(&G.r, 1, p0, p0, 1, cw.rr, 1, ws, st(), rn);
+      defl_active(cw.rr, cw.bb, tol2, cw.active, cw.drun, nsys, it == 0, st(), run);
+      // Q_0 = r, Q_1 = (A - c) Q_0 / h, Q_{i+1} = 2 (A - c) Q_i / h - Q_{i-1}; W_i = A Q_i
+      cw.Q[0] = G.r;
+      for (int i = 0; i < s; ++i) {
+        op(l, cw.W[i], cw.Q[i], cw.drun);
+        if (i + 1 == s) break;
+        if (i == 0) {
+          Vec in2[2] = {cw.W[0], cw.Q[0]};
+          blas_maxpy(cw.Q[1], in2, 2, cw.c1, 2, 1.0, false, st(), cw.drun);
+        } else {
+          Vec in3[3] = {cw.W[i], cw.Q[i], cw.Q[i - 1]};
+          blas_maxpy(cw.Q[i + 1], in3, 3, cw.c2, 3, 1.0, false, st(), cw.drun);
+        }
+      }
+      // minimum residual over span(W): (W^dag W) a = W^dag r, x += sum_i a_i Q_i
+      std::vector<Vec> L(s + 1);
+      L[0] = G.r;
+      for (int i = 0; i < s; ++i) L[i + 1] = cw.W[i];
+      Epilogue ep;
+      ep.kind = EPI_CA;
+      ep.s = s;
+      ep.d2a = cw.coef;
+      blas_pair_dots(L.data(), s + 1, cw.pi, cw.pj, cw.np, cw.gram, kMaxPairs, ws, st(), cw.drun, ep);
+      mask_coef(cw.coef, s, s, cw.active, nsys, st(), cw.drun);
+      blas_maxpy(G.x, cw.Q.data(), s, cw.coef, s, 1.0, true, st(), cw.drun);
+    }
+  }
+
   // solve on level l (>= 2): G = lev[l], input lev[l].b, output lev[l].x
   void coarse_solve(int l, const int* run) {
     const CoarseLevel& C = c.coarse[l - 2];
     GcrWork& G = lev[l];
     const bool coarsest = (l == nlev + 1);
+    if (coarsest && C.defl_k > 0) {
+      deflated_solve(l, run);
+      return;
+    }
     if (persistent_solve(l, run)) return;
     if (coarsest && C.dense) {
       if (vp == P64) dense_apply(G.x, G.b, C.D64.p, P64, C.nd, st(), run);
@@ -876,6 +987,185 @@ struct SetupOp {
 
 }  // namespace
 
+namespace {
+
+// The k lowest singular triplets of the coarsest operator A (Table 1's
+// SVD-deflated coarsest solve) by Chebyshev-filtered subspace iteration on
+// A^dag A in FP64: a block of kw = k + guard vectors is multiplied by the
+// Chebyshev polynomial T_d((2 A^dag A - (a + b)) / (b - a)), which damps the
+// spectrum on [a, b] (a = the block's largest Ritz value, b = 1.2 x a power
+// iteration estimate of lambda_max) and grows the part below a; the degree is
+// capped so that the growth over the block stays below 1e4 (the Gram matrix of
+// the filtered block then keeps its rank in FP64).  Rayleigh-Ritz after each
+// filter makes the block orthonormal with ascending Ritz values.  Converged
+// when every wanted pair has |A^dag A v - lambda v| <= 1e-10 b.  Then
+// sigma = sqrt(lambda), U = A V / sigma; the solve keeps V and U / sigma.
+void build_deflation(Context& c, CoarseLevel& C, const void* start, int where) {
+  const auto& P = c.params;
+  const int k = P.coarsest_deflate;
+  const int kw = k + defl_guard(k);
+  const long long n = (long long)C.g.V * C.N;
+  SMG_REQUIRE(kw <= kDeflMaxBlock, "coarsest_deflate: k + max(4, k/4) must be at most 64");
+  SMG_REQUIRE(kw <= n, "coarsest_deflate: more vectors than coarsest unknowns");
+  cudaStream_t st = c.stream;
+  const size_t vb = (size_t)n * kw * sizeof(double2);
+  DevBuf blk;
+  blk.alloc(vb * 5);
+  auto mk = [&](void* ptr, int ns) { Vec v; v.p = ptr; v.n = n; v.nsys = ns; v.prec = P64; return v; };
+  void* buf[5];
+  for (int i = 0; i < 5; ++i) buf[i] = (char*)blk.p + vb * i;
+  Vec V = mk(buf[0], kw), W = mk(buf[1], kw), X = mk(buf[2], kw);
+  void* tp[2] = {buf[3], buf[4]};     // two more Chebyshev iterates
+  upload(V.p, start, vb, where, st);
+  // A and A^dag of the level's operator (X^{-1} A_hat in block mode), FP64
+  DevBuf sdag;
+  sdag.alloc(C.S64.bytes);
+  coarse_dagger(sdag.as<double2>(), C.S64.as<double2>(), C.g, C.N, st);
+  const Stored SA{C.S64.p, nullptr, 1.0f, S64}, SD{sdag.p, nullptr, 1.0f, S64};
+  CoarseParams cp;
+  cp.g = C.g; cp.N = C.N; cp.allow_tc = 0;
+  const size_t kk = (size_t)kw * kw;
+  DevBuf sm;
+  sm.alloc(sizeof(double2) * (6 * kk + 4 * (size_t)kw + 8) + sizeof(double) * kw);
+  double2* G = sm.as<double2>();
+  double2* H = G + kk;
+  double2* Y = H + kk;
+  double2* rrs = Y + kk;               // 3 kk
+  double2* coef = rrs + 3 * kk;        // [kw][3] recurrence / shift coefficients
+  double2* dots = coef + 3 * kw;       // kw
+  double2* small = dots + kw;          // 8
+  double* lamd = (double*)(small + 8);
+  std::vector<double> lam(kw);
+  auto set_coef = [&](const std::vector<double2>& row) {
+    std::vector<double2> h((size_t)kw * row.size());
+    for (int s = 0; s < kw; ++s)
+      for (size_t j = 0; j < row.size(); ++j) h[s * row.size() + j] = row[j];
+    SMG_CUDA_OK(cudaMemcpyAsync(coef, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice, st));
+  };
+  // lambda_max(A^dag A) by 30 power steps on the first start vector
+  double rq = 0.0;
+  {
+    Vec x = mk(buf[3], 1), y = mk(buf[4], 1), z = mk(buf[2], 1);
+    blas_copy(x, mk(V.p, 1), st);
+    const int pi[3] = {0, 0, 1}, pj[3] = {1, 0, 1};
+    for (int it = 0; it < 30; ++it) {
+      coarse_apply(y, x, cp, SA, st);
+      coarse_apply(z, y, cp, SD, st);
+      Vec xz[2] = {x, z};
+      blas_pair_dots(xz, 2, pi, pj, 3, small, 3, c.ws, st);
+      double2 h[3];
+      SMG_CUDA_OK(cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, st));
+      SMG_CUDA_OK(cudaStreamSynchronize(st));
+      SMG_REQUIRE(h[1].x > 0.0 && h[2].x > 0.0, "coarsest_deflate: zero power-iteration vector");
+      rq = h[0].x / h[1].x;
+      const double2 nz = make_double2(std::sqrt(h[2].x), 0.0);
+      SMG_CUDA_OK(cudaMemcpyAsync(small + 4, &nz, sizeof(nz), cudaMemcpyHostToDevice, st));
+      blas_copy(x, z, st);
+      blas_scale(x, small + 4, true, st);
+    }
+  }
+  double b = 1.2 * rq;
+  auto ritz = [&]() {
+    block_gram(V, V, G, c.ws, st);
+    block_gram(W, W, H, c.ws, st);
+    rayleigh_ritz(G, H, kw, Y, lamd, rrs, st);
+    block_combine(X, V, Y, kw, st);
+    std::swap(V.p, X.p);
+    block_combine(X, W, Y, kw, st);
+    std::swap(W.p, X.p);
+    SMG_CUDA_OK(cudaMemcpyAsync(lam.data(), lamd, sizeof(double) * kw, cudaMemcpyDeviceToHost, st));
+    SMG_CUDA_OK(cudaStreamSynchronize(st));
+    SMG_REQUIRE(lam[0] < 1e299, "coarsest_deflate: the start block has no usable direction");
+  };
+  coarse_apply(W, V, cp, SA, st);
+  ritz();
+  const int max_it = 200;
+  int it = 0;
+  double res = 0.0;
+  for (; it < max_it; ++it) {
+    // Chebyshev filter on [a, b]
+    double a = lam[0];
+    for (int j = 0; j < kw; ++j)
+      if (lam[j] < 1e299) a = std::max(a, lam[j]);   // the largest Ritz value of the block
+    b = std::max(b, 1.05 * a);
+    if (!(a < b)) a = 0.5 * b;
+    const double xmin = std::fabs((2.0 * lam[0] - a - b) / (b - a));
+    int deg = 20;
+    if (xmin > 1.0) deg = std::max(1, std::min(20, (int)(std::acosh(1e4) / std::acosh(xmin))));
+    Vec T0 = V, T1 = mk(tp[0], kw), Tn = mk(tp[1], kw);
+    coarse_apply(W, T0, cp, SA, st);
+    coarse_apply(X, W, cp, SD, st);
+    set_coef({make_double2(2.0 / (b - a), 0.0), make_double2(-(a + b) / (b - a), 0.0)});
+    Vec in2[2] = {X, T0};
+    blas_maxpy(T1, in2, 2, coef, 2, 1.0, false, st);
+    if (deg > 1) set_coef({make_double2(4.0 / (b - a), 0.0), make_double2(-2.0 * (a + b) / (b - a), 0.0),
+                           make_double2(-1.0, 0.0)});
+    for (int j = 1; j < deg; ++j) {
+      coarse_apply(W, T1, cp, SA, st);
+      coarse_apply(X, W, cp, SD, st);
+      Vec in3[3] = {X, T1, T0};
+      blas_maxpy(Tn, in3, 3, coef, 3, 1.0, false, st);
+      std::swap(T0.p, T1.p);    // T0 <- T1
+      std::swap(T1.p, Tn.p);    // T1 <- Tn, Tn <- the old T0 (free)
+    }
+    // V <- T1; {T0, T1, Tn} is always a permutation of the three iterate
+    // buffers, so T0 and Tn are the free pair
+    V.p = T1.p;
+    tp[0] = T0.p;
+    tp[1] = Tn.p;
+    coarse_apply(W, V, cp, SA, st);
+    ritz();
+    // residuals of the k wanted pairs: A^dag W_j - lambda_j V_j
+    coarse_apply(X, W, cp, SD, st);
+    {
+      std::vector<double2> h(kw);
+      for (int s = 0; s < kw; ++s) h[s] = make_double2(lam[s] < 1e299 ? lam[s] : 0.0, 0.0);
+      SMG_CUDA_OK(cudaMemcpyAsync(coef, h.data(), sizeof(double2) * kw, cudaMemcpyHostToDevice, st));
+    }
+    blas_maxpy(X, &V, 1, coef, 1, -1.0, true, st);
+    const int p0[1] = {0};
+    blas_pair_dots(&X, 1, p0, p0, 1, dots, 1, c.ws, st);
+    std::vector<double2> d(kw);
+    SMG_CUDA_OK(cudaMemcpyAsync(d.data(), dots, sizeof(double2) * kw, cudaMemcpyDeviceToHost, st));
+    SMG_CUDA_OK(cudaStreamSynchronize(st));
+    res = 0.0;
+    for (int j = 0; j < k; ++j) res = std::max(res, std::sqrt(std::max(d[j].x, 0.0)) / b);
+    if (res <= 1e-10) { ++it; break; }
+  }
+  SMG_REQUIRE(lam[k - 1] > 0.0 && lam[k - 1] < 1e299, "coarsest_deflate: fewer than k usable directions");
+  C.defl_k = k;
+  C.defl_iters = it;
+  C.defl_res = res;
+  C.sigma.resize(k);
+  for (int j = 0; j < k; ++j) C.sigma[j] = std::sqrt(lam[j]);
+  C.cheb_lmin = C.sigma[k - 1];
+  C.cheb_lmax = std::sqrt(rq);
+  // U / sigma = A V / sigma^2
+  {
+    std::vector<double2> h(k);
+    for (int j = 0; j < k; ++j) h[j] = make_double2(lam[j], 0.0);
+    SMG_CUDA_OK(cudaMemcpyAsync(coef, h.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, st));
+    Vec Wk = mk(W.p, k);
+    blas_scale(Wk, coef, true, st);
+  }
+  const size_t kb64 = (size_t)n * k * sizeof(double2);
+  C.dV64.alloc(kb64);
+  C.dU64.alloc(kb64);
+  SMG_CUDA_OK(cudaMemcpyAsync(C.dV64.p, V.p, kb64, cudaMemcpyDeviceToDevice, st));
+  SMG_CUDA_OK(cudaMemcpyAsync(C.dU64.p, W.p, kb64, cudaMemcpyDeviceToDevice, st));
+  C.dV32.alloc((size_t)n * k * sizeof(float2));
+  C.dU32.alloc((size_t)n * k * sizeof(float2));
+  Vec v32 = mk(C.dV32.p, k);
+  v32.prec = P32;
+  Vec u32 = mk(C.dU32.p, k);
+  u32.prec = P32;
+  blas_copy(v32, mk(C.dV64.p, k), st);
+  blas_copy(u32, mk(C.dU64.p, k), st);
+  SMG_CUDA_OK(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
 void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, int where) {
   SMG_REQUIRE(c.gauge_set && c.mass_set, "mg_setup needs set_gauge and set_mass first");
   SMG_REQUIRE(P.n_coarse >= 1 && P.n_coarse <= SMG_MAX_COARSE, "n_coarse must be 1..3");
@@ -885,6 +1175,10 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
   SMG_REQUIRE(P.precision >= SMG_PREC_DOUBLE && P.precision <= SMG_PREC_HALF, "bad precision");
   SMG_REQUIRE(P.setup_maxiter >= 0 && P.max_outer >= 1, "bad iteration caps");
   SMG_REQUIRE(phi0 != nullptr, "phi0 must hold one start array per coarsening");
+  SMG_REQUIRE(P.coarsest_deflate >= 0 && P.coarsest_deflate + defl_guard(P.coarsest_deflate) <= kDeflMaxBlock,
+              "coarsest_deflate must be 0..51");
+  SMG_REQUIRE(P.coarsest_deflate == 0 || (P.coarsest_cheb_s >= 1 && P.coarsest_cheb_s <= 8),
+              "coarsest_cheb_s must be 1..8");
   c.engine.reset();
   c.setup_done = false;
   c.params = P;
@@ -1087,6 +1381,10 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
     SMG_CUDA_OK(cudaStreamSynchronize(st));
     fg = cg;
     ndof = N;
+  }
+  if (P.coarsest_deflate > 0 && !c.coarse.back().dense) {
+    SMG_REQUIRE(phi0[P.n_coarse] != nullptr, "coarsest_deflate needs the start block phi0[n_coarse]");
+    build_deflation(c, c.coarse.back(), phi0[P.n_coarse], where);
   }
   c.setup_done = true;
 }
@@ -1411,6 +1709,21 @@ void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* 
     coarse_apply(vout, vin, p, S, c.stream);
     conv_out(c, out, vout, where);
   }
+}
+
+void ctx_coarse_solve(Context& c, int l, int nsys, const void* in, void* out, int where) {
+  SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "coarse_solve: bad level");
+  SMG_REQUIRE(nsys >= 1 && nsys <= 16, "coarse_solve: 1 <= nsys <= 16");
+  const CoarseLevel& C = c.coarse[l];
+  const long long n = (long long)C.g.V * C.N;
+  Engine E(c, nsys, std::vector<double>(1, c.mass), nsys);
+  const int lv = l + 2;
+  Scratch s;
+  Vec vin = conv_in(c, s.a, in, n, nsys, E.vp, where);
+  blas_copy(E.lev[lv].b, vin, c.stream);
+  E.coarse_solve(lv, nullptr);
+  E.check_persistent_error();
+  conv_out(c, out, E.lev[lv].x, where);
 }
 
 // Fermion action S = phi^dag (M^dag M)^{-1} phi with its vectors:

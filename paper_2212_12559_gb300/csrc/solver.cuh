@@ -55,6 +55,13 @@ struct CoarseLevel {
   bool block = false;       // the level's operator is X^{-1} A_hat (Sec. 2.3)
   DevBuf Sraw64, Xinv64, Xinv32;   // block mode: A_hat (near-null CGNE) and X^{-1} [Vc][N][N]
   StoredBuf Sraws;          // block mode: A_hat in preconditioner precision
+  // deflated coarsest level (Table 1): V (right singular vectors) and
+  // U diag(1/sigma) (left ones over sigma), [k][Vc][N], FP64 and FP32
+  int defl_k = 0;
+  DevBuf dV64, dU64, dV32, dU32;
+  std::vector<double> sigma;
+  double cheb_lmin = 0.0, cheb_lmax = 0.0, defl_res = 0.0;
+  int defl_iters = 0;
   bool dense = false;       // exact coarsest solve
   DevBuf D64, D32;          // dense inverse
   int nd = 0;
@@ -140,6 +147,7 @@ int ctx_multishift_cg(Context& c, const void* b, int nshift, const double* masse
                       int where, smg_solve_info* info);
 int ctx_propagators(Context& c, const void* b, int nmass, const double* masses, int n_mg, void* x, double tol,
                     int cg_maxiter, int where, smg_solve_info* info);
+void ctx_coarse_solve(Context& c, int l, int nsys, const void* in, void* out, int where);
 int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* masses, void* x, double tol, int where,
               smg_solve_info* info);
 void ctx_apply_fine(Context& c, int op, int prec, int nsys, const void* in, void* out, int where);

@@ -130,6 +130,19 @@ def test_svd_deflation(coarse):
     assert it <= it_plain
 
 
+def test_chebyshev_ca_gcr_interval_only_conditions(coarse):
+    """The Chebyshev interval changes the basis, not the space: two intervals
+    (the exact [sigma_k, sigma_max] and a perturbed one) give the same
+    minimum-residual correction."""
+    S, Ad = coarse
+    r = inputs.gaussian_field(S.lat.V, S.n, 50)
+    sv = np.linalg.svd(Ad, compute_uv=False)
+    apply = lambda v: (Ad @ v.ravel()).reshape(v.shape)
+    e1 = ca_gcr_chebyshev(apply, r, 5, float(np.sort(sv)[3]), float(sv.max()))
+    e2 = ca_gcr_chebyshev(apply, r, 5, 0.7 * float(np.sort(sv)[3]), 1.1 * float(sv.max()))
+    assert np.linalg.norm(e1 - e2) <= 1e-9 * np.linalg.norm(e1)
+
+
 def test_chebyshev_basis_is_chebyshev_polynomials(coarse):
     from numpy.polynomial import chebyshev as C
     S, Ad = coarse
