@@ -99,6 +99,12 @@ typedef struct smg_mg_params {
                                       0.25 ||b|| or inner_maxiter cycles.  Default 0 (GCR). */
   int coarsest_cheb_s;             /* Chebyshev basis length of that CA-GCR, 1..8 (Table 1: 16;
                                       this build's reduction holds the Gram of at most 8) */
+  int coarsest_schur;              /* Table 1 level-3 operator: 1 = the deflated coarsest solve runs
+                                      on the even/odd Schur complement S = 1 - K_eo K_oe of the
+                                      block-preconditioned operator 1 + K (needs block_coarse,
+                                      coarsest_deflate > 0 and even coarse extents): right-hand side
+                                      c_e - K_eo c_o, singular triplets and CA-GCR of S, then
+                                      x_o = c_o - K_oe x_e.  Default 0. */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */

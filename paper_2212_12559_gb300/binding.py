@@ -52,6 +52,7 @@ class MGParams(ctypes.Structure):
         ("block_coarse", ctypes.c_int),
         ("coarsest_deflate", ctypes.c_int),
         ("coarsest_cheb_s", ctypes.c_int),
+        ("coarsest_schur", ctypes.c_int),
     ]
 
 

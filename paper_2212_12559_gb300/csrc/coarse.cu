@@ -337,6 +337,26 @@ __global__ void __launch_bounds__(kBlockPrecThreads) block_precondition_kernel(d
   }
 }
 
+// out(X) = even(X) on even coarse sites, odd(X) on odd ones (a null source
+// gives zeros), per system; in place when out is one of the sources.
+template <typename C>
+__global__ void parity_pick_kernel(C* __restrict__ out, const C* even, const C* odd, Geom g, int N, long long n,
+                                   long long total, const int* __restrict__ run) {
+  if (run != nullptr && *run == 0) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)((e % n) / N);
+    int c[4];
+    g.coords(X, c);
+    const C* src = ((c[0] + c[1] + c[2] + c[3]) & 1) ? odd : even;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (src != nullptr) v = src[e];
+    out[e] = v;
+  }
+}
+
 // v[s](X) <- Xinv(X) v[s](X) in place, one CTA per (site, system): the site's
 // N entries are staged in shared memory, each warp takes rows with its lanes
 // on consecutive columns of X^{-1}.
@@ -697,6 +717,25 @@ void block_diag_apply(const Vec& v, const void* Xinv, Prec xprec, int N, cudaStr
   else
     launch_k(block_diag_kernel<float2>, grid, dim3(128), sizeof(float2) * N, st, (float2*)v.p,
              (const float2*)Xinv, V, N, run);
+  SMG_LAUNCH_OK();
+}
+
+void parity_pick(const Vec& out, const Vec* even, const Vec* odd, const Geom& g, int N, cudaStream_t st,
+                 const int* run) {
+  SMG_REQUIRE(out.n == (long long)g.V * N, "parity_pick: shape mismatch");
+  for (const Vec* v : {even, odd})
+    SMG_REQUIRE(v == nullptr || (v->n == out.n && v->nsys == out.nsys && v->prec == out.prec),
+                "parity_pick: source shape mismatch");
+  const long long total = out.n * out.nsys;
+  const unsigned grid = grid_cap(total, 256);
+  if (out.prec == P64)
+    launch_k(parity_pick_kernel<double2>, dim3(grid), dim3(256), 0, st, (double2*)out.p,
+             (const double2*)(even ? even->p : nullptr), (const double2*)(odd ? odd->p : nullptr), g, N, out.n,
+             total, run);
+  else
+    launch_k(parity_pick_kernel<float2>, dim3(grid), dim3(256), 0, st, (float2*)out.p,
+             (const float2*)(even ? even->p : nullptr), (const float2*)(odd ? odd->p : nullptr), g, N, out.n,
+             total, run);
   SMG_LAUNCH_OK();
 }
 

@@ -135,6 +135,10 @@ void block_precondition(double2* S64, double2* Xinv, const Geom& g, int N, int* 
 // v[s](X) <- Xinv(X) v[s](X) on a coarse batch; Xinv in v's precision
 void block_diag_apply(const Vec& v, const void* Xinv, Prec xprec, int N, cudaStream_t st, const int* run = nullptr);
 
+// out = even sites of *even, odd sites of *odd (null: zero) on a coarse batch
+void parity_pick(const Vec& out, const Vec* even, const Vec* odd, const Geom& g, int N, cudaStream_t st,
+                 const int* run = nullptr);
+
 // ------------------------------------------------------- dense coarsest op
 void dense_from_stencil(double2* Dn, const double2* S64, const Geom& g, int N, cudaStream_t st);
 // In-place Gauss-Jordan inverse with partial pivoting (FP64); returns false if singular.

@@ -214,6 +214,28 @@ struct PhaseTimer {
   ~PhaseTimer() { for (auto e : pool) cudaEventDestroy(e); }
 };
 
+namespace {
+
+// Even/odd Schur complement of a block-preconditioned coarse operator
+// A = 1 + K (self blocks exactly 1, every hop changes the site parity):
+// with R(u) = u - A u = -K u,  S v = v - K_eo K_oe v = mask_e(v - R(mask_o(R(v))))
+// for v that vanishes on odd sites.  The masks also drop what the rounding of
+// stored (FP16 / FP32) identity self blocks leaves on the wrong parity.  With
+// the adjoint stencil the same steps give S^dag.  t1, t2: scratch like v.
+void schur_apply(const Vec& out, const Vec& in, const CoarseParams& cp0, const Stored& S, const Vec& t1,
+                 const Vec& t2, cudaStream_t st, const int* run) {
+  CoarseParams cp = cp0;
+  cp.sub_from = in.p;
+  coarse_apply(t1, in, cp, S, st, run);                  // t1 = R(in)
+  parity_pick(t1, nullptr, &t1, cp.g, cp.N, st, run);    // its odd part
+  cp.sub_from = t1.p;
+  coarse_apply(t2, t1, cp, S, st, run);                  // t2 = R(t1)
+  blas_sub(t1, in, t2, st, run);                         // in - t2
+  parity_pick(out, &t1, nullptr, cp.g, cp.N, st, run);   // its even part
+}
+
+}  // namespace
+
 // -------------------------------------------------------------------- engine
 // Work areas and operator closures for one batch size and mass set.
 struct Engine {
@@ -258,6 +280,7 @@ struct Engine {
             *bb = nullptr;
     int *active = nullptr, *drun = nullptr;
     int pi[kMaxPairs], pj[kMaxPairs], np = 0;
+    Vec t1, t2, t3, xe, rhs;          // Schur form: scratch, x_e and c_e - K_eo c_o
   } cw;
   // graph of K_0
   cudaGraphExec_t graph = nullptr;
@@ -332,12 +355,16 @@ struct Engine {
       const int s = P.coarsest_cheb_s;
       cw.s = s;
       const size_t vb = (size_t)n * ns * prec_bytes(vp);
-      cw.vbuf.alloc(vb * (2 * s));
+      cw.vbuf.alloc(vb * (2 * s + (C.schur ? 5 : 0)));
       cw.Q.assign(s, Vec());
       cw.W.assign(s, Vec());
       for (int i = 0; i < s; ++i) {
         cw.W[i] = mkv((char*)cw.vbuf.p + vb * i, n, vp);
         if (i > 0) cw.Q[i] = mkv((char*)cw.vbuf.p + vb * (s + i), n, vp);
+      }
+      if (C.schur) {
+        Vec* sv[5] = {&cw.t1, &cw.t2, &cw.t3, &cw.xe, &cw.rhs};
+        for (int i = 0; i < 5; ++i) *sv[i] = mkv((char*)cw.vbuf.p + vb * (2 * s + i), n, vp);
       }
       cw.np = 0;
       for (int i = 0; i < s; ++i)
@@ -617,10 +644,10 @@ struct Engine {
 
   // Table 1's coarsest solver: the deflated start x0 = V diag(1/sigma) U^dag b,
   // then up to inner_maxiter Chebyshev-basis CA-GCR(s) corrections, each one
-  // only for the systems whose residual is still above 0.25 ||b||
-  void deflated_solve(int l, const int* run) {
-    const CoarseLevel& C = c.coarse[l - 2];
-    GcrWork& G = lev[l];
+  // only for the systems whose residual is still above 0.25 ||b||.  A(o, i,
+  // run, sub) applies the operator (o = sub - A i when sub is given); r: residual scratch.
+  template <class Op>
+  void defl_cheb(const CoarseLevel& C, Op&& A, const Vec& b, const Vec& x, const Vec& r, const int* run) {
     const int s = cw.s;
     const long long n = (long long)C.g.V * C.N;
     Vec Ub;
@@ -628,20 +655,20 @@ struct Engine {
     Ub.n = n; Ub.nsys = C.defl_k; Ub.prec = vp;
     Vec Vb = Ub;
     Vb.p = vp == P64 ? C.dV64.p : C.dV32.p;
-    block_gram(Ub, G.b, cw.yd, ws, st(), run);
-    block_combine(G.x, Vb, cw.yd, nsys, st(), run);
+    block_gram(Ub, b, cw.yd, ws, st(), run);
+    block_combine(x, Vb, cw.yd, nsys, st(), run);
     const int p0[1] = {0};
-    blas_pair_dots(&G.b, 1, p0, p0, 1, cw.bb, 1, ws, st(), run);
+    blas_pair_dots(&b, 1, p0, p0, 1, cw.bb, 1, ws, st(), run);
     const double tol2 = c.params.inner_tol * c.params.inner_tol;
     for (int it = 0; it < c.params.inner_maxiter; ++it) {
       const int* rn = it == 0 ? run : cw.drun;
-      op(l, G.r, G.x, rn, &G.b);                        // r = b - A x
-      blas_pair_dots(&G.r, 1, p0, p0, 1, cw.rr, 1, ws, st(), rn);
+      A(r, x, rn, &b);                                   // r = b - A x
+      blas_pair_dots(&r, 1, p0, p0, 1, cw.rr, 1, ws, st(), rn);
       defl_active(cw.rr, cw.bb, tol2, cw.active, cw.drun, nsys, it == 0, st(), run);
       // Q_0 = r, Q_1 = (A - c) Q_0 / h, Q_{i+1} = 2 (A - c) Q_i / h - Q_{i-1}; W_i = A Q_i
-      cw.Q[0] = G.r;
+      cw.Q[0] = r;
       for (int i = 0; i < s; ++i) {
-        op(l, cw.W[i], cw.Q[i], cw.drun);
+        A(cw.W[i], cw.Q[i], cw.drun, nullptr);
         if (i + 1 == s) break;
         if (i == 0) {
           Vec in2[2] = {cw.W[0], cw.Q[0]};
@@ -653,7 +680,7 @@ struct Engine {
       }
       // minimum residual over span(W): (W^dag W) a = W^dag r, x += sum_i a_i Q_i
       std::vector<Vec> L(s + 1);
-      L[0] = G.r;
+      L[0] = r;
       for (int i = 0; i < s; ++i) L[i + 1] = cw.W[i];
       Epilogue ep;
       ep.kind = EPI_CA;
@@ -661,8 +688,41 @@ struct Engine {
       ep.d2a = cw.coef;
       blas_pair_dots(L.data(), s + 1, cw.pi, cw.pj, cw.np, cw.gram, kMaxPairs, ws, st(), cw.drun, ep);
       mask_coef(cw.coef, s, s, cw.active, nsys, st(), cw.drun);
-      blas_maxpy(G.x, cw.Q.data(), s, cw.coef, s, 1.0, true, st(), cw.drun);
+      blas_maxpy(x, cw.Q.data(), s, cw.coef, s, 1.0, true, st(), cw.drun);
     }
+  }
+
+  // The deflated coarsest solve, on A or (Schur form) on S = 1 - K_eo K_oe of
+  // A = 1 + K:  c_e - K_eo c_o = (c + R(c_o))_e with R(u) = u - A u = -K u,
+  // S x_e = that, then x_o = c_o - K_oe x_e = (c + R(x_e))_o.
+  void deflated_solve(int l, const int* run) {
+    const CoarseLevel& C = c.coarse[l - 2];
+    GcrWork& G = lev[l];
+    CoarseParams cp;
+    cp.g = C.g; cp.N = C.N;
+    auto A = [&](const Vec& o, const Vec& i, const int* rr, const Vec* sub) {
+      if (!C.schur) { op(l, o, i, rr, sub); return; }
+      if (sub == nullptr) { schur_apply(o, i, cp, C.Ss.st, cw.t1, cw.t2, st(), rr); return; }
+      schur_apply(cw.t3, i, cp, C.Ss.st, cw.t1, cw.t2, st(), rr);
+      blas_sub(o, *sub, cw.t3, st(), rr);
+    };
+    if (!C.schur) {
+      defl_cheb(C, A, G.b, G.x, G.r, run);
+      return;
+    }
+    CoarseParams cr = cp;
+    parity_pick(cw.t1, nullptr, &G.b, C.g, C.N, st(), run);      // c_o
+    cr.sub_from = cw.t1.p;
+    coarse_apply(cw.t2, cw.t1, cr, C.Ss.st, st(), run);           // R(c_o)
+    Vec in2[2] = {G.b, cw.t2};
+    blas_maxpy(cw.t1, in2, 2, c.ones, 2, 1.0, false, st(), run);  // c + R(c_o)
+    parity_pick(cw.rhs, &cw.t1, nullptr, C.g, C.N, st(), run);
+    defl_cheb(C, A, cw.rhs, cw.xe, G.r, run);
+    cr.sub_from = cw.xe.p;
+    coarse_apply(cw.t2, cw.xe, cr, C.Ss.st, st(), run);           // R(x_e)
+    Vec in2b[2] = {G.b, cw.t2};
+    blas_maxpy(cw.t1, in2b, 2, c.ones, 2, 1.0, false, st(), run);
+    parity_pick(G.x, &cw.xe, &cw.t1, C.g, C.N, st(), run);
   }
 
   // solve on level l (>= 2): G = lev[l], input lev[l].b, output lev[l].x
@@ -1017,13 +1077,35 @@ void build_deflation(Context& c, CoarseLevel& C, const void* start, int where) {
   Vec V = mk(buf[0], kw), W = mk(buf[1], kw), X = mk(buf[2], kw);
   void* tp[2] = {buf[3], buf[4]};     // two more Chebyshev iterates
   upload(V.p, start, vb, where, st);
-  // A and A^dag of the level's operator (X^{-1} A_hat in block mode), FP64
+  // A and A^dag of the level's operator (X^{-1} A_hat in block mode), FP64;
+  // with the Schur form, S and S^dag on vectors that vanish on odd sites
   DevBuf sdag;
   sdag.alloc(C.S64.bytes);
   coarse_dagger(sdag.as<double2>(), C.S64.as<double2>(), C.g, C.N, st);
   const Stored SA{C.S64.p, nullptr, 1.0f, S64}, SD{sdag.p, nullptr, 1.0f, S64};
   CoarseParams cp;
   cp.g = C.g; cp.N = C.N; cp.allow_tc = 0;
+  DevBuf sbuf;
+  Vec t1, t2;
+  if (C.schur) {
+    SMG_REQUIRE(2 * kw <= n, "coarsest_deflate: more vectors than even-site unknowns");
+    sbuf.alloc(vb * 2);
+    t1 = mk(sbuf.p, kw);
+    t2 = mk((char*)sbuf.p + vb, kw);
+    parity_pick(V, &V, nullptr, C.g, C.N, st);
+  }
+  auto applyA = [&](const Vec& o, const Vec& i) {
+    if (!C.schur) { coarse_apply(o, i, cp, SA, st); return; }
+    Vec a = t1, b = t2;
+    a.nsys = b.nsys = i.nsys;
+    schur_apply(o, i, cp, SA, a, b, st, nullptr);
+  };
+  auto applyAd = [&](const Vec& o, const Vec& i) {
+    if (!C.schur) { coarse_apply(o, i, cp, SD, st); return; }
+    Vec a = t1, b = t2;
+    a.nsys = b.nsys = i.nsys;
+    schur_apply(o, i, cp, SD, a, b, st, nullptr);
+  };
   const size_t kk = (size_t)kw * kw;
   DevBuf sm;
   sm.alloc(sizeof(double2) * (6 * kk + 4 * (size_t)kw + 8) + sizeof(double) * kw);
@@ -1049,8 +1131,8 @@ void build_deflation(Context& c, CoarseLevel& C, const void* start, int where) {
     blas_copy(x, mk(V.p, 1), st);
     const int pi[3] = {0, 0, 1}, pj[3] = {1, 0, 1};
     for (int it = 0; it < 30; ++it) {
-      coarse_apply(y, x, cp, SA, st);
-      coarse_apply(z, y, cp, SD, st);
+      applyA(y, x);
+      applyAd(z, y);
       Vec xz[2] = {x, z};
       blas_pair_dots(xz, 2, pi, pj, 3, small, 3, c.ws, st);
       double2 h[3];
@@ -1077,7 +1159,7 @@ void build_deflation(Context& c, CoarseLevel& C, const void* start, int where) {
     SMG_CUDA_OK(cudaStreamSynchronize(st));
     SMG_REQUIRE(lam[0] < 1e299, "coarsest_deflate: the start block has no usable direction");
   };
-  coarse_apply(W, V, cp, SA, st);
+  applyA(W, V);
   ritz();
   const int max_it = 200;
   int it = 0;
@@ -1093,16 +1175,16 @@ void build_deflation(Context& c, CoarseLevel& C, const void* start, int where) {
     int deg = 20;
     if (xmin > 1.0) deg = std::max(1, std::min(20, (int)(std::acosh(1e4) / std::acosh(xmin))));
     Vec T0 = V, T1 = mk(tp[0], kw), Tn = mk(tp[1], kw);
-    coarse_apply(W, T0, cp, SA, st);
-    coarse_apply(X, W, cp, SD, st);
+    applyA(W, T0);
+    applyAd(X, W);
     set_coef({make_double2(2.0 / (b - a), 0.0), make_double2(-(a + b) / (b - a), 0.0)});
     Vec in2[2] = {X, T0};
     blas_maxpy(T1, in2, 2, coef, 2, 1.0, false, st);
     if (deg > 1) set_coef({make_double2(4.0 / (b - a), 0.0), make_double2(-2.0 * (a + b) / (b - a), 0.0),
                            make_double2(-1.0, 0.0)});
     for (int j = 1; j < deg; ++j) {
-      coarse_apply(W, T1, cp, SA, st);
-      coarse_apply(X, W, cp, SD, st);
+      applyA(W, T1);
+      applyAd(X, W);
       Vec in3[3] = {X, T1, T0};
       blas_maxpy(Tn, in3, 3, coef, 3, 1.0, false, st);
       std::swap(T0.p, T1.p);    // T0 <- T1
@@ -1113,10 +1195,10 @@ void build_deflation(Context& c, CoarseLevel& C, const void* start, int where) {
     V.p = T1.p;
     tp[0] = T0.p;
     tp[1] = Tn.p;
-    coarse_apply(W, V, cp, SA, st);
+    applyA(W, V);
     ritz();
     // residuals of the k wanted pairs: A^dag W_j - lambda_j V_j
-    coarse_apply(X, W, cp, SD, st);
+    applyAd(X, W);
     {
       std::vector<double2> h(kw);
       for (int s = 0; s < kw; ++s) h[s] = make_double2(lam[s] < 1e299 ? lam[s] : 0.0, 0.0);
@@ -1383,8 +1465,15 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
     ndof = N;
   }
   if (P.coarsest_deflate > 0 && !c.coarse.back().dense) {
+    CoarseLevel& C = c.coarse.back();
     SMG_REQUIRE(phi0[P.n_coarse] != nullptr, "coarsest_deflate needs the start block phi0[n_coarse]");
-    build_deflation(c, c.coarse.back(), phi0[P.n_coarse], where);
+    C.schur = P.coarsest_schur != 0;
+    if (C.schur) {
+      SMG_REQUIRE(C.block, "coarsest_schur needs block_coarse (identity self blocks)");
+      for (int mu = 0; mu < 4; ++mu)
+        SMG_REQUIRE(C.g.L[mu] % 2 == 0, "coarsest_schur needs even coarse extents (every hop changes parity)");
+    }
+    build_deflation(c, C, phi0[P.n_coarse], where);
   }
   c.setup_done = true;
 }

@@ -210,3 +210,38 @@ def test_deflated_coarsest_in_kcycle():
     b = inputs.gaussian_field(lat.V, 3, 2003)
     xs, it, res = mg.solve(b, tol=1e-10)
     assert res <= 1e-10
+
+
+def test_schur_deflated_coarsest_in_kcycle():
+    """Table 1's level-3 form: the deflated Chebyshev-basis CA-GCR on the
+    even/odd Schur complement of the block-preconditioned coarsest operator.
+    One coarsest solve equals the Schur solve of the same deflated iteration
+    done by hand, with all of S's triplets deflated it is the exact solution,
+    and the outer solve reaches 1e-10 on M."""
+    from oracle.mg import MGParams, MultigridSolver
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims)
+    thin = inputs.random_su3_links(dims, 1004)
+    op = Staggered(lat, thin, None, 0.0, 0.1)
+    kw = dict(agg=[(4, 4, 4, 4)], nvec=[4], setup_maxiter=30, dense_max=0, block_coarse=True,
+              coarsest_deflate=8, coarsest_cheb_s=4)
+    phi = [inputs.gaussian_fields(4, lat.V, 3, 3007)]
+    mg = MultigridSolver(op, MGParams(coarsest_schur=True, **kw), phi)
+    lev = mg.levels[-1]
+    assert mg.schur is not None and mg.defl[0].shape == (len(mg.schur.even) * lev.n, 8)
+    rc = inputs.gaussian_field(lev.lat.V, lev.n, 8)
+    x = mg.coarse_solve(2, rc)
+    rcx = np.einsum("xij,xj->xi", mg.xinv[-1], rc)   # block mode: the level solves X^{-1} A_hat x = X^{-1} rc
+    sc = SchurCoarse(lev)
+    rhs, c = sc.schur_rhs(rcx)
+    xe = mg.deflated_coarsest_op(sc.schur_apply, rhs)
+    assert np.linalg.norm(x - sc.reconstruct(xe, c)) <= 1e-13 * np.linalg.norm(x)
+    Sd = mg.schur_dense()
+    Ad = lev.dense()
+    Ue, se, Ve = lowest_singular_triplets(Sd, Sd.shape[0])
+    xe_full = (Ve @ ((Ue.conj().T @ rhs.ravel()) / se)).reshape(rhs.shape)
+    xs = np.linalg.solve(Ad, rcx.ravel())
+    assert np.linalg.norm(sc.reconstruct(xe_full, c).ravel() - xs) <= 1e-10 * np.linalg.norm(xs)
+    b = inputs.gaussian_field(lat.V, 3, 2004)
+    _, it, res = mg.solve(b, tol=1e-10)
+    assert res <= 1e-10
