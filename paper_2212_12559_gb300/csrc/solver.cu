@@ -1805,6 +1805,9 @@ void ctx_coarse_solve(Context& c, int l, int nsys, const void* in, void* out, in
   SMG_REQUIRE(nsys >= 1 && nsys <= 16, "coarse_solve: 1 <= nsys <= 16");
   const CoarseLevel& C = c.coarse[l];
   const long long n = (long long)C.g.V * C.N;
+  // a new engine may grow the context's constant arrays, which a cached
+  // engine's captured graph points into: drop the cached one first
+  c.engine.reset();
   Engine E(c, nsys, std::vector<double>(1, c.mass), nsys);
   const int lv = l + 2;
   Scratch s;
