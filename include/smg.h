@@ -105,6 +105,13 @@ typedef struct smg_mg_params {
                                       coarsest_deflate > 0 and even coarse extents): right-hand side
                                       c_e - K_eo c_o, singular triplets and CA-GCR of S, then
                                       x_o = c_o - K_oe x_e.  Default 0. */
+  int schur_coarse;                /* Table 1 level-2 operator: 1 = every coarse level that is not
+                                      the coarsest runs its GCR and post-smoother on the Schur
+                                      complement S of its block-preconditioned operator (needs
+                                      block_coarse and even coarse extents), right-hand side
+                                      c_e - K_eo c_o, preconditioned by the K-cycle on the embedded
+                                      residual (r_e, 0) (for x_o = c_o - K_oe x_e the full residual
+                                      is exactly that), x_o reconstructed.  Default 0. */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */

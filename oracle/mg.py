@@ -47,6 +47,16 @@ through its even/odd Schur complement S = 1 - K_eo K_oe (oracle/schur.py):
 the right-hand side c_e - K_eo c_o, the deflated Chebyshev-basis CA-GCR on S
 with the singular triplets of S, then x_o = c_o - K_oe x_e.
 
+``schur_coarse`` (with ``block_coarse``) puts the intermediate coarse levels
+(level 2 of Table 1: "MG-preconditioned GCR" on the "Schur-preconditioned"
+operator) in the same form: the level's GCR and post-smoother run on S with
+right-hand side c_e - K_eo c_o, and the K-cycle below preconditions S as
+follows.  For an even iterate x_e completed by x_o = c_o - K_oe x_e, the full
+residual of A x = c is (r_e, 0) with r_e = c_e - K_eo c_o - S x_e the Schur
+residual; so the K-cycle applied to the embedded residual (r_e, 0) corrects
+the full system, and its even part corrects x_e.  Its coarse operator is the
+Galerkin product of the full block-preconditioned operator (Sec. 2.3).
+
 Readings taken where the paper is silent: no pre-smoothing anywhere (Table 1
 lists none), "0.25 or 8 iterations" stops at whichever comes first, the
 coarse levels use the un-preconditioned Galerkin operator (the Schur form of
@@ -83,6 +93,7 @@ class MGParams:
     coarsest_deflate: int = 0     # > 0: SVD-deflated Chebyshev-basis CA-GCR on the coarsest level
     coarsest_cheb_s: int = 16
     coarsest_schur: bool = False  # with coarsest_deflate: deflated CA-GCR on the even/odd Schur complement
+    schur_coarse: bool = False    # intermediate coarse levels: GCR and smoother on the Schur complement
 
 
 class MultigridSolver:
@@ -155,6 +166,13 @@ class MultigridSolver:
             x, _, _ = gcr(lop.apply, rc, tol=self.p.inner_tol, maxiter=self.p.inner_maxiter,
                           nkrylov=self.p.inner_maxiter, true_residual=False)
             return x
+        if self.p.schur_coarse:
+            sc = SchurCoarse(lop)
+            rhs, c = sc.schur_rhs(rc)
+            xe, _, _ = gcr(sc.schur_apply, rhs, precond=lambda r: self.kcycle_schur(l, sc, r),
+                           tol=self.p.inner_tol, maxiter=self.p.inner_maxiter,
+                           nkrylov=self.p.inner_maxiter, true_residual=False)
+            return sc.reconstruct(xe, c)
         x, _, _ = gcr(lop.apply, rc, precond=lambda r: self.kcycle(l, r),
                       tol=self.p.inner_tol, maxiter=self.p.inner_maxiter,
                       nkrylov=self.p.inner_maxiter, true_residual=False)
@@ -183,6 +201,16 @@ class MultigridSolver:
         T = self.transfers[l - 1]
         e = T.prolong(self.coarse_solve(l + 1, T.restrict(r)))
         e = e + ca_gcr(lop.apply, r - lop.apply(e), self.p.smoother_s)
+        return e
+
+    def kcycle_schur(self, l, sc, re):
+        """K-cycle for the Schur system of level l: the full-system K-cycle on
+        the embedded residual (r_e, 0) (restrict, coarse solve, prolong), its
+        even part, then CA-GCR(s) post-smoothing on S."""
+        T = self.transfers[l - 1]
+        full = sc._embed(re, sc.even)
+        e = T.prolong(self.coarse_solve(l + 1, T.restrict(full)))[sc.even]
+        e = e + ca_gcr(sc.schur_apply, re - sc.schur_apply(e), self.p.smoother_s)
         return e
 
     def precondition(self, r):

@@ -53,6 +53,7 @@ class MGParams(ctypes.Structure):
         ("coarsest_deflate", ctypes.c_int),
         ("coarsest_cheb_s", ctypes.c_int),
         ("coarsest_schur", ctypes.c_int),
+        ("schur_coarse", ctypes.c_int),
     ]
 
 

@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kBlockPrecThreads) block_precondition_kernel(d
 // out(X) = even(X) on even coarse sites, odd(X) on odd ones (a null source
 // gives zeros), per system; in place when out is one of the sources.
 template <typename C>
-__global__ void parity_pick_kernel(C* __restrict__ out, const C* even, const C* odd, Geom g, int N, long long n,
+__global__ void parity_pick_kernel(C* out, const C* even, const C* odd, Geom g, int N, long long n,
                                    long long total, const int* __restrict__ run) {
   if (run != nullptr && *run == 0) return;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;

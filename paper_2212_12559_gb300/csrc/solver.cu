@@ -282,6 +282,10 @@ struct Engine {
     int pi[kMaxPairs], pj[kMaxPairs], np = 0;
     Vec t1, t2, t3, xe, rhs;          // Schur form: scratch, x_e and c_e - K_eo c_o
   } cw;
+  // intermediate levels in Schur form: scratch t1..t3 and the saved right-hand side c, per level
+  std::vector<std::vector<Vec>> sch;
+  DevBuf schbuf;
+  bool schur_lvl(int l) const { return l >= 2 && c.coarse[l - 2].schur_level; }
   // graph of K_0
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
@@ -348,6 +352,24 @@ struct Engine {
     }
     c.ensure_consts(ns * 2 + 2);
     ws.get(sizeof(double2) * (size_t)(152 * 4) * kMaxPairs * ns);
+    {
+      sch.assign(nlev + 2, std::vector<Vec>());
+      size_t sb = 0;
+      for (int l = 2; l <= nlev; ++l)
+        if (schur_lvl(l)) sb += (size_t)4 * c.coarse[l - 2].g.V * c.coarse[l - 2].N * ns * prec_bytes(vp);
+      if (sb > 0) {
+        schbuf.alloc(sb);
+        size_t o = 0;
+        for (int l = 2; l <= nlev; ++l) {
+          if (!schur_lvl(l)) continue;
+          const long long n = (long long)c.coarse[l - 2].g.V * c.coarse[l - 2].N;
+          for (int i = 0; i < 4; ++i) {
+            sch[l].push_back(mkv((char*)schbuf.p + o, n, vp));
+            o += (size_t)n * ns * prec_bytes(vp);
+          }
+        }
+      }
+    }
     if (c.coarse.back().defl_k > 0) {
       SMG_REQUIRE(ns <= kDeflMaxBlock, "a deflated coarsest level solves at most 64 systems at once");
       const CoarseLevel& C = c.coarse.back();
@@ -401,7 +423,7 @@ struct Engine {
     {
       const int l = c.coarse.back().dense ? nlev : nlev + 1;
       const bool deflated_target = (l == nlev + 1 && c.coarse.back().defl_k > 0);
-      if (P.persistent && vp == P32 && l >= 2 && !deflated_target) {
+      if (P.persistent && vp == P32 && l >= 2 && !deflated_target && !schur_lvl(l)) {
         const CoarseLevel& C = c.coarse[l - 2];
         const int nvec_next = l <= nlev ? c.coarse[l - 1].tg.nvec : 0;
         persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, (long long)C.g.V * C.N, sp);
@@ -474,6 +496,16 @@ struct Engine {
       const CoarseLevel& C = c.coarse[l - 2];
       CoarseParams p;
       p.g = C.g; p.N = C.N;
+      if (C.schur_level) {      // the Schur complement S of an intermediate level
+        const std::vector<Vec>& T = sch[l];
+        if (sub == nullptr) {
+          schur_apply(out, in, p, C.Ss.st, T[0], T[1], st(), run);
+        } else {
+          schur_apply(T[2], in, p, C.Ss.st, T[0], T[1], st(), run);
+          blas_sub(out, *sub, T[2], st(), run);
+        }
+        return;
+      }
       p.sub_from = sub ? sub->p : nullptr;
       coarse_apply(out, in, p, C.Ss.st, st(), run);
     }
@@ -744,6 +776,25 @@ struct Engine {
     if (coarsest) {
       auto pre = [&](const Vec& z, const Vec& r, const int* rr) { blas_copy(z, r, st(), rr); };
       gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
+    } else if (C.schur_level) {
+      // c_e - K_eo c_o = (c + R(c_o))_e, GCR on S, x_o = (c + R(x_e))_o
+      const std::vector<Vec>& T = sch[l];
+      CoarseParams cr;
+      cr.g = C.g; cr.N = C.N;
+      blas_copy(T[3], G.b, st(), run);
+      parity_pick(T[0], nullptr, &T[3], C.g, C.N, st(), run);
+      cr.sub_from = T[0].p;
+      coarse_apply(T[1], T[0], cr, C.Ss.st, st(), run);
+      Vec in2[2] = {T[3], T[1]};
+      blas_maxpy(T[0], in2, 2, c.ones, 2, 1.0, false, st(), run);
+      parity_pick(G.b, &T[0], nullptr, C.g, C.N, st(), run);
+      auto pre = [&](const Vec& z, const Vec& r, const int* rr) { kcycle(l, z, r, rr); };
+      gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
+      cr.sub_from = G.x.p;
+      coarse_apply(T[1], G.x, cr, C.Ss.st, st(), run);
+      Vec in2b[2] = {T[3], T[1]};
+      blas_maxpy(T[0], in2b, 2, c.ones, 2, 1.0, false, st(), run);
+      parity_pick(G.x, &G.x, &T[0], C.g, C.N, st(), run);
     } else {
       auto pre = [&](const Vec& z, const Vec& r, const int* rr) { kcycle(l, z, r, rr); };
       gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
@@ -765,6 +816,8 @@ struct Engine {
     if (l == 1) { pe(); pb("K1.prolong"); }
     dbg("K.ec", lev[l + 1].x);
     prolong_op(e, lev[l + 1].x, C.tg, C.Ps.st, st(), run);
+    // a Schur-form level keeps the even part of the full-system correction
+    if (schur_lvl(l)) parity_pick(e, &e, nullptr, c.coarse[l - 2].g, c.coarse[l - 2].N, st(), run);
     if (l == 1) { pe(); pb("K1.smoother(A)"); }
     dbg("K.e", e);
     SmoothWork& S = (l == 1) ? sm_f : sm_c[l];
@@ -1464,6 +1517,14 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
     fg = cg;
     ndof = N;
   }
+  if (P.schur_coarse)
+    for (int l = 0; l + 1 < P.n_coarse; ++l) {
+      CoarseLevel& C = c.coarse[l];
+      SMG_REQUIRE(C.block, "schur_coarse needs block_coarse (identity self blocks)");
+      for (int mu = 0; mu < 4; ++mu)
+        SMG_REQUIRE(C.g.L[mu] % 2 == 0, "schur_coarse needs even coarse extents (every hop changes parity)");
+      C.schur_level = true;
+    }
   if (P.coarsest_deflate > 0 && !c.coarse.back().dense) {
     CoarseLevel& C = c.coarse.back();
     SMG_REQUIRE(phi0[P.n_coarse] != nullptr, "coarsest_deflate needs the start block phi0[n_coarse]");

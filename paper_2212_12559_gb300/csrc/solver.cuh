@@ -59,6 +59,7 @@ struct CoarseLevel {
   // U diag(1/sigma) (left ones over sigma), [k][Vc][N], FP64 and FP32
   int defl_k = 0;
   bool schur = false;       // deflated solve on the even/odd Schur complement (vectors vanish on odd sites)
+  bool schur_level = false; // intermediate level: GCR and smoother on the Schur complement
   DevBuf dV64, dU64, dV32, dU32;
   std::vector<double> sigma;
   double cheb_lmin = 0.0, cheb_lmax = 0.0, defl_res = 0.0;

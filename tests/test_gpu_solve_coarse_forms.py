@@ -261,3 +261,64 @@ def test_schur_deflated_coarsest_in_kcycle(binding, prec):
     check_solution(op, b, x, x_o, res_o)
     if prec == 0:
         assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
+
+
+def schur_level2_problem(binding, prec, inner_tol=0.25, inner_maxiter=8, persistent=0, smoother_s=8):
+    """Three-level naive problem on 8^4 (level 2: 2^4 sites x N = 8, block-
+    preconditioned, in Schur form; level 3 one site, dense), oracle CGNE
+    near-null vectors of A and of A_hat fed to both sides."""
+    from oracle.coarse import FineLevelOp, Transfer, galerkin, near_null_vectors
+    from oracle.mg import MGParams, MultigridSolver
+    dims, mass = (8, 8, 8, 8), 0.1
+    fat, naik, c, op = make(dims, False, mass, seed=1005)
+    agg = [(4, 4, 4, 4), (2, 2, 2, 2)]
+    lop = FineLevelOp(KahlerDirac(op))
+    raw1, _ = near_null_vectors(lop, inputs.gaussian_fields(4, op.lat.V, 3, 3012), 1e-6, 50)
+    S1 = galerkin(lop, Transfer(op.lat, 3, lop.chirality(), agg[0], raw1))
+    raw2, _ = near_null_vectors(S1, inputs.gaussian_fields(4, S1.lat.V, S1.n, 3013), 1e-6, 50)
+    kw = dict(agg=agg, nvec=[4, 4], setup_maxiter=0, block_coarse=True, schur_coarse=True,
+              inner_tol=inner_tol, inner_maxiter=inner_maxiter, smoother_s=smoother_s)
+    mg = MultigridSolver(op, MGParams(**kw), [raw1, raw2])
+    sv = binding.Solver(dims)
+    sv.set_gauge(fat, naik, c)
+    sv.set_mass(mass)
+    kw.update(n_coarse=2, block_coarse=1, schur_coarse=1, precision=prec, persistent=persistent)
+    sv.mg_setup(binding.default_params(**kw), [raw1, raw2])
+    return op, mg, sv
+
+
+def test_schur_level2_solve(binding):
+    """One level-2 solve in Schur form (right-hand side c_e - K_eo c_o, four
+    GCR steps on S preconditioned by the K-cycle on (r_e, 0) with CA-GCR(2)
+    smoothing on S, reconstruction of x_o) equals the oracle's element by
+    element (FP64, no early stop; a short smoother keeps its power basis well
+    conditioned, so both sides' least-squares solves keep every direction)."""
+    from oracle.schur import SchurCoarse
+    from oracle.solvers import gcr
+    op, mg, sv = schur_level2_problem(binding, binding.PREC_DOUBLE, inner_tol=1e-14, inner_maxiter=4,
+                                      smoother_s=2)
+    lev = mg.levels[1]
+    sc = SchurCoarse(lev)
+    rc = inputs.gaussian_fields(2, lev.lat.V, lev.n, 3014)
+    x = sv.coarse_solve(0, rc)
+    for q in range(2):
+        rhs, cc = sc.schur_rhs(rc[q])
+        xe, _, _ = gcr(sc.schur_apply, rhs, precond=lambda r: mg.kcycle_schur(2, sc, r), tol=1e-14, maxiter=4,
+                       nkrylov=4, true_residual=False)
+        assert rel(x[q], sc.reconstruct(xe, cc)) <= 1e-8
+
+
+@pytest.mark.parametrize("prec,persistent", [(0, 0), (2, 1)])
+def test_schur_level2_in_kcycle(binding, prec, persistent):
+    """The three-level solve with level 2 in Schur form converges on the full
+    M (mixed precision: the persistent solver steps aside for the Schur
+    level); in FP64 the outer iteration count follows the oracle's."""
+    op, mg, sv = schur_level2_problem(binding, prec, persistent=persistent)
+    b = inputs.gaussian_field(op.lat.V, 3, 2007)
+    x_o, it_o, res_o = mg.solve(b, 1e-10)
+    assert res_o <= 1e-10
+    x, info = sv.solve(b, 1e-10)
+    assert info.converged == 1 and info.true_residual <= 1e-10
+    check_solution(op, b, x, x_o, res_o)
+    if prec == 0:
+        assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)

@@ -245,3 +245,29 @@ def test_schur_deflated_coarsest_in_kcycle():
     b = inputs.gaussian_field(lat.V, 3, 2004)
     _, it, res = mg.solve(b, tol=1e-10)
     assert res <= 1e-10
+
+
+def test_schur_level2_in_kcycle():
+    """Table 1's level 2 in Schur form (GCR on S = 1 - K_eo K_oe preconditioned
+    by the K-cycle on the embedded residual (r_e, 0)) inside the three-level
+    K-cycle: the outer solve reaches 1e-10 on M, and one level-2 solve is an
+    exact solution of the level's full system when the inner tolerance is
+    tight (the reconstruction x_o = c_o - K_oe x_e closes the odd rows)."""
+    from oracle.mg import MGParams, MultigridSolver
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims)
+    thin = inputs.random_su3_links(dims, 1005)
+    op = Staggered(lat, thin, None, 0.0, 0.1)
+    phi = [inputs.gaussian_fields(4, lat.V, 3, 3010), inputs.gaussian_fields(4, 16, 8, 3011)]
+    kw = dict(agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[4, 4], setup_maxiter=30, block_coarse=True,
+              schur_coarse=True)
+    mg = MultigridSolver(op, MGParams(inner_tol=1e-12, inner_maxiter=60, **kw), phi)
+    lev = mg.levels[1]
+    rc = inputs.gaussian_field(lev.lat.V, lev.n, 12)
+    x = mg.coarse_solve(2, rc)
+    rcx = np.einsum("xij,xj->xi", mg.xinv[1], rc)
+    assert np.linalg.norm(rcx - lev.apply(x)) <= 1e-10 * np.linalg.norm(rcx)
+    mg = MultigridSolver(op, MGParams(**kw), phi)
+    b = inputs.gaussian_field(lat.V, 3, 2006)
+    _, it, res = mg.solve(b, tol=1e-10)
+    assert res <= 1e-10
