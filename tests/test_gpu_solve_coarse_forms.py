@@ -322,3 +322,28 @@ def test_schur_level2_in_kcycle(binding, prec, persistent):
     check_solution(op, b, x, x_o, res_o)
     if prec == 0:
         assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
+
+
+def test_coarse_form_options_refused(binding):
+    """Setups the coarse-level options cannot serve are refused before any
+    work: Schur forms without identity self blocks, a deflation block wider
+    than the kernels' 64 vectors, a deflated coarsest level without its start
+    block."""
+    dims, mass = (8, 8, 8, 8), 0.1
+    fat, naik, c, op = make(dims, False, mass, seed=1006)
+    phi = inputs.gaussian_fields(4, op.lat.V, 3, 3015)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(mass)
+    base = dict(nvec=[4], setup_maxiter=0, dense_max=0)
+    start = inputs.gaussian_fields(binding.deflation_block(8), 16, 8, 3016)
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(coarsest_deflate=8, coarsest_schur=1, **base), [phi, start])
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(coarsest_deflate=60, **base), [phi, start])
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(coarsest_deflate=8, **base), [phi])
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[4, 4],
+                                          setup_maxiter=0, schur_coarse=1),
+                   [phi, inputs.gaussian_fields(4, 16, 8, 3017)])
