@@ -13,7 +13,8 @@
 // * block_combine: a vector block times a small coefficient matrix;
 // * rayleigh_ritz: one CTA, two cyclic Jacobi eigen-decompositions (of the
 //   Gram matrix G = V^dag V, then of G^{-1/2} H G^{-1/2}), in FP64;
-// * the per-system flags of the deflated solve's 0.25 / iteration-cap rule.
+// * the per-system Gram sums and minimum-residual coefficients of the
+//   coarsest Chebyshev-basis CA-GCR, and the flags of its 0.25 / cycle-cap rule.
 #include <algorithm>
 
 #include "defl.cuh"
@@ -257,6 +258,115 @@ __global__ void __launch_bounds__(kRRThreads) rayleigh_ritz_kernel(const double2
   for (int j = t; j < k; j += kRRThreads) lam[j] = lv[perm[j]];
 }
 
+// partial[s][b][p] = this CTA's share of the upper-triangle pair sums of system s
+template <typename C>
+__global__ void __launch_bounds__(kGramThreads) multi_gram_kernel(MultiPtr v, int nv, long long n,
+                                                                  double2* __restrict__ partial,
+                                                                  const int* __restrict__ run) {
+  if (run != nullptr && *run == 0) return;
+  constexpr int TR = 32;
+  __shared__ C tile[kCaBasisMax + 1][TR];
+  const int t = threadIdx.x;
+  const int s = blockIdx.y;
+  const int np = nv * (nv + 1) / 2;
+  int pi = 0, pj = 0;
+  if (t < np) {                       // pair t -> (i, j), i <= j, row order
+    int rem = t;
+    while (rem >= nv - pi) { rem -= nv - pi; ++pi; }
+    pj = pi + rem;
+  }
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long r0 = (long long)blockIdx.x * per;
+  const long long r1 = r0 + per < n ? r0 + per : n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (long long base = r0; base < r1; base += TR) {
+    const int cnt = (int)(r1 - base < TR ? r1 - base : TR);
+    for (int e = t; e < nv * TR; e += kGramThreads) {
+      const int vi = e / TR, r = e % TR;
+      C val;
+      val.x = 0;
+      val.y = 0;
+      if (r < cnt) val = ((const C*)v.p[vi])[(size_t)s * n + base + r];
+      tile[vi][r] = val;
+    }
+    __syncthreads();
+    if (t < np)
+      for (int r = 0; r < cnt; ++r) {
+        const C a = tile[pi][r], b = tile[pj][r];
+        acc.x += (double)a.x * b.x + (double)a.y * b.y;
+        acc.y += (double)a.x * b.y - (double)a.y * b.x;
+      }
+    __syncthreads();
+  }
+  if (t < np) partial[((size_t)s * gridDim.x + blockIdx.x) * np + t] = acc;
+}
+
+// out[s][p] = sum_b partial[s][b][p]
+__global__ void multi_gram_final_kernel(const double2* __restrict__ partial, int nb, int np, int nsys,
+                                        double2* __restrict__ out, const int* __restrict__ run) {
+  if (run != nullptr && *run == 0) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= np * nsys) return;
+  const int s = q / np, p = q % np;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = 0; b < nb; ++b) acc = cadd(acc, partial[((size_t)s * nb + b) * np + p]);
+  out[q] = acc;
+}
+
+// One CTA per system: H = W^dag W (m x m) from the pair sums over [r, W_0..],
+// H = Q diag(lam) Q^dag by cyclic Jacobi, a = Q diag(1/lam) Q^dag (W^dag r)
+// over the eigenvalues above drop x max.
+__global__ void __launch_bounds__(kRRThreads) cagcr_coef_kernel(const double2* __restrict__ gram, int m,
+                                                                double drop, const int* __restrict__ active,
+                                                                double2* __restrict__ coef, double2* scratch,
+                                                                const int* __restrict__ run) {
+  if (run != nullptr && *run == 0) return;
+  __shared__ double red[kRRThreads];
+  __shared__ double2 gq[kCaBasisMax];    // Q^dag g / lam
+  __shared__ double lv[kCaBasisMax];
+  const int s = blockIdx.x;
+  const int t = threadIdx.x;
+  const int nv = m + 1;
+  const int np = nv * (nv + 1) / 2;
+  const double2* g = gram + (size_t)s * np;
+  double2* H = scratch + (size_t)s * 2 * m * m;
+  double2* Q = H + (size_t)m * m;
+  // vector list index 0 is r, 1 + i is W_i; pair (a, b), a <= b, sits at a nv - a (a - 1) / 2 + b - a
+  auto pidx = [&](int a, int b) { return a * nv - a * (a - 1) / 2 + (b - a); };
+  for (int e = t; e < m * m; e += kRRThreads) {
+    const int i = e / m, j = e % m;
+    const double2 v = i <= j ? g[pidx(1 + i, 1 + j)] : g[pidx(1 + j, 1 + i)];
+    H[e] = i <= j ? v : make_double2(v.x, -v.y);   // <W_i, W_j> = conj(<W_j, W_i>)
+  }
+  __syncthreads();
+  cta_jacobi(H, Q, m, red);
+  if (t == 0) {
+    double lmax = 0.0;
+    for (int i = 0; i < m; ++i) lmax = fmax(lmax, H[(size_t)i * m + i].x);
+    for (int i = 0; i < m; ++i) {
+      const double l = H[(size_t)i * m + i].x;
+      lv[i] = (lmax > 0.0 && l > drop * lmax) ? 1.0 / l : 0.0;
+    }
+  }
+  __syncthreads();
+  // gq_k = (sum_i conj(Q_ik) <W_i, r>) / lam_k ; <W_i, r> is pair (0, 1 + i) conjugated
+  for (int k = t; k < m; k += kRRThreads) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < m; ++i) {
+      const double2 wr0 = g[pidx(0, 1 + i)];             // <r, W_i>
+      cfmac(acc, Q[(size_t)i * m + k], make_double2(wr0.x, -wr0.y));
+    }
+    gq[k] = cscale(acc, lv[k]);
+  }
+  __syncthreads();
+  const bool on = active == nullptr || active[s] != 0;
+  for (int i = t; i < m; i += kRRThreads) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < m; ++k) cfma(acc, Q[(size_t)i * m + k], gq[k]);
+    coef[(size_t)s * m + i] = on ? acc : make_double2(0.0, 0.0);
+  }
+}
+
 __global__ void defl_active_kernel(const double2* __restrict__ rr, const double2* __restrict__ bb, double tol2,
                                    int* __restrict__ active, int* __restrict__ drun, int nsys, int first,
                                    const int* __restrict__ run_outer) {
@@ -274,15 +384,6 @@ __global__ void defl_active_kernel(const double2* __restrict__ rr, const double2
   }
   __syncthreads();
   if (threadIdx.x == 0) *drun = any;
-}
-
-__global__ void mask_coef_kernel(double2* __restrict__ coef, int ldc, int m, const int* __restrict__ active,
-                                 int nsys, const int* __restrict__ run) {
-  if (run != nullptr && *run == 0) return;
-  for (int e = threadIdx.x; e < nsys * m; e += blockDim.x) {
-    const int s = e / m, i = e % m;
-    if (active[s] == 0) coef[(size_t)s * ldc + i] = make_double2(0.0, 0.0);
-  }
 }
 
 }  // namespace
@@ -326,15 +427,40 @@ void rayleigh_ritz(const double2* G, const double2* H, int k, double2* Y, double
   SMG_LAUNCH_OK();
 }
 
+void multi_gram(const Vec* vs, int nv, double2* out, Workspace& ws, cudaStream_t st, const int* run) {
+  SMG_REQUIRE(nv >= 1 && nv <= kCaBasisMax + 1 && nv <= kMaxVecs, "multi_gram: 1 <= nv <= 17");
+  MultiPtr mp{};
+  for (int i = 0; i < nv; ++i) {
+    SMG_REQUIRE(vs[i].n == vs[0].n && vs[i].nsys == vs[0].nsys && vs[i].prec == vs[0].prec,
+                "multi_gram: vector shapes differ");
+    mp.p[i] = vs[i].p;
+  }
+  const int np = nv * (nv + 1) / 2;
+  const long long n = vs[0].n;
+  const int nsys = vs[0].nsys;
+  const int nb = (int)std::min<long long>(2 * 152 / std::max(1, nsys) + 1, (n + 255) / 256);
+  double2* partial = (double2*)ws.get(sizeof(double2) * (size_t)nb * np * nsys);
+  const dim3 grid(nb, nsys);
+  if (vs[0].prec == P64)
+    launch_k(multi_gram_kernel<double2>, grid, dim3(kGramThreads), 0, st, mp, nv, n, partial, run);
+  else
+    launch_k(multi_gram_kernel<float2>, grid, dim3(kGramThreads), 0, st, mp, nv, n, partial, run);
+  launch_k(multi_gram_final_kernel, dim3(ceil_div((long long)np * nsys, 256)), dim3(256), 0, st,
+           (const double2*)partial, nb, np, nsys, out, run);
+  SMG_LAUNCH_OK();
+}
+
+void cagcr_coef(const double2* gram, int m, double drop, const int* active, double2* coef, double2* scratch,
+                int nsys, cudaStream_t st, const int* run) {
+  SMG_REQUIRE(m >= 1 && m <= kCaBasisMax && nsys >= 1, "cagcr_coef: 1 <= m <= 16");
+  launch_k(cagcr_coef_kernel, dim3(nsys), dim3(kRRThreads), 0, st, gram, m, drop, active, coef, scratch, run);
+  SMG_LAUNCH_OK();
+}
+
 void defl_active(const double2* rr, const double2* bb, double tol2, int* active, int* drun, int nsys, bool first,
                  cudaStream_t st, const int* run_outer) {
   launch_k(defl_active_kernel, dim3(1), dim3(128), 0, st, rr, bb, tol2, active, drun, nsys, first ? 1 : 0,
            run_outer);
-  SMG_LAUNCH_OK();
-}
-
-void mask_coef(double2* coef, int ldc, int m, const int* active, int nsys, cudaStream_t st, const int* run) {
-  launch_k(mask_coef_kernel, dim3(1), dim3(128), 0, st, coef, ldc, m, active, nsys, run);
   SMG_LAUNCH_OK();
 }
 

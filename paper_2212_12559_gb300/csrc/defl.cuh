@@ -33,7 +33,20 @@ void rayleigh_ritz(const double2* G, const double2* H, int k, double2* Y, double
 // When run_outer is set and 0, only *drun = 0.
 void defl_active(const double2* rr, const double2* bb, double tol2, int* active, int* drun, int nsys, bool first,
                  cudaStream_t st, const int* run_outer);
-// coef[s * ldc + i] = 0 for every system s with active[s] == 0, i < m.
-void mask_coef(double2* coef, int ldc, int m, const int* active, int nsys, cudaStream_t st, const int* run);
+
+constexpr int kCaBasisMax = 16;      // Chebyshev-basis CA-GCR length on the coarsest level (Table 1: 16)
+
+// Per-system Gram sums of a vector list: out[s][p] = <vs[i], vs[j]> for the
+// pairs i <= j in row order of the upper triangle (p = i nv - i (i - 1) / 2 +
+// j - i), FP64 sums; nv <= kCaBasisMax + 1.  All vectors batched alike.
+void multi_gram(const Vec* vs, int nv, double2* out, Workspace& ws, cudaStream_t st, const int* run = nullptr);
+// Minimum-residual coefficients of CA-GCR(m) from multi_gram over the list
+// [r, W_0 .. W_{m-1}]: a = argmin |r - sum_i a_i W_i| through the
+// eigen-decomposition of the Gram matrix W^dag W (one CTA per system, cyclic
+// Jacobi in FP64), eigenvalues at or below drop x the largest left out (the
+// minimum-norm least-squares solution).  coef[s * m + i]; 0 for systems with
+// active[s] == 0.  scratch: 2 m^2 double2 per system.
+void cagcr_coef(const double2* gram, int m, double drop, const int* active, double2* coef, double2* scratch,
+                int nsys, cudaStream_t st, const int* run = nullptr);
 
 }  // namespace smg

@@ -279,7 +279,7 @@ struct Engine {
     double2 *c1 = nullptr, *c2 = nullptr, *gram = nullptr, *coef = nullptr, *yd = nullptr, *rr = nullptr,
             *bb = nullptr;
     int *active = nullptr, *drun = nullptr;
-    int pi[kMaxPairs], pj[kMaxPairs], np = 0;
+    double2 *mgram = nullptr, *cscr = nullptr;   // per-system Gram sums, normal-equation scratch
     Vec t1, t2, t3, xe, rhs;          // Schur form: scratch, x_e and c_e - K_eo c_o
   } cw;
   // intermediate levels in Schur form: scratch t1..t3 and the saved right-hand side c, per level
@@ -388,19 +388,17 @@ struct Engine {
         Vec* sv[5] = {&cw.t1, &cw.t2, &cw.t3, &cw.xe, &cw.rhs};
         for (int i = 0; i < 5; ++i) *sv[i] = mkv((char*)cw.vbuf.p + vb * (2 * s + i), n, vp);
       }
-      cw.np = 0;
-      for (int i = 0; i < s; ++i)
-        for (int j = i; j < s; ++j) { cw.pi[cw.np] = i + 1; cw.pj[cw.np] = j + 1; ++cw.np; }
-      for (int i = 0; i < s; ++i) { cw.pi[cw.np] = i + 1; cw.pj[cw.np] = 0; ++cw.np; }
-      const size_t nd = (size_t)ns * (2 + 3 + kMaxPairs + s + 2) + (size_t)C.defl_k * ns;
+      const int npg = (s + 1) * (s + 2) / 2;       // Gram pairs of [r, W_0 .. W_{s-1}]
+      const size_t nd = (size_t)ns * (2 + 3 + npg + s + 2 + 2 * s * s) + (size_t)C.defl_k * ns;
       cw.sbuf.alloc(sizeof(double2) * nd + sizeof(int) * (ns + 1));
       cw.c1 = cw.sbuf.as<double2>();
       cw.c2 = cw.c1 + 2 * ns;
-      cw.gram = cw.c2 + 3 * ns;
-      cw.coef = cw.gram + (size_t)kMaxPairs * ns;
+      cw.mgram = cw.c2 + 3 * ns;
+      cw.coef = cw.mgram + (size_t)npg * ns;
       cw.rr = cw.coef + (size_t)s * ns;
       cw.bb = cw.rr + ns;
-      cw.yd = cw.bb + ns;
+      cw.cscr = cw.bb + ns;
+      cw.yd = cw.cscr + (size_t)2 * s * s * ns;
       cw.active = (int*)(cw.yd + (size_t)C.defl_k * ns);
       cw.drun = cw.active + ns;
       // T = (A - c) / h maps [sigma_k, sigma_max] to [-1, 1]
@@ -416,6 +414,7 @@ struct Engine {
       }
       SMG_CUDA_OK(cudaMemcpyAsync(cw.c1, hc.data(), sizeof(double2) * hc.size(), cudaMemcpyHostToDevice, c.stream));
       ws.get(sizeof(double2) * (size_t)(2 * 152) * C.defl_k * ns);
+      ws.get(sizeof(double2) * (size_t)(2 * 152 / ns + 1) * npg * ns);
       SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
     }
     // one cooperative launch for the last GCR level when its coarser level is
@@ -710,16 +709,14 @@ struct Engine {
           blas_maxpy(cw.Q[i + 1], in3, 3, cw.c2, 3, 1.0, false, st(), cw.drun);
         }
       }
-      // minimum residual over span(W): (W^dag W) a = W^dag r, x += sum_i a_i Q_i
+      // minimum residual over span(W): (W^dag W) a = W^dag r, x += sum_i a_i Q_i;
+      // Gram eigenvalues below 1e-12 (FP64 vectors) or 1e-6 (FP32) of the
+      // largest are rounding noise of the sums and are left out
       std::vector<Vec> L(s + 1);
       L[0] = r;
       for (int i = 0; i < s; ++i) L[i + 1] = cw.W[i];
-      Epilogue ep;
-      ep.kind = EPI_CA;
-      ep.s = s;
-      ep.d2a = cw.coef;
-      blas_pair_dots(L.data(), s + 1, cw.pi, cw.pj, cw.np, cw.gram, kMaxPairs, ws, st(), cw.drun, ep);
-      mask_coef(cw.coef, s, s, cw.active, nsys, st(), cw.drun);
+      multi_gram(L.data(), s + 1, cw.mgram, ws, st(), cw.drun);
+      cagcr_coef(cw.mgram, s, vp == P64 ? 1e-12 : 1e-6, cw.active, cw.coef, cw.cscr, nsys, st(), cw.drun);
       blas_maxpy(x, cw.Q.data(), s, cw.coef, s, 1.0, true, st(), cw.drun);
     }
   }
@@ -1312,8 +1309,8 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
   SMG_REQUIRE(phi0 != nullptr, "phi0 must hold one start array per coarsening");
   SMG_REQUIRE(P.coarsest_deflate >= 0 && P.coarsest_deflate + defl_guard(P.coarsest_deflate) <= kDeflMaxBlock,
               "coarsest_deflate must be 0..51");
-  SMG_REQUIRE(P.coarsest_deflate == 0 || (P.coarsest_cheb_s >= 1 && P.coarsest_cheb_s <= 8),
-              "coarsest_cheb_s must be 1..8");
+  SMG_REQUIRE(P.coarsest_deflate == 0 || (P.coarsest_cheb_s >= 1 && P.coarsest_cheb_s <= kCaBasisMax),
+              "coarsest_cheb_s must be 1..16");
   c.engine.reset();
   c.setup_done = false;
   c.params = P;

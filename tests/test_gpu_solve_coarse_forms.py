@@ -138,7 +138,7 @@ def test_block_coarse_solve_matches_oracle(binding):
             assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
 
 
-def deflation_problem(binding, prec, k=8, s=8, inner_tol=0.25, inner_maxiter=8):
+def deflation_problem(binding, prec, k=8, s=16, inner_tol=0.25, inner_maxiter=8):
     """Two-level naive problem on 8x8x4x4 (coarsest level 2x2x1x1 x N = 8, 32
     unknowns) whose coarsest level is solved iteratively (dense_max = 0) with
     Table 1's SVD deflation; oracle CGNE near-null vectors fed to both sides."""
@@ -192,8 +192,8 @@ def test_deflated_coarsest_singular_values_and_solve(binding):
 
 @pytest.mark.parametrize("prec", [0, 2])
 def test_deflated_coarsest_in_kcycle(binding, prec):
-    """The outer solve with the deflated Chebyshev-basis CA-GCR coarsest level
-    converges on the full M; in FP64 its outer iteration count follows the
+    """The outer solve with the deflated Chebyshev-basis CA-GCR(16) coarsest
+    level (Table 1) converges on the full M; in FP64 its outer iteration count follows the
     oracle's K-cycle with the same coarsest solver."""
     op, mg, sv = deflation_problem(binding, prec)
     b = inputs.gaussian_field(op.lat.V, 3, 2003)
@@ -252,7 +252,7 @@ def test_schur_deflated_coarsest(binding):
 def test_schur_deflated_coarsest_in_kcycle(binding, prec):
     """The outer solve with the Schur-form deflated coarsest level converges on
     the full M; in FP64 its outer iteration count follows the oracle's."""
-    op, mg, sv = schur_problem(binding, prec, s=8, inner_tol=0.25, inner_maxiter=8)
+    op, mg, sv = schur_problem(binding, prec, s=16, inner_tol=0.25, inner_maxiter=8)
     b = inputs.gaussian_field(op.lat.V, 3, 2005)
     x_o, it_o, res_o = mg.solve(b, 1e-10)
     assert res_o <= 1e-10
