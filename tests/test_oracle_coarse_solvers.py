@@ -271,3 +271,35 @@ def test_schur_level2_in_kcycle():
     b = inputs.gaussian_field(lat.V, 3, 2006)
     _, it, res = mg.solve(b, tol=1e-10)
     assert res <= 1e-10
+
+
+def test_schur_spectrum_closed_form(coarse):
+    """Independent of the Schur code's own formulas: for the bipartite
+    A' = [[1, K_eo], [K_oe, 1]], A' (x_e, x_o) = lam (x_e, x_o) gives
+    K_eo K_oe x_e = (lam - 1)^2 x_e, so every eigenvalue mu of
+    S = 1 - K_eo K_oe belongs to the pair lam = 1 +- sqrt(1 - mu) of A' (the
+    even and odd site counts are equal, so these pairs are all of A's
+    spectrum)."""
+    S, _ = coarse
+    sc = SchurCoarse(S)
+    ne, N = len(sc.even), S.n
+    Sd = np.empty((ne * N, ne * N), dtype=np.complex128)
+    for j in range(ne * N):
+        e = np.zeros(ne * N, dtype=np.complex128)
+        e[j] = 1.0
+        Sd[:, j] = sc.schur_apply(e.reshape(ne, N)).ravel()
+    V, n = S.lat.V, S.lat.V * N
+    Bd = np.empty((n, n), dtype=np.complex128)
+    for j in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = 1.0
+        Bd[:, j] = sc.block_apply(e.reshape(V, N)).ravel()
+    mu = np.linalg.eigvals(Sd)
+    root = np.sqrt(1.0 - mu)
+    pred = np.concatenate([1.0 + root, 1.0 - root])
+    lam = np.linalg.eigvals(Bd)
+    scale = np.abs(lam).max()
+    # every predicted value has an eigenvalue of A' next to it, and vice versa
+    d1 = np.abs(pred[:, None] - lam[None, :]).min(axis=1)
+    d2 = np.abs(lam[:, None] - pred[None, :]).min(axis=1)
+    assert d1.max() <= 1e-8 * scale and d2.max() <= 1e-8 * scale
