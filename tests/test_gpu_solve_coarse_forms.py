@@ -347,3 +347,46 @@ def test_coarse_form_options_refused(binding):
         s.mg_setup(binding.default_params(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[4, 4],
                                           setup_maxiter=0, schur_coarse=1),
                    [phi, inputs.gaussian_fields(4, 16, 8, 3017)])
+
+
+def test_deflation_at_16x4_coarsest(binding):
+    """The deflation at the 16^4 three-level workload's coarsest level (2^4
+    sites x N = 64, 1024 unknowns; near-null vectors by the GPU's own setup):
+    the GPU's singular values equal the dense SVD of the GPU's coarsest
+    stencil, and a deflated coarsest solve of three systems (two CA-GCR(4)
+    cycles) equals the same steps done densely.  k sits at a gap of the
+    singular values, so the deflation space, and with it x0, is unique."""
+    from oracle.solvers import ca_gcr_chebyshev, lowest_singular_triplets
+    dims, mass = (16, 16, 16, 16), 0.05
+    fat, naik, c, op = make(dims, True, mass, seed=1002)
+    phi = [inputs.gaussian_fields(24, op.lat.V, 3, 3002), inputs.gaussian_fields(32, 256, 48, 3003)]
+    kw = dict(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[24, 32], setup_maxiter=100, dense_max=0,
+              precision=binding.PREC_DOUBLE, coarsest_cheb_s=4, inner_tol=1e-12, inner_maxiter=2)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(mass)
+    s.mg_setup(binding.default_params(**kw), phi)
+    L = s.coarse_op(1)
+    Vc, N = L.shape[0], L.shape[1]
+    Sc = CoarseStencil(Lattice((2, 2, 2, 2)), L[:, :, 0, :].copy(),
+                       np.stack([L[:, :, 1 + 2 * mu, :] for mu in range(4)]),
+                       np.stack([L[:, :, 2 + 2 * mu, :] for mu in range(4)]))
+    Ad = Sc.dense()
+    sv = np.sort(np.linalg.svd(Ad, compute_uv=False))
+    gaps = [kk for kk in range(16, 33) if sv[kk] > 1.02 * sv[kk - 1]]
+    assert gaps, "no singular-value gap between 16 and 32"
+    k = gaps[-1]
+    s.mg_setup(binding.default_params(coarsest_deflate=k, **kw),
+               phi + [inputs.gaussian_fields(binding.deflation_block(k), Vc, N, 3004)])
+    got, info = s.deflation()
+    assert rel(got, sv[:k]) <= 1e-9, (got, sv[:k])
+    assert info["residual"] <= 1e-10
+    U, sig, Vr = lowest_singular_triplets(Ad, k)
+    apply = lambda v: (Ad @ v.ravel()).reshape(v.shape)
+    rc = inputs.gaussian_fields(3, Vc, N, 3005)
+    x = s.coarse_solve(1, rc)
+    for q in range(3):
+        xr = (Vr @ ((U.conj().T @ rc[q].ravel()) / sig)).reshape(rc[q].shape)
+        for _ in range(2):
+            xr = xr + ca_gcr_chebyshev(apply, rc[q] - apply(xr), 4, float(sig[-1]), float(sv[-1]))
+        assert rel(x[q], xr) <= 1e-8
