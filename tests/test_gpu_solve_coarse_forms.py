@@ -390,3 +390,24 @@ def test_deflation_at_16x4_coarsest(binding):
         for _ in range(2):
             xr = xr + ca_gcr_chebyshev(apply, rc[q] - apply(xr), 4, float(sig[-1]), float(sv[-1]))
         assert rel(x[q], xr) <= 1e-8
+
+
+@pytest.mark.parametrize("forms", [dict(block_coarse=1), dict(block_coarse=1, schur_coarse=1)])
+def test_coarse_forms_at_16x4_workload(binding, forms):
+    """The 16^4 HISQ-shaped three-level workload (truncated level-1 operator,
+    24 / 32 vectors, FP32 with FP16 storage, graph-replayed K-cycle) with the
+    block-preconditioned coarse levels, and with level 2 in Schur form as
+    well: the solve meets 1e-10 on the full M (recomputed by the oracle)."""
+    dims, mass = (16, 16, 16, 16), 0.01
+    fat, naik, c, op = make(dims, True, mass, seed=1002)
+    phi = [inputs.gaussian_fields(24, op.lat.V, 3, 3002), inputs.gaussian_fields(32, 256, 48, 3003)]
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(mass)
+    s.mg_setup(binding.default_params(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[24, 32],
+                                      setup_maxiter=300, precision=binding.PREC_HALF, use_graph=1,
+                                      truncate_naik=1, max_outer=300, **forms), phi)
+    b = inputs.gaussian_field(op.lat.V, 3, 2002)
+    x, info = s.solve(b, 1e-10)
+    assert info.converged == 1
+    assert np.linalg.norm(b - op.M(x)) <= 1e-10 * np.linalg.norm(b)
