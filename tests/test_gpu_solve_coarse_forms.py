@@ -1,6 +1,8 @@
 """GPU parity of the coarse-level operator forms of Sec. 2.3 and Table 1
 through the C ABI, judged by the oracle: the block-preconditioned coarse
-operators X^{-1} A_hat (stencils, X^{-1}, the K-cycle solve).
+operators X^{-1} A_hat (stencils, X^{-1}, the K-cycle solve), the
+SVD-deflated Chebyshev-basis CA-GCR coarsest solver, and the even/odd Schur
+forms of the coarsest and intermediate levels.
 
 Tolerances: the FP64 stencils and X^{-1} to 1e-11 relative (the self blocks
 are well conditioned, condition number about 1.1 on these fields); coarse
@@ -62,6 +64,31 @@ def check_solution(op, b, x, x_ref, tol_ref):
     assert r <= 1e-10, r
     err = np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)
     assert err <= bound(op, 1e-10 + tol_ref), err
+
+
+def test_coarse_form_options_refused(binding):
+    """Setups the coarse-level options cannot serve are refused before any
+    work: Schur forms without identity self blocks, a deflation block wider
+    than the kernels' 64 vectors, a deflated coarsest level without its start
+    block."""
+    dims, mass = (8, 8, 8, 8), 0.1
+    fat, naik, c, op = make(dims, False, mass, seed=1006)
+    phi = inputs.gaussian_fields(4, op.lat.V, 3, 3015)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(mass)
+    base = dict(nvec=[4], setup_maxiter=0, dense_max=0)
+    start = inputs.gaussian_fields(binding.deflation_block(8), 16, 8, 3016)
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(coarsest_deflate=8, coarsest_schur=1, **base), [phi, start])
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(coarsest_deflate=60, **base), [phi, start])
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(coarsest_deflate=8, **base), [phi])
+    with pytest.raises(binding.SmgError):
+        s.mg_setup(binding.default_params(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[4, 4],
+                                          setup_maxiter=0, schur_coarse=1),
+                   [phi, inputs.gaussian_fields(4, 16, 8, 3017)])
 
 
 def test_block_preconditioned_setup_cross_fed(binding):
@@ -322,31 +349,6 @@ def test_schur_level2_in_kcycle(binding, prec, persistent):
     check_solution(op, b, x, x_o, res_o)
     if prec == 0:
         assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
-
-
-def test_coarse_form_options_refused(binding):
-    """Setups the coarse-level options cannot serve are refused before any
-    work: Schur forms without identity self blocks, a deflation block wider
-    than the kernels' 64 vectors, a deflated coarsest level without its start
-    block."""
-    dims, mass = (8, 8, 8, 8), 0.1
-    fat, naik, c, op = make(dims, False, mass, seed=1006)
-    phi = inputs.gaussian_fields(4, op.lat.V, 3, 3015)
-    s = binding.Solver(dims)
-    s.set_gauge(fat, naik, c)
-    s.set_mass(mass)
-    base = dict(nvec=[4], setup_maxiter=0, dense_max=0)
-    start = inputs.gaussian_fields(binding.deflation_block(8), 16, 8, 3016)
-    with pytest.raises(binding.SmgError):
-        s.mg_setup(binding.default_params(coarsest_deflate=8, coarsest_schur=1, **base), [phi, start])
-    with pytest.raises(binding.SmgError):
-        s.mg_setup(binding.default_params(coarsest_deflate=60, **base), [phi, start])
-    with pytest.raises(binding.SmgError):
-        s.mg_setup(binding.default_params(coarsest_deflate=8, **base), [phi])
-    with pytest.raises(binding.SmgError):
-        s.mg_setup(binding.default_params(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[4, 4],
-                                          setup_maxiter=0, schur_coarse=1),
-                   [phi, inputs.gaussian_fields(4, 16, 8, 3017)])
 
 
 def test_deflation_at_16x4_coarsest(binding):
