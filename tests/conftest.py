@@ -13,6 +13,18 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
+LATE_MODULES = ("test_gpu_solve_coarse_forms.py",)
+
+
+def pytest_collection_modifyitems(config, items):
+    """The coarse-level form tests (the newest GPU paths) run after the rest of
+    the suite, so that under -x a failure there cannot hide the results of the
+    established tests."""
+    late = [it for it in items if it.fspath.basename in LATE_MODULES]
+    if late:
+        items[:] = [it for it in items if it.fspath.basename not in LATE_MODULES] + late
+
+
 @pytest.fixture(scope="session")
 def lib():
     """The C-ABI library, loaded once (GPU tests only)."""

@@ -5,7 +5,7 @@ cannot take cudaMalloc's implicit synchronisation, use it.  Checked here
 through the C ABI against the existing entry point that reduces with the
 context's allocated scratch: smg_fermion_action returns S = <Y, Y> and
 dS/dm = -2 m <X, X>; the same sums from smg_dot_noalloc, on two calls in a
-row, must agree to rounding (1e-12 relative).  Collected last on purpose.
+row, must agree to rounding (1e-12 relative).  Collected after the solver tests.
 """
 import numpy as np
 import pytest
