@@ -396,15 +396,21 @@ def test_deflation_at_16x4_coarsest(binding):
         assert rel(x[q], xr) <= 1e-8
 
 
-@pytest.mark.parametrize("forms", [dict(block_coarse=1), dict(block_coarse=1, schur_coarse=1)])
+@pytest.mark.parametrize("forms", [dict(block_coarse=1), dict(block_coarse=1, schur_coarse=1),
+                                   dict(block_coarse=1, schur_coarse=1, dense_max=0, coarsest_deflate=16,
+                                        coarsest_schur=1)])
 def test_coarse_forms_at_16x4_workload(binding, forms):
     """The 16^4 HISQ-shaped three-level workload (truncated level-1 operator,
     24 / 32 vectors, FP32 with FP16 storage, graph-replayed K-cycle) with the
-    block-preconditioned coarse levels, and with level 2 in Schur form as
-    well: the solve meets 1e-10 on the full M (recomputed by the oracle)."""
+    block-preconditioned coarse levels, with level 2 in Schur form as well,
+    and with all of Table 1's coarse forms (level 3 by the deflated
+    Chebyshev-basis CA-GCR(16) on its Schur complement): the solve meets 1e-10
+    on the full M (recomputed by the oracle)."""
     dims, mass = (16, 16, 16, 16), 0.01
     fat, naik, c, op = make(dims, True, mass, seed=1002)
     phi = [inputs.gaussian_fields(24, op.lat.V, 3, 3002), inputs.gaussian_fields(32, 256, 48, 3003)]
+    if forms.get("coarsest_deflate", 0):
+        phi.append(inputs.gaussian_fields(binding.deflation_block(forms["coarsest_deflate"]), 16, 64, 3004))
     s = binding.Solver(dims)
     s.set_gauge(fat, naik, c)
     s.set_mass(mass)
