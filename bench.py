@@ -174,11 +174,12 @@ def build_problem(cfg, torch, dev, seed_offset=0, dims=None):
     return c, s, phi0, src
 
 
-def setup(binding, s, c, phi0, precision, use_graph, setup_maxiter=2000, max_outer=500, truncate_naik=0):
+def setup(binding, s, c, phi0, precision, use_graph, setup_maxiter=2000, max_outer=500, truncate_naik=0,
+          inner=(0.25, 8)):
     prec = {"double": binding.PREC_DOUBLE, "single": binding.PREC_SINGLE, "mixed": binding.PREC_HALF}[precision]
     p = binding.default_params(n_coarse=len(c["nvec"]), agg=c["agg"], nvec=c["nvec"], precision=prec,
                                use_graph=use_graph, setup_maxiter=setup_maxiter, max_outer=max_outer,
-                               truncate_naik=truncate_naik)
+                               truncate_naik=truncate_naik, inner_tol=float(inner[0]), inner_maxiter=int(inner[1]))
     t0 = time.perf_counter()
     s.mg_setup(p, phi0)
     return time.perf_counter() - t0
@@ -377,7 +378,7 @@ def run_batched(args):
     masses = np.array([c["mass"]]) if c["masses"] is None else inputs.log_masses(0.001, 0.05, 8)
     log(f"inputs ready (dims {c['dims']}); setup")
     t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer,
-                    args.truncate_naik)
+                    args.truncate_naik, (args.inner_tol, args.inner_maxiter))
     setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
     log(f"setup {t_setup:.1f} s, CGNE iterations {setup_iters}")
     b = torch.from_numpy(c["sources"]).to(dev)
@@ -422,6 +423,7 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "f32+f16 storage, f64 outer", "data": "synthetic",
         "config": {"workload": WORKLOADS[cfg], "dims": list(c["dims"]), "systems_per_step": nsys,
                    "masses": [float(m) for m in masses], "setup_s": t_setup, "setup_cgne_iters": setup_iters,
+                   "inner_tol": args.inner_tol, "inner_maxiter": args.inner_maxiter,
                    "outer_iters": infos[0].iterations, "all_converged": all(i.converged for i in infos),
                    "max_true_residual": max(i.true_residual for i in infos),
                    "l2": "flushed (512 MB write) before every timed batch"},
@@ -602,6 +604,11 @@ def main():
     ap.add_argument("--truncate-naik", type=int, default=1,
                     help="Table 1 level-1 operator: 1 = truncated (Naik hops dropped from the pseudo-fine "
                          "operator), 0 = KD-preconditioned HISQ; the outer operator is the full M either way")
+    ap.add_argument("--inner-tol", type=float, default=0.25,
+                    help="inner GCR tolerance of levels >= 1 for the light-mass workloads (--config 3/4; "
+                         "Table 1: 0.25)")
+    ap.add_argument("--inner-maxiter", type=int, default=8,
+                    help="inner GCR iteration cap for --config 3/4 (Table 1: 8; at most 16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--setup-maxiter", type=int, default=2000,
