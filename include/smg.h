@@ -247,8 +247,12 @@ enum {
   SMG_KERNEL_RESTRICT = 2,  /* R of coarsening l                            */
   SMG_KERNEL_PROLONG = 3,   /* P of coarsening l                            */
   SMG_KERNEL_COARSE = 4,    /* 9-point coarse operator of coarsening l      */
-  SMG_KERNEL_A = 5          /* A = (B+m)^{-1} M on the fine lattice (Eq. 2):  */
+  SMG_KERNEL_A = 5,         /* A = (B+m)^{-1} M on the fine lattice (Eq. 2):  */
                             /* the dslash and block launches of one apply   */
+  SMG_KERNEL_COARSE_SOLVE = 6  /* one solve of the level coarsening l produces,
+                                  as the K-cycle runs it (dense inverse,
+                                  deflated Chebyshev CA-GCR, Schur form or GCR
+                                  with the K-cycle below), synthetic rhs  */
 };
 /* Average device milliseconds of one launch of `kernel` on nsys systems, in
  * the setup's preconditioner precision (FP64 before mg_setup), timed with

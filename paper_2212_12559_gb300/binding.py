@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsmg.so")
 SMG_HOST, SMG_DEVICE = 0, 1
 PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 OP_M, OP_MDAG, OP_KD, OP_KDDAG, OP_A, OP_ADAG = range(6)
-K_DSLASH, K_KD, K_RESTRICT, K_PROLONG, K_COARSE, K_A = range(6)
+K_DSLASH, K_KD, K_RESTRICT, K_PROLONG, K_COARSE, K_A, K_COARSE_SOLVE = range(7)
 MAX_COARSE = 3
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_STATE",
           -5: "ERR_NOT_CONVERGED", -6: "ERR_BREAKDOWN", -7: "ERR_TIMEOUT"}

@@ -1970,7 +1970,39 @@ double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep) {
   if (!c.kd_valid) ctx_build_kd(c);
   long long nin = (long long)c.g.V * 3, nout = nin;
   const CoarseLevel* C = nullptr;
-  SMG_REQUIRE(kernel >= SMG_KERNEL_DSLASH && kernel <= SMG_KERNEL_A, "time_kernel: unknown kernel");
+  SMG_REQUIRE(kernel >= SMG_KERNEL_DSLASH && kernel <= SMG_KERNEL_COARSE_SOLVE, "time_kernel: unknown kernel");
+  if (kernel == SMG_KERNEL_COARSE_SOLVE) {
+    // a whole coarse-level solve through an engine of nsys systems; the
+    // engine's work areas are set up before the timed launches
+    SMG_REQUIRE(c.setup_done && l >= 0 && l < (int)c.coarse.size(), "time_kernel: bad level");
+    SMG_REQUIRE(nsys <= 16, "time_kernel: at most 16 systems for a coarse solve");
+    c.engine.reset();
+    Engine E(c, nsys, std::vector<double>(1, c.mass), nsys);
+    const int lv = l + 2;
+    synth_fill(E.lev[lv].b.p, E.vp == P64 ? S64 : S32, E.lev[lv].b.n * nsys, 17u, c.stream);
+    DevBuf keep;
+    keep.alloc(E.lev[lv].b.bytes());
+    SMG_CUDA_OK(cudaMemcpyAsync(keep.p, E.lev[lv].b.p, keep.bytes, cudaMemcpyDeviceToDevice, c.stream));
+    auto solve_once = [&]() {
+      // a Schur-form solve overwrites its right-hand side: restore it each time
+      SMG_CUDA_OK(cudaMemcpyAsync(E.lev[lv].b.p, keep.p, keep.bytes, cudaMemcpyDeviceToDevice, c.stream));
+      E.coarse_solve(lv, nullptr);
+    };
+    solve_once();
+    cudaEvent_t e0, e1;
+    SMG_CUDA_OK(cudaEventCreate(&e0));
+    SMG_CUDA_OK(cudaEventCreate(&e1));
+    SMG_CUDA_OK(cudaEventRecord(e0, c.stream));
+    for (int i = 0; i < nrep; ++i) solve_once();
+    SMG_CUDA_OK(cudaEventRecord(e1, c.stream));
+    SMG_CUDA_OK(cudaEventSynchronize(e1));
+    float ms = 0;
+    SMG_CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    E.check_persistent_error();
+    return (double)ms / nrep;
+  }
   if (kernel >= SMG_KERNEL_RESTRICT && kernel <= SMG_KERNEL_COARSE) {
     SMG_REQUIRE(c.setup_done && l >= 0 && l < (int)c.coarse.size(), "time_kernel: bad level");
     C = &c.coarse[l];

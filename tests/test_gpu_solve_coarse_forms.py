@@ -389,6 +389,8 @@ def test_deflation_at_16x4_coarsest(binding):
     apply = lambda v: (Ad @ v.ravel()).reshape(v.shape)
     rc = inputs.gaussian_fields(3, Vc, N, 3005)
     x = s.coarse_solve(1, rc)
+    ms = s.time_kernel(binding.K_COARSE_SOLVE, 1, 3, 5)      # the timing hook runs the same solve
+    assert 0.0 < ms < 1e4
     for q in range(3):
         xr = (Vr @ ((U.conj().T @ rc[q].ravel()) / sig)).reshape(rc[q].shape)
         for _ in range(2):
