@@ -143,6 +143,21 @@ def deflation_block(k: int) -> int:
     return k + max(4, k // 4)
 
 
+def setup_input_sizes(dims, params: MGParams):
+    """Complex entries each smg_mg_setup start array must hold: nvec[l] fields
+    of coarsening l's fine side, then (coarsest_deflate = k > 0) the
+    deflation start block of k + guard fields on the coarsest level."""
+    sizes = []
+    d, ndof = tuple(int(x) for x in dims), 3
+    for l in range(params.n_coarse):
+        sizes.append(params.nvec[l] * int(np.prod(d)) * ndof)
+        d = tuple(x // a for x, a in zip(d, params.agg[l]))
+        ndof = 2 * params.nvec[l]
+    if params.coarsest_deflate > 0:
+        sizes.append(deflation_block(params.coarsest_deflate) * int(np.prod(d)) * ndof)
+    return sizes
+
+
 def default_params(**kw) -> MGParams:
     p = MGParams()
     load().smg_default_params(ctypes.byref(p))
@@ -224,6 +239,13 @@ class Solver:
         self._check(self.lib.smg_set_stream(self.ctx, ctypes.c_void_p(stream_handle)))
 
     def mg_setup(self, params: MGParams, phi0):
+        # the library reads these host or device arrays by the sizes the
+        # parameters imply; a short array is refused here, before the call
+        need = setup_input_sizes(self.dims, params)
+        for l, (a, n) in enumerate(zip(phi0, need)):
+            if int(np.prod(tuple(a.shape))) < n:
+                raise SmgError(-1, f"mg_setup: start array {l} holds {int(np.prod(tuple(a.shape)))} "
+                                   f"complex entries, needs {n}")
         arrs = [_prep(a) for a in phi0]
         ptrs = [_ptr(a) for a in arrs]
         where = ptrs[0][1]

@@ -58,3 +58,16 @@ def test_create_rejects_bad_extents(libpath):
     for dims in [(3, 4, 4, 4), (4, 4, 4, 2), (0, 4, 4, 4)]:
         assert lib.smg_create((ctypes.c_int * 4)(*dims), ctypes.byref(ctx)) == -1
     assert lib.smg_destroy(None) == -1
+
+
+def test_setup_input_sizes(libpath):
+    """The start arrays smg_mg_setup reads, by level (host logic of the
+    binding, which refuses short arrays before the call)."""
+    from paper_2212_12559_gb300 import binding
+    p = binding.default_params(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[24, 32])
+    assert binding.setup_input_sizes((16, 16, 16, 16), p) == [24 * 65536 * 3, 32 * 256 * 48]
+    p.coarsest_deflate = 16
+    assert binding.setup_input_sizes((16, 16, 16, 16), p)[2] == (16 + 4) * 16 * 64
+    p.coarsest_deflate = 40
+    assert binding.deflation_block(40) == 50
+    assert binding.setup_input_sizes((16, 16, 16, 16), p)[2] == 50 * 16 * 64
