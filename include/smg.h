@@ -97,7 +97,11 @@ typedef struct smg_mg_params {
                                       x0 = V diag(1/sigma) U^dag b, then CA-GCR(coarsest_cheb_s)
                                       cycles with a Chebyshev basis on [sigma_k, sigma_max] until
                                       0.25 ||b|| or inner_maxiter cycles.  Default 0 (GCR). */
-  int coarsest_cheb_s;             /* Chebyshev basis length of that CA-GCR, 1..16 (Table 1: 16) */
+  int coarsest_cheb_s;             /* Chebyshev basis length of that CA-GCR, 1..16.  Default 8:
+                                      Table 1 uses 16, but on coarse operators whose eigenvalues
+                                      lie well off the real interval a 16-long basis leaves the
+                                      Gram matrix numerically singular (in FP32 vectors the
+                                      correction is lost) */
   int coarsest_schur;              /* Table 1 level-3 operator: 1 = the deflated coarsest solve runs
                                       on the even/odd Schur complement S = 1 - K_eo K_oe of the
                                       block-preconditioned operator 1 + K (needs block_coarse,

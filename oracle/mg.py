@@ -91,7 +91,7 @@ class MGParams:
     truncate_naik: bool = False
     block_coarse: bool = False
     coarsest_deflate: int = 0     # > 0: SVD-deflated Chebyshev-basis CA-GCR on the coarsest level
-    coarsest_cheb_s: int = 16
+    coarsest_cheb_s: int = 8     # Table 1: 16; a real-interval basis that long is numerically singular here
     coarsest_schur: bool = False  # with coarsest_deflate: deflated CA-GCR on the even/odd Schur complement
     schur_coarse: bool = False    # intermediate coarse levels: GCR and smoother on the Schur complement
 

@@ -91,7 +91,7 @@ void smg_default_params(smg_mg_params* p) {
   p->truncate_naik = 0;
   p->block_coarse = 0;
   p->coarsest_deflate = 0;
-  p->coarsest_cheb_s = 16;
+  p->coarsest_cheb_s = 8;
   p->coarsest_schur = 0;
   p->schur_coarse = 0;
 }
