@@ -115,6 +115,12 @@ typedef struct smg_mg_params {
                                       c_e - K_eo c_o, preconditioned by the K-cycle on the embedded
                                       residual (r_e, 0) (for x_o = c_o - K_oe x_e the full residual
                                       is exactly that), x_o reconstructed.  Default 0. */
+  int coarsest_basis;              /* basis of the coarsest CA-GCR: 0 = Chebyshev polynomials of
+                                      [sigma_k, sigma_max] (Table 1, default); 1 = the shifted power
+                                      basis ((A - c)/h)^k r of the disk around that interval's
+                                      centre, well conditioned when the spectrum fills a disk
+                                      rather than lying near the real interval (both span the same
+                                      Krylov space) */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */

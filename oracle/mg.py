@@ -39,7 +39,10 @@ interval [sigma_k, sigma_max] (the k-th singular value, the first one not
 deflated, up to the largest one, which bounds the real part of every
 eigenvalue), to the level's 0.25 / 8-step rule.  The interval only conditions
 the basis: the correction is the minimum-residual one over K_s(A, r) for any
-interval.
+interval.  ``coarsest_basis = "shifted"`` builds the same Krylov space from
+the power basis ((A - c)/h)^k r of the disk around the interval's centre,
+which stays well conditioned when the spectrum fills a disk rather than
+lying near the real interval (the synthetic coarse operators here).
 
 Table 1 runs that coarsest solver on the "Schur-preconditioned" operator:
 ``coarsest_schur`` (with ``coarsest_deflate``) solves the coarsest system
@@ -74,7 +77,7 @@ from .coarse import FineLevelOp, Transfer, block_preconditioned, galerkin, near_
 from .dirac import KahlerDirac, Staggered
 from .lattice import Lattice
 from .schur import SchurCoarse
-from .solvers import ca_gcr, ca_gcr_chebyshev, gcr, lowest_singular_triplets, norm
+from .solvers import ca_gcr, ca_gcr_basis, gcr, lowest_singular_triplets, norm
 
 
 @dataclass
@@ -92,6 +95,7 @@ class MGParams:
     block_coarse: bool = False
     coarsest_deflate: int = 0     # > 0: SVD-deflated Chebyshev-basis CA-GCR on the coarsest level
     coarsest_cheb_s: int = 8     # Table 1: 16; a real-interval basis that long is numerically singular here
+    coarsest_basis: str = "chebyshev"   # or "shifted": the power basis of the disk around the interval's centre
     coarsest_schur: bool = False  # with coarsest_deflate: deflated CA-GCR on the even/odd Schur complement
     schur_coarse: bool = False    # intermediate coarse levels: GCR and smoother on the Schur complement
 
@@ -191,7 +195,7 @@ class MultigridSolver:
         for _ in range(self.p.inner_maxiter):
             if norm(r) <= target:
                 break
-            x = x + ca_gcr_chebyshev(apply, r, self.p.coarsest_cheb_s, lmin, lmax)
+            x = x + ca_gcr_basis(apply, r, self.p.coarsest_cheb_s, lmin, lmax, self.p.coarsest_basis)
             r = rc - apply(x)
         return x
 

@@ -211,6 +211,31 @@ def ca_gcr_chebyshev(apply, r, s: int, lmin: float, lmax: float):
     return sum(ak * q for ak, q in zip(a, Q))
 
 
+def shifted_power_basis(apply, r, s: int, lmin: float, lmax: float):
+    """q_k = ((A - c)/h)^k r for k < s, c = (lmax + lmin)/2, h = (lmax - lmin)/2:
+    the Faber (power) basis of the disk |z - c| <= h, which stays well
+    conditioned when the spectrum fills a disk around c rather than lying on
+    the real interval [lmin, lmax]."""
+    c = 0.5 * (lmax + lmin)
+    h = 0.5 * (lmax - lmin)
+    Q = [r]
+    while len(Q) < s:
+        Q.append((apply(Q[-1]) - c * Q[-1]) / h)
+    return Q
+
+
+def ca_gcr_basis(apply, r, s: int, lmin: float, lmax: float, basis: str = "chebyshev"):
+    """CA-GCR(s) with the Chebyshev basis of [lmin, lmax] (Table 1) or the
+    shifted power basis of the disk around its centre; both span K_s(A, r), so
+    in exact arithmetic the minimum-residual correction is the same."""
+    if basis == "chebyshev":
+        return ca_gcr_chebyshev(apply, r, s, lmin, lmax)
+    Q = shifted_power_basis(apply, r, s, lmin, lmax)
+    W = np.stack([apply(q).ravel() for q in Q], axis=1)
+    a, *_ = np.linalg.lstsq(W, r.ravel(), rcond=None)
+    return sum(ak * q for ak, q in zip(a, Q))
+
+
 def lowest_singular_triplets(dense, k: int):
     """The k smallest singular values of a (small) dense operator with their
     left (U) and right (V) singular vectors: A V = U diag(sigma)."""

@@ -54,6 +54,7 @@ class MGParams(ctypes.Structure):
         ("coarsest_cheb_s", ctypes.c_int),
         ("coarsest_schur", ctypes.c_int),
         ("schur_coarse", ctypes.c_int),
+        ("coarsest_basis", ctypes.c_int),
     ]
 
 

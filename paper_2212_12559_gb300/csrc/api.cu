@@ -94,6 +94,7 @@ void smg_default_params(smg_mg_params* p) {
   p->coarsest_cheb_s = 8;
   p->coarsest_schur = 0;
   p->schur_coarse = 0;
+  p->coarsest_basis = 0;
 }
 
 int smg_create(const int dims[4], smg_ctx** out) {

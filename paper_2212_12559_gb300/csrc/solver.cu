@@ -696,14 +696,16 @@ struct Engine {
       A(r, x, rn, &b);                                   // r = b - A x
       blas_pair_dots(&r, 1, p0, p0, 1, cw.rr, 1, ws, st(), rn);
       defl_active(cw.rr, cw.bb, tol2, cw.active, cw.drun, nsys, it == 0, st(), run);
-      // Q_0 = r, Q_1 = (A - c) Q_0 / h, Q_{i+1} = 2 (A - c) Q_i / h - Q_{i-1}; W_i = A Q_i
+      // Chebyshev: Q_0 = r, Q_1 = (A - c) Q_0 / h, Q_{i+1} = 2 (A - c) Q_i / h - Q_{i-1};
+      // shifted power basis: Q_{i+1} = (A - c) Q_i / h;  W_i = A Q_i
       cw.Q[0] = r;
+      const bool shifted = c.params.coarsest_basis == 1;
       for (int i = 0; i < s; ++i) {
         A(cw.W[i], cw.Q[i], cw.drun, nullptr);
         if (i + 1 == s) break;
-        if (i == 0) {
-          Vec in2[2] = {cw.W[0], cw.Q[0]};
-          blas_maxpy(cw.Q[1], in2, 2, cw.c1, 2, 1.0, false, st(), cw.drun);
+        if (i == 0 || shifted) {
+          Vec in2[2] = {cw.W[i], cw.Q[i]};
+          blas_maxpy(cw.Q[i + 1], in2, 2, cw.c1, 2, 1.0, false, st(), cw.drun);
         } else {
           Vec in3[3] = {cw.W[i], cw.Q[i], cw.Q[i - 1]};
           blas_maxpy(cw.Q[i + 1], in3, 3, cw.c2, 3, 1.0, false, st(), cw.drun);
@@ -1311,6 +1313,7 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
               "coarsest_deflate must be 0..51");
   SMG_REQUIRE(P.coarsest_deflate == 0 || (P.coarsest_cheb_s >= 1 && P.coarsest_cheb_s <= kCaBasisMax),
               "coarsest_cheb_s must be 1..16");
+  SMG_REQUIRE(P.coarsest_basis == 0 || P.coarsest_basis == 1, "coarsest_basis must be 0 or 1");
   c.engine.reset();
   c.setup_done = false;
   c.params = P;

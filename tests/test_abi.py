@@ -48,7 +48,7 @@ def test_params_struct_layout(libpath):
     assert p.nkrylov == 16 and p.dense_max == 4096 and p.use_graph == 0
     assert p.persistent == 1 and p.truncate_naik == 0 and p.block_coarse == 0
     assert p.coarsest_deflate == 0 and p.coarsest_cheb_s == 8 and p.coarsest_schur == 0
-    assert p.schur_coarse == 0
+    assert p.schur_coarse == 0 and p.coarsest_basis == 0
 
 
 def test_create_rejects_bad_extents(libpath):

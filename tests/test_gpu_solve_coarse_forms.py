@@ -165,7 +165,7 @@ def test_block_coarse_solve_matches_oracle(binding):
             assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
 
 
-def deflation_problem(binding, prec, k=8, s=8, inner_tol=0.25, inner_maxiter=8):
+def deflation_problem(binding, prec, k=8, s=8, inner_tol=0.25, inner_maxiter=8, basis=0):
     """Two-level naive problem on 8x8x4x4 (coarsest level 2x2x1x1 x N = 8, 32
     unknowns) whose coarsest level is solved iteratively (dense_max = 0) with
     Table 1's SVD deflation; oracle CGNE near-null vectors fed to both sides."""
@@ -177,14 +177,15 @@ def deflation_problem(binding, prec, k=8, s=8, inner_tol=0.25, inner_maxiter=8):
     raw, _ = near_null_vectors(lop, inputs.gaussian_fields(4, op.lat.V, 3, 3004), 1e-6, 50)
     mg = MultigridSolver(op, MGParams(agg=[(4, 4, 4, 4)], nvec=[4], setup_maxiter=0, dense_max=0,
                                       coarsest_deflate=k, coarsest_cheb_s=s, inner_tol=inner_tol,
-                                      inner_maxiter=inner_maxiter), [raw])
+                                      inner_maxiter=inner_maxiter,
+                                      coarsest_basis="shifted" if basis else "chebyshev"), [raw])
     start = inputs.gaussian_fields(binding.deflation_block(k), 4, 8, 3005)
     sv = binding.Solver(dims)
     sv.set_gauge(fat, naik, c)
     sv.set_mass(mass)
     sv.mg_setup(binding.default_params(nvec=[4], setup_maxiter=0, dense_max=0, precision=prec,
                                        coarsest_deflate=k, coarsest_cheb_s=s, inner_tol=inner_tol,
-                                       inner_maxiter=inner_maxiter), [raw, start])
+                                       inner_maxiter=inner_maxiter, coarsest_basis=basis), [raw, start])
     return op, mg, sv
 
 
@@ -219,22 +220,23 @@ def test_deflated_coarsest_singular_values_and_solve(binding):
         assert r <= 0.25 or abs(r - r_ref) <= 1e-6, (r, r_ref)
 
 
-@pytest.mark.parametrize("prec,s", [(0, 8), (2, 8), (0, 16)])
-def test_deflated_coarsest_in_kcycle(binding, prec, s):
-    """The outer solve with the deflated Chebyshev-basis CA-GCR coarsest level
-    converges on the full M, with s = 8 and with Table 1's s = 16; in FP64
-    with s = 8 its outer iteration count follows the oracle's K-cycle with the
-    same coarsest solver (at s = 16 the basis's Gram matrix has eigenvalues
-    below 1e-12 of its largest, where a normal-equation solve and the
-    oracle's least-squares solve may keep different directions)."""
-    op, mg, sv = deflation_problem(binding, prec, s=s)
+@pytest.mark.parametrize("prec,s,basis", [(0, 8, 0), (2, 8, 0), (0, 16, 0), (0, 16, 1), (2, 16, 1)])
+def test_deflated_coarsest_in_kcycle(binding, prec, s, basis):
+    """The outer solve with the deflated CA-GCR coarsest level converges on
+    the full M, with s = 8 and with Table 1's s = 16, in the Chebyshev basis
+    and in the shifted power basis; in FP64 its outer iteration count follows
+    the oracle's K-cycle with the same coarsest solver, except for the
+    Chebyshev basis at s = 16, whose Gram matrix has eigenvalues below 1e-12
+    of its largest here (a normal-equation solve and the oracle's
+    least-squares solve may keep different directions)."""
+    op, mg, sv = deflation_problem(binding, prec, s=s, basis=basis)
     b = inputs.gaussian_field(op.lat.V, 3, 2003)
     x_o, it_o, res_o = mg.solve(b, 1e-10)
     assert res_o <= 1e-10
     x, info = sv.solve(b, 1e-10)
     assert info.converged == 1 and info.true_residual <= 1e-10
     check_solution(op, b, x, x_o, res_o)
-    if prec == 0 and s == 8:
+    if prec == 0 and (s == 8 or basis == 1):
         assert abs(info.iterations - it_o) <= max(2, 0.15 * it_o), (info.iterations, it_o)
 
 
@@ -259,6 +261,20 @@ def schur_problem(binding, prec, k=8, s=4, inner_tol=1e-12, inner_maxiter=2):
     kw.update(block_coarse=1, coarsest_schur=1, precision=prec)
     sv.mg_setup(binding.default_params(**kw), [raw, start])
     return op, mg, sv
+
+
+def test_shifted_basis_coarsest_solve(binding):
+    """The coarsest CA-GCR in the shifted power basis ((A - c)/h)^k r: the
+    deflated start plus two CA-GCR(4) cycles equals the oracle's element by
+    element (FP64, no early stop)."""
+    k = 8
+    op, mg, sv = deflation_problem(binding, binding.PREC_DOUBLE, k=k, s=4, inner_tol=1e-12, inner_maxiter=2,
+                                   basis=1)
+    lev = mg.levels[-1]
+    rc = inputs.gaussian_fields(2, lev.lat.V, lev.n, 3006)
+    x = sv.coarse_solve(0, rc)
+    for q in range(2):
+        assert rel(x[q], mg.deflated_coarsest(lev, rc[q])) <= 1e-8
 
 
 def test_schur_deflated_coarsest(binding):

@@ -22,8 +22,8 @@ from oracle.coarse import FineLevelOp, Transfer, galerkin
 from oracle.dirac import KahlerDirac, Staggered
 from oracle.lattice import Lattice
 from oracle.schur import SchurCoarse
-from oracle.solvers import (ca_gcr, ca_gcr_chebyshev, chebyshev_basis, gcr, lowest_singular_triplets,
-                            svd_deflated_gcr)
+from oracle.solvers import (ca_gcr, ca_gcr_basis, ca_gcr_chebyshev, chebyshev_basis, gcr,
+                            lowest_singular_triplets, shifted_power_basis, svd_deflated_gcr)
 from paper_2212_12559_gb300 import inputs
 
 
@@ -303,3 +303,23 @@ def test_schur_spectrum_closed_form(coarse):
     d1 = np.abs(pred[:, None] - lam[None, :]).min(axis=1)
     d2 = np.abs(lam[:, None] - pred[None, :]).min(axis=1)
     assert d1.max() <= 1e-8 * scale and d2.max() <= 1e-8 * scale
+
+
+@pytest.mark.parametrize("s", [3, 6, 10])
+def test_shifted_power_basis_ca_gcr(coarse, s):
+    """The shifted power basis is ((A - c)/h)^k r (matrix powers, not the
+    recurrence), and CA-GCR(s) with it reaches the Arnoldi minimum residual
+    over K_s(A, r), like the Chebyshev basis."""
+    S, Ad = coarse
+    r = inputs.gaussian_field(S.lat.V, S.n, 51)
+    lmin, lmax = 0.05, 3.0
+    c, h = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    apply = lambda v: (Ad @ v.ravel()).reshape(v.shape)
+    Q = shifted_power_basis(apply, r, s, lmin, lmax)
+    T = (Ad - c * np.eye(Ad.shape[0])) / h
+    for k, q in enumerate(Q):
+        ref = np.linalg.matrix_power(T, k) @ r.ravel()
+        assert np.linalg.norm(q.ravel() - ref) <= 1e-10 * np.linalg.norm(ref)
+    e = ca_gcr_basis(apply, r, s, lmin, lmax, "shifted").ravel()
+    got = np.linalg.norm(r.ravel() - Ad @ e)
+    assert abs(got - arnoldi_min_residual(Ad, r.ravel(), s)) <= 1e-9 * np.linalg.norm(r)
