@@ -71,3 +71,46 @@ def test_setup_input_sizes(libpath):
     p.coarsest_deflate = 40
     assert binding.deflation_block(40) == 50
     assert binding.setup_input_sizes((16, 16, 16, 16), p)[2] == 50 * 16 * 64
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "smg.h"
+int main(void) {
+  smg_mg_params p;
+  long long plan[10];
+  smg_default_params(&p);
+  if (smg_persist_plan(256, 48, 1, 32, SMG_PREC_HALF, 152, 232448, plan) != SMG_OK) return 2;
+  printf("%d %d %d %d %d %d %lld %lld %lld\n", p.n_coarse, p.nvec[0], p.inner_maxiter, p.coarsest_cheb_s,
+         p.block_coarse, p.coarsest_basis, plan[0], plan[1], plan[2]);
+  return 0;
+}
+"""
+
+
+def test_plain_c_client(libpath, tmp_path):
+    """The boundary is a C ABI: a C99 program built against include/smg.h and
+    linked to libsmg.so reads the defaults and a persistent launch plan (host
+    only, no GPU call) exactly as the Python binding does."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(libpath)
+    cudalib = "/usr/local/cuda/lib64"
+    cmd = [cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"), str(src),
+           "-o", str(exe), f"-L{libdir}", "-lsmg", f"-Wl,-rpath,{libdir}", f"-Wl,-rpath,{cudalib}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    from paper_2212_12559_gb300 import binding
+    p = binding.default_params()
+    q = binding.persist_plan(256, 48, 1, 32, binding.PREC_HALF, 152, 232448)
+    want = [p.n_coarse, p.nvec[0], p.inner_maxiter, p.coarsest_cheb_s, p.block_coarse, p.coarsest_basis,
+            q["grid"], q["per"], q["nslot"]]
+    assert [int(v) for v in r.stdout.split()] == want
