@@ -739,6 +739,24 @@ void parity_pick(const Vec& out, const Vec* even, const Vec* odd, const Geom& g,
   SMG_LAUNCH_OK();
 }
 
+// Even/odd Schur complement of a block-preconditioned coarse operator
+// A = 1 + K (self blocks exactly 1, every hop changes the site parity):
+// with R(u) = u - A u = -K u,  S v = v - K_eo K_oe v = mask_e(v - R(mask_o(R(v))))
+// for v that vanishes on odd sites.  The masks also drop what the rounding of
+// stored (FP16 / FP32) identity self blocks leaves on the wrong parity.  With
+// the adjoint stencil the same steps give S^dag.  t1, t2: scratch like v.
+void schur_apply(const Vec& out, const Vec& in, const CoarseParams& cp0, const Stored& S, const Vec& t1,
+                 const Vec& t2, cudaStream_t st, const int* run) {
+  CoarseParams cp = cp0;
+  cp.sub_from = in.p;
+  coarse_apply(t1, in, cp, S, st, run);                  // t1 = R(in)
+  parity_pick(t1, nullptr, &t1, cp.g, cp.N, st, run);    // its odd part
+  cp.sub_from = t1.p;
+  coarse_apply(t2, t1, cp, S, st, run);                  // t2 = R(t1)
+  blas_sub(t1, in, t2, st, run);                         // in - t2
+  parity_pick(out, &t1, nullptr, cp.g, cp.N, st, run);   // its even part
+}
+
 void dense_apply(const Vec& out, const Vec& in, const void* Dinv, Prec dprec, int n, cudaStream_t st,
                  const int* run) {
   SMG_REQUIRE(in.n == n && out.n == n && in.nsys == out.nsys && in.prec == out.prec, "dense_apply: shape mismatch");

@@ -139,6 +139,13 @@ void block_diag_apply(const Vec& v, const void* Xinv, Prec xprec, int N, cudaStr
 void parity_pick(const Vec& out, const Vec* even, const Vec* odd, const Geom& g, int N, cudaStream_t st,
                  const int* run = nullptr);
 
+// S v = mask_e(v - R(mask_o(R(v)))), R(u) = u - A u, for the Schur complement
+// S = 1 - K_eo K_oe of a coarse operator A = 1 + K with identity self blocks,
+// on fields that vanish on the odd sites (S^dag with the adjoint stencil);
+// t1, t2: scratch shaped like v.
+void schur_apply(const Vec& out, const Vec& in, const CoarseParams& cp, const Stored& S, const Vec& t1,
+                 const Vec& t2, cudaStream_t st, const int* run = nullptr);
+
 // ------------------------------------------------------- dense coarsest op
 void dense_from_stencil(double2* Dn, const double2* S64, const Geom& g, int N, cudaStream_t st);
 // In-place Gauss-Jordan inverse with partial pivoting (FP64); returns false if singular.

@@ -149,6 +149,9 @@ int ctx_multishift_cg(Context& c, const void* b, int nshift, const double* masse
                       int where, smg_solve_info* info);
 int ctx_propagators(Context& c, const void* b, int nmass, const double* masses, int n_mg, void* x, double tol,
                     int cg_maxiter, int where, smg_solve_info* info);
+// The k = coarsest_deflate lowest singular triplets of the coarsest level C
+// (or of its Schur complement when C.schur) from the start block `start`.
+void build_deflation(Context& c, CoarseLevel& C, const void* start, int where);
 void ctx_coarse_solve(Context& c, int l, int nsys, const void* in, void* out, int where);
 int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* masses, void* x, double tol, int where,
               smg_solve_info* info);
