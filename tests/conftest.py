@@ -20,9 +20,13 @@ def pytest_collection_modifyitems(config, items):
     """The coarse-level form tests (the newest GPU paths) run after the rest of
     the suite, so that under -x a failure there cannot hide the results of the
     established tests."""
-    late = [it for it in items if it.fspath.basename in LATE_MODULES]
+    def module(it):
+        path = getattr(it, "path", None)
+        return path.name if path is not None else os.path.basename(str(it.fspath))
+
+    late = [it for it in items if module(it) in LATE_MODULES]
     if late:
-        items[:] = [it for it in items if it.fspath.basename not in LATE_MODULES] + late
+        items[:] = [it for it in items if module(it) not in LATE_MODULES] + late
 
 
 @pytest.fixture(scope="session")
