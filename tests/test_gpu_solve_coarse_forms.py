@@ -378,7 +378,8 @@ def test_deflation_at_16x4_coarsest(binding):
     the GPU's singular values equal the dense SVD of the GPU's coarsest
     stencil, and a deflated coarsest solve of three systems (two CA-GCR(4)
     cycles) equals the same steps done densely.  k sits at a gap of the
-    singular values, so the deflation space, and with it x0, is unique."""
+    singular values, so the deflation space, and with it x0, is unique.  The
+    largest block the kernels take (k = 51) finds the 51 lowest values too."""
     from oracle.solvers import ca_gcr_chebyshev, lowest_singular_triplets
     dims, mass = (16, 16, 16, 16), 0.05
     fat, naik, c, op = make(dims, True, mass, seed=1002)
@@ -415,6 +416,12 @@ def test_deflation_at_16x4_coarsest(binding):
         for _ in range(2):
             xr = xr + ca_gcr_chebyshev(apply, rc[q] - apply(xr), 4, float(sig[-1]), float(sv[-1]))
         assert rel(x[q], xr) <= 1e-8
+    # the largest block the kernels take: k = 51 (51 + 12 guard vectors = 63 <= 64)
+    s.mg_setup(binding.default_params(coarsest_deflate=51, **kw),
+               phi + [inputs.gaussian_fields(binding.deflation_block(51), Vc, N, 3006)])
+    got, info = s.deflation()
+    assert info["residual"] <= 1e-10
+    assert rel(got, sv[:51]) <= 1e-9
 
 
 @pytest.mark.parametrize("forms", [dict(block_coarse=1), dict(block_coarse=1, schur_coarse=1),
