@@ -299,7 +299,8 @@ SMG_API long long smg_kernel_launches(void);
  * a latency-critical loop that cannot take cudaMalloc's implicit device
  * synchronisation).  It reduces in a fixed file-scope device array of
  * 8192 partial sums (128 KiB per device, held until the process exits), so
- * nsys must not exceed 8192 (SMG_ERR_ARG otherwise); no cudaMalloc/cudaFree or
+ * nsys must not exceed 8192 (SMG_ERR_ARG otherwise); x, y and out must be
+ * 16-byte aligned (SMG_ERR_ARG otherwise); no cudaMalloc/cudaFree or
  * allocating library routine is called.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) and should come before
  * any stream capture.  Work is enqueued on the context's stream and the call

@@ -62,9 +62,10 @@ Galerkin product of the full block-preconditioned operator (Sec. 2.3).
 
 Readings taken where the paper is silent: no pre-smoothing anywhere (Table 1
 lists none), "0.25 or 8 iterations" stops at whichever comes first, the
-coarse levels use the un-preconditioned Galerkin operator (the Schur form of
-Table 1 is not built), and the outer GCR restarts every 16 directions with
-the residual recomputed at each restart.
+coarse levels use the un-preconditioned Galerkin operator unless
+``block_coarse`` / ``schur_coarse`` / ``coarsest_schur`` select Table 1's
+block-preconditioned and Schur forms above, and the outer GCR restarts every
+16 directions with the residual recomputed at each restart.
 """
 from __future__ import annotations
 

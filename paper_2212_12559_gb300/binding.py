@@ -434,9 +434,10 @@ class Solver:
     def dot_noalloc(self, x, y, out):
         """out[s] = <x_s, y_s> for device tensors x, y ([nsys, ...] complex128) into
         the caller's device tensor out (nsys complex128); enqueued on the
-        context's stream, no allocation inside the library."""
-        nsys = x.shape[0]
-        n = x.numel() // nsys
+        context's stream, no allocation inside the library.  The library
+        cannot tell host from device pointers, so the tensors are checked here
+        (ValueError) before any pointer reaches it."""
+        nsys, n = check_dot_noalloc_args(x, y, out)
         self._check(self.lib.smg_dot_noalloc(self.ctx, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                              n, nsys, ctypes.c_void_p(out.data_ptr())))
         return out
@@ -453,6 +454,35 @@ class Solver:
         v = ctypes.c_int()
         self._check(self.lib.smg_setup_iterations(self.ctx, l, ctypes.byref(v)))
         return v.value
+
+
+def check_dot_noalloc_args(x, y, out):
+    """(nsys, n) of a dot_noalloc call on torch tensors x, y of shape
+    [nsys, ...] and out of at least nsys entries; ValueError unless all three
+    are contiguous complex128 CUDA tensors on one device with y shaped like x.
+    A host tensor, a narrower dtype or a short y / out would make the kernel
+    read or write outside the caller's buffers."""
+    import torch
+    for name, t in (("x", x), ("y", y), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"dot_noalloc: {name} must be a torch tensor")
+        if t.dtype != torch.complex128:
+            raise ValueError(f"dot_noalloc: {name} must be complex128")
+        if not t.is_contiguous():
+            raise ValueError(f"dot_noalloc: {name} must be contiguous")
+    if x.dim() < 1 or x.shape[0] < 1 or x.numel() == 0:
+        raise ValueError("dot_noalloc: x must hold at least one non-empty system")
+    if tuple(y.shape) != tuple(x.shape):
+        raise ValueError("dot_noalloc: y must have the shape of x")
+    nsys = int(x.shape[0])
+    if out.numel() < nsys:
+        raise ValueError("dot_noalloc: out must hold nsys entries")
+    for name, t in (("x", x), ("y", y), ("out", out)):
+        if not t.is_cuda:
+            raise ValueError(f"dot_noalloc: {name} must be a CUDA tensor")
+    if not (x.device == y.device == out.device):
+        raise ValueError("dot_noalloc: x, y and out must be on one device")
+    return nsys, x.numel() // nsys
 
 
 def _prep(a):

@@ -141,6 +141,7 @@ __device__ void epilogue_system(const Epilogue& e, int s, const double2* o) {
       }
       const double ww = o[k].x - sumc;
       const double2 wr = o[k + 1];
+      const double rr = o[k + 2].x;      // |r|^2 before this step
       const double g = sqrt(fmax(ww, 0.0));
       const bool gfin = g > 0.0 && isfinite(g);
       const bool ok = e.ia[s] && gfin;
@@ -151,7 +152,10 @@ __device__ void epilogue_system(const Epilogue& e, int s, const double2* o) {
       e.d2e[s] = make_double2(-a.x, -a.y);
       if (e.ia[s]) {
         e.ib[s] = k + 1;
-        const double r2 = e.db[s] - (a.x * a.x + a.y * a.y);
+        // |r - a w_k|^2 = |r|^2 - |a|^2 from this step's own |r|^2: a running
+        // difference from |b|^2 carries a rounding error of about 1e-16 |b|^2,
+        // which hides residuals below 1e-8 |b| from a 1e-10 test
+        const double r2 = rr - (a.x * a.x + a.y * a.y);
         e.db[s] = r2;
         // converged, stagnated (w_k in the span of w_0..w_{k-1}) or non-finite
         if (!(r2 > e.dc[s]) || !gfin) e.ia[s] = 0;

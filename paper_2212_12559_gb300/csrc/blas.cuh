@@ -42,7 +42,7 @@ enum EpiKind {
   EPI_NONE = 0,
   EPI_GCR_INIT,    // sums: |r|^2.  r02=da, r2=db, thr2=dc, active=ia, nk=ib, run; tol2 or abs_target
   EPI_GCR_BETA1,   // sums: <w_j, w_k>, j<k (first CGS pass).  beta=d2a [K][K]
-  EPI_GCR_STEP,    // sums: <w_j, w_k> (second pass), |w_k|^2, <w_k, r>.  beta=d2a, gamma=d2b,
+  EPI_GCR_STEP,    // sums: <w_j, w_k> (second pass), |w_k|^2, <w_k, r>, |r|^2.  beta=d2a, gamma=d2b,
                    //   alpha=d2c, ginv=d2d, na=d2e, r2=db, thr2=dc, active=ia, nk=ib, run, run_outer
   EPI_CA,          // sums: CA-GCR Gram pairs.  coef=d2a [s]
   EPI_CGNE_INIT,   // sums: |r|^2.  rr_prev=da, rr0=db, active=ia, iters=ib, run

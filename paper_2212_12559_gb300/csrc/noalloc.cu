@@ -21,6 +21,8 @@
 // Every call shares the array: the arrival counter is cleared at the start of
 // each call (cudaMemsetAsync on the call's stream), and calls that overlap
 // on the GPU (different streams, no ordering between them) race on it.
+#include <stdint.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -83,6 +85,9 @@ __global__ void __launch_bounds__(kThreads) dot_noalloc_kernel(const double2* __
 std::string dot_noalloc(const void* x, const void* y, long long n, int nsys, void* out, cudaStream_t st) {
   if (x == nullptr || y == nullptr || out == nullptr) return "dot_noalloc: null pointer";
   if (n < 1) return "dot_noalloc: n must be >= 1";
+  // the kernel reads and writes whole FP64 complex numbers (16 bytes)
+  if ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)out)) & 15u)
+    return "dot_noalloc: buffers must be 16-byte aligned";
   if (nsys < 1 || nsys > kNoAllocPartials)
     return "dot_noalloc: nsys must be 1.." + std::to_string(kNoAllocPartials) +
            " (the fixed scratch holds that many partial sums)";

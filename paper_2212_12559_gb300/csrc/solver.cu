@@ -549,13 +549,16 @@ struct Engine {
         blas_pair_dots(G.w.data(), k + 1, pi, pj, k, G.tmp, K + 2, ws, st(), G.run, ep);
         blas_maxpy(G.w[k], G.w.data(), k, G.tmp, K + 2, -1.0, true, st(), G.run);
       }
-      // second pass: <w_j, w_k>, |w_k|^2, <w_k, r>
+      // second pass: <w_j, w_k>, |w_k|^2, <w_k, r>, |r|^2 (the residual before
+      // this step's update, summed afresh so that the convergence test never
+      // rests on a running difference of squares)
       Vec vv[kMaxVecs + 1];
       for (int j = 0; j <= k; ++j) vv[j] = G.w[j];
       vv[k + 1] = G.r;
       for (int j = 0; j < k; ++j) { pi[j] = j; pj[j] = k; }
       pi[k] = k; pj[k] = k;
       pi[k + 1] = k; pj[k + 1] = k + 1;
+      pi[k + 2] = k + 1; pj[k + 2] = k + 1;
       {
         Epilogue ep;
         ep.kind = EPI_GCR_STEP;
@@ -563,7 +566,7 @@ struct Engine {
         ep.d2a = G.beta; ep.d2b = G.gamma; ep.d2c = G.alpha; ep.d2d = G.ginv; ep.d2e = G.na;
         ep.db = (double*)G.r2; ep.dc = G.thr2;
         ep.ia = G.active; ep.ib = G.nk; ep.run = G.run; ep.run_outer = run_outer;
-        blas_pair_dots(vv, k + 2, pi, pj, k + 2, G.tmp, K + 2, ws, st(), G.run, ep);
+        blas_pair_dots(vv, k + 2, pi, pj, k + 3, G.tmp, K + 2, ws, st(), G.run, ep);
       }
       blas_gcr_update(G.w.data(), k, G.tmp, K + 2, G.ginv, G.r, G.na, st(), G.run);
       if (lvl1) pe();

@@ -114,3 +114,27 @@ def test_plain_c_client(libpath, tmp_path):
     want = [p.n_coarse, p.nvec[0], p.inner_maxiter, p.coarsest_cheb_s, p.block_coarse, p.coarsest_basis,
             q["grid"], q["per"], q["nslot"]]
     assert [int(v) for v in r.stdout.split()] == want
+
+
+def test_dot_noalloc_argument_checks():
+    """The binding refuses, before any pointer reaches the library, the
+    tensors that would make the no-allocation reduction read or write outside
+    the caller's buffers: a narrower dtype, a strided view, a y of another
+    shape, an out shorter than nsys, host memory (host-only checks)."""
+    import torch
+    from paper_2212_12559_gb300.binding import check_dot_noalloc_args
+    x = torch.zeros(2, 8, dtype=torch.complex128)
+    out = torch.zeros(2, dtype=torch.complex128)
+    cases = [
+        (x.to(torch.complex64), x, out, "complex128"),
+        (x, x, out.to(torch.complex64), "complex128"),
+        (torch.zeros(8, 2, dtype=torch.complex128).t(), x, out, "contiguous"),
+        (x, torch.zeros(2, 7, dtype=torch.complex128), out, "shape"),
+        (x, x, torch.zeros(1, dtype=torch.complex128), "nsys entries"),
+        (x, x, out, "CUDA"),
+        (x.numpy(), x, out, "torch tensor"),
+        (torch.zeros(0, 8, dtype=torch.complex128), torch.zeros(0, 8, dtype=torch.complex128), out, "non-empty"),
+    ]
+    for a, b, o, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            check_dot_noalloc_args(a, b, o)

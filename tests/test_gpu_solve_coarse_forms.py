@@ -210,14 +210,20 @@ def test_deflated_coarsest_singular_values_and_solve(binding):
     for q in range(2):
         ref = mg.deflated_coarsest(lev, rc[q])
         assert rel(x[q], ref) <= 1e-8
+    # the default solve (s = 8, 0.25 or eight cycles) element by element: its
+    # basis is well conditioned here (Gram eigenvalues above 1e-7 of the
+    # largest), so the normal-equation solve and the oracle's least squares
+    # give the same correction to rounding
     op, mg, sv = deflation_problem(binding, binding.PREC_DOUBLE, k=k, s=8)
     lev = mg.levels[-1]
     x = sv.coarse_solve(0, rc)
     for q in range(2):
-        r = np.linalg.norm(rc[q] - lev.apply(x[q])) / np.linalg.norm(rc[q])
         ref = mg.deflated_coarsest(lev, rc[q])
+        assert rel(x[q], ref) <= 1e-8, rel(x[q], ref)
+        assert np.abs(x[q] - ref).max() <= 1e-8 * np.abs(ref).max()
+        r = np.linalg.norm(rc[q] - lev.apply(x[q])) / np.linalg.norm(rc[q])
         r_ref = np.linalg.norm(rc[q] - lev.apply(ref)) / np.linalg.norm(rc[q])
-        assert r <= 0.25 or abs(r - r_ref) <= 1e-6, (r, r_ref)
+        assert abs(r - r_ref) <= 1e-6 * max(r_ref, 1e-3), (r, r_ref)
 
 
 @pytest.mark.parametrize("prec,s,basis", [(0, 8, 0), (2, 8, 0), (0, 16, 0), (0, 16, 1), (2, 16, 1)])
