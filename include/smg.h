@@ -161,6 +161,26 @@ SMG_API int smg_set_mass(smg_ctx* ctx, double mass);
  * are used as the near-null vectors unchanged. */
 SMG_API int smg_mg_setup(smg_ctx* ctx, const smg_mg_params* params, const void* const* phi0, int where);
 
+/* Sec. 3.2 generates the near-null vectors and the coarsest level's singular
+ * vectors once, at the lightest mass, saves them and reuses them for every
+ * later solve.  smg_save_setup writes the current setup to the file `path`:
+ * the parameters, the near-null vectors of every coarsening as the setup
+ * produced them (before chiral doubling and block orthonormalisation), the
+ * CGNE iteration counts and, with a deflated coarsest level, its singular
+ * values and vectors; a hash of the contents closes the file.  Nothing about
+ * the gauge field is stored.  SMG_ERR_STATE before mg_setup; SMG_ERR_ARG when
+ * the file cannot be written. */
+SMG_API int smg_save_setup(smg_ctx* ctx, const char* path);
+/* Rebuilds the hierarchy from a file written by smg_save_setup, for the
+ * context's current gauge field and mass (set_gauge and set_mass first): the
+ * saved vectors are block-orthonormalised and coarsened exactly as
+ * smg_mg_setup does (no CGNE, no singular-vector iteration), so with the
+ * gauge field and mass of the save every coarse operator is bit for bit the
+ * one saved with.  Replaces any previous setup.  SMG_ERR_ARG when the file
+ * is missing, truncated, fails its hash or was saved for other lattice
+ * extents; SMG_ERR_STATE without a gauge field or mass. */
+SMG_API int smg_load_setup(smg_ctx* ctx, const char* path);
+
 /* Sec. 3.2: solves M x = b to ||b - M x|| <= tol ||b|| (recomputed in FP64).
  * b, x: V*3 complex FP64.  x is output only (zero initial guess).
  * Returns SMG_ERR_NOT_CONVERGED (with x the last iterate) at max_outer. */
@@ -276,6 +296,57 @@ SMG_API int smg_time_kernel(smg_ctx* ctx, int kernel, int l, int nsys, int nrep,
  * context's stream).  Allocates and frees its own stencil and fields. */
 SMG_API int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int nsys, int prec, int nrep,
                                    double* ms_per_launch);
+/* Kernels of the 9-point coarse apply (Sec. 3.1: the paper's coarse stencil
+ * exposes extra parallelism beyond the volume; here the choice is a kernel
+ * per shape).  CORES: one CTA per site and system, a warp per row, any
+ * precision; MMA: mma.sync tensor-core GEMM over several systems (FP16
+ * stencil, FP32 vectors, N % 16 == 0, N <= 128, nsys >= 2); TC_*: tcgen05 + TMA
+ * GEMM over up to 16 systems per launch (FP16 stencil, FP32 vectors, N = 128,
+ * nsys >= 2) with 1 or 2 persistent CTAs per SM and a 4- or 6-stage stencil
+ * ring.  AUTO: the autotuner's choice (below). */
+enum {
+  SMG_COARSE_AUTO = 0,
+  SMG_COARSE_CORES = 1,
+  SMG_COARSE_MMA = 2,
+  SMG_COARSE_TC_1x4 = 3,
+  SMG_COARSE_TC_2x4 = 4,
+  SMG_COARSE_TC_1x6 = 5
+};
+/* The coarse apply (Sec. 3.1) of a caller's stencil: stencil is FP64
+ * [Vc][N][9][N] complex ([site][row][direction][column]; direction 0 self,
+ * 1 + 2mu forward, 2 + 2mu backward) on the periodic coarse lattice cdims[4],
+ * packed to the storage of `prec` as smg_mg_setup packs its own (FP16 with
+ * one FP32 scale per row for SMG_PREC_HALF); in, out: [nsys][Vc][N] FP64,
+ * rounded to the vector precision of `prec`; path: SMG_COARSE_*.
+ * SMG_ERR_ARG when the path does not serve the shape; SMG_ERR_TIMEOUT when a
+ * bounded wait of the tcgen05 kernel gave up. */
+SMG_API int smg_coarse_apply_stencil(smg_ctx* ctx, const int cdims[4], int N, int prec, int path,
+                                     const void* stencil, int nsys, const void* in, void* out, int where);
+/* Host only: the SMG_COARSE_* kernels that serve N components, nsys systems
+ * and precision `prec`, the untuned default first; writes up to cap of them
+ * and returns how many there are (SMG_ERR_ARG on bad arguments). */
+SMG_API int smg_coarse_paths(int N, int nsys, int prec, int* paths, int cap);
+
+/* Autotuner of launch shapes (an implementation service; the paper has no
+ * counterpart).  The first time a kernel family meets a shape with more than
+ * one candidate (today: the coarse apply's kernels), every candidate runs on
+ * that shape's real operator data into scratch output, timed with CUDA
+ * events on the calling stream, and the fastest serves the shape for the rest
+ * of the process; nothing is tuned while a stream is being captured into a
+ * graph (the untuned default serves instead).  mode: 1 = tune (default),
+ * 0 = always the untuned default.  The table is process-wide. */
+SMG_API int smg_tune_mode(int mode);
+/* The table as text, one shape per line: key, chosen path id, its name, then
+ * name=ms for each timed candidate, tab separated.  Writes at most cap bytes
+ * (NUL-terminated) and returns the size the whole text needs. */
+SMG_API long long smg_tune_table(char* buf, long long cap);
+/* Writes the table to a file / merges a file's entries (key and path id of
+ * each line) into the table, so that a later process skips the timing.
+ * SMG_ERR_ARG on an unreadable or malformed file. */
+SMG_API int smg_tune_save(const char* path);
+SMG_API int smg_tune_load(const char* path);
+SMG_API int smg_tune_clear(void);
+
 /* Launch plan of the persistent coarse-level solver (host only, no device
  * needed): a level of V sites with N components, nsys systems, nvec_next
  * near-null vectors of the next level (0: coarsest, no restriction), storage
@@ -286,6 +357,15 @@ SMG_API int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int 
  * and staging area.  Returns SMG_ERR_ARG on a bad shape. */
 SMG_API int smg_persist_plan(int V, int N, int nsys, int nvec_next, int prec, int sms, long long smem_cap,
                              long long out[10]);
+
+/* Test hook for the bounded waits (no counterpart in the paper): the grid
+ * barriers of the persistent coarse-level solver give up after limit_ns
+ * nanoseconds (default 2 s; 1000 <= limit_ns <= 2e9) and, with
+ * extra_arrivals = 1, expect one arrival that never comes, so that every
+ * barrier wait runs out.  The kernel then records an error, lets its bulk
+ * copies land and returns; the solve returns SMG_ERR_TIMEOUT and clears the
+ * barrier words.  (limit 2e9, extra 0) restores normal operation. */
+SMG_API int smg_debug_persist_barrier(smg_ctx* ctx, long long limit_ns, int extra_arrivals);
 
 /* Total kernels launched by the library in this process (a CUDA-graph replay
  * counts every kernel node it runs). */

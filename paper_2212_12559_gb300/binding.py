@@ -29,7 +29,9 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_get_coarse_op", "smg_restrict", "smg_prolong", "smg_coarse_apply", "smg_force",
            "smg_setup_iterations", "smg_time_kernel", "smg_kernel_launches", "smg_fermion_action", "smg_dot_noalloc",
            "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators", "smg_persist_plan",
-           "smg_get_coarse_xinv", "smg_get_deflation", "smg_coarse_solve"]
+           "smg_get_coarse_xinv", "smg_get_deflation", "smg_coarse_solve", "smg_save_setup", "smg_load_setup",
+           "smg_coarse_apply_stencil", "smg_coarse_paths", "smg_tune_mode", "smg_tune_table", "smg_tune_save",
+           "smg_tune_load", "smg_tune_clear", "smg_debug_persist_barrier"]
 
 
 class MGParams(ctypes.Structure):
@@ -92,6 +94,16 @@ def load(path: str = LIB_PATH):
         "smg_set_mass": (i, [vp, d]),
         "smg_mg_setup": (i, [vp, ctypes.POINTER(MGParams), ctypes.POINTER(vp), i]),
         "smg_solve": (i, [vp, vp, vp, d, i, ctypes.POINTER(SolveInfo)]),
+        "smg_coarse_apply_stencil": (i, [vp, ctypes.POINTER(ctypes.c_int), i, i, i, vp, i, vp, vp, i]),
+        "smg_coarse_paths": (i, [i, i, i, ip, i]),
+        "smg_tune_mode": (i, [i]),
+        "smg_debug_persist_barrier": (i, [vp, ctypes.c_longlong, i]),
+        "smg_tune_table": (ctypes.c_longlong, [ctypes.c_char_p, ctypes.c_longlong]),
+        "smg_tune_save": (i, [ctypes.c_char_p]),
+        "smg_tune_load": (i, [ctypes.c_char_p]),
+        "smg_tune_clear": (i, []),
+        "smg_save_setup": (i, [vp, ctypes.c_char_p]),
+        "smg_load_setup": (i, [vp, ctypes.c_char_p]),
         "smg_multi_solve": (i, [vp, i, vp, i, ctypes.POINTER(d), vp, d, i, ctypes.POINTER(SolveInfo)]),
         "smg_multishift_cg": (i, [vp, vp, i, ctypes.POINTER(d), vp, d, i, i, ctypes.POINTER(SolveInfo)]),
         "smg_persist_plan": (i, [i, i, i, i, i, i, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
@@ -126,6 +138,57 @@ def load(path: str = LIB_PATH):
 
 def kernel_launches() -> int:
     return int(load().smg_kernel_launches())
+
+
+COARSE_AUTO, COARSE_CORES, COARSE_MMA, COARSE_TC_1x4, COARSE_TC_2x4, COARSE_TC_1x6 = range(6)
+
+
+def coarse_paths(N, nsys, prec):
+    """Coarse-apply kernels (COARSE_*) that serve a shape, the untuned default first (host only)."""
+    out = (ctypes.c_int * 8)()
+    n = load().smg_coarse_paths(int(N), int(nsys), int(prec), out, 8)
+    if n < 0:
+        raise SmgError(n, "coarse_paths: bad arguments")
+    return list(out)[:n]
+
+
+def tune_mode(mode):
+    rc = load().smg_tune_mode(int(mode))
+    if rc != 0:
+        raise SmgError(rc, "tune_mode: 0 or 1")
+
+
+def tune_table():
+    """The autotuner's table: list of (key, path id, name, {candidate: ms})."""
+    lib = load()
+    need = lib.smg_tune_table(None, 0)
+    buf = ctypes.create_string_buffer(int(need))
+    lib.smg_tune_table(buf, need)
+    rows = []
+    for line in buf.value.decode().splitlines():
+        f = line.split("\t")
+        times = {}
+        for t in f[3:]:
+            k, _, v = t.rpartition("=")
+            times[k] = float(v)
+        rows.append((f[0], int(f[1]), f[2] if len(f) > 2 else "", times))
+    return rows
+
+
+def tune_save(path):
+    rc = load().smg_tune_save(os.fsencode(path))
+    if rc != 0:
+        raise SmgError(rc, f"tune_save: cannot write {path}")
+
+
+def tune_load(path):
+    rc = load().smg_tune_load(os.fsencode(path))
+    if rc != 0:
+        raise SmgError(rc, f"tune_load: cannot read {path}")
+
+
+def tune_clear():
+    load().smg_tune_clear()
 
 
 def persist_plan(V, N, nsys, nvec_next, prec, sms, smem_cap):
@@ -256,6 +319,28 @@ class Solver:
         self._check(self.lib.smg_mg_setup(self.ctx, ctypes.byref(params), arr, where))
         self.params = params
         self._keep = arrs
+
+    def save_setup(self, path):
+        """Writes the current setup (parameters, near-null vectors, deflation) to `path`."""
+        self._check(self.lib.smg_save_setup(self.ctx, os.fsencode(path)))
+
+    def load_setup(self, path):
+        """Rebuilds the hierarchy from a file of save_setup for the current gauge field and mass."""
+        self._check(self.lib.smg_load_setup(self.ctx, os.fsencode(path)))
+        self.params = self._read_params(path)
+
+    @staticmethod
+    def _read_params(path):
+        """The smg_mg_params block of a saved setup (binding bookkeeping: the
+        level shapes the array getters need)."""
+        with open(path, "rb") as f:
+            head = f.read(8 + 4 + 4 + 16 + 8 + 4)
+            if head[:8] != b"SMGSETUP":
+                raise SmgError(-1, f"{path} is not a saved setup")
+            p = MGParams()
+            raw = f.read(ctypes.sizeof(MGParams))
+            ctypes.memmove(ctypes.byref(p), raw, ctypes.sizeof(MGParams))
+        return p
 
     def solve(self, b, tol=1e-10, x=None):
         b = _prep(b)
@@ -442,6 +527,21 @@ class Solver:
                                              n, nsys, ctypes.c_void_p(out.data_ptr())))
         return out
 
+    def coarse_apply_stencil(self, cdims, stencil, v, prec=PREC_HALF, path=0):
+        """The coarse apply of a caller's FP64 stencil [Vc][N][9][N] on v [nsys][Vc][N]
+        through kernel `path` (COARSE_*; 0 = the autotuner's choice)."""
+        stencil = _prep(stencil)
+        v = _prep(v)
+        N = int(stencil.shape[1])
+        out = _like(v)
+        ps, where = _ptr(stencil)
+        pi, _ = _ptr(v)
+        po, _ = _ptr(out)
+        arr = (ctypes.c_int * 4)(*[int(c) for c in cdims])
+        self._check(self.lib.smg_coarse_apply_stencil(self.ctx, arr, N, int(prec), int(path), ps, int(v.shape[0]),
+                                                      pi, po, where))
+        return out
+
     def bench_coarse_apply(self, cdims, N, nsys=1, prec=PREC_HALF, nrep=20):
         """ms per launch of the coarse apply on a synthetic stencil of this shape."""
         v = ctypes.c_double()
@@ -449,6 +549,11 @@ class Solver:
         self._check(self.lib.smg_bench_coarse_apply(self.ctx, arr, int(N), int(nsys), int(prec), int(nrep),
                                                     ctypes.byref(v)))
         return v.value
+
+    def debug_persist_barrier(self, limit_ns=2000000000, extra_arrivals=0):
+        """Test hook: grid-barrier wait limit of the persistent coarse solver and
+        an extra expected arrival that never comes (extra_arrivals = 1)."""
+        self._check(self.lib.smg_debug_persist_barrier(self.ctx, int(limit_ns), int(extra_arrivals)))
 
     def setup_iterations(self, l):
         v = ctypes.c_int()

@@ -1,10 +1,13 @@
 // The C ABI of libsmg (declared in include/smg.h): argument checks, error
 // translation and host/device staging around the solver in solver.cu.
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "persist.cuh"
 #include "solver.cuh"
+#include "tune.cuh"
 
 namespace smg {
 std::string dot_noalloc(const void* x, const void* y, long long n, int nsys, void* out, cudaStream_t st);
@@ -162,6 +165,24 @@ int smg_mg_setup(smg_ctx* ctx, const smg_mg_params* params, const void* const* p
     SMG_REQUIRE(params != nullptr && valid_where(where), "mg_setup: null params or bad `where`");
     if (!c.gauge_set || !c.mass_set) throw smg::StateError("mg_setup needs set_gauge and set_mass first");
     smg::ctx_mg_setup(c, *params, phi0, where);
+    return SMG_OK;
+  });
+}
+
+int smg_save_setup(smg_ctx* ctx, const char* path) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(path != nullptr, "save_setup: null path");
+    if (!c.setup_done) throw smg::StateError("save_setup needs mg_setup first");
+    smg::ctx_save_setup(c, path);
+    return SMG_OK;
+  });
+}
+
+int smg_load_setup(smg_ctx* ctx, const char* path) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(path != nullptr, "load_setup: null path");
+    if (!c.gauge_set || !c.mass_set) throw smg::StateError("load_setup needs set_gauge and set_mass first");
+    smg::ctx_load_setup(c, path);
     return SMG_OK;
   });
 }
@@ -387,6 +408,75 @@ int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int nsys, in
     *ms_per_launch = smg::ctx_bench_coarse(c, cdims, N, nsys, prec, nrep);
     return SMG_OK;
   });
+}
+
+int smg_coarse_apply_stencil(smg_ctx* ctx, const int cdims[4], int N, int prec, int path, const void* stencil,
+                             int nsys, const void* in, void* out, int where) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(cdims && stencil && in && out && valid_where(where), "coarse_apply_stencil: null argument");
+    smg::ctx_coarse_apply_stencil(c, cdims, N, prec, path, stencil, nsys, in, out, where);
+    return SMG_OK;
+  });
+}
+
+int smg_coarse_paths(int N, int nsys, int prec, int* paths, int cap) {
+  if (paths == nullptr || cap < 1 || N < 1 || nsys < 1 || prec < SMG_PREC_DOUBLE || prec > SMG_PREC_HALF)
+    return SMG_ERR_ARG;
+  const smg::Prec vp = prec == SMG_PREC_DOUBLE ? smg::P64 : smg::P32;
+  const smg::Store sp = prec == SMG_PREC_DOUBLE ? smg::S64 : (prec == SMG_PREC_SINGLE ? smg::S32 : smg::S16);
+  return smg::coarse_path_list(N, nsys, vp, sp, true, paths, cap);
+}
+
+int smg_debug_persist_barrier(smg_ctx* ctx, long long limit_ns, int extra_arrivals) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(limit_ns >= 1000 && limit_ns <= 2000000000LL && (extra_arrivals == 0 || extra_arrivals == 1),
+                "debug_persist_barrier: limit in [1 us, 2 s], extra arrivals 0 or 1");
+    c.dbg_bar_limit_ns = (unsigned long long)limit_ns;
+    c.dbg_bar_extra = extra_arrivals;
+    return SMG_OK;
+  });
+}
+
+int smg_tune_mode(int mode) {
+  if (mode != 0 && mode != 1) return SMG_ERR_ARG;
+  smg::tune_set_mode(mode);
+  return SMG_OK;
+}
+
+long long smg_tune_table(char* buf, long long cap) {
+  const std::string t = smg::tune_table_text();
+  if (buf != nullptr && cap > 0) {
+    const size_t m = std::min((size_t)(cap - 1), t.size());
+    std::memcpy(buf, t.data(), m);
+    buf[m] = '\0';
+  }
+  return (long long)t.size() + 1;
+}
+
+int smg_tune_load(const char* path) {
+  if (path == nullptr) return SMG_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (f == nullptr) return SMG_ERR_ARG;
+  std::string text;
+  char buf[4096];
+  size_t m;
+  while ((m = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, m);
+  std::fclose(f);
+  return smg::tune_table_load(text) < 0 ? SMG_ERR_ARG : SMG_OK;
+}
+
+int smg_tune_save(const char* path) {
+  if (path == nullptr) return SMG_ERR_ARG;
+  FILE* f = std::fopen(path, "wb");
+  if (f == nullptr) return SMG_ERR_ARG;
+  const std::string t = smg::tune_table_text();
+  const bool ok = std::fwrite(t.data(), 1, t.size(), f) == t.size();
+  return (std::fclose(f) == 0 && ok) ? SMG_OK : SMG_ERR_ARG;
+}
+
+int smg_tune_clear(void) {
+  smg::tune_table_clear();
+  return SMG_OK;
 }
 
 int smg_dot_noalloc(smg_ctx* ctx, const void* x, const void* y, long long n, int nsys, void* out) {

@@ -8,10 +8,12 @@
 // sit in shared memory.  FP16 storage keeps one FP32 scale per (site, row),
 // the 16-bit analogue of the paper's fixed-point coarse links with a norm.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 
 #include "ops.cuh"
 #include "stencil_row.cuh"
+#include "tune.cuh"
 
 namespace smg {
 namespace {
@@ -558,17 +560,6 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(float2* __restric
   (void)n;
 }
 
-// Multi-RHS coarse apply path: 0 CUDA cores only, 1 mma.sync, 2 tcgen05 where it
-// applies (N = 128) else mma.sync.  SMG_COARSE_TC selects; default 2.
-int coarse_tc_mode() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("SMG_COARSE_TC");
-    v = (e != nullptr && e[0] >= '0' && e[0] <= '2') ? e[0] - '0' : 2;
-  }
-  return v;
-}
-
 unsigned grid_cap(long long total, int threads) {
   long long g = (total + threads - 1) / threads;
   if (g > 16384) g = 16384;
@@ -596,38 +587,66 @@ void launch_mma(const Vec& out, const Vec& in, const CoarseParams& p, const Stor
   SMG_LAUNCH_OK();
 }
 
-// Tensor-core multi-RHS path: FP32 vectors, FP16 stencil, N a multiple of 16
-// (at most 128: 8 warps per CTA), full operator.
-bool coarse_mma_ok(const Vec& in, const CoarseParams& p, const Stored& S) {
-  return in.prec == P32 && S.s == S16 && in.nsys >= 2 && p.part < 0 && p.N % 16 == 0 && p.N <= 128 &&
-         S.scale != nullptr;
+bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op) {
+  const bool multi16 = vp == P32 && s == S16 && nsys >= 2 && full_op;
+  switch (path) {
+    case CPATH_CORES: return 9 * (size_t)N * prec_bytes(vp) <= 48 * 1024;
+    case CPATH_MMA: return multi16 && N % 16 == 0 && N <= 128;
+    case CPATH_UMMA_1x4:
+    case CPATH_UMMA_2x4:
+    case CPATH_UMMA_1x6: return multi16 && N == 128;
+    default: return false;
+  }
 }
 
-void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
-                  const int* run) {
-  SMG_REQUIRE(in.n == (long long)p.g.V * p.N && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
-              "coarse_apply: shape mismatch");
-  const int tc = p.allow_tc ? coarse_tc_mode() : 0;
-  if (tc == 2 && coarse_umma_ok(in, p, S)) {
-    static int* err = nullptr;
-    if (err == nullptr) {
-      SMG_CUDA_OK(cudaMalloc(&err, sizeof(int)));
-      SMG_CUDA_OK(cudaMemset(err, 0, sizeof(int)));
-      SMG_CUDA_OK(cudaDeviceSynchronize());
+int coarse_path_list(int N, int nsys, Prec vp, Store s, bool full_op, int* out, int cap) {
+  int n = 0;
+  for (int path : {CPATH_UMMA_2x4, CPATH_UMMA_1x4, CPATH_UMMA_1x6, CPATH_MMA, CPATH_CORES})
+    if (coarse_path_ok(path, N, nsys, vp, s, full_op)) {
+      if (out != nullptr && n < cap) out[n] = path;
+      ++n;
     }
-    coarse_apply_umma(out, in, p, S, err, st, run);
-    return;
+  return n;
+}
+
+namespace {
+const char* path_name(int path) {
+  switch (path) {
+    case CPATH_CORES: return "cuda-cores warp/row";
+    case CPATH_MMA: return "mma.sync m16n8k16";
+    case CPATH_UMMA_1x4: return "tcgen05 1 CTA/SM 4 stages";
+    case CPATH_UMMA_2x4: return "tcgen05 2 CTA/SM 4 stages";
+    case CPATH_UMMA_1x6: return "tcgen05 1 CTA/SM 6 stages";
+    default: return "?";
   }
-  if (tc >= 1 && coarse_mma_ok(in, p, S)) {
-    for (int s0 = 0; s0 < in.nsys; s0 += kMmaMaxRhs) {
-      const int nr = std::min(kMmaMaxRhs, in.nsys - s0);
-      const int nt = (2 * nr + 7) / 8;
-      if (nt <= 1) launch_mma<1>(out, in, p, S, st, run, s0);
-      else if (nt == 2) launch_mma<2>(out, in, p, S, st, run, s0);
-      else if (nt == 3) launch_mma<3>(out, in, p, S, st, run, s0);
-      else launch_mma<4>(out, in, p, S, st, run, s0);
-    }
-    return;
+}
+
+// Candidate paths of a shape, the untuned default first.
+std::vector<TuneCandidate> coarse_candidates(int N, int nsys, Prec vp, Store s, bool full_op) {
+  int ids[CPATH_COUNT];
+  const int n = coarse_path_list(N, nsys, vp, s, full_op, ids, CPATH_COUNT);
+  std::vector<TuneCandidate> c;
+  for (int i = 0; i < n; ++i) c.push_back({ids[i], path_name(ids[i])});
+  return c;
+}
+
+void coarse_launch(int path, const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
+                   const int* run) {
+  switch (path) {
+    case CPATH_UMMA_1x4: coarse_apply_umma(out, in, p, S, coarse_umma_err(), st, run, 1, 4); return;
+    case CPATH_UMMA_2x4: coarse_apply_umma(out, in, p, S, coarse_umma_err(), st, run, 2, 4); return;
+    case CPATH_UMMA_1x6: coarse_apply_umma(out, in, p, S, coarse_umma_err(), st, run, 1, 6); return;
+    case CPATH_MMA:
+      for (int s0 = 0; s0 < in.nsys; s0 += kMmaMaxRhs) {
+        const int nr = std::min(kMmaMaxRhs, in.nsys - s0);
+        const int nt = (2 * nr + 7) / 8;
+        if (nt <= 1) launch_mma<1>(out, in, p, S, st, run, s0);
+        else if (nt == 2) launch_mma<2>(out, in, p, S, st, run, s0);
+        else if (nt == 3) launch_mma<3>(out, in, p, S, st, run, s0);
+        else launch_mma<4>(out, in, p, S, st, run, s0);
+      }
+      return;
+    default: break;
   }
   const size_t smem = (size_t)9 * p.N * prec_bytes(in.prec);
   SMG_REQUIRE(smem <= 48 * 1024, "coarse_apply: N too large");
@@ -635,20 +654,60 @@ void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const St
   int4 agg = make_int4(p.agg[0], p.agg[1], p.agg[2], p.agg[3]);
   if (in.prec == P64) {
     SMG_REQUIRE(S.s == S64, "coarse_apply: FP64 vectors need FP64 stencil");
-    launch_k(coarse_apply_kernel<double, double2>, dim3(grid), dim3(256), smem, st, (double2*)out.p, (const double2*)in.p,
-                                                                  (const double2*)S.p, nullptr, p.g, p.N, p.part,
-                                                                  agg, (const double2*)p.sub_from, run);
+    launch_k(coarse_apply_kernel<double, double2>, dim3(grid), dim3(256), smem, st, (double2*)out.p,
+             (const double2*)in.p, (const double2*)S.p, nullptr, p.g, p.N, p.part, agg, (const double2*)p.sub_from,
+             run);
   } else if (S.s == S32) {
     launch_k(coarse_apply_kernel<float, float2>, dim3(grid), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p,
-                                                                (const float2*)S.p, nullptr, p.g, p.N, p.part,
-                                                                agg, (const float2*)p.sub_from, run);
+             (const float2*)S.p, nullptr, p.g, p.N, p.part, agg, (const float2*)p.sub_from, run);
   } else {
     SMG_REQUIRE(S.s == S16, "coarse_apply: unsupported storage");
-    launch_k(coarse_apply_kernel<float, __half2>, dim3(grid), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p,
-                                                                 (const __half2*)S.p, S.scale, p.g, p.N, p.part,
-                                                                 agg, (const float2*)p.sub_from, run);
+    launch_k(coarse_apply_kernel<float, __half2>, dim3(grid), dim3(256), smem, st, (float2*)out.p,
+             (const float2*)in.p, (const __half2*)S.p, S.scale, p.g, p.N, p.part, agg, (const float2*)p.sub_from,
+             run);
   }
   SMG_LAUNCH_OK();
+}
+}  // namespace
+
+// The kernel is CoarseParams::path when given; otherwise the autotuner's
+// choice for the shape (timed once on this stencil and these inputs into a
+// scratch output), CUDA cores when allow_tc = 0.
+void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
+                  const int* run) {
+  SMG_REQUIRE(in.n == (long long)p.g.V * p.N && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
+              "coarse_apply: shape mismatch");
+  const bool full = p.part < 0;
+  int path = p.allow_tc ? p.path : CPATH_CORES;
+  if (path == CPATH_AUTO) {
+    const std::vector<TuneCandidate> cands = coarse_candidates(p.N, in.nsys, in.prec, S.s, full);
+    SMG_REQUIRE(!cands.empty(), "coarse_apply: no kernel serves this shape");
+    if (cands.size() == 1) {
+      path = cands[0].id;
+    } else {
+      char key[160];
+      std::snprintf(key, sizeof(key), "coarse_apply V=%d N=%d nsys=%d vec=%s store=%s sub=%d", p.g.V, p.N, in.nsys,
+                    in.prec == P64 ? "f64" : "f32", S.s == S16 ? "f16" : (S.s == S32 ? "f32" : "f64"),
+                    p.sub_from != nullptr ? 1 : 0);
+      // candidates write a scratch output (freed after tuning)
+      struct Scratch {
+        void* p = nullptr;
+        ~Scratch() { if (p) cudaFree(p); }
+      } scratch;
+      path = tune_pick(key, cands, st, [&](int id) {
+        if (scratch.p == nullptr) {
+          SMG_CUDA_OK(cudaMalloc(&scratch.p, out.bytes()));
+        }
+        Vec o = out;
+        o.p = scratch.p;
+        coarse_launch(id, o, in, p, S, st, nullptr);
+      });
+    }
+  } else {
+    SMG_REQUIRE(coarse_path_ok(path, p.N, in.nsys, in.prec, S.s, full),
+                "coarse_apply: the requested kernel does not serve this shape");
+  }
+  coarse_launch(path, out, in, p, S, st, run);
 }
 
 void synth_fill(void* dst, Store s, long long n, unsigned seed, cudaStream_t st) {

@@ -208,4 +208,30 @@ void build_deflation(Context& c, CoarseLevel& C, const void* start, int where) {
   SMG_CUDA_OK(cudaStreamSynchronize(st));
 }
 
+// The deflation state of a saved setup: V and U diag(1/sigma) in FP64 as they
+// were saved, their FP32 copies derived as build_deflation derives them.
+void restore_deflation(Context& c, CoarseLevel& C, const DeflRestore& r) {
+  const long long n = (long long)C.g.V * C.N;
+  SMG_REQUIRE(r.k == c.params.coarsest_deflate && (int)r.sigma.size() == r.k && r.V && r.U,
+              "load_setup: deflation block does not match the parameters");
+  cudaStream_t st = c.stream;
+  C.defl_k = r.k;
+  C.defl_iters = r.iters;
+  C.defl_res = r.res;
+  C.sigma = r.sigma;
+  C.cheb_lmin = r.lmin;
+  C.cheb_lmax = r.lmax;
+  const size_t kb64 = (size_t)n * r.k * sizeof(double2);
+  C.dV64.alloc(kb64);
+  C.dU64.alloc(kb64);
+  upload(C.dV64.p, r.V, kb64, SMG_HOST, st);
+  upload(C.dU64.p, r.U, kb64, SMG_HOST, st);
+  C.dV32.alloc((size_t)n * r.k * sizeof(float2));
+  C.dU32.alloc((size_t)n * r.k * sizeof(float2));
+  auto mk = [&](void* p, Prec pr) { Vec v; v.p = p; v.n = n; v.nsys = r.k; v.prec = pr; return v; };
+  blas_copy(mk(C.dV32.p, P32), mk(C.dV64.p, P64), st);
+  blas_copy(mk(C.dU32.p, P32), mk(C.dU64.p, P64), st);
+  SMG_CUDA_OK(cudaStreamSynchronize(st));
+}
+
 }  // namespace smg

@@ -108,13 +108,31 @@ struct CoarseParams {
   int agg[4] = {1, 1, 1, 1};
   const void* sub_from = nullptr;   // when set: out = sub_from - A_hat in
   int allow_tc = 1;          // 0: keep FP32 inputs (no FP16 rounding of the vectors), e.g. for the setup
+  int path = 0;              // CPATH_*: 0 = the tuned (or default) choice for the shape
 };
+// Kernels of the coarse apply: CUDA cores (one CTA per site and system, a warp
+// per row), mma.sync m16n8k16 (several systems, N % 16 == 0, N <= 128), and
+// tcgen05 + TMA (several systems, N = 128) with 1 or 2 CTAs per SM and a 4- or
+// 6-stage stencil ring.
+enum {
+  CPATH_AUTO = 0, CPATH_CORES = 1, CPATH_MMA = 2, CPATH_UMMA_1x4 = 3, CPATH_UMMA_2x4 = 4, CPATH_UMMA_1x6 = 5,
+  CPATH_COUNT = 6
+};
+// Whether a path serves a shape (host logic only).
+bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op);
+// The paths that serve a shape in the autotuner's order (the untuned default
+// first): writes up to cap of them, returns how many there are.
+int coarse_path_list(int N, int nsys, Prec vp, Store s, bool full_op, int* out, int cap);
 void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, cudaStream_t st,
                   const int* run = nullptr);
 // tcgen05 / TMA multi-RHS path (N = 128, FP16 stencil, FP32 vectors, >= 2 systems); err: device int
 bool coarse_umma_ok(const Vec& in, const CoarseParams& p, const Stored& S);
 void coarse_apply_umma(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, int* err,
-                       cudaStream_t st, const int* run = nullptr);
+                       cudaStream_t st, const int* run = nullptr, int ctas_per_sm = 2, int stages = 4);
+// Device error word of the tcgen05 coarse apply (set when a CTA gave up on a
+// bounded wait); read_and_clear returns whether it was set.
+int* coarse_umma_err();
+bool coarse_umma_err_read_and_clear(cudaStream_t st);
 // Hash-based synthetic values in [-1, 1) (benchmark inputs of a given shape)
 void synth_fill(void* dst, Store s, long long n, unsigned seed, cudaStream_t st);
 // S64 stencil -> stored copy in precision dst.s

@@ -31,8 +31,8 @@
 //
 // Grid barriers use one 64-bit arrival counter that only grows during a
 // launch (barrier b completes when it reaches b * gridDim); the last CTA to
-// exit clears it.  Every wait is bounded (2 s of %globaltimer); on expiry the
-// kernel sets an error word that the host reads, and returns.
+// exit clears it.  Every wait is bounded (2 s of %globaltimer by default); on
+// expiry the kernel sets an error word that the host reads, and returns.
 #include "ca_solve.cuh"
 #include "persist.cuh"
 #include "stencil_row.cuh"
@@ -128,8 +128,8 @@ __device__ bool grid_sync(const PersistArgs& a, Shared& sh, unsigned long long& 
     __threadfence();
     atomicAdd(a.bar, 1ull);
     const unsigned long long t0 = gtime();
-    while (ld_acquire(a.bar) < target) {
-      if (*(volatile int*)a.err != 0 || gtime() - t0 > 2000000000ull) {
+    while (ld_acquire(a.bar) < target + (unsigned long long)a.bar_extra) {
+      if (*(volatile int*)a.err != 0 || gtime() - t0 > a.bar_limit_ns) {
         atomicExch(a.err, 1);
         sh.ok = 0;
         break;

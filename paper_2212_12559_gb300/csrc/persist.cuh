@@ -50,6 +50,9 @@ struct PersistArgs {
   unsigned long long* bar;   // barrier arrival counter, 0 between launches
   unsigned* exitc;           // CTAs that finished (the last one clears both counters)
   int* err;                  // set to 1 when a barrier wait times out
+  unsigned long long bar_limit_ns = 2000000000ull;   // limit of one grid-barrier wait
+  int bar_extra = 0;         // arrivals each barrier expects beyond the grid's: 0 in every
+                             // solve; 1 (test hook) makes every barrier wait run out
   const int* run;            // skip the launch when *run == 0
   unsigned long long* trace; // optional phase trace (see persist.cu), or nullptr
   int trace_cap;

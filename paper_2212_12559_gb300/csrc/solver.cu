@@ -616,6 +616,8 @@ struct Engine {
     a.bar = (unsigned long long*)((char*)pbuf.p + pbuf.bytes - 64);
     a.exitc = (unsigned*)((char*)pbuf.p + pbuf.bytes - 64 + 8);
     a.err = (int*)((char*)pbuf.p + pbuf.bytes - 64 + 16);
+    a.bar_limit_ns = c.dbg_bar_limit_ns;
+    a.bar_extra = c.dbg_bar_extra;
     a.run = run;
     a.trace = nullptr;
     a.trace_cap = 0;
@@ -641,7 +643,11 @@ struct Engine {
     return true;
   }
 
+  // Bounded device waits that gave up since the last check: the tcgen05
+  // coarse apply's error word, then the persistent solver's.
   void check_persistent_error() {
+    if (coarse_umma_err_read_and_clear(st()))
+      throw StateError("timeout: a bounded wait of the tcgen05 coarse apply gave up");
     if (!persistent) return;
     int err = 0;
     SMG_CUDA_OK(cudaMemcpyAsync(&err, (char*)pbuf.p + pbuf.bytes - 64 + 16, sizeof(int), cudaMemcpyDeviceToHost,
@@ -1082,7 +1088,7 @@ struct SetupOp {
 }  // namespace
 
 
-void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, int where) {
+void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, int where, const DeflRestore* restore) {
   SMG_REQUIRE(c.gauge_set && c.mass_set, "mg_setup needs set_gauge and set_mass first");
   SMG_REQUIRE(P.n_coarse >= 1 && P.n_coarse <= SMG_MAX_COARSE, "n_coarse must be 1..3");
   SMG_REQUIRE(P.inner_maxiter >= 1 && P.inner_maxiter <= 16, "inner_maxiter must be 1..16");
@@ -1197,7 +1203,10 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
       SMG_CUDA_OK(cudaStreamSynchronize(st));
       for (int v : hit) C.setup_iters = std::max(C.setup_iters, v);
     }
-    // ---- chiral doubling + block orthonormalisation (FP64)
+    // ---- chiral doubling + block orthonormalisation (FP64); the vectors as
+    // the setup produced them are kept for smg_save_setup
+    C.pre64.alloc(raw.bytes);
+    SMG_CUDA_OK(cudaMemcpyAsync(C.pre64.p, raw.p, raw.bytes, cudaMemcpyDeviceToDevice, st));
     block_orthonormalize(raw.as<double2>(), C.tg, st);
     C.raw64 = std::move(raw);
     C.P64.alloc(S64, (size_t)n * nvec, 0);
@@ -1309,14 +1318,16 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
     }
   if (P.coarsest_deflate > 0 && !c.coarse.back().dense) {
     CoarseLevel& C = c.coarse.back();
-    SMG_REQUIRE(phi0[P.n_coarse] != nullptr, "coarsest_deflate needs the start block phi0[n_coarse]");
+    SMG_REQUIRE(restore != nullptr || phi0[P.n_coarse] != nullptr,
+                "coarsest_deflate needs the start block phi0[n_coarse]");
     C.schur = P.coarsest_schur != 0;
     if (C.schur) {
       SMG_REQUIRE(C.block, "coarsest_schur needs block_coarse (identity self blocks)");
       for (int mu = 0; mu < 4; ++mu)
         SMG_REQUIRE(C.g.L[mu] % 2 == 0, "coarsest_schur needs even coarse extents (every hop changes parity)");
     }
-    build_deflation(c, C, phi0[P.n_coarse], where);
+    if (restore != nullptr) restore_deflation(c, C, *restore);
+    else build_deflation(c, C, phi0[P.n_coarse], where);
   }
   c.setup_done = true;
 }
@@ -1700,6 +1711,51 @@ int ctx_fermion_action(Context& c, const void* phi, void* X, void* Y, double tol
     info[1] = i2;
   }
   return (rc1 == SMG_OK && rc2 == SMG_OK) ? SMG_OK : SMG_ERR_NOT_CONVERGED;
+}
+
+// The 9-point coarse apply (Sec. 3.1) on a caller's FP64 stencil
+// [Vc][N][9][N], packed to the storage of `prec` as mg_setup packs its own,
+// through kernel `path` (CPATH_*; 0 = the autotuner's choice).
+void ctx_coarse_apply_stencil(Context& c, const int cdims[4], int N, int prec, int path, const void* stencil,
+                              int nsys, const void* in, void* out, int where) {
+  SMG_REQUIRE(N >= 1 && N <= 256 && nsys >= 1 && nsys <= 256, "coarse_apply_stencil: bad sizes");
+  SMG_REQUIRE(prec >= SMG_PREC_DOUBLE && prec <= SMG_PREC_HALF, "coarse_apply_stencil: bad precision");
+  SMG_REQUIRE(path >= CPATH_AUTO && path < CPATH_COUNT, "coarse_apply_stencil: bad path");
+  Geom g;
+  g.V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    SMG_REQUIRE(cdims[mu] >= 1 && cdims[mu] <= 4096, "coarse_apply_stencil: bad extents");
+    g.L[mu] = cdims[mu];
+    g.V *= cdims[mu];
+  }
+  const Store sp = store_of(prec);
+  const Prec vp = vprec_of(prec);
+  SMG_REQUIRE(path == CPATH_AUTO || coarse_path_ok(path, N, nsys, vp, sp, true),
+              "coarse_apply_stencil: that kernel does not serve this shape");
+  const long long nc = (long long)g.V * N;
+  DevBuf s64;
+  s64.alloc((size_t)nc * 9 * N * sizeof(double2));
+  upload(s64.p, stencil, s64.bytes, where, c.stream);
+  StoredBuf S;
+  if (sp != S64) {
+    S.alloc(sp, (size_t)nc * 9 * N, (size_t)nc);
+    coarse_pack(S.st, s64.as<double2>(), g, N, c.stream);
+  } else {
+    S.st = Stored{s64.p, nullptr, 1.0f, S64};
+  }
+  Scratch sc;
+  Vec vin = conv_in(c, sc.a, in, nc, nsys, vp, where);
+  sc.b.alloc(vin.bytes());
+  Vec vout = vin;
+  vout.p = sc.b.p;
+  CoarseParams p;
+  p.g = g;
+  p.N = N;
+  p.path = path;
+  coarse_apply(vout, vin, p, S.st, c.stream);
+  const bool tc_err = coarse_umma_err_read_and_clear(c.stream);
+  if (tc_err) throw StateError("timeout: a bounded wait of the tcgen05 coarse apply gave up");
+  conv_out(c, out, vout, where);
 }
 
 // Coarse 9-point apply on a synthetic stencil of a given shape (storage per

@@ -68,6 +68,18 @@ struct CoarseLevel {
   DevBuf D64, D32;          // dense inverse
   int nd = 0;
   int setup_iters = 0;
+  DevBuf pre64;             // near-null vectors as the setup produced them (before chiral
+                            // doubling and block orthonormalisation), FP64 [nvec][V][ndof]:
+                            // what smg_save_setup writes
+};
+
+// Deflation state of the coarsest level read back from a saved setup.
+struct DeflRestore {
+  int k = 0, iters = 0;
+  double lmin = 0.0, lmax = 0.0, res = 0.0;
+  std::vector<double> sigma;
+  const void* V = nullptr;   // host FP64 [k][Vc][N]
+  const void* U = nullptr;   // host FP64 U diag(1/sigma), [k][Vc][N]
 };
 
 // Per-system scalars and vectors of one batched GCR.
@@ -123,6 +135,10 @@ struct Context {
   DevBuf consts;               // +1 / -1 coefficient arrays
   double2 *ones = nullptr, *mones = nullptr;
   int nconst = 0;
+  // test hook (smg_debug_persist_barrier): grid-barrier wait limit and extra
+  // expected arrivals of the persistent coarse solver
+  unsigned long long dbg_bar_limit_ns = 2000000000ull;
+  int dbg_bar_extra = 0;
   ~Context();
 
   Prec vprec() const { return params.precision == SMG_PREC_DOUBLE ? P64 : P32; }
@@ -144,7 +160,13 @@ struct Context {
 // Host entry points used by the C ABI (api.cu).
 void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik, int where);
 void ctx_set_mass(Context& c, double m);
-void ctx_mg_setup(Context& c, const smg_mg_params& p, const void* const* phi0, int where);
+void ctx_mg_setup(Context& c, const smg_mg_params& p, const void* const* phi0, int where,
+                  const DeflRestore* restore = nullptr);
+// Checkpoint of the setup (Sec. 3.2: near-null and singular vectors generated
+// once and reused): save writes it, load rebuilds the hierarchy from it for the
+// context's gauge field and mass (setup_io.cu).
+void ctx_save_setup(Context& c, const char* path);
+void ctx_load_setup(Context& c, const char* path);
 int ctx_multishift_cg(Context& c, const void* b, int nshift, const double* masses, void* x, double tol, int maxiter,
                       int where, smg_solve_info* info);
 int ctx_propagators(Context& c, const void* b, int nmass, const double* masses, int n_mg, void* x, double tol,
@@ -152,6 +174,8 @@ int ctx_propagators(Context& c, const void* b, int nmass, const double* masses, 
 // The k = coarsest_deflate lowest singular triplets of the coarsest level C
 // (or of its Schur complement when C.schur) from the start block `start`.
 void build_deflation(Context& c, CoarseLevel& C, const void* start, int where);
+// The same state from a saved setup (no subspace iteration).
+void restore_deflation(Context& c, CoarseLevel& C, const DeflRestore& r);
 void ctx_coarse_solve(Context& c, int l, int nsys, const void* in, void* out, int where);
 int ctx_solve(Context& c, int nrhs, const void* b, int nshift, const double* masses, void* x, double tol, int where,
               smg_solve_info* info);
@@ -160,6 +184,8 @@ void ctx_transfer(Context& c, int which, int l, int prec, int nsys, const void* 
 void ctx_build_kd(Context& c);
 double ctx_time_kernel(Context& c, int kernel, int l, int nsys, int nrep);
 double ctx_bench_coarse(Context& c, const int cdims[4], int N, int nsys, int prec, int nrep);
+void ctx_coarse_apply_stencil(Context& c, const int cdims[4], int N, int prec, int path, const void* stencil,
+                              int nsys, const void* in, void* out, int where);
 int ctx_fermion_action(Context& c, const void* phi, void* X, void* Y, double tol, int where, double* S,
                        double* dSdm, smg_solve_info* info);
 void upload(void* dst, const void* src, size_t bytes, int where, cudaStream_t st);

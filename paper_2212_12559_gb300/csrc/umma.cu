@@ -34,13 +34,13 @@ namespace {
 constexpr int UM = 128;          // GEMM rows = components per coarse site
 constexpr int UN = 32;           // GEMM columns = 2 x 16 systems
 constexpr int UKC = 64;          // FP16 K elements per stage (one 128-byte swizzle row)
-constexpr int STAGES = 4;
 constexpr int A_BYTES = UM * UKC * 2;   // 16 KiB
 constexpr int B_BYTES = UN * UKC * 2;   // 4 KiB
 constexpr int UTHREADS = 256;
 constexpr int NBUILD = UTHREADS - 64;   // warps 2..7 build the B tiles
 constexpr int kMaxRhsU = 16;
 
+template <int STAGES>
 struct UmmaSmem {
   uint8_t a[STAGES][A_BYTES];
   uint8_t b[STAGES][B_BYTES];
@@ -138,6 +138,7 @@ __device__ __forceinline__ unsigned pack_h2(float lo, float hi) {
   return *reinterpret_cast<unsigned*>(&h);
 }
 
+template <int STAGES>
 __global__ void __launch_bounds__(UTHREADS, 1) coarse_umma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   float2* __restrict__ out,
                                                                   const float2* __restrict__ in,
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) coarse_umma_kernel(const __grid_c
                                                                   int* __restrict__ gerr, const int* run) {
   if (run != nullptr && *run == 0) return;
   extern __shared__ unsigned char umma_raw[];
-  UmmaSmem& sm = *reinterpret_cast<UmmaSmem*>(
+  UmmaSmem<STAGES>& sm = *reinterpret_cast<UmmaSmem<STAGES>*>(
       (unsigned char*)(((unsigned long long)umma_raw + 1023) & ~1023ull));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int N = UM;
@@ -337,11 +338,60 @@ bool coarse_umma_ok(const Vec& in, const CoarseParams& p, const Stored& S) {
   return in.prec == P32 && S.s == S16 && S.scale != nullptr && p.part < 0 && p.N == UM && in.nsys >= 2;
 }
 
+int* coarse_umma_err() {
+  static int* err[64] = {};
+  int dev = 0;
+  SMG_CUDA_OK(cudaGetDevice(&dev));
+  SMG_REQUIRE(dev >= 0 && dev < 64, "coarse_apply_umma: device ordinal out of range");
+  if (err[dev] == nullptr) {
+    SMG_CUDA_OK(cudaMalloc(&err[dev], sizeof(int)));
+    SMG_CUDA_OK(cudaMemset(err[dev], 0, sizeof(int)));
+    SMG_CUDA_OK(cudaDeviceSynchronize());
+  }
+  return err[dev];
+}
+
+bool coarse_umma_err_read_and_clear(cudaStream_t st) {
+  int* e = coarse_umma_err();
+  int h = 0;
+  SMG_CUDA_OK(cudaMemcpyAsync(&h, e, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SMG_CUDA_OK(cudaStreamSynchronize(st));
+  if (h != 0) {
+    SMG_CUDA_OK(cudaMemsetAsync(e, 0, sizeof(int), st));
+    SMG_CUDA_OK(cudaStreamSynchronize(st));
+  }
+  return h != 0;
+}
+
+namespace {
+template <int STAGES>
+void launch_umma(const CUtensorMap& map, const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S,
+                 int* err, cudaStream_t st, const int* run, int grid) {
+  const size_t smem = sizeof(UmmaSmem<STAGES>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    SMG_CUDA_OK(cudaFuncSetAttribute(coarse_umma_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    attr = true;
+  }
+  for (int s0 = 0; s0 < in.nsys; s0 += kMaxRhsU) {
+    coarse_umma_kernel<STAGES><<<grid, UTHREADS, smem, st>>>(map, (float2*)out.p, (const float2*)in.p, S.scale, p.g,
+                                                             in.nsys, s0, in.n, (const float2*)p.sub_from, err, run);
+    SMG_LAUNCH_OK();
+  }
+}
+}  // namespace
+
 // err: device int, set to 1 if a CTA gave up on a wait (host reads it).
+// ctas_per_sm: persistent CTAs per SM (1 or 2); stages: depth of the stencil
+// ring (4 or 6; 6 stages leave room for one CTA per SM only).
 void coarse_apply_umma(const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S, int* err,
-                       cudaStream_t st, const int* run) {
+                       cudaStream_t st, const int* run, int ctas_per_sm, int stages) {
   SMG_REQUIRE(coarse_umma_ok(in, p, S), "coarse_apply_umma: unsupported shape or precision");
   SMG_REQUIRE(((unsigned long long)S.p & 15ull) == 0, "coarse_apply_umma: stencil not 16-byte aligned");
+  SMG_REQUIRE((ctas_per_sm == 1 || ctas_per_sm == 2) && (stages == 4 || stages == 6) &&
+                  !(stages == 6 && ctas_per_sm == 2),
+              "coarse_apply_umma: 1 or 2 CTAs per SM, 4 or 6 stages (6 with one CTA per SM)");
   // 2D view of the stencil: K = 18N FP16 per row (innermost), rows = Vc * N
   CUtensorMap map;
   const cuuint64_t gdim[2] = {(cuuint64_t)18 * UM, (cuuint64_t)p.g.V * UM};
@@ -352,21 +402,12 @@ void coarse_apply_umma(const Vec& out, const Vec& in, const CoarseParams& p, con
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   SMG_REQUIRE(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled failed for the coarse stencil");
-  const size_t smem = sizeof(UmmaSmem) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    SMG_CUDA_OK(cudaFuncSetAttribute(coarse_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
   int dev = 0, sms = 0;
   SMG_CUDA_OK(cudaGetDevice(&dev));
   SMG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::min(p.g.V, 2 * sms);
-  for (int s0 = 0; s0 < in.nsys; s0 += kMaxRhsU) {
-    coarse_umma_kernel<<<grid, UTHREADS, smem, st>>>(map, (float2*)out.p, (const float2*)in.p, S.scale, p.g,
-                                                     in.nsys, s0, in.n, (const float2*)p.sub_from, err, run);
-    SMG_LAUNCH_OK();
-  }
+  const int grid = std::min(p.g.V, ctas_per_sm * sms);
+  if (stages == 4) launch_umma<4>(map, out, in, p, S, err, st, run, grid);
+  else launch_umma<6>(map, out, in, p, S, err, st, run, grid);
 }
 
 }  // namespace smg
