@@ -205,3 +205,27 @@ def test_multi_rhs_coarse_apply(binding, nvec, nsys):
     got = s.coarse_apply(0, v, binding.PREC_HALF)
     for k in range(nsys):
         assert rel(got[k], S.apply(v[k])) <= TOL[2], (k, rel(got[k], S.apply(v[k])))
+
+
+@pytest.mark.parametrize("hisq", [False, True])
+@pytest.mark.parametrize("k", [1, 5, 20])
+def test_setup_cgne_matches_oracle(binding, hisq, k):
+    """The near-null CGNE (Craig's method on A phi = 0, Table 1's setup solver)
+    in FP64 from the oracle's starts: k iterations on the GPU and in the
+    oracle are the same deterministic recurrence, so the block-orthonormal
+    vectors agree to rounding (1e-10; a CPU run with starts perturbed by 1e-15
+    moves them by 3e-14 at k = 20)."""
+    from oracle.coarse import near_null_vectors
+    dims, mass = (8, 8, 8, 8), 0.05
+    fat, naik, c, op = make(dims, hisq, mass, seed=1071)
+    phi = inputs.gaussian_fields(4, op.lat.V, 3, 3071)
+    lop = FineLevelOp(KahlerDirac(op))
+    raw, its = near_null_vectors(lop, phi, 1e-30, k)
+    assert its == [k] * 4
+    T = Transfer(op.lat, 3, lop.chirality(), (4, 4, 4, 4), raw)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(mass)
+    s.mg_setup(binding.default_params(nvec=[4], setup_maxiter=k, setup_tol=1e-30), [phi])
+    assert s.setup_iterations(0) == k
+    assert rel(s.null_vectors(0), T.P) <= 1e-10
