@@ -16,7 +16,11 @@
 // site that is about 4 x (11 + 13) load instructions instead of the ~290 of
 // a thread per (site, colour) reading link rows, and each link is stored once.
 // The sign flip is exact in every storage precision.
+#include <cstdio>
+#include <vector>
+
 #include "ops.cuh"
+#include "tune.cuh"
 
 namespace smg {
 namespace {
@@ -104,38 +108,50 @@ __device__ __forceinline__ void hop3(float2 (&acc)[3], const uint4 (&raw)[NCH], 
   }
 }
 
-// The hops of direction mu out of site x.  All their loads (the records of
-// x, x - mu and x - 3mu; the neighbour spinors) come first and are
-// independent of each other, so a thread has ~11 16-byte and 12 8-byte loads
-// available to be in flight together before its arithmetic.
+// The link records one (site, mu) thread needs: its own record and the
+// needed chunks of the records of x - mu and x - 3mu, with the neighbour
+// sites of the four hops.  Loaded once and reused for every system of the
+// batch the thread handles.
 template <typename SL, int K>
-__device__ __forceinline__ void hop_dir_eager(float2 (&acc)[3], const uint4* __restrict__ base,
-                                              const float2* __restrict__ vin, const Geom& g, int x, int mu,
-                                              const int (&c)[4], float cf, float cn) {
-  constexpr int RE = record_entries<SL>(K);
-  constexpr int NCH = RE * (int)sizeof(SL) / 16;
-  const int xf1 = g.shift(c, mu, 1), xb1 = g.shift(c, mu, -1);
-  int xf3 = 0, xb3 = 0;
-  if constexpr (K == 2) { xf3 = g.shift(c, mu, 3); xb3 = g.shift(c, mu, -3); }
+struct HopLinks {
+  static constexpr int RE = record_entries<SL>(K);
+  static constexpr int NCH = RE * (int)sizeof(SL) / 16;
   uint4 own[NCH], bf[NCH], bn[NCH];
+  int xf1, xb1, xf3, xb3;
+  __device__ __forceinline__ void load(const uint4* __restrict__ base, const Geom& g, int x, int mu,
+                                       const int (&c)[4]) {
+    xf1 = g.shift(c, mu, 1);
+    xb1 = g.shift(c, mu, -1);
+    xf3 = xb3 = 0;
+    if constexpr (K == 2) { xf3 = g.shift(c, mu, 3); xb3 = g.shift(c, mu, -3); }
+    load_chunks(own, base + ((size_t)x * 4 + mu) * NCH, 0, NCH);
+    load_chunks(bf, base + ((size_t)xb1 * 4 + mu) * NCH, chunk_lo<SL>(0), chunk_hi<SL>(0));
+    if constexpr (K == 2) load_chunks(bn, base + ((size_t)xb3 * 4 + mu) * NCH, chunk_lo<SL>(9), chunk_hi<SL>(9));
+  }
+};
+
+// The hops of direction mu out of site x for one system: the neighbour
+// spinor loads come first and are independent of each other (12 8-byte
+// loads with Naik links), then the arithmetic.
+template <typename SL, int K>
+__device__ __forceinline__ void hop_dir(float2 (&acc)[3], const HopLinks<SL, K>& L, const float2* __restrict__ vin,
+                                        float cf, float cn) {
+  constexpr int NCH = HopLinks<SL, K>::NCH;
   float2 pf1[3], pb1[3], pf3[3], pb3[3];
-  load_chunks(own, base + ((size_t)x * 4 + mu) * NCH, 0, NCH);
-  load_chunks(bf, base + ((size_t)xb1 * 4 + mu) * NCH, chunk_lo<SL>(0), chunk_hi<SL>(0));
-  if constexpr (K == 2) load_chunks(bn, base + ((size_t)xb3 * 4 + mu) * NCH, chunk_lo<SL>(9), chunk_hi<SL>(9));
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    pf1[b] = vin[(size_t)xf1 * 3 + b];
-    pb1[b] = vin[(size_t)xb1 * 3 + b];
+    pf1[b] = vin[(size_t)L.xf1 * 3 + b];
+    pb1[b] = vin[(size_t)L.xb1 * 3 + b];
     if constexpr (K == 2) {
-      pf3[b] = vin[(size_t)xf3 * 3 + b];
-      pb3[b] = vin[(size_t)xb3 * 3 + b];
+      pf3[b] = vin[(size_t)L.xf3 * 3 + b];
+      pb3[b] = vin[(size_t)L.xb3 * 3 + b];
     }
   }
-  hop3<SL, NCH, false>(acc, own, 0, pf1, cf);
-  hop3<SL, NCH, true>(acc, bf, 0, pb1, cf);
+  hop3<SL, NCH, false>(acc, L.own, 0, pf1, cf);
+  hop3<SL, NCH, true>(acc, L.bf, 0, pb1, cf);
   if constexpr (K == 2) {
-    hop3<SL, NCH, false>(acc, own, 9, pf3, cn);
-    hop3<SL, NCH, true>(acc, bn, 9, pb3, cn);
+    hop3<SL, NCH, false>(acc, L.own, 9, pf3, cn);
+    hop3<SL, NCH, true>(acc, L.bn, 9, pb3, cn);
   }
 }
 
@@ -150,47 +166,66 @@ __device__ __forceinline__ void sum_quad(float2 (&acc)[3]) {
     }
 }
 
-// out = m in + D in (or m in - D in with dagger; or sub_from - that)
-template <typename SL, int K>
+// out = m in + D in (or m in - D in with dagger; or sub_from - that).  Each
+// CTA serves SB systems (blockIdx.y picks the group): the link records are
+// loaded once per (site, mu) thread and applied to every system of the group.
+template <typename SL, int K, int SB>
 __global__ void __launch_bounds__(256) hop_dslash_kernel(float2* __restrict__ out, const float2* __restrict__ in,
                                                          const SL* __restrict__ H, float cf, float cn,
                                                          const double* __restrict__ mass, double mass0, int dagger,
-                                                         Geom g, const float2* __restrict__ sub_from,
+                                                         Geom g, const float2* __restrict__ sub_from, int nsys,
                                                          const int* run) {
   if (run != nullptr && *run == 0) return;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = tid < g.V * 4;
   const int x = valid ? tid >> 2 : g.V - 1, mu = tid & 3;
-  const int s = blockIdx.y;
-  const float2* vin = in + (size_t)s * g.V * 3;
   int c[4];
   g.coords(x, c);
-  float2 acc[3];
+  HopLinks<SL, K> L;
+  L.load(reinterpret_cast<const uint4*>(H), g, x, mu, c);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) acc[a] = make_float2(0.f, 0.f);
-  hop_dir_eager<SL, K>(acc, reinterpret_cast<const uint4*>(H), vin, g, x, mu, c, cf, cn);
-  sum_quad(acc);
-  if (!valid || mu == 3) return;
-  // lane mu writes colour mu
-  float2 v = mu == 0 ? acc[0] : (mu == 1 ? acc[1] : acc[2]);
-  if (dagger) v = make_float2(-v.x, -v.y);
-  const float m = (float)(mass != nullptr ? mass[s] : mass0);
-  const size_t oi = (size_t)s * g.V * 3 + (size_t)x * 3 + mu;
-  const float2 self = in[oi];
-  v.x = fmaf(m, self.x, v.x);
-  v.y = fmaf(m, self.y, v.y);
-  if (sub_from != nullptr) v = csub(sub_from[oi], v);
-  out[oi] = v;
+  for (int sb = 0; sb < SB; ++sb) {
+    const int s = blockIdx.y * SB + sb;
+    if (s >= nsys) break;                     // the same for the whole CTA
+    const float2* vin = in + (size_t)s * g.V * 3;
+    float2 acc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[a] = make_float2(0.f, 0.f);
+    hop_dir<SL, K>(acc, L, vin, cf, cn);
+    sum_quad(acc);
+    if (valid && mu != 3) {
+      // lane mu writes colour mu
+      float2 v = mu == 0 ? acc[0] : (mu == 1 ? acc[1] : acc[2]);
+      if (dagger) v = make_float2(-v.x, -v.y);
+      const float m = (float)(mass != nullptr ? mass[s] : mass0);
+      const size_t oi = (size_t)s * g.V * 3 + (size_t)x * 3 + mu;
+      const float2 self = in[oi];
+      v.x = fmaf(m, self.x, v.x);
+      v.y = fmaf(m, self.y, v.y);
+      if (sub_from != nullptr) v = csub(sub_from[oi], v);
+      out[oi] = v;
+    }
+  }
+}
+
+template <typename SL, int K, int SB>
+void launch_hop(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
+  dim3 grid(ceil_div((long long)p.g.V * 4, 256), ceil_div(p.nsys, SB));
+  const float cf = 0.5f * p.hop.gscale;
+  const float cn = (float)(0.5 * p.c_naik) * p.hop_naik_scale;
+  launch_k(hop_dslash_kernel<SL, K, SB>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p,
+           (const SL*)p.hop.p, cf, cn, p.mass, p.mass0, p.dagger, p.g, (const float2*)p.sub_from, p.nsys, run);
+  SMG_LAUNCH_OK();
 }
 
 template <typename SL, int K>
-void launch_hop(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
-  dim3 grid(ceil_div((long long)p.g.V * 4, 256), p.nsys);
-  const float cf = 0.5f * p.hop.gscale;
-  const float cn = (float)(0.5 * p.c_naik) * p.hop_naik_scale;
-  launch_k(hop_dslash_kernel<SL, K>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p, (const SL*)p.hop.p, cf, cn,
-                                                 p.mass, p.mass0, p.dagger, p.g, (const float2*)p.sub_from, run);
-  SMG_LAUNCH_OK();
+void launch_hop_sb(int sb, const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
+  switch (sb) {
+    case 1: launch_hop<SL, K, 1>(out, in, p, st, run); break;
+    case 2: launch_hop<SL, K, 2>(out, in, p, st, run); break;
+    case 4: launch_hop<SL, K, 4>(out, in, p, st, run); break;
+    default: launch_hop<SL, K, 8>(out, in, p, st, run); break;
+  }
 }
 
 template <typename SL, int K>
@@ -226,16 +261,44 @@ bool hop_dslash_ok(const Vec& in, const DslashParams& p) {
   return p.hop.p != nullptr && p.part < 0 && in.prec == P32 && (p.hop.s == S16 || p.hop.s == S32);
 }
 
-void hop_dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
+// Systems per CTA of the phase-folded dslash: 1, 2, 4 or 8 (links read once
+// per group); the autotuner times the ones that fit the batch.
+void hop_dslash_sb(int sb, const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
   SMG_REQUIRE(in.n == (long long)p.g.V * 3 && out.n == in.n, "dslash: field size does not match the lattice");
   SMG_REQUIRE(in.nsys == p.nsys && out.nsys == p.nsys && in.prec == P32 && out.prec == P32, "dslash: batch mismatch");
+  SMG_REQUIRE(sb == 1 || sb == 2 || sb == 4 || sb == 8, "dslash: 1, 2, 4 or 8 systems per CTA");
   if (p.hop.s == S16) {
-    if (p.hop_kinds == 2) launch_hop<__half2, 2>(out, in, p, st, run);
-    else launch_hop<__half2, 1>(out, in, p, st, run);
+    if (p.hop_kinds == 2) launch_hop_sb<__half2, 2>(sb, out, in, p, st, run);
+    else launch_hop_sb<__half2, 1>(sb, out, in, p, st, run);
   } else {
-    if (p.hop_kinds == 2) launch_hop<float2, 2>(out, in, p, st, run);
-    else launch_hop<float2, 1>(out, in, p, st, run);
+    if (p.hop_kinds == 2) launch_hop_sb<float2, 2>(sb, out, in, p, st, run);
+    else launch_hop_sb<float2, 1>(sb, out, in, p, st, run);
   }
+}
+
+void hop_dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
+  if (p.nsys == 1) {
+    hop_dslash_sb(1, out, in, p, st, run);
+    return;
+  }
+  std::vector<TuneCandidate> cands;
+  for (int sb : {1, 2, 4, 8})
+    if (sb == 1 || sb < 2 * p.nsys) cands.push_back({sb, sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA"
+                                                                   : sb == 4 ? "4 systems/CTA" : "8 systems/CTA"});
+  char key[160];
+  std::snprintf(key, sizeof(key), "hop_dslash V=%d nsys=%d store=%s naik=%d sub=%d", p.g.V, p.nsys,
+                p.hop.s == S16 ? "f16" : "f32", p.hop_kinds == 2 ? 1 : 0, p.sub_from != nullptr ? 1 : 0);
+  struct Scratch {
+    void* p = nullptr;
+    ~Scratch() { if (p) cudaFree(p); }
+  } scratch;
+  const int sb = tune_pick(key, cands, st, [&](int id) {
+    if (scratch.p == nullptr) SMG_CUDA_OK(cudaMalloc(&scratch.p, out.bytes()));
+    Vec o = out;
+    o.p = scratch.p;
+    hop_dslash_sb(id, o, in, p, st, nullptr);
+  });
+  hop_dslash_sb(sb, out, in, p, st, run);
 }
 
 }  // namespace smg

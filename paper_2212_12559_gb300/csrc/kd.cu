@@ -7,7 +7,12 @@
 // the fat links and inverts it in FP64 (Gauss-Jordan with partial pivoting,
 // one CTA per hypercube, the augmented 48x96 matrix in shared memory).
 // kd_apply multiplies every hypercube of a batched field by its inverse.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
 #include "ops.cuh"
+#include "tune.cuh"
 
 namespace smg {
 namespace {
@@ -139,47 +144,88 @@ struct KdSet {
   const float* scale[16];
 };
 
-// 4 hypercubes per CTA, one thread per output row.
-template <typename R, typename SL>
+// 4 hypercubes per CTA, one thread per output row; SB systems per CTA
+// (blockIdx.y picks the group, which shares one block inverse), so each block
+// entry is read once for the whole group.
+template <typename R, typename SL, int SB>
 __global__ void __launch_bounds__(192) kd_apply_kernel(typename cplx<R>::T* __restrict__ out,
                                                        const typename cplx<R>::T* __restrict__ in, KdSet kd,
                                                        const int* __restrict__ sys_map, int dagger, long long nblk,
                                                        Geom g, const typename cplx<R>::T* __restrict__ sub_from,
-                                                       const int* run) {
+                                                       int nsys, const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
-  __shared__ C vin[4][NB];
-  const int s = blockIdx.y;
+  __shared__ C vin[SB][4][NB];
+  const int s0 = blockIdx.y * SB;
+  const int ns = min(SB, nsys - s0);
   const int lb = threadIdx.x / NB, r = threadIdx.x % NB;
   const long long blk = (long long)blockIdx.x * 4 + lb;
-  const long long off = (long long)s * g.V * 3;
-  const int kidx = sys_map != nullptr ? sys_map[s] : 0;
+  const long long vs = (long long)g.V * 3;
+  const int kidx = sys_map != nullptr ? sys_map[s0] : 0;
   const SL* K = (const SL*)kd.p[kidx];
   const float* sc = kd.scale[kidx];
   int site = 0;
   if (blk < nblk) {
     site = hypercube_site(g, (int)blk, r / 3);
-    vin[lb][r] = in[off + (size_t)site * 3 + (r % 3)];
+#pragma unroll
+    for (int sb = 0; sb < SB; ++sb)
+      if (sb < ns) vin[sb][lb][r] = in[(s0 + sb) * vs + (size_t)site * 3 + (r % 3)];
   }
   __syncthreads();
   if (blk >= nblk) return;
   const SL* Kb = K + (size_t)blk * NB * NB;
-  C acc = C{0, 0};
+  C acc[SB];
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb) acc[sb] = C{0, 0};
   if (!dagger) {
 #pragma unroll 8
-    for (int c = 0; c < NB; ++c) cfma(acc, ld<R>(Kb, (size_t)c * NB + r), vin[lb][c]);
-    if (sc != nullptr) acc = cscale(acc, (R)sc[blk * NB + r]);
+    for (int c = 0; c < NB; ++c) {
+      const C k = ld<R>(Kb, (size_t)c * NB + r);
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) cfma(acc[sb], k, vin[sb][lb][c]);
+    }
+    if (sc != nullptr) {
+      const R f = (R)sc[blk * NB + r];
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) acc[sb] = cscale(acc[sb], f);
+    }
   } else {
 #pragma unroll 8
     for (int c = 0; c < NB; ++c) {
       C k = ld<R>(Kb, (size_t)r * NB + c);
       if (sc != nullptr) k = cscale(k, (R)sc[blk * NB + c]);
-      cfmac(acc, k, vin[lb][c]);
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) cfmac(acc[sb], k, vin[sb][lb][c]);
     }
   }
-  const size_t oi = off + (size_t)site * 3 + (r % 3);
-  if (sub_from != nullptr) acc = csub(sub_from[oi], acc);
-  out[oi] = acc;
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb) {
+    if (sb >= ns) break;
+    const size_t oi = (s0 + sb) * vs + (size_t)site * 3 + (r % 3);
+    C v = acc[sb];
+    if (sub_from != nullptr) v = csub(sub_from[oi], v);
+    out[oi] = v;
+  }
+}
+
+template <typename R, typename SL, int SB>
+void launch_kd(const Vec& out, const Vec& in, const KdSet& set, const int* sys_map, int dagger, long long nblk,
+               const Geom& g, const void* sub_from, cudaStream_t st, const int* run) {
+  using C = typename cplx<R>::T;
+  dim3 grid(ceil_div(nblk, 4), ceil_div(in.nsys, SB));
+  launch_k(kd_apply_kernel<R, SL, SB>, grid, dim3(192), 0, st, (C*)out.p, (const C*)in.p, set, sys_map, dagger, nblk,
+           g, (const C*)sub_from, in.nsys, run);
+}
+
+template <typename R, typename SL>
+void launch_kd_sb(int sb, const Vec& out, const Vec& in, const KdSet& set, const int* sys_map, int dagger,
+                  long long nblk, const Geom& g, const void* sub_from, cudaStream_t st, const int* run) {
+  switch (sb) {
+    case 1: launch_kd<R, SL, 1>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+    case 2: launch_kd<R, SL, 2>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+    case 4: launch_kd<R, SL, 4>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+    default: launch_kd<R, SL, 8>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+  }
 }
 
 }  // namespace
@@ -204,7 +250,7 @@ void kd_pack(Stored& dst, const double2* inv64, long long nblk, cudaStream_t st)
 }
 
 void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, const int* sys_map, int nkd,
-              int dagger, cudaStream_t st, const int* run, const void* sub_from) {
+              int dagger, cudaStream_t st, const int* run, const void* sub_from, int kd_run) {
   SMG_REQUIRE(in.n == (long long)g.V * 3 && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
               "kd_apply: shape mismatch");
   SMG_REQUIRE(nkd >= 1 && nkd <= 16, "kd_apply: 1..16 block inverses");
@@ -215,21 +261,45 @@ void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, co
     set.scale[i] = kd[i].s == S16 ? kd[i].scale : nullptr;
   }
   const long long nblk = g.V / 16;
-  dim3 grid(ceil_div(nblk, 4), in.nsys);
-  if (in.prec == P64) {
-    SMG_REQUIRE(kd[0].s == S64, "kd_apply: FP64 vectors need FP64 blocks");
-    launch_k(kd_apply_kernel<double, double2>, dim3(grid), dim3(192), 0, st, (double2*)out.p, (const double2*)in.p, set, sys_map,
-                                                           dagger, nblk, g, (const double2*)sub_from, run);
-  } else if (kd[0].s == S32) {
-    launch_k(kd_apply_kernel<float, float2>, dim3(grid), dim3(192), 0, st, (float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
-                                                         nblk, g, (const float2*)sub_from, run);
-  } else if (kd[0].s == S16) {
-    launch_k(kd_apply_kernel<float, __half2>, dim3(grid), dim3(192), 0, st, (float2*)out.p, (const float2*)in.p, set, sys_map, dagger,
-                                                          nblk, g, (const float2*)sub_from, run);
-  } else {
-    SMG_REQUIRE(false, "kd_apply: unsupported precision pair");
+  // consecutive systems that share one block inverse: all of them with one
+  // inverse, else kd_run (systems per mass), which a group may not straddle
+  const int run_len = (sys_map == nullptr) ? in.nsys : std::max(1, kd_run);
+  auto go = [&](int sb, const Vec& o, const int* rr) {
+    if (in.prec == P64) {
+      SMG_REQUIRE(kd[0].s == S64, "kd_apply: FP64 vectors need FP64 blocks");
+      launch_kd_sb<double, double2>(sb, o, in, set, sys_map, dagger, nblk, g, sub_from, st, rr);
+    } else if (kd[0].s == S32) {
+      launch_kd_sb<float, float2>(sb, o, in, set, sys_map, dagger, nblk, g, sub_from, st, rr);
+    } else if (kd[0].s == S16) {
+      launch_kd_sb<float, __half2>(sb, o, in, set, sys_map, dagger, nblk, g, sub_from, st, rr);
+    } else {
+      SMG_REQUIRE(false, "kd_apply: unsupported precision pair");
+    }
+    SMG_LAUNCH_OK();
+  };
+  std::vector<TuneCandidate> cands;
+  for (int sb : {1, 2, 4, 8})
+    if (sb == 1 || (sb < 2 * in.nsys && run_len % sb == 0))
+      cands.push_back({sb, sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA" : sb == 4 ? "4 systems/CTA"
+                                                                                      : "8 systems/CTA"});
+  int sb = 1;
+  if (cands.size() > 1) {
+    char key[160];
+    std::snprintf(key, sizeof(key), "kd_apply V=%d nsys=%d run=%d vec=%s store=%s dag=%d sub=%d", g.V, in.nsys,
+                  run_len, in.prec == P64 ? "f64" : "f32", kd[0].s == S16 ? "f16" : (kd[0].s == S32 ? "f32" : "f64"),
+                  dagger, sub_from != nullptr ? 1 : 0);
+    struct Scratch {
+      void* p = nullptr;
+      ~Scratch() { if (p) cudaFree(p); }
+    } scratch;
+    sb = tune_pick(key, cands, st, [&](int id) {
+      if (scratch.p == nullptr) SMG_CUDA_OK(cudaMalloc(&scratch.p, out.bytes()));
+      Vec o = out;
+      o.p = scratch.p;
+      go(id, o, nullptr);
+    });
   }
-  SMG_LAUNCH_OK();
+  go(sb, out, run);
 }
 
 }  // namespace smg

@@ -69,9 +69,12 @@ void kd_build(double2* inv64, const Geom& g, const double2* fat64, double mass, 
 // block, [nblk][48 col][48 row]) in storage `dst.s` (per-(block,row) scale for FP16).
 void kd_pack(Stored& dst, const double2* inv64, long long nblk, cudaStream_t st);
 // out[s] = K[sys_map[s]] in[s] (or K^dag).  kd[] holds one packed inverse per mass.
-// With sub_from: out = sub_from - K in (residual form).
+// With sub_from: out = sub_from - K in (residual form).  kd_run: with a
+// sys_map, the number of consecutive systems that share one inverse (systems
+// per mass), so that several systems per CTA can read each block once.
 void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, const int* sys_map, int nkd,
-              int dagger, cudaStream_t st, const int* run = nullptr, const void* sub_from = nullptr);
+              int dagger, cudaStream_t st, const int* run = nullptr, const void* sub_from = nullptr,
+              int kd_run = 1);
 
 // ------------------------------------------------------- transfer operators
 // A level's lattice with `ndof` components per site; aggregates of agg[]

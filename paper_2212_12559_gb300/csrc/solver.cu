@@ -270,7 +270,10 @@ struct Engine {
   bool graph_tried = false;
   long long graph_nodes = 0;
 
-  Engine(Context& ctx, int ns, const std::vector<double>& ms, int nrhs) : c(ctx), nsys(ns), masses(ms) {
+  int nrhs_ = 1;                    // systems per mass (consecutive)
+
+  Engine(Context& ctx, int ns, const std::vector<double>& ms, int nrhs)
+      : c(ctx), nsys(ns), masses(ms), nrhs_(nrhs) {
     const auto& P = c.params;
     nlev = P.n_coarse;
     vp = c.vprec();
@@ -457,7 +460,7 @@ struct Engine {
     dslash(out, in, p, st(), run);
   }
   void Binv(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
-    kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run, sub ? sub->p : nullptr);
+    kd_apply(out, in, c.g, kd_s.data(), sys_map, nkd, 0, st(), run, sub ? sub->p : nullptr, nrhs_);
   }
   // A_1 = (B+m)^{-1} M_1; M_1 = M, or m + D_fat for the truncated operator
   void As(const Vec& out, const Vec& in, const int* run, const Vec* sub = nullptr) {
