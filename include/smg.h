@@ -69,8 +69,9 @@ typedef struct smg_mg_params {
   int nvec[SMG_MAX_COARSE];        /* near-null vectors per coarsening; coarse dof = 2*nvec */
   double setup_tol;                /* CGNE relative residual for near-null vectors: 1e-6 */
   int setup_maxiter;               /* CGNE iteration cap: 2000 (0 = use phi0 as given) */
-  double inner_tol;                /* inner GCR tolerance on levels >= 1: 0.25 */
-  int inner_maxiter;               /* inner GCR iteration cap: 8 */
+  double inner_tol;                /* inner GCR tolerance on levels >= 1: 0.25 (levels >= 2: see
+                                      coarse_inner_tol) */
+  int inner_maxiter;               /* inner GCR iteration cap: 8 (at most 16) */
   int smoother_s;                  /* CA-GCR(s) post-smoother length: 8 */
   int dense_max;                   /* coarsest level solved exactly when its dof <= dense_max */
   int nkrylov;                     /* outer GCR restart length: 16 */
@@ -121,6 +122,11 @@ typedef struct smg_mg_params {
                                       centre, well conditioned when the spectrum fills a disk
                                       rather than lying near the real interval (both span the same
                                       Krylov space) */
+  double coarse_inner_tol;         /* inner GCR tolerance of levels >= 2 (the Galerkin levels and
+                                      the coarsest level's iterative solve); 0 = inner_tol.  Table 1
+                                      gives every level 0.25; a tighter level-1 rule with Table 1's
+                                      rule below it cuts the coarse work at light masses */
+  int coarse_inner_maxiter;        /* iteration cap of those levels, 1..16; 0 = inner_maxiter */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */

@@ -99,6 +99,16 @@ class MGParams:
     coarsest_basis: str = "chebyshev"   # or "shifted": the power basis of the disk around the interval's centre
     coarsest_schur: bool = False  # with coarsest_deflate: deflated CA-GCR on the even/odd Schur complement
     schur_coarse: bool = False    # intermediate coarse levels: GCR and smoother on the Schur complement
+    coarse_inner_tol: float = 0.0     # levels >= 2: their own inner tolerance (0: inner_tol)
+    coarse_inner_maxiter: int = 0     # levels >= 2: their own iteration cap (0: inner_maxiter)
+
+    def tol_of(self, l: int) -> float:
+        """Inner GCR tolerance of level l >= 1."""
+        return self.coarse_inner_tol if (l >= 2 and self.coarse_inner_tol > 0) else self.inner_tol
+
+    def maxiter_of(self, l: int) -> int:
+        """Inner GCR iteration cap of level l >= 1."""
+        return self.coarse_inner_maxiter if (l >= 2 and self.coarse_inner_maxiter > 0) else self.inner_maxiter
 
 
 class MultigridSolver:
@@ -168,19 +178,19 @@ class MultigridSolver:
                 if self.schur is not None:
                     return self.schur.solve(rc, lambda apply, rhs: self.deflated_coarsest_op(apply, rhs))
                 return self.deflated_coarsest(lop, rc)
-            x, _, _ = gcr(lop.apply, rc, tol=self.p.inner_tol, maxiter=self.p.inner_maxiter,
-                          nkrylov=self.p.inner_maxiter, true_residual=False)
+            x, _, _ = gcr(lop.apply, rc, tol=self.p.tol_of(l), maxiter=self.p.maxiter_of(l),
+                          nkrylov=self.p.maxiter_of(l), true_residual=False)
             return x
         if self.p.schur_coarse:
             sc = SchurCoarse(lop)
             rhs, c = sc.schur_rhs(rc)
             xe, _, _ = gcr(sc.schur_apply, rhs, precond=lambda r: self.kcycle_schur(l, sc, r),
-                           tol=self.p.inner_tol, maxiter=self.p.inner_maxiter,
-                           nkrylov=self.p.inner_maxiter, true_residual=False)
+                           tol=self.p.tol_of(l), maxiter=self.p.maxiter_of(l),
+                           nkrylov=self.p.maxiter_of(l), true_residual=False)
             return sc.reconstruct(xe, c)
         x, _, _ = gcr(lop.apply, rc, precond=lambda r: self.kcycle(l, r),
-                      tol=self.p.inner_tol, maxiter=self.p.inner_maxiter,
-                      nkrylov=self.p.inner_maxiter, true_residual=False)
+                      tol=self.p.tol_of(l), maxiter=self.p.maxiter_of(l),
+                      nkrylov=self.p.maxiter_of(l), true_residual=False)
         return x
 
     def deflated_coarsest(self, lop, rc):
@@ -192,8 +202,9 @@ class MultigridSolver:
         U, sig, V, lmin, lmax = self.defl
         x = (V @ ((U.conj().T @ rc.ravel()) / sig)).reshape(rc.shape)
         r = rc - apply(x)
-        target = self.p.inner_tol * norm(rc)
-        for _ in range(self.p.inner_maxiter):
+        lc = len(self.levels)              # the coarsest level's number (levels[0] is level 1)
+        target = self.p.tol_of(lc) * norm(rc)
+        for _ in range(self.p.maxiter_of(lc)):
             if norm(r) <= target:
                 break
             x = x + ca_gcr_basis(apply, r, self.p.coarsest_cheb_s, lmin, lmax, self.p.coarsest_basis)

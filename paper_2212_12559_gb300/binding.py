@@ -57,6 +57,8 @@ class MGParams(ctypes.Structure):
         ("coarsest_schur", ctypes.c_int),
         ("schur_coarse", ctypes.c_int),
         ("coarsest_basis", ctypes.c_int),
+        ("coarse_inner_tol", ctypes.c_double),
+        ("coarse_inner_maxiter", ctypes.c_int),
     ]
 
 

@@ -98,6 +98,8 @@ void smg_default_params(smg_mg_params* p) {
   p->coarsest_schur = 0;
   p->schur_coarse = 0;
   p->coarsest_basis = 0;
+  p->coarse_inner_tol = 0.0;
+  p->coarse_inner_maxiter = 0;
 }
 
 int smg_create(const int dims[4], smg_ctx** out) {

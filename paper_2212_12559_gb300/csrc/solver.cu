@@ -327,7 +327,7 @@ struct Engine {
       const CoarseLevel& C = c.coarse[l - 2];
       const long long n = (long long)C.g.V * C.N;
       const bool coarsest = (l == nlev + 1);
-      lev[l].alloc(n, ns, vp, (coarsest && C.dense) ? 0 : P.inner_maxiter);
+      lev[l].alloc(n, ns, vp, (coarsest && C.dense) ? 0 : c.inner_maxiter_of(l));
       if (!coarsest) sm_c[l].alloc(n, ns, vp, P.smoother_s);
       tmp_c[l] = mkv((char*)cbuf.p + off, n, vp);
       off += (size_t)n * ns * prec_bytes(vp);
@@ -407,7 +407,7 @@ struct Engine {
       if (P.persistent && vp == P32 && l >= 2 && !deflated_target && !schur_lvl(l)) {
         const CoarseLevel& C = c.coarse[l - 2];
         const int nvec_next = l <= nlev ? c.coarse[l - 1].tg.nvec : 0;
-        persistent = persist_supported(ns, P.inner_maxiter, P.smoother_s, C.N, (long long)C.g.V * C.N, sp);
+        persistent = persist_supported(ns, c.inner_maxiter_of(l), P.smoother_s, C.N, (long long)C.g.V * C.N, sp);
         if (persistent) {
           pplan = persist_plan(C.g, C.N, ns, nvec_next, sp);
           pbuf.alloc(persist_buffer_bytes(pplan, nvec_next));
@@ -606,7 +606,7 @@ struct Engine {
     }
     a.s = c.params.smoother_s;
     a.K = G.K;
-    a.tol2 = c.params.inner_tol * c.params.inner_tol;
+    a.tol2 = c.inner_tol_of(l) * c.inner_tol_of(l);
     a.nsys = nsys;
     a.b = (float2*)G.b.p; a.x = (float2*)G.x.p; a.r = (float2*)G.r.p;
     for (int k = 0; k < G.K; ++k) { a.z[k] = (float2*)G.z[k].p; a.w[k] = (float2*)G.w[k].p; }
@@ -681,8 +681,9 @@ struct Engine {
     block_combine(x, Vb, cw.yd, nsys, st(), run);
     const int p0[1] = {0};
     blas_pair_dots(&b, 1, p0, p0, 1, cw.bb, 1, ws, st(), run);
-    const double tol2 = c.params.inner_tol * c.params.inner_tol;
-    for (int it = 0; it < c.params.inner_maxiter; ++it) {
+    const int lv = nlev + 1;    // the coarsest level
+    const double tol2 = c.inner_tol_of(lv) * c.inner_tol_of(lv);
+    for (int it = 0; it < c.inner_maxiter_of(lv); ++it) {
       const int* rn = it == 0 ? run : cw.drun;
       A(r, x, rn, &b);                                   // r = b - A x
       blas_pair_dots(&r, 1, p0, p0, 1, cw.rr, 1, ws, st(), rn);
@@ -765,7 +766,7 @@ struct Engine {
     auto A = [&](const Vec& o, const Vec& i, const int* r) { op(l, o, i, r); };
     if (coarsest) {
       auto pre = [&](const Vec& z, const Vec& r, const int* rr) { blas_copy(z, r, st(), rr); };
-      gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
+      gcr(G, A, pre, c.inner_tol_of(l), nullptr, run, false, false);
     } else if (C.schur_level) {
       // c_e - K_eo c_o = (c + R(c_o))_e, GCR on S, x_o = (c + R(x_e))_o
       const std::vector<Vec>& T = sch[l];
@@ -779,7 +780,7 @@ struct Engine {
       blas_maxpy(T[0], in2, 2, c.ones, 2, 1.0, false, st(), run);
       parity_pick(G.b, &T[0], nullptr, C.g, C.N, st(), run);
       auto pre = [&](const Vec& z, const Vec& r, const int* rr) { kcycle(l, z, r, rr); };
-      gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
+      gcr(G, A, pre, c.inner_tol_of(l), nullptr, run, false, false);
       cr.sub_from = G.x.p;
       coarse_apply(T[1], G.x, cr, C.Ss.st, st(), run);
       Vec in2b[2] = {T[3], T[1]};
@@ -787,7 +788,7 @@ struct Engine {
       parity_pick(G.x, &G.x, &T[0], C.g, C.N, st(), run);
     } else {
       auto pre = [&](const Vec& z, const Vec& r, const int* rr) { kcycle(l, z, r, rr); };
-      gcr(G, A, pre, c.params.inner_tol, nullptr, run, false, false);
+      gcr(G, A, pre, c.inner_tol_of(l), nullptr, run, false, false);
     }
   }
 
@@ -826,7 +827,7 @@ struct Engine {
     dbg("K0.b1", G.b);
     auto A = [&](const Vec& o, const Vec& i, const int* rr) { As(o, i, rr); };
     auto pre = [&](const Vec& zz, const Vec& rr, const int* run) { kcycle(1, zz, rr, run); };
-    gcr(G, A, pre, c.params.inner_tol, nullptr, nullptr, false, false);
+    gcr(G, A, pre, c.inner_tol_of(1), nullptr, nullptr, false, false);
     dbg("K0.x1", G.x);
     pb("K0.smoother(M)");
     Ms(sm_f.V[0], G.x, nullptr, &r_s);   // V0 = r - M e
@@ -1095,6 +1096,8 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
   SMG_REQUIRE(c.gauge_set && c.mass_set, "mg_setup needs set_gauge and set_mass first");
   SMG_REQUIRE(P.n_coarse >= 1 && P.n_coarse <= SMG_MAX_COARSE, "n_coarse must be 1..3");
   SMG_REQUIRE(P.inner_maxiter >= 1 && P.inner_maxiter <= 16, "inner_maxiter must be 1..16");
+  SMG_REQUIRE(P.coarse_inner_maxiter >= 0 && P.coarse_inner_maxiter <= 16, "coarse_inner_maxiter must be 0..16");
+  SMG_REQUIRE(P.coarse_inner_tol >= 0.0 && P.coarse_inner_tol < 1.0, "coarse_inner_tol must be in [0, 1)");
   SMG_REQUIRE(P.nkrylov >= 1 && P.nkrylov <= 16, "nkrylov must be 1..16");
   SMG_REQUIRE(P.smoother_s >= 1 && P.smoother_s <= 10, "smoother_s must be 1..10");
   SMG_REQUIRE(P.precision >= SMG_PREC_DOUBLE && P.precision <= SMG_PREC_HALF, "bad precision");

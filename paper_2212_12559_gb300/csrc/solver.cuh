@@ -142,6 +142,13 @@ struct Context {
   ~Context();
 
   Prec vprec() const { return params.precision == SMG_PREC_DOUBLE ? P64 : P32; }
+  // inner GCR rule of level l >= 1 (levels >= 2 may have their own)
+  double inner_tol_of(int l) const {
+    return (l >= 2 && params.coarse_inner_tol > 0.0) ? params.coarse_inner_tol : params.inner_tol;
+  }
+  int inner_maxiter_of(int l) const {
+    return (l >= 2 && params.coarse_inner_maxiter > 0) ? params.coarse_inner_maxiter : params.inner_maxiter;
+  }
   Store sstore() const {
     return params.precision == SMG_PREC_DOUBLE ? S64 : (params.precision == SMG_PREC_SINGLE ? S32 : S16);
   }

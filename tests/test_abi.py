@@ -49,6 +49,7 @@ def test_params_struct_layout(libpath):
     assert p.persistent == 1 and p.truncate_naik == 0 and p.block_coarse == 0
     assert p.coarsest_deflate == 0 and p.coarsest_cheb_s == 8 and p.coarsest_schur == 0
     assert p.schur_coarse == 0 and p.coarsest_basis == 0
+    assert p.coarse_inner_tol == 0.0 and p.coarse_inner_maxiter == 0
 
 
 def test_create_rejects_bad_extents(libpath):
@@ -81,8 +82,8 @@ int main(void) {
   long long plan[10];
   smg_default_params(&p);
   if (smg_persist_plan(256, 48, 1, 32, SMG_PREC_HALF, 152, 232448, plan) != SMG_OK) return 2;
-  printf("%d %d %d %d %d %d %lld %lld %lld\n", p.n_coarse, p.nvec[0], p.inner_maxiter, p.coarsest_cheb_s,
-         p.block_coarse, p.coarsest_basis, plan[0], plan[1], plan[2]);
+  printf("%d %d %d %d %d %d %lld %lld %lld %d\n", p.n_coarse, p.nvec[0], p.inner_maxiter, p.coarsest_cheb_s,
+         p.block_coarse, p.coarsest_basis, plan[0], plan[1], plan[2], (int)sizeof(smg_mg_params));
   return 0;
 }
 """
@@ -112,7 +113,7 @@ def test_plain_c_client(libpath, tmp_path):
     p = binding.default_params()
     q = binding.persist_plan(256, 48, 1, 32, binding.PREC_HALF, 152, 232448)
     want = [p.n_coarse, p.nvec[0], p.inner_maxiter, p.coarsest_cheb_s, p.block_coarse, p.coarsest_basis,
-            q["grid"], q["per"], q["nslot"]]
+            q["grid"], q["per"], q["nslot"], ctypes.sizeof(binding.MGParams)]
     assert [int(v) for v in r.stdout.split()] == want
 
 
