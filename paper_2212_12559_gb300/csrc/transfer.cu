@@ -10,7 +10,11 @@
 // P[x][d][k] if chi(x,d) == s and zero otherwise.  With k fastest the
 // restriction's threads (one per k) read consecutive entries and each
 // prolongation thread (one per (x, d)) reads one contiguous run.
+#include <cstdio>
+#include <vector>
+
 #include "ops.cuh"
+#include "tune.cuh"
 
 namespace smg {
 namespace {
@@ -199,12 +203,15 @@ __global__ void __launch_bounds__(256) restrict_kernel(typename cplx<R>::T* __re
 // 16 bytes): thread t owns the chunk of vectors kc = t % (nvec / VPC) and
 // every (t / (nvec / VPC))-th row of the aggregate, so a CTA of 512 threads
 // keeps ~10 independent loads per thread in flight; the row groups are then
-// added in two fixed-order passes.
-template <typename R, typename SL>
+// added in two fixed-order passes.  A CTA serves SB systems (blockIdx.y picks
+// the group): each prolongator chunk is loaded once and applied to all of
+// them, and the partial sums of the systems are added one system after the
+// other in the same shared-memory area.
+template <typename R, typename SL, int SB>
 __global__ void __launch_bounds__(512) restrict_vec_kernel(typename cplx<R>::T* __restrict__ out,
                                                            const typename cplx<R>::T* __restrict__ in,
                                                            const SL* __restrict__ P, R pscale, TransferGeom t,
-                                                           const int* run) {
+                                                           int nsys, const int* run) {
   using C = typename cplx<R>::T;
   constexpr int VPC = 16 / (int)sizeof(SL);
   constexpr int kRed = 8;                                     // first-pass partial sums per output
@@ -216,83 +223,110 @@ __global__ void __launch_bounds__(512) restrict_vec_kernel(typename cplx<R>::T* 
   const int nd = t.ndof, half = nd / 2;
   C* part = reinterpret_cast<C*>(rs_smem);                    // [groups][2][nv]
   C* red = part + (size_t)groups * 2 * nv;                    // [kRed][2][nv]
-  C* vx = red + (size_t)kRed * 2 * nv;                        // [npos][nd]
-  int* xs = reinterpret_cast<int*>(vx + (size_t)npos * nd);   // site of each position
-  int* xpar = xs + npos;                                      // its parity
-  const int X = blockIdx.x, s = blockIdx.y;
+  C* vx = red + (size_t)kRed * 2 * nv;                        // [SB][npos][nd]
+  int* xs = reinterpret_cast<int*>(vx + (size_t)SB * npos * nd);   // site of each position
+  int* xpar = xs + npos;                                          // its parity
+  const int X = blockIdx.x, s0 = blockIdx.y * SB;
+  const int ns = min(SB, nsys - s0);
   const long long nf = (long long)t.fine.V * nd;
-  const C* vin = in + (size_t)s * nf;
   for (int p = threadIdx.x; p < npos; p += blockDim.x) {
     const int x = agg_site(t, X, p);
     xs[p] = x;
     xpar[p] = site_parity(t.fine, x);
   }
   __syncthreads();
-  for (int rr = threadIdx.x; rr < npos * nd; rr += blockDim.x) {
+  for (int e = threadIdx.x; e < ns * npos * nd; e += blockDim.x) {
+    const int sb = e / (npos * nd), rr = e - sb * (npos * nd);
     const int p = rr / nd, d = rr - p * nd;
-    vx[rr] = vin[(size_t)xs[p] * nd + d];
+    vx[e] = in[(size_t)(s0 + sb) * nf + (size_t)xs[p] * nd + d];
   }
   __syncthreads();
   const int kc = threadIdx.x % nch, g = threadIdx.x / nch;
-  if (g < groups) {
-    C acc0[VPC], acc1[VPC];
+  C acc0[SB][VPC], acc1[SB][VPC];
 #pragma unroll
-    for (int u = 0; u < VPC; ++u) { acc0[u] = C{0, 0}; acc1[u] = C{0, 0}; }
-#pragma unroll 4
+  for (int sb = 0; sb < SB; ++sb)
+#pragma unroll
+    for (int u = 0; u < VPC; ++u) { acc0[sb][u] = C{0, 0}; acc1[sb][u] = C{0, 0}; }
+  if (g < groups) {
+#pragma unroll 2
     for (int rr = g; rr < npos * nd; rr += groups) {
       const int p = rr / nd, d = rr - p * nd;
       const int chi = t.chi_mode == 0 ? xpar[p] : (d >= half ? 1 : 0);
       const uint4 raw = __ldg(reinterpret_cast<const uint4*>(P + ((size_t)xs[p] * nd + d) * nv) + kc);
       const SL* pe = reinterpret_cast<const SL*>(&raw);
-      const C v = vx[rr];
 #pragma unroll
-      for (int u = 0; u < VPC; ++u) {
-        const C pv = ld<R>(pe, u);
-        if (chi == 0) cfmac(acc0[u], pv, v);
-        else cfmac(acc1[u], pv, v);
+      for (int sb = 0; sb < SB; ++sb) {
+        if (sb >= ns) break;
+        const C v = vx[(size_t)sb * npos * nd + rr];
+#pragma unroll
+        for (int u = 0; u < VPC; ++u) {
+          const C pv = ld<R>(pe, u);
+          if (chi == 0) cfmac(acc0[sb][u], pv, v);
+          else cfmac(acc1[sb][u], pv, v);
+        }
       }
     }
-#pragma unroll
-    for (int u = 0; u < VPC; ++u) {
-      part[((size_t)g * 2 + 0) * nv + kc * VPC + u] = acc0[u];
-      part[((size_t)g * 2 + 1) * nv + kc * VPC + u] = acc1[u];
-    }
   }
-  __syncthreads();
   const int N = 2 * nv;
-  for (int e = threadIdx.x; e < kRed * N; e += blockDim.x) {
-    const int j = e / N, i = e - j * N;
-    C sum = C{0, 0};
-    for (int gg = j; gg < groups; gg += kRed) sum = cadd(sum, part[(size_t)gg * N + i]);
-    red[(size_t)j * N + i] = sum;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    C sum = C{0, 0};
-    for (int j = 0; j < kRed; ++j) sum = cadd(sum, red[(size_t)j * N + i]);
-    out[(size_t)s * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb) {
+    if (sb >= ns) break;
+    if (g < groups) {
+#pragma unroll
+      for (int u = 0; u < VPC; ++u) {
+        part[((size_t)g * 2 + 0) * nv + kc * VPC + u] = acc0[sb][u];
+        part[((size_t)g * 2 + 1) * nv + kc * VPC + u] = acc1[sb][u];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kRed * N; e += blockDim.x) {
+      const int j = e / N, i = e - j * N;
+      C sum = C{0, 0};
+      for (int gg = j; gg < groups; gg += kRed) sum = cadd(sum, part[(size_t)gg * N + i]);
+      red[(size_t)j * N + i] = sum;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      C sum = C{0, 0};
+      for (int j = 0; j < kRed; ++j) sum = cadd(sum, red[(size_t)j * N + i]);
+      out[(size_t)(s0 + sb) * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
+    }
+    __syncthreads();
   }
 }
 
-template <typename R, typename SL>
+// e(x, d) = sum_k P_k(x, d) ec(X(x), chi(x, d), k) for SB systems per thread
+// (blockIdx.y picks the group): the prolongator row is read once for all.
+template <typename R, typename SL, int SB>
 __global__ void prolong_kernel(typename cplx<R>::T* __restrict__ out, const typename cplx<R>::T* __restrict__ in,
-                               const SL* __restrict__ P, R pscale, TransferGeom t, const int* run) {
+                               const SL* __restrict__ P, R pscale, TransferGeom t, int nsys, const int* run) {
   using C = typename cplx<R>::T;
   if (run != nullptr && *run == 0) return;
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nf = (long long)t.fine.V * t.ndof;
   if (e >= nf) return;
-  const int s = blockIdx.y;
+  const int s0 = blockIdx.y * SB;
+  const int ns = min(SB, nsys - s0);
   const int x = (int)(e / t.ndof), d = (int)(e % t.ndof);
   const int X = coarse_of(t, x);
   const int chi = chirality(t, x, d);
   const int N = 2 * t.nvec;
-  const C* vc = in + (size_t)s * t.coarse.V * N + (size_t)X * N + chi * t.nvec;
+  const size_t cstride = (size_t)t.coarse.V * N;
+  const C* vc = in + (size_t)s0 * cstride + (size_t)X * N + chi * t.nvec;
   const SL* Px = P + (size_t)e * t.nvec;
-  C acc = C{0, 0};
+  C acc[SB];
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb) acc[sb] = C{0, 0};
 #pragma unroll 4
-  for (int k = 0; k < t.nvec; ++k) cfma(acc, ld<R>(Px, k), vc[k]);
-  out[(size_t)s * nf + e] = cscale(acc, pscale);
+  for (int k = 0; k < t.nvec; ++k) {
+    const C pk = ld<R>(Px, k);
+#pragma unroll
+    for (int sb = 0; sb < SB; ++sb)
+      if (sb < ns) cfma(acc[sb], pk, vc[sb * cstride + k]);
+  }
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb)
+    if (sb < ns) out[(size_t)(s0 + sb) * nf + e] = cscale(acc[sb], pscale);
 }
 
 // Raise a kernel's dynamic shared-memory limit once (not a stream operation,
@@ -330,41 +364,137 @@ void transfer_pack(Stored& dst, const double2* raw, const TransferGeom& t, cudaS
   SMG_LAUNCH_OK();
 }
 
+namespace {
+// the restrict kernels for SB systems per CTA; false when the shared memory
+// of the vectorised kernel does not fit (the caller then takes the plain one)
+template <int SB>
+bool launch_restrict_vec(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                         const int* run) {
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  const size_t cb = prec_bytes(in.prec);
+  const int vpc = (int)(16 / store_bytes(P.s));
+  if (t.nvec % vpc != 0) return false;
+  const int groups = 512 / (t.nvec / vpc);
+  const size_t smem = cb * ((size_t)groups * 2 * t.nvec + 8 * 2 * t.nvec + (size_t)SB * npos * t.ndof) +
+                      sizeof(int) * 2 * npos;
+  if (smem > 200 * 1024) return false;
+  dim3 grid(t.coarse.V, ceil_div(in.nsys, SB));
+  if (in.prec == P64) {
+    SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
+    auto k = restrict_vec_kernel<double, double2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(512), smem, st, (double2*)out.p, (const double2*)in.p, (const double2*)P.p,
+             (double)P.gscale, t, in.nsys, run);
+  } else if (P.s == S32) {
+    auto k = restrict_vec_kernel<float, float2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(512), smem, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t,
+             in.nsys, run);
+  } else {
+    SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
+    auto k = restrict_vec_kernel<float, __half2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(512), smem, st, (float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t,
+             in.nsys, run);
+  }
+  SMG_LAUNCH_OK();
+  return true;
+}
+
+bool restrict_vec_sb(int sb, const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                     const int* run) {
+  switch (sb) {
+    case 1: return launch_restrict_vec<1>(out, in, t, P, st, run);
+    case 2: return launch_restrict_vec<2>(out, in, t, P, st, run);
+    case 4: return launch_restrict_vec<4>(out, in, t, P, st, run);
+    default: return launch_restrict_vec<8>(out, in, t, P, st, run);
+  }
+}
+
+template <int SB>
+void launch_prolong(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                    const int* run) {
+  dim3 grid(ceil_div(out.n, 256), ceil_div(in.nsys, SB));
+  if (in.prec == P64) {
+    SMG_REQUIRE(P.s == S64, "prolong: FP64 vectors need FP64 prolongator");
+    launch_k(prolong_kernel<double, double2, SB>, grid, dim3(256), 0, st, (double2*)out.p, (const double2*)in.p,
+             (const double2*)P.p, (double)P.gscale, t, in.nsys, run);
+  } else if (P.s == S32) {
+    launch_k(prolong_kernel<float, float2, SB>, grid, dim3(256), 0, st, (float2*)out.p, (const float2*)in.p,
+             (const float2*)P.p, P.gscale, t, in.nsys, run);
+  } else {
+    SMG_REQUIRE(P.s == S16, "prolong: unsupported storage");
+    launch_k(prolong_kernel<float, __half2, SB>, grid, dim3(256), 0, st, (float2*)out.p, (const float2*)in.p,
+             (const __half2*)P.p, P.gscale, t, in.nsys, run);
+  }
+  SMG_LAUNCH_OK();
+}
+
+void prolong_sb(int sb, const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                const int* run) {
+  switch (sb) {
+    case 1: launch_prolong<1>(out, in, t, P, st, run); break;
+    case 2: launch_prolong<2>(out, in, t, P, st, run); break;
+    case 4: launch_prolong<4>(out, in, t, P, st, run); break;
+    default: launch_prolong<8>(out, in, t, P, st, run); break;
+  }
+}
+
+const char* sb_name(int sb) {
+  return sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA" : sb == 4 ? "4 systems/CTA" : "8 systems/CTA";
+}
+
+// the autotuner's choice of systems per CTA for one transfer launch
+template <class F>
+int pick_sb(const char* family, const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P,
+            cudaStream_t st, F&& launch) {
+  if (in.nsys == 1) return 1;
+  std::vector<TuneCandidate> cands;
+  for (int sb : {1, 2, 4, 8})
+    if (sb == 1 || sb < 2 * in.nsys) cands.push_back({sb, sb_name(sb)});
+  char key[192];
+  std::snprintf(key, sizeof(key), "%s V=%d nvec=%d ndof=%d nsys=%d vec=%s store=%s", family, t.fine.V, t.nvec,
+                t.ndof, in.nsys, in.prec == P64 ? "f64" : "f32",
+                P.s == S16 ? "f16" : (P.s == S32 ? "f32" : "f64"));
+  struct Scratch {
+    void* p = nullptr;
+    ~Scratch() { if (p) cudaFree(p); }
+  } scratch;
+  return tune_pick(key, cands, st, [&](int id) {
+    if (scratch.p == nullptr) SMG_CUDA_OK(cudaMalloc(&scratch.p, out.bytes()));
+    Vec o = out;
+    o.p = scratch.p;
+    launch(id, o);
+  });
+}
+}  // namespace
+
 void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
                  const int* run) {
   SMG_REQUIRE(in.n == (long long)t.fine.V * t.ndof && out.n == (long long)t.coarse.V * 2 * t.nvec,
               "restrict: field sizes do not match the transfer");
   SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec && t.nvec <= 128, "restrict: batch/precision mismatch");
-  dim3 grid(t.coarse.V, in.nsys);
   const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
   const size_t cb = prec_bytes(in.prec);
   const int vpc = (int)(16 / store_bytes(P.s));
   if (t.nvec % vpc == 0) {
-    // vectorised kernel: 512 threads, nvec / vpc threads per row
+    // vectorised kernel: 512 threads, nvec / vpc threads per row; systems per
+    // CTA by the autotuner among the group sizes whose shared memory fits
     const int groups = 512 / (t.nvec / vpc);
-    const size_t smem = cb * ((size_t)groups * 2 * t.nvec + 8 * 2 * t.nvec + (size_t)npos * t.ndof) +
-                        sizeof(int) * 2 * npos;
-    if (smem <= 200 * 1024) {
-      if (in.prec == P64) {
-        SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
-        auto k = restrict_vec_kernel<double, double2>;
-        ensure_smem(k, smem);
-        launch_k(k, dim3(grid), dim3(512), smem, st, (double2*)out.p, (const double2*)in.p, (const double2*)P.p, (double)P.gscale,
-                                   t, run);
-      } else if (P.s == S32) {
-        auto k = restrict_vec_kernel<float, float2>;
-        ensure_smem(k, smem);
-        launch_k(k, dim3(grid), dim3(512), smem, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t, run);
-      } else {
-        SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
-        auto k = restrict_vec_kernel<float, __half2>;
-        ensure_smem(k, smem);
-        launch_k(k, dim3(grid), dim3(512), smem, st, (float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t, run);
-      }
-      SMG_LAUNCH_OK();
+    auto fits = [&](int sb) {
+      return cb * ((size_t)groups * 2 * t.nvec + 8 * 2 * t.nvec + (size_t)sb * npos * t.ndof) +
+                 sizeof(int) * 2 * npos <= 200 * 1024;
+    };
+    if (fits(1)) {
+      int sb = pick_sb("restrict", out, in, t, P, st, [&](int id, const Vec& o) {
+        if (!fits(id) || !restrict_vec_sb(id, o, in, t, P, st, nullptr)) restrict_vec_sb(1, o, in, t, P, st, nullptr);
+      });
+      if (!fits(sb)) sb = 1;
+      restrict_vec_sb(sb, out, in, t, P, st, run);
       return;
     }
   }
+  dim3 grid(t.coarse.V, in.nsys);
   const size_t smem = cb * (512 + (size_t)npos * t.ndof) + sizeof(int) * 2 * npos;
   SMG_REQUIRE(smem <= 200 * 1024, "restrict: aggregate too large for shared memory");
   if (in.prec == P64) {
@@ -390,20 +520,9 @@ void prolong_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stor
   SMG_REQUIRE(out.n == (long long)t.fine.V * t.ndof && in.n == (long long)t.coarse.V * 2 * t.nvec,
               "prolong: field sizes do not match the transfer");
   SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec, "prolong: batch/precision mismatch");
-  dim3 grid(ceil_div(out.n, 256), in.nsys);
-  if (in.prec == P64) {
-    SMG_REQUIRE(P.s == S64, "prolong: FP64 vectors need FP64 prolongator");
-    launch_k(prolong_kernel<double, double2>, dim3(grid), dim3(256), 0, st, (double2*)out.p, (const double2*)in.p,
-                                                          (const double2*)P.p, (double)P.gscale, t, run);
-  } else if (P.s == S32) {
-    launch_k(prolong_kernel<float, float2>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p,
-                                                        P.gscale, t, run);
-  } else {
-    SMG_REQUIRE(P.s == S16, "prolong: unsupported storage");
-    launch_k(prolong_kernel<float, __half2>, dim3(grid), dim3(256), 0, st, (float2*)out.p, (const float2*)in.p,
-                                                         (const __half2*)P.p, P.gscale, t, run);
-  }
-  SMG_LAUNCH_OK();
+  const int sb = pick_sb("prolong", out, in, t, P, st,
+                         [&](int id, const Vec& o) { prolong_sb(id, o, in, t, P, st, nullptr); });
+  prolong_sb(sb, out, in, t, P, st, run);
 }
 
 }  // namespace smg

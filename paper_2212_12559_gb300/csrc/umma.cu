@@ -14,7 +14,8 @@
 //                  accumulate in 32 TMEM columns) per stage, tcgen05.commit
 //                  frees the stage;
 //   warps 2..7     build the matching 32 x 64 FP16 B tile (same swizzle) of
-//                  each stage from the FP32 vectors (float4 loads);
+//                  each stage from the FP32 vectors (float4 loads, the next
+//                  chunk's loads issued before the current one is converted);
 //   all warps      per-site scale pass before the K loop, and the epilogue:
 //                  tcgen05.ld of the 128 x 32 accumulator (warp w owns TMEM
 //                  lanes 32(w%4).. = rows and 16 of the 32 columns), row
@@ -241,32 +242,46 @@ __global__ void __launch_bounds__(UTHREADS, 1) coarse_umma_kernel(const __grid_c
       }
     } else {
       // B tile of chunk c: rows n = 2r + im (32), 64 FP16 along K = 32 complex
-      // entries jj = 32c + 0..31; 16-byte granules (4 complex) at swizzled slots.
+      // entries jj = 32c + 0..31; 16-byte granules (4 complex) at swizzled
+      // slots.  Builder thread bt < 128 owns system r = bt / 8 and granule
+      // column cc = bt % 8 of every chunk: one pair of 16-byte loads feeds both
+      // rows (Re and Im) of its system, and the loads of chunk c + 1 are issued
+      // before chunk c is converted, so two chunks' reads are in flight.
       const int bt = tid - 64;
+      const bool owns = bt < kMaxRhsU * 8;
+      const int r = bt >> 3, cc = bt & 7;
+      const bool live = owns && r < nrhs;
+      float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+      auto fetch = [&](int c) {
+        if (!live) return;
+        const int jj = 32 * c + 4 * cc;                     // 4 complex, never across a direction (N % 4 == 0)
+        const int dir = jj / N, j = jj - dir * N;
+        const float4* src =
+            reinterpret_cast<const float4*>(in + (size_t)(s0 + r) * sys_stride + (size_t)sm.nb[dir] * N + j);
+        q0 = src[0];
+        q1 = src[1];
+      };
+      fetch(0);
       for (int c = 0; c < nchunk; ++c) {
         const long long i = it0 + c;
         const int s = (int)(i % STAGES);
         const long long round = i / STAGES;
+        const float4 p0 = q0, p1 = q1;
+        if (c + 1 < nchunk) fetch(c + 1);
         if (round > 0 && !mbar_wait(&sm.empty[s], (unsigned)((round - 1) & 1), err)) { atomicExch((int*)err, 1); break; }
-        for (int gidx = bt; gidx < UN * 8; gidx += NBUILD) {
-          const int n = gidx >> 3, cc = gidx & 7;
-          const int r = n >> 1, im = n & 1;
-          uint4 v4 = make_uint4(0u, 0u, 0u, 0u);
-          if (r < nrhs) {
-            const float sg = sm.sig[r];
-            const int jj = 32 * c + 4 * cc;                 // 4 complex, never across a direction (N % 4 == 0)
-            const int dir = jj / N, j = jj - dir * N;
-            const float4* src = reinterpret_cast<const float4*>(in + (size_t)(s0 + r) * sys_stride +
-                                                                (size_t)sm.nb[dir] * N + j);
-            const float4 p0 = src[0], p1 = src[1];
-            const float re[4] = {p0.x * sg, p0.z * sg, p1.x * sg, p1.z * sg};
-            const float ii[4] = {p0.y * sg, p0.w * sg, p1.y * sg, p1.w * sg};
-            unsigned w[4];
+        if (owns) {
+          const float sg = live ? sm.sig[r] : 0.f;
+          const float re[4] = {p0.x * sg, p0.z * sg, p1.x * sg, p1.z * sg};
+          const float ii[4] = {p0.y * sg, p0.w * sg, p1.y * sg, p1.w * sg};
+          unsigned wr[4], wi[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) w[q] = im ? pack_h2(ii[q], re[q]) : pack_h2(re[q], -ii[q]);
-            v4 = make_uint4(w[0], w[1], w[2], w[3]);
+          for (int q = 0; q < 4; ++q) {
+            wr[q] = pack_h2(re[q], -ii[q]);   // row 2r:     (Re, -Im)
+            wi[q] = pack_h2(ii[q], re[q]);    // row 2r + 1: (Im,  Re)
           }
-          *reinterpret_cast<uint4*>(sm.b[s] + n * 128 + ((cc ^ (n & 7)) << 4)) = v4;
+          const int n0 = 2 * r, n1 = 2 * r + 1;
+          *reinterpret_cast<uint4*>(sm.b[s] + n0 * 128 + ((cc ^ (n0 & 7)) << 4)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+          *reinterpret_cast<uint4*>(sm.b[s] + n1 * 128 + ((cc ^ (n1 & 7)) << 4)) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&sm.full_b[s]);
