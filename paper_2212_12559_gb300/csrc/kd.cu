@@ -261,9 +261,10 @@ void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, co
     set.scale[i] = kd[i].s == S16 ? kd[i].scale : nullptr;
   }
   const long long nblk = g.V / 16;
-  // consecutive systems that share one block inverse: all of them with one
-  // inverse, else kd_run (systems per mass), which a group may not straddle
-  const int run_len = (sys_map == nullptr) ? in.nsys : std::max(1, kd_run);
+  // with several inverses a group of systems may not straddle two masses:
+  // kd_run consecutive systems share one inverse, and the group size must
+  // divide it; with one inverse any group size serves
+  const int run_len = (sys_map == nullptr) ? 0 : std::max(1, kd_run);
   auto go = [&](int sb, const Vec& o, const int* rr) {
     if (in.prec == P64) {
       SMG_REQUIRE(kd[0].s == S64, "kd_apply: FP64 vectors need FP64 blocks");
@@ -279,7 +280,7 @@ void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, co
   };
   std::vector<TuneCandidate> cands;
   for (int sb : {1, 2, 4, 8})
-    if (sb == 1 || (sb < 2 * in.nsys && run_len % sb == 0))
+    if (sb == 1 || (sb < 2 * in.nsys && (run_len == 0 || run_len % sb == 0)))
       cands.push_back({sb, sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA" : sb == 4 ? "4 systems/CTA"
                                                                                       : "8 systems/CTA"});
   int sb = 1;
