@@ -181,11 +181,16 @@ SMG_API int smg_save_setup(smg_ctx* ctx, const char* path);
  * context's current gauge field and mass (set_gauge and set_mass first): the
  * saved vectors are block-orthonormalised and coarsened exactly as
  * smg_mg_setup does (no CGNE, no singular-vector iteration), so with the
- * gauge field and mass of the save every coarse operator is bit for bit the
- * one saved with.  Replaces any previous setup.  SMG_ERR_ARG when the file
- * is missing, truncated, fails its hash or was saved for other lattice
- * extents; SMG_ERR_STATE without a gauge field or mass. */
-SMG_API int smg_load_setup(smg_ctx* ctx, const char* path);
+ * gauge field, mass and parameters of the save every coarse operator is bit
+ * for bit the one saved with.  params: NULL for the saved parameters, or
+ * parameters with the same level structure (n_coarse, agg, nvec,
+ * block_coarse, coarsest_schur, coarsest_deflate) whose other settings
+ * (precision, inner rules, smoother, graph, persistence, ...) replace the
+ * saved ones, e.g. to run the same vectors in FP64.  Replaces any previous
+ * setup.  SMG_ERR_ARG when the file is missing, truncated, fails its hash,
+ * was saved for other lattice extents or does not match params' level
+ * structure; SMG_ERR_STATE without a gauge field or mass. */
+SMG_API int smg_load_setup(smg_ctx* ctx, const char* path, const smg_mg_params* params);
 
 /* Sec. 3.2: solves M x = b to ||b - M x|| <= tol ||b|| (recomputed in FP64).
  * b, x: V*3 complex FP64.  x is output only (zero initial guess).

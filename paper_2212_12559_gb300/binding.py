@@ -105,7 +105,7 @@ def load(path: str = LIB_PATH):
         "smg_tune_load": (i, [ctypes.c_char_p]),
         "smg_tune_clear": (i, []),
         "smg_save_setup": (i, [vp, ctypes.c_char_p]),
-        "smg_load_setup": (i, [vp, ctypes.c_char_p]),
+        "smg_load_setup": (i, [vp, ctypes.c_char_p, ctypes.POINTER(MGParams)]),
         "smg_multi_solve": (i, [vp, i, vp, i, ctypes.POINTER(d), vp, d, i, ctypes.POINTER(SolveInfo)]),
         "smg_multishift_cg": (i, [vp, vp, i, ctypes.POINTER(d), vp, d, i, i, ctypes.POINTER(SolveInfo)]),
         "smg_persist_plan": (i, [i, i, i, i, i, i, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
@@ -326,10 +326,12 @@ class Solver:
         """Writes the current setup (parameters, near-null vectors, deflation) to `path`."""
         self._check(self.lib.smg_save_setup(self.ctx, os.fsencode(path)))
 
-    def load_setup(self, path):
-        """Rebuilds the hierarchy from a file of save_setup for the current gauge field and mass."""
-        self._check(self.lib.smg_load_setup(self.ctx, os.fsencode(path)))
-        self.params = self._read_params(path)
+    def load_setup(self, path, params=None):
+        """Rebuilds the hierarchy from a file of save_setup for the current gauge
+        field and mass, with the saved parameters or `params` (same level structure)."""
+        self._check(self.lib.smg_load_setup(self.ctx, os.fsencode(path),
+                                            None if params is None else ctypes.byref(params)))
+        self.params = self._read_params(path) if params is None else params
 
     @staticmethod
     def _read_params(path):

@@ -180,11 +180,11 @@ int smg_save_setup(smg_ctx* ctx, const char* path) {
   });
 }
 
-int smg_load_setup(smg_ctx* ctx, const char* path) {
+int smg_load_setup(smg_ctx* ctx, const char* path, const smg_mg_params* params) {
   return guarded(ctx, [&](smg::Context& c) {
     SMG_REQUIRE(path != nullptr, "load_setup: null path");
     if (!c.gauge_set || !c.mass_set) throw smg::StateError("load_setup needs set_gauge and set_mass first");
-    smg::ctx_load_setup(c, path);
+    smg::ctx_load_setup(c, path, params);
     return SMG_OK;
   });
 }

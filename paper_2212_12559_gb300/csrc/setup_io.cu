@@ -137,7 +137,7 @@ void ctx_save_setup(Context& c, const char* path) {
   w.close();
 }
 
-void ctx_load_setup(Context& c, const char* path) {
+void ctx_load_setup(Context& c, const char* path, const smg_mg_params* over) {
   SMG_REQUIRE(path != nullptr, "load_setup: null path");
   SMG_REQUIRE(c.gauge_set && c.mass_set, "load_setup needs set_gauge and set_mass first");
   Reader r(path);
@@ -199,7 +199,22 @@ void ctx_load_setup(Context& c, const char* path) {
   uint64_t got = 0;
   SMG_REQUIRE(std::fread(&got, 1, sizeof(got), r.f) == sizeof(got), "load_setup: " + r.path + " is truncated");
   SMG_REQUIRE(got == want, "load_setup: checksum mismatch in " + r.path);
-  // rebuild: the saved vectors are used as given (no CGNE), the deflation state restored
+  // rebuild: the saved vectors are used as given (no CGNE), the deflation state
+  // restored; other solver settings may replace the saved ones when the level
+  // structure the vectors belong to is the same
+  if (over != nullptr) {
+    bool same = over->n_coarse == P.n_coarse && over->block_coarse == P.block_coarse &&
+                over->coarsest_schur == P.coarsest_schur && over->coarsest_deflate == P.coarsest_deflate;
+    for (int l = 0; l < P.n_coarse && same; ++l) {
+      same = over->nvec[l] == P.nvec[l];
+      for (int mu = 0; mu < 4; ++mu) same = same && over->agg[l][mu] == P.agg[l][mu];
+    }
+    SMG_REQUIRE(same, "load_setup: the parameters' level structure (n_coarse, agg, nvec, block_coarse, "
+                      "coarsest_schur, coarsest_deflate) differs from the saved setup's");
+    const int keep_iters = P.setup_maxiter;
+    P = *over;
+    P.setup_maxiter = keep_iters;
+  }
   smg_mg_params Q = P;
   Q.setup_maxiter = 0;
   std::vector<const void*> phi0;

@@ -173,7 +173,7 @@ void ctx_mg_setup(Context& c, const smg_mg_params& p, const void* const* phi0, i
 // once and reused): save writes it, load rebuilds the hierarchy from it for the
 // context's gauge field and mass (setup_io.cu).
 void ctx_save_setup(Context& c, const char* path);
-void ctx_load_setup(Context& c, const char* path);
+void ctx_load_setup(Context& c, const char* path, const smg_mg_params* over = nullptr);
 int ctx_multishift_cg(Context& c, const void* b, int nshift, const double* masses, void* x, double tol, int maxiter,
                       int where, smg_solve_info* info);
 int ctx_propagators(Context& c, const void* b, int nmass, const double* masses, int n_mg, void* x, double tol,

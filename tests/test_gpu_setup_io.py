@@ -111,6 +111,11 @@ def test_load_refuses_bad_files(binding, tmp_path):
     for ctx, path, msg in ((s, flipped, "checksum"), (s, short, "truncated"), (other, good, "extents"),
                            (s, tmp_path / "missing.smg", "cannot open")):
         with pytest.raises(binding.SmgError) as e:
-            ctx._check(ctx.lib.smg_load_setup(ctx.ctx, str(path).encode()))
+            ctx._check(ctx.lib.smg_load_setup(ctx.ctx, str(path).encode(), None))
         assert e.value.code == -1 and msg in str(e.value), str(e.value)
     s.load_setup(good)
+    # other solver settings on the same vectors; another level structure is refused
+    s.load_setup(good, binding.default_params(nvec=[4], precision=binding.PREC_HALF, inner_tol=0.1))
+    with pytest.raises(binding.SmgError) as e:
+        s.load_setup(good, binding.default_params(nvec=[6]))
+    assert e.value.code == -1 and "level structure" in str(e.value)
