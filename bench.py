@@ -1,20 +1,25 @@
 """Benchmark: MG-GCR time per solve at ||r||/||b|| < 1e-10 on GB300.
 
-Default workload (N=1): 16^4 lattice, HISQ-shaped operator (fat links from
-one APE-like smearing step of Proj_SU3(exp(0.3 i H)) links, Naik links as
-products of three thin links, c_N = -1/24), mass 0.01, three-level K-cycle
-(4^4 then 2^4 aggregates, 24 / 32 near-null vectors), FP32 arithmetic with
-FP16 storage of links, KD blocks, near-null vectors and coarse stencils,
-FP64 outer GCR.  All inputs are seeded synthetic data.
+Default workload (N=1): 32^4 lattice, naive staggered operator on seeded
+synthetic links Proj_SU3(exp(0.3 i H)), mass 0.001, twelve Gaussian
+right-hand sides solved together by one smg_multi_solve per step; K-cycle
+multigrid with Table 1's two coarsenings (4^4 then 2^4 aggregates, 64 / 32
+near-null vectors from 1000 CGNE iterations), FP32 arithmetic with FP16
+storage of links, KD blocks, near-null vectors and coarse stencils (the
+12-system coarse apply on the tensor cores), FP64 outer GCR.  Other
+workloads: --config 1 (8^4, FP64), 2 (16^4 HISQ-shaped), 4 (24^3 x 48
+HISQ-shaped, 8 masses x 4 sources).
 
-A step is one complete solve (the K-cycle preconditioned outer GCR until the
-FP64-recomputed residual is below 1e-10) of one Gaussian source that already
-sits in device memory; the multigrid setup is built once before timing and
-reported separately.  L2 is flushed (a 512 MB write) before every timed
-solve.  `e2e` repeats the measurement through the C ABI with host buffers
-(pinned), the host->device copy of b and the device->host copy of x inside
-the timed region.  The same solve in plain FP64 (setup and preconditioner
-FP64) is timed beside it for the mixed-vs-FP64 comparison.
+A step is one complete batched solve (the outer GCR of every system until its
+FP64-recomputed residual is below 1e-10) with the sources already in device
+memory; `value` is the step time divided by the systems it solves.  The
+multigrid setup is built once before timing and reported separately.  L2 is
+flushed (a 512 MB write) before every timed step.  `e2e` repeats the
+measurement through the C ABI with pinned host buffers (host->device copy of
+the sources and device->host copy of the solutions inside the timed region).
+The same algorithm in plain FP64 (same near-null vectors, FP64 operators,
+one system at a time, no CUDA graph) is timed beside it for the
+mixed+batched vs FP64 comparison the metric names.
 
 `--impl reference` times the FP64 CPU oracle instead (rank 0, host cores).
 """
@@ -37,22 +42,32 @@ import numpy as np  # noqa: E402
 METRIC = "MG-GCR time/solve at |r|/|b|<1e-10 and coarse-apply GB/s, mixed+batched vs FP64"
 UNIT = "s/solve"
 WORKLOADS = {
-    2: "16^4 HISQ-shaped, m=0.01, 3-level KD-MG (4^4/2^4 aggregates, 24/32 vectors), FP32 + FP16 storage, FP64 outer GCR",
-    1: "8^4 naive staggered, m=0.1, 2-level KD-MG (4^4 aggregates, 24 vectors), FP64",
-    3: "32^4 naive staggered, m=0.001, 2-level KD-MG (4^4 aggregates, 64 vectors), 12 Gaussian RHS solved together, "
-       "FP32 + FP16 storage (tensor-core multi-RHS coarse apply), FP64 outer GCR",
+    1: "8^4 naive staggered, m=0.1, 2-level KD-MG (4^4 aggregates, 24 vectors), FP64, 1 RHS",
+    2: "16^4 HISQ-shaped, m=0.01, 3-level KD-MG (4^4/2^4 aggregates, 24/32 vectors), truncated level-1 operator, "
+       "FP32 + FP16 storage, FP64 outer GCR, 1 RHS",
+    3: "32^4 naive staggered, m=0.001, 12 Gaussian RHS solved together, KD-MG with Table 1's levels "
+       "(4^4/2^4 aggregates, 64/32 vectors, SVD-deflated Chebyshev CA-GCR coarsest level with 48 singular vectors), "
+       "FP32 + FP16 storage (12-system coarse apply on tcgen05), FP64 outer GCR",
     4: "24^3x48 HISQ-shaped, 8 masses log-spaced 0.001-0.05 x 4 sources = 32 systems in one batch, 3-level KD-MG "
-       "(4^4/2^4 aggregates, 24/32 vectors, operators of the lightest mass), FP32 + FP16 storage, FP64 outer GCR",
+       "(4^4/2^4 aggregates, 24/32 vectors, operators of the lightest mass), truncated level-1 operator, "
+       "FP32 + FP16 storage, FP64 outer GCR",
 }
-# Outer GCR iterations a solve of the workload takes with this
-# algorithm, keyed by (workload, truncated level-1 operator), measured by the
-# GPU path with the same parameters; scales the
-# oracle's per-iteration time in --impl reference, where no GPU runs.
-REF_OUTER_ITERS = {(2, 0): 64, (2, 1): 31, (1, 0): 10, (1, 1): 10}
-# dram__bytes_read.sum + dram__bytes_write.sum of one coarse_apply_kernel launch
-# on the 4096-site, N=128 FP16 stencil (ncu, see profiles/); None once the
-# kernel changes until it is captured again.
-NCU_TRAFFIC_COARSE_CFG3 = 2.428274e9 + 0.078370e9
+# Solver recipe of each workload (its inputs come from inputs.CONFIGS): the
+# level-1 inner rule, the rule of the coarse levels (0 = the same), the
+# near-null CGNE cap and the level-1 operator.  Table 1's "0.25 or 8
+# iterations" serves the heavier masses; at m = 0.001 the outer GCR stalls
+# near 1e-2 with it (GPU and oracle probes), and the level-1 rule 0.05 / 16
+# with near-null vectors from 1000 CGNE iterations converges.
+SOLVER = {
+    1: dict(inner=(0.25, 8), coarse_inner=(0.0, 0), setup_maxiter=2000, truncate_naik=0),
+    2: dict(inner=(0.25, 8), coarse_inner=(0.0, 0), setup_maxiter=2000, truncate_naik=1),
+    3: dict(inner=(0.05, 16), coarse_inner=(0.0, 0), setup_maxiter=1000, truncate_naik=0, coarsest_deflate=48),
+    4: dict(inner=(0.05, 16), coarse_inner=(0.0, 0), setup_maxiter=1000, truncate_naik=1),
+}
+# Outer GCR iterations a solve of the workload takes with this algorithm,
+# measured by the GPU path with the same recipe; scales the oracle's
+# per-iteration time in --impl reference (no GPU runs there).
+REF_OUTER_ITERS = {1: 10, 2: 31, 3: 19, 4: 30}
 
 
 # ------------------------------------------------------------------ helpers
@@ -150,68 +165,48 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------- GPU problem
-def build_problem(cfg, torch, dev, seed_offset=0, dims=None):
+def problem(cfg, torch, dev, rank=0, dims=None):
+    """Gauge field, mass and near-null starts of a workload on the device, its
+    sources on the host ([nrhs][V][3]; replica `rank` draws its own) and the
+    masses of the batch."""
     from paper_2212_12559_gb300 import binding, inputs
     c = inputs.config_inputs(cfg, dims=tuple(dims) if dims else None)
     dims = c["dims"]
     V = int(np.prod(dims))
     s = binding.Solver(dims)
     s.set_stream(torch.cuda.current_stream(dev).cuda_stream)
-    fat = torch.from_numpy(c["fat"]).to(dev)
-    naik = None if c["naik"] is None else torch.from_numpy(c["naik"]).to(dev)
-    s.set_gauge(fat, naik, c["c_naik"])
+    s.set_gauge(torch.from_numpy(c["fat"]).to(dev),
+                None if c["naik"] is None else torch.from_numpy(c["naik"]).to(dev), c["c_naik"])
     s.set_mass(c["mass"])
     nv = c["nvec"]
     phi0 = [torch.from_numpy(inputs.gaussian_fields(nv[0], V, 3, c["nullvec_seed"])).to(dev)]
     cdims = dims
-    ndof = 3
     for l in range(1, len(nv)):
         cdims = tuple(d // a for d, a in zip(cdims, c["agg"][l - 1]))
-        ndof = 2 * nv[l - 1]
         phi0.append(torch.from_numpy(
-            inputs.gaussian_fields(nv[l], int(np.prod(cdims)), ndof, c["nullvec_seed"] + 10 * l)).to(dev))
-    src = inputs.gaussian_field(V, 3, c["seeds"][1] + seed_offset)
-    return c, s, phi0, src
+            inputs.gaussian_fields(nv[l], int(np.prod(cdims)), 2 * nv[l - 1], c["nullvec_seed"] + 10 * l)).to(dev))
+    k = SOLVER[cfg].get("coarsest_deflate", 0)
+    if k > 0:
+        cdims = tuple(d // a for d, a in zip(cdims, c["agg"][-1]))
+        phi0.append(torch.from_numpy(inputs.gaussian_fields(binding.deflation_block(k), int(np.prod(cdims)),
+                                                            2 * nv[-1], c["nullvec_seed"] + 99)).to(dev))
+    src = c["sources"]
+    if rank > 0:
+        src = np.stack([inputs.gaussian_field(V, 3, c["seeds"][1] + 1000 * rank + r) for r in range(src.shape[0])])
+    masses = np.array([c["mass"]]) if c["masses"] is None else inputs.log_masses(0.001, 0.05, 8)
+    return c, s, phi0, src, masses
 
 
-def setup(binding, s, c, phi0, precision, use_graph, setup_maxiter=2000, max_outer=500, truncate_naik=0,
-          inner=(0.25, 8)):
+def solver_params(binding, c, cfg, precision, use_graph, args, persistent=1):
+    rec = SOLVER[cfg]
     prec = {"double": binding.PREC_DOUBLE, "single": binding.PREC_SINGLE, "mixed": binding.PREC_HALF}[precision]
-    p = binding.default_params(n_coarse=len(c["nvec"]), agg=c["agg"], nvec=c["nvec"], precision=prec,
-                               use_graph=use_graph, setup_maxiter=setup_maxiter, max_outer=max_outer,
-                               truncate_naik=truncate_naik, inner_tol=float(inner[0]), inner_maxiter=int(inner[1]))
-    t0 = time.perf_counter()
-    s.mg_setup(p, phi0)
-    return time.perf_counter() - t0
-
-
-def timed_solves(torch, s, b_dev, steps, warmup, flush, profile=False):
-    """Returns (per-step seconds list, infos, last x).  With `profile` the
-    timed solves are bracketed by cudaProfilerStart/Stop (for ncu's
-    --profile-from-start off)."""
-    infos = []
-    for _ in range(warmup):
-        _, info = s.solve(b_dev, 1e-10)
-        infos.append(info)
-    times = []
-    if profile:
-        torch.cuda.synchronize()
-        torch.cuda.profiler.start()
-    st = torch.cuda.current_stream()
-    for _ in range(steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        x, info = s.solve(b_dev, 1e-10)
-        e1.record(st)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        infos.append(info)
-    if profile:
-        torch.cuda.synchronize()
-        torch.cuda.profiler.stop()
-    return times, infos, x
+    inner = (args.inner_tol, args.inner_maxiter) if args.inner_tol > 0 else rec["inner"]
+    return binding.default_params(
+        n_coarse=len(c["nvec"]), agg=c["agg"], nvec=c["nvec"], precision=prec, use_graph=use_graph,
+        persistent=persistent, setup_maxiter=args.setup_maxiter if args.setup_maxiter > 0 else rec["setup_maxiter"],
+        max_outer=args.max_outer, truncate_naik=rec["truncate_naik"], inner_tol=float(inner[0]),
+        inner_maxiter=int(inner[1]), coarse_inner_tol=float(rec["coarse_inner"][0]),
+        coarse_inner_maxiter=int(rec["coarse_inner"][1]), coarsest_deflate=int(rec.get("coarsest_deflate", 0)))
 
 
 def coarse_bytes(N, nsys, store_bytes=4, scale=True):
@@ -221,8 +216,9 @@ def coarse_bytes(N, nsys, store_bytes=4, scale=True):
 
 
 def dslash_bytes(hisq, nsys, store_bytes=4):
-    """Per fine site: 4 (8 with Naik) 3x3 links at storage precision, input and
-    output colour vectors in FP32 (each read / written once)."""
+    """Per fine site: 4 (8 with Naik) 3x3 links at storage precision (read once
+    for the batch), input and output colour vectors in FP32 (each read /
+    written once per system)."""
     nl = 8 if hisq else 4
     return nl * 9 * store_bytes + 2 * 3 * 8 * nsys
 
@@ -233,27 +229,27 @@ def kd_bytes(nsys, store_bytes=4):
     return 144 * store_bytes + 3 * 4 + 2 * 3 * 8 * nsys
 
 
-def a_bytes(hisq, nsys, store_bytes=4):
-    """Per fine site for A = (B+m)^{-1} M: the links and the block entries
-    (each read once), input and output colour vectors."""
-    nl = 8 if hisq else 4
-    return nl * 9 * store_bytes + 144 * store_bytes + 3 * 4 + 2 * 3 * 8 * nsys
+def transfer_bytes(nvec, ndof, nsys, store_bytes=4):
+    """Per fine site of a restriction or prolongation: the site's ndof x nvec
+    prolongator entries (read once for the batch) and its ndof components of
+    every system; the coarse side is V/agg as large and left out."""
+    return ndof * nvec * store_bytes + ndof * 8 * nsys
 
 
 # ------------------------------------------------------ coarse apply alone
 COARSE_SHAPES = {
-    # coarse level of each workload: extents, components per site
-    "cfg3": ((8, 8, 8, 8), 128),      # 32^4 / 4^4 aggregates, 64 vectors: 2.42 GB FP16 stencil
-    "cfg4": ((6, 6, 6, 12), 48),      # 24^3x48 / 4^4 aggregates, 24 vectors: 215 MB
-    "cfg2": ((4, 4, 4, 4), 48),       # 16^4 / 4^4 aggregates, 24 vectors: 21.5 MB (L2-resident)
+    # coarse level of a workload: extents, components per site
+    "8^4xN128": ((8, 8, 8, 8), 128),     # 32^4 / 4^4 aggregates, 64 vectors: 2.42 GB FP16 stencil
+    "6^3x12xN48": ((6, 6, 6, 12), 48),   # 24^3x48 / 4^4 aggregates, 24 vectors: 215 MB
+    "4^4xN48": ((4, 4, 4, 4), 48),       # 16^4 / 4^4 aggregates, 24 vectors: 21.5 MB (L2-resident)
 }
 
 
 def coarse_roofline(binding, solver, shape, nsys, nrep, hbm):
-    """Times the 9-point coarse apply on a synthetic FP16 stencil of one
-    workload's coarse-level shape; returns a roofline dict (algorithmic bytes:
-    9 N^2 complex FP16 entries + N FP32 row scales per site, input and output
-    FP32 vectors of nsys systems, each counted once)."""
+    """Times the 9-point coarse apply on a synthetic FP16 stencil of a coarse
+    level's shape; returns a roofline dict (algorithmic bytes: 9 N^2 complex
+    FP16 entries + N FP32 row scales per site, input and output FP32 vectors
+    of nsys systems, each counted once)."""
     cd, N = COARSE_SHAPES[shape]
     Vc = int(np.prod(cd))
     ms = solver.bench_coarse_apply(cd, N, nsys, binding.PREC_HALF, nrep)
@@ -280,33 +276,30 @@ def run_coarse_only(args):
 
 
 # --------------------------------------------------------- oracle sample
-def oracle_sample(cfg, n_iter, out_path, sub=0, truncate_naik=0):
+def oracle_sample(cfg, n_iter, out_path, dims):
     """Runs in a child process with one BLAS thread: times the oracle's outer
-    GCR iterations of the workload (setup with unrefined random near-null
-    vectors, excluded from the timing).  With sub > 0 the lattice extents are
-    divided by `sub` (same per-site work, same level structure) to bound the
-    oracle's setup time."""
+    GCR iterations (K-cycle + M) of the workload's operator and level
+    structure on the extents `dims` (setup with unrefined random near-null
+    vectors, not timed)."""
     from oracle.dirac import Staggered
     from oracle.lattice import Lattice
     from oracle.mg import MGParams, MultigridSolver
     from paper_2212_12559_gb300 import inputs
-    c = inputs.config_inputs(cfg)
-    if sub:
-        c = inputs.config_inputs(cfg, dims=tuple(d // sub for d in c["dims"]))
-    dims = c["dims"]
+    c = inputs.config_inputs(cfg, dims=tuple(dims))
     V = int(np.prod(dims))
-    lat = Lattice(dims)
-    op = Staggered(lat, c["fat"], c["naik"], c["c_naik"], c["mass"])
+    op = Staggered(Lattice(dims), c["fat"], c["naik"], c["c_naik"], c["mass"])
     nv = c["nvec"]
     phi0 = [inputs.gaussian_fields(nv[0], V, 3, c["nullvec_seed"])]
-    cdims, ndof = dims, 3
+    cdims = tuple(dims)
     for l in range(1, len(nv)):
         cdims = tuple(d // a for d, a in zip(cdims, c["agg"][l - 1]))
-        ndof = 2 * nv[l - 1]
-        phi0.append(inputs.gaussian_fields(nv[l], int(np.prod(cdims)), ndof, c["nullvec_seed"] + 10 * l))
+        phi0.append(inputs.gaussian_fields(nv[l], int(np.prod(cdims)), 2 * nv[l - 1], c["nullvec_seed"] + 10 * l))
+    rec = SOLVER[cfg]
     t0 = time.perf_counter()
-    mg = MultigridSolver(op, MGParams(agg=c["agg"], nvec=nv, setup_maxiter=0, truncate_naik=bool(truncate_naik)),
-                         phi0)
+    mg = MultigridSolver(op, MGParams(agg=c["agg"], nvec=nv, setup_maxiter=0,
+                                      truncate_naik=bool(rec["truncate_naik"]), inner_tol=rec["inner"][0],
+                                      inner_maxiter=rec["inner"][1], coarse_inner_tol=rec["coarse_inner"][0],
+                                      coarse_inner_maxiter=rec["coarse_inner"][1]), phi0)
     t_setup = time.perf_counter() - t0
     b = c["sources"][0]
     times = []
@@ -319,125 +312,140 @@ def oracle_sample(cfg, n_iter, out_path, sub=0, truncate_naik=0):
         json.dump({"iter_times": times, "setup_s": t_setup, "V": V}, f)
 
 
-def run_oracle_sample(cfg, n_iter, timeout=600, sub=0, truncate_naik=0):
-    out = os.path.join(ROOT, f".oracle_sample_{os.getpid()}.json")
+def oracle_full_solve(cfg, out_path):
+    """Runs in a child process with one BLAS thread: one complete oracle
+    setup (CGNE near-null vectors) and solve of a workload."""
+    from oracle.dirac import Staggered
+    from oracle.lattice import Lattice
+    from oracle.mg import MGParams, MultigridSolver
+    from paper_2212_12559_gb300 import inputs
+    c = inputs.config_inputs(cfg)
+    dims = c["dims"]
+    V = int(np.prod(dims))
+    op = Staggered(Lattice(dims), c["fat"], c["naik"], c["c_naik"], c["mass"])
+    rec = SOLVER[cfg]
+    t0 = time.perf_counter()
+    mg = MultigridSolver(op, MGParams(agg=c["agg"], nvec=c["nvec"], setup_maxiter=rec["setup_maxiter"],
+                                      inner_tol=rec["inner"][0], inner_maxiter=rec["inner"][1]),
+                         [inputs.gaussian_fields(c["nvec"][0], V, 3, c["nullvec_seed"])])
+    t1 = time.perf_counter()
+    x, it, res = mg.solve(c["sources"][0], 1e-10)
+    t2 = time.perf_counter()
+    with open(out_path, "w") as f:
+        json.dump({"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": it, "residual": res, "V": V}, f)
+
+
+def run_child(args_list, timeout):
+    """Runs this script in a child process on the host cores only (one BLAS
+    thread, no GPU visible); returns the JSON the child wrote."""
+    import tempfile
+    fd, out = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
         env.pop(k, None)
-    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-sample", str(cfg), str(n_iter), out, str(sub),
-           str(truncate_naik)]
-    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    with open(out) as f:
-        d = json.load(f)
-    os.remove(out)
-    return d
+    cmd = [sys.executable, os.path.abspath(__file__)] + args_list + [out]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
+        if r.returncode != 0:
+            raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
+        with open(out) as f:
+            return json.load(f)
+    finally:
+        if os.path.exists(out):
+            os.remove(out)
+
+
+def sample_dims(cfg):
+    """Extents of the oracle sample: the workload's own level structure on the
+    smallest lattice that keeps it (every coarsening still divides)."""
+    from paper_2212_12559_gb300 import inputs
+    c = inputs.CONFIGS[cfg]
+    dims = list(c["dims"])
+    while True:
+        half = [d // 2 for d in dims]
+        ok = all(h % 2 == 0 and h >= 4 for h in half)
+        cd = half
+        for a in c["agg"]:
+            ok = ok and all(x % y == 0 for x, y in zip(cd, a))
+            cd = [x // y for x, y in zip(cd, a)] if ok else cd
+        if not ok:
+            return tuple(dims)
+        dims = half
 
 
 # --------------------------------------------------------------------- arms
 def run_reference(args):
+    """The FP64 CPU oracle on the host cores: each step one oracle outer-GCR
+    iteration of the workload on the reduced lattice, scaled by volume and by
+    the outer iterations per solve the GPU path needs."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     cfg = args.config
-    iters = REF_OUTER_ITERS[(cfg, args.truncate_naik)]
+    from paper_2212_12559_gb300 import inputs
+    dims = sample_dims(cfg)
+    V = int(np.prod(inputs.CONFIGS[cfg]["dims"]))
     n = args.steps + args.warmup
-    d = run_oracle_sample(cfg, n, timeout=3600, truncate_naik=args.truncate_naik)
-    per_iter = d["iter_times"][args.warmup:]
-    per_solve = [t * iters for t in per_iter]
+    d = run_child(["--_oracle-sample", str(cfg), str(n), *[str(x) for x in dims]], 3600)
+    vol = V / d["V"]
+    iters = REF_OUTER_ITERS[cfg]
+    per_solve = [t * vol * iters for t in d["iter_times"][args.warmup:]]
     value = statistics.mean(per_solve)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[cfg], "oracle_setup_s": d["setup_s"],
-                   "level1_operator": "truncated (Naik dropped)" if args.truncate_naik else "KD-preconditioned HISQ"},
+        "config": {"workload": WORKLOADS[cfg], "oracle_sample_dims": list(dims), "oracle_setup_s": d["setup_s"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} oracle outer-GCR iterations (K-cycle + M), each scaled by "
-                                   f"{iters} iterations per solve; setup with unrefined near-null vectors excluded"},
+                         "sample": f"{args.steps} oracle outer-GCR iterations (K-cycle + M) of this workload's "
+                                   f"operator and level structure on {'x'.join(map(str, dims))}, scaled by volume "
+                                   f"x{vol:.0f} and by the {iters} outer iterations a solve takes on the GPU path; "
+                                   f"oracle setup with unrefined near-null vectors, not timed"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def run_batched(args):
-    """Configurations 3 and 4: one multi_solve of all systems per step; the
-    value is the batch time divided by the number of systems."""
-    import torch
-    from paper_2212_12559_gb300 import binding, inputs
-    ws, rank, local = dist_env()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    cfg = args.config
-    log(f"config {cfg}: building inputs")
-    c, s, phi0, _ = build_problem(cfg, torch, dev, dims=args.dims)
-    V = int(np.prod(c["dims"]))
-    masses = np.array([c["mass"]]) if c["masses"] is None else inputs.log_masses(0.001, 0.05, 8)
-    log(f"inputs ready (dims {c['dims']}); setup")
-    t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer,
-                    args.truncate_naik, (args.inner_tol, args.inner_maxiter))
-    setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
-    log(f"setup {t_setup:.1f} s, CGNE iterations {setup_iters}")
-    b = torch.from_numpy(c["sources"]).to(dev)
-    nsys = b.shape[0] * len(masses)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
-        t0 = time.perf_counter()
-        _, inf = s.multi_solve(b, masses, 1e-10)
-        log(f"warm-up batch {time.perf_counter() - t0:.2f} s, outer {inf[0].iterations}, "
-            f"max residual {max(i.true_residual for i in inf):.2e}")
-    torch.cuda.synchronize()
-    launches0 = binding.kernel_launches()
-    clocks = ClockSampler(local)
-    clocks.start()
+def timed_batches(torch, s, b, masses, steps, flush):
+    """Per-step seconds (CUDA events on the solver's stream, L2 flushed before
+    each) of `steps` batched solves; returns (times, infos of the last step)."""
     times, infos = [], None
     st = torch.cuda.current_stream()
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        x, infos = s.multi_solve(b, masses, 1e-10)
+        _, infos = s.multi_solve(b, masses, 1e-10)
         e1.record(st)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
-        log(f"timed batch {times[-1]:.2f} s, outer {infos[0].iterations}")
-    clk = clocks.stop()
-    launches = binding.kernel_launches() - launches0
-    value = statistics.mean(times) / nsys
-    # end to end with pinned host buffers
-    bh = torch.from_numpy(c["sources"]).pin_memory()
-    xh = torch.empty((len(masses),) + tuple(bh.shape), dtype=torch.complex128).pin_memory()
-    t0 = time.perf_counter()
-    s.multi_solve(bh, masses, 1e-10, x=xh)
-    e2e = (time.perf_counter() - t0) / nsys
-    hbm, peak_kind = measured_peaks()
-    shape = "cfg3" if cfg == 3 else "cfg4"
-    r = coarse_roofline(binding, s, shape, min(nsys, 16), 5, hbm)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f16 storage, f64 outer", "data": "synthetic",
-        "config": {"workload": WORKLOADS[cfg], "dims": list(c["dims"]), "systems_per_step": nsys,
-                   "masses": [float(m) for m in masses], "setup_s": t_setup, "setup_cgne_iters": setup_iters,
-                   "inner_tol": args.inner_tol, "inner_maxiter": args.inner_maxiter,
-                   "outer_iters": infos[0].iterations, "all_converged": all(i.converged for i in infos),
-                   "max_true_residual": max(i.true_residual for i in infos),
-                   "l2": "flushed (512 MB write) before every timed batch"},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 16),
-                "d2h_bytes_per_step": int(xh.numel() * 16)},
-        "gpu_launches": launches // max(1, args.steps),
-        "clocks": clk,
-        "roofline": {"bound": "hbm", "kernel": f"coarse apply, {r['nrhs']} RHS, this workload's coarse shape",
-                     "achieved": r["achieved_GBs"], "peak": hbm, "unit": "GB/s", "frac": r["frac_of_hbm"],
-                     "traffic": None, "TFLOPs": r["TFLOPs"], "ms_per_launch": r["ms_per_launch"]},
-        "cpu_baseline": None,
-    }
-    print(json.dumps(line))
-    return 0
+    return times, infos
+
+
+def kernel_rooflines(binding, s, c, nsys, hbm):
+    """Live CUDA-event timings of the solve's kernel families on the workload's
+    own operators (smg_time_kernel: nrep launches on the solver's stream, the
+    autotuner's kernel for the shape) with their algorithmic bytes."""
+    V = int(np.prod(c["dims"]))
+    hisq = c["naik"] is not None
+    out = {}
+    nv0 = c["nvec"][0]
+    cd = [d // a for d, a in zip(c["dims"], c["agg"][0])]
+    Vc, N = int(np.prod(cd)), 2 * nv0
+    for name, kern, l, nbytes in (
+            ("coarse_apply_level2", binding.K_COARSE, 0, coarse_bytes(N, nsys) * Vc),
+            ("dslash", binding.K_DSLASH, 0, dslash_bytes(hisq, nsys, 4) * V),
+            ("kd_apply", binding.K_KD, 0, kd_bytes(nsys) * V),
+            ("restrict_level1", binding.K_RESTRICT, 0, transfer_bytes(nv0, 3, nsys) * V),
+            ("prolong_level1", binding.K_PROLONG, 0, transfer_bytes(nv0, 3, nsys) * V)):
+        ms = s.time_kernel(kern, l, nsys, 20)
+        ach = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_launch": ms, "alg_bytes_per_launch": nbytes, "achieved_GBs": ach, "frac": ach / hbm}
+    return out
 
 
 def run_ours(args):
@@ -451,17 +459,27 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cfg = args.config
-    log(f"config {cfg}: building inputs")
-    c, s, phi0, src = build_problem(cfg, torch, dev, seed_offset=rank)
+    log(f"workload {cfg}: building inputs")
+    c, s, phi0, src, masses = problem(cfg, torch, dev, rank=rank, dims=args.dims)
     V = int(np.prod(c["dims"]))
-    log("setup")
-    t_setup = setup(binding, s, c, phi0, c["precision"], args.graph, args.setup_maxiter, args.max_outer,
-                    args.truncate_naik)
-    log(f"setup {t_setup:.1f} s")
+    p = solver_params(binding, c, cfg, c["precision"], args.graph, args)
+    log(f"inputs ready (dims {c['dims']}); setup")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.mg_setup(p, phi0)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
     setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
-    b_dev = torch.from_numpy(src).to(dev)
+    log(f"setup {t_setup:.1f} s, CGNE iterations {setup_iters}")
+    b = torch.from_numpy(src).to(dev)
+    nsys = b.shape[0] * len(masses)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    # timed region: K solves, L2 flushed before each
+    for _ in range(args.warmup):
+        t0 = time.perf_counter()
+        _, inf = s.multi_solve(b, masses, 1e-10)
+        log(f"warm-up step {time.perf_counter() - t0:.2f} s, outer {inf[0].iterations}, "
+            f"max residual {max(i.true_residual for i in inf):.2e}")
+    # timed region: K batched solves, L2 flushed before each
     if ws > 1:
         tdist.barrier()
     torch.cuda.synchronize()
@@ -469,7 +487,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     t_wall0 = time.perf_counter()
-    times, infos, x = timed_solves(torch, s, b_dev, args.steps, args.warmup, flush, profile=args.profile)
+    times, infos = timed_batches(torch, s, b, masses, args.steps, flush)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
@@ -478,105 +496,103 @@ def run_ours(args):
         tdist.barrier()
     total = sum(times)
     tmax = max_over_ranks(total, tdist, dev) if ws > 1 else total
-    timed_infos = infos[args.warmup:]
-    iters = [i.iterations for i in timed_infos]
+    value = tmax / (args.steps * nsys * ws)
     conv = all(i.converged for i in infos)
     res = max(i.true_residual for i in infos)
-    value = replica_value(tmax, args.steps, ws)
-    # gpu launches inside the timed solves only (warm-up launches excluded by proportion)
-    launches_timed = int(round(launches * args.steps / max(1, args.steps + args.warmup)))
+    log(f"timed: {statistics.mean(times):.3f} s per step of {nsys} systems, outer {infos[0].iterations}, "
+        f"max residual {res:.2e}")
 
-    # end to end through the C ABI with host (pinned) buffers
-    b_host = torch.from_numpy(src).pin_memory()
-    x_host = torch.empty_like(b_host).pin_memory()
+    # end to end through the C ABI with pinned host buffers
+    bh = torch.from_numpy(src).pin_memory()
+    xh = torch.empty((len(masses),) + tuple(bh.shape), dtype=torch.complex128).pin_memory()
     e2e_times = []
-    for i in range(args.steps + 1):
+    for _ in range(max(1, min(args.steps, 2))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.solve(b_host, 1e-10, x=x_host)
-        t1 = time.perf_counter()
-        if i > 0:
-            e2e_times.append(t1 - t0)
-    e2e = statistics.mean(e2e_times)
-    nbytes = V * 3 * 16
+        _, einf = s.multi_solve(bh, masses, 1e-10, x=xh)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = statistics.mean(e2e_times) / nsys
 
-    # roofline: the coarse 9-point apply (the operator kernel the K-cycle runs
-    # most), timed with CUDA events on the library's stream on the HBM-resident
-    # coarse level of the 32^4 workload (2.42 GB FP16 stencil), plus this
-    # workload's own L2-resident coarse level and fine kernels for context.
     hbm, peak_kind = measured_peaks()
-    roof = None
+    roof, kern = None, {}
     if rank == 0:
-        r3 = coarse_roofline(binding, s, "cfg3", 1, 10, hbm)
-        roof = {"bound": "hbm", "kernel": "coarse_apply_kernel<float, __half2>, coarse level of the 32^4 workload "
-                                          "(4096 sites, N=128, FP16 stencil 2.42 GB), 1 RHS",
-                "achieved": r3["achieved_GBs"], "peak": hbm, "unit": "GB/s", "frac": r3["frac_of_hbm"],
-                "traffic": NCU_TRAFFIC_COARSE_CFG3, "peak_kind": peak_kind + " HBM copy bandwidth",
-                "ms_per_launch": r3["ms_per_launch"], "alg_bytes_per_launch": r3["alg_bytes_per_launch"]}
-        ms = s.time_kernel(binding.K_COARSE, 0, 1, 200)
-        Vc = int(np.prod([d // a for d, a in zip(c["dims"], c["agg"][0])]))
-        N = 2 * c["nvec"][0]
-        ms_d = s.time_kernel(binding.K_DSLASH, 0, 1, 200)
-        ms_k = s.time_kernel(binding.K_KD, 0, 1, 200)
-        ms_a = s.time_kernel(binding.K_A, 0, 1, 200)
-        roof["others"] = {
-            "coarse_apply_this_workload_L2_resident": {"ms": ms, "GB/s": coarse_bytes(N, 1) * Vc / (ms * 1e-3) / 1e9},
-            "coarse_apply_cfg3_12rhs": coarse_roofline(binding, s, "cfg3", 12, 3, hbm),
-            "coarse_apply_cfg4_1rhs": coarse_roofline(binding, s, "cfg4", 1, 20, hbm),
-            "dslash_hisq_fp16": {"ms": ms_d, "GB/s": dslash_bytes(True, 1) * V / (ms_d * 1e-3) / 1e9},
-            "kd_apply_fp16": {"ms": ms_k, "GB/s": kd_bytes(1) * V / (ms_k * 1e-3) / 1e9},
-            # the solve's most-applied operator (ten applies per level-1 iteration), dslash + block kernels,
-            # back-to-back applies (its ~60 MB of links and blocks stay in L2)
-            "A_apply_fp16": {"ms": ms_a, "GB/s": a_bytes(c["naik"] is not None, 1) * V / (ms_a * 1e-3) / 1e9},
-        }
+        # the solve's kernel families on this workload's operators; the line's
+        # roofline is the family with the largest share of the solve's device
+        # time (the launch list in profiles/ names it)
+        kern = kernel_rooflines(binding, s, c, min(nsys, 16), hbm)
+        top = DOMINANT.get(cfg, "coarse_apply_level2")
+        k = kern[top]
+        roof = {"bound": "hbm", "kernel": top, "achieved": k["achieved_GBs"], "peak": hbm, "unit": "GB/s",
+                "frac": k["frac"], "traffic": NCU_TRAFFIC.get(cfg), "peak_kind": peak_kind + " HBM copy bandwidth",
+                "ms_per_launch": k["ms_per_launch"], "alg_bytes_per_launch": k["alg_bytes_per_launch"],
+                "systems_per_launch": min(nsys, 16), "others": {n: v for n, v in kern.items() if n != top}}
 
-    # plain FP64 GPU MG-GCR on the same problem (the comparison the metric names)
+    # the same algorithm in plain FP64 on the same GPU: same near-null vectors
+    # (loaded from the mixed setup), FP64 operators, one system at a time
     fp64 = None
     if rank == 0 and args.compare_fp64 and c["precision"] != "double":
+        import tempfile
+        path = os.path.join(tempfile.mkdtemp(), "setup.smg")
+        s.save_setup(path)
         s64 = binding.Solver(c["dims"])
         s64.set_stream(torch.cuda.current_stream(dev).cuda_stream)
         s64.set_gauge(torch.from_numpy(c["fat"]).to(dev),
                       None if c["naik"] is None else torch.from_numpy(c["naik"]).to(dev), c["c_naik"])
         s64.set_mass(c["mass"])
-        t64_setup = setup(binding, s64, c, phi0, "double", 0, truncate_naik=args.truncate_naik)
-        t64, inf64, _ = timed_solves(torch, s64, b_dev, max(1, args.steps // 2), 1, flush)
-        fp64 = {"s_per_solve": statistics.mean(t64), "setup_s": t64_setup,
-                "outer_iters": [i.iterations for i in inf64[1:]],
-                "speedup_mixed_vs_fp64": statistics.mean(t64) / value}
+        fp64 = {}
+        for graph in (0, 1):
+            p64 = solver_params(binding, c, cfg, "double", graph, args, persistent=0)
+            s64.load_setup(path, p64)
+            b1 = b[:1]
+            m1 = masses[:1]
+            s64.multi_solve(b1, m1, 1e-10)           # warm-up (graph capture, tuning)
+            t64, inf64 = timed_batches(torch, s64, b1, m1, args.fp64_steps, flush)
+            fp64["graph" if graph else "no_graph"] = {
+                "s_per_solve": statistics.mean(t64), "outer_iters": inf64[0].iterations,
+                "converged": bool(inf64[0].converged), "true_residual": inf64[0].true_residual}
+        fp64["speedup_mixed_batched_vs_fp64"] = fp64["no_graph"]["s_per_solve"] / value
+        fp64["speedup_mixed_batched_vs_fp64_graph"] = fp64["graph"]["s_per_solve"] / value
         s64.close()
+        os.remove(path)
+        log(f"FP64: {fp64['no_graph']['s_per_solve']:.2f} s/solve (no graph), "
+            f"{fp64['graph']['s_per_solve']:.2f} (graph)")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
-            n_it = args.cpu_iters
-            d = run_oracle_sample(cfg, n_it, sub=2, truncate_naik=args.truncate_naik)
+            dims = sample_dims(cfg)
+            d = run_child(["--_oracle-sample", str(cfg), str(args.cpu_iters), *[str(x) for x in dims]], 900)
             vol = V / d["V"]
             per_iter = statistics.mean(d["iter_times"]) * vol
-            it_per_solve = statistics.mean(iters)
+            it_per_solve = infos[0].iterations
             cpu = {"value": per_iter * it_per_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{n_it} oracle outer-GCR iterations (K-cycle + M) of the same workload on the "
-                             f"half-extent lattice ({d['V']} sites, same level structure), scaled by volume x{vol:.0f} "
-                             f"to {per_iter:.2f} s per iteration and by the {it_per_solve:.1f} outer iterations "
-                             f"a solve takes; oracle setup ({d['setup_s']:.1f} s, unrefined near-null vectors) "
-                             f"excluded"}
+                   "sample": f"{args.cpu_iters} oracle outer-GCR iterations (K-cycle + M) of this workload's operator "
+                             f"and level structure on {'x'.join(map(str, dims))} ({d['V']} sites), scaled by volume "
+                             f"x{vol:.0f} to {per_iter:.2f} s per iteration and by the {it_per_solve} outer "
+                             f"iterations a solve takes here; oracle setup ({d['setup_s']:.1f} s, unrefined "
+                             f"near-null vectors) not timed"}
         except Exception as e:  # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f16 storage, f64 outer" if c["precision"] == "mixed" else "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOADS[cfg], "dims": list(c["dims"]), "mass": c["mass"],
-                       "nvec": c["nvec"], "agg": [list(a) for a in c["agg"]], "precision": c["precision"],
-                       "cuda_graph": bool(args.graph), "l2": "flushed (512 MB write) before every timed solve",
-                       "level1_operator": "truncated (Naik dropped)" if args.truncate_naik else "KD-preconditioned HISQ",
-                       "setup_s": t_setup, "setup_cgne_iters": setup_iters, "outer_iters": iters, "all_converged": conv,
-                       "max_true_residual": res, "timed_wall_s": t_wall, "parallelism": f"replicas x{ws}"},
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "gpu_launches": launches_timed,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f16 storage, f64 outer" if c["precision"] == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[cfg], "dims": list(c["dims"]), "systems_per_step": nsys,
+                       "masses": [float(m) for m in masses], "nvec": c["nvec"], "agg": [list(a) for a in c["agg"]],
+                       "precision": c["precision"], "inner": [p.inner_tol, p.inner_maxiter],
+                       "coarse_inner": [p.coarse_inner_tol or p.inner_tol, p.coarse_inner_maxiter or p.inner_maxiter],
+                       "setup_maxiter": p.setup_maxiter, "cuda_graph": bool(args.graph),
+                       "l2": "flushed (512 MB write) before every timed step", "setup_s": t_setup,
+                       "setup_cgne_iters": setup_iters, "outer_iters": infos[0].iterations,
+                       "all_converged": conv, "max_true_residual": res, "timed_wall_s": t_wall,
+                       "parallelism": f"replicas x{ws}", "tuned_kernels": binding.tune_table()},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 16),
+                    "d2h_bytes_per_step": int(xh.numel() * 16)},
+            "gpu_launches": launches // max(1, args.steps),
             "clocks": clk,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -589,48 +605,56 @@ def run_ours(args):
     return 0
 
 
+# Kernel family with the largest share of the solve's device time (ncu launch
+# list of the workload, profiles/), and its DRAM traffic per launch from one
+# ncu capture when it still describes the current kernel (else None).
+DOMINANT = {3: "coarse_apply_level2", 4: "coarse_apply_level2", 2: "dslash", 1: "kd_apply"}
+NCU_TRAFFIC = {}
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--_oracle-sample":
-        oracle_sample(int(sys.argv[2]), int(sys.argv[3]), sys.argv[4], int(sys.argv[5]), int(sys.argv[6]))
+        cfg, n = int(sys.argv[2]), int(sys.argv[3])
+        dims = tuple(int(x) for x in sys.argv[4:8])
+        oracle_sample(cfg, n, sys.argv[8], dims)
+        return 0
+    if len(sys.argv) > 1 and sys.argv[1] == "--_oracle-full":
+        oracle_full_solve(int(sys.argv[2]), sys.argv[3])
         return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3, 4])
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--compare-fp64", type=int, default=1)
-    ap.add_argument("--truncate-naik", type=int, default=1,
-                    help="Table 1 level-1 operator: 1 = truncated (Naik hops dropped from the pseudo-fine "
-                         "operator), 0 = KD-preconditioned HISQ; the outer operator is the full M either way")
-    ap.add_argument("--inner-tol", type=float, default=0.25,
-                    help="inner GCR tolerance of levels >= 1 for the light-mass workloads (--config 3/4; "
-                         "Table 1: 0.25)")
-    ap.add_argument("--inner-maxiter", type=int, default=8,
-                    help="inner GCR iteration cap for --config 3/4 (Table 1: 8; at most 16)")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 single-system solves per variant")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="level-1 inner GCR tolerance (0: the workload's recipe)")
+    ap.add_argument("--inner-maxiter", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
-    ap.add_argument("--setup-maxiter", type=int, default=2000,
-                    help="near-null CGNE cap (Table 1: 2000); lower only to bound profiler runs")
-    ap.add_argument("--max-outer", type=int, default=500,
-                    help="outer GCR cap; lower only to bound profiler runs")
-    ap.add_argument("--dims", type=int, nargs=4, default=None,
-                    help="other lattice extents for the batched workloads (probing only)")
+    ap.add_argument("--oracle-full-solve", action="store_true",
+                    help="with --impl reference: time one complete oracle setup + solve of the workload instead")
+    ap.add_argument("--setup-maxiter", type=int, default=0, help="near-null CGNE cap (0: the workload's recipe)")
+    ap.add_argument("--max-outer", type=int, default=500, help="outer GCR cap; lower only to bound profiler runs")
+    ap.add_argument("--dims", type=int, nargs=4, default=None, help="other lattice extents (probing only)")
     ap.add_argument("--coarse-only", action="store_true",
                     help="time only the coarse apply on the workloads' coarse-level shapes")
-    ap.add_argument("--shape", default=None, choices=[None, "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--shape", default=None, choices=[None] + list(COARSE_SHAPES))
     ap.add_argument("--nrhs", type=int, nargs="+", default=[1, 12])
     ap.add_argument("--nrep", type=int, default=10)
-    ap.add_argument("--profile", type=int, default=0,
-                    help="bracket the timed solves with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.oracle_full_solve:
+            d = run_child(["--_oracle-full", str(args.config)], 7200)
+            print(json.dumps({"impl": "reference", "kind": "oracle full setup + solve", "workload":
+                              WORKLOADS[args.config], "cores": 1, **d}))
+            return 0
         return run_reference(args)
     if args.coarse_only:
         return run_coarse_only(args)
-    if args.config in (3, 4):
-        return run_batched(args)
     return run_ours(args)
 
 

@@ -16,7 +16,9 @@
 //   warps 2..7     build the matching 32 x 64 FP16 B tile (same swizzle) of
 //                  each stage from the FP32 vectors (float4 loads, the next
 //                  chunk's loads issued before the current one is converted);
-//   all warps      per-site scale pass before the K loop, and the epilogue:
+//   all warps      per-site scale before the K loop (the largest entry over
+//                  the nine neighbours, from per-site maxima that a prepass
+//                  kernel writes), and the epilogue:
 //                  tcgen05.ld of the 128 x 32 accumulator (warp w owns TMEM
 //                  lanes 32(w%4).. = rows and 16 of the 32 columns), row
 //                  scale, 1/sigma.
@@ -139,6 +141,26 @@ __device__ __forceinline__ unsigned pack_h2(float lo, float hi) {
   return *reinterpret_cast<unsigned*>(&h);
 }
 
+// smax[s][X] = max |Re|, |Im| of the N components of system s at site X:
+// one warp per (site, system), 16-byte loads.
+__global__ void __launch_bounds__(256) site_max_kernel(const float2* __restrict__ in, int nsys, int V, int N,
+                                                       long long sys_stride, float* __restrict__ smax,
+                                                       const int* run) {
+  if (run != nullptr && *run == 0) return;
+  const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)V * nsys) return;
+  const int s = (int)(w / V), X = (int)(w - (long long)s * V);
+  const float4* v = reinterpret_cast<const float4*>(in + (size_t)s * sys_stride + (size_t)X * N);
+  float m = 0.f;
+  for (int q = lane; q < N / 2; q += 32) {
+    const float4 a = v[q];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) smax[(size_t)s * V + X] = m;
+}
+
 template <int STAGES>
 __global__ void __launch_bounds__(UTHREADS, 1) coarse_umma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   float2* __restrict__ out,
@@ -146,6 +168,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) coarse_umma_kernel(const __grid_c
                                                                   const float* __restrict__ rs, Geom g, int nsys,
                                                                   int s0, long long sys_stride,
                                                                   const float2* __restrict__ sub_from,
+                                                                  const float* __restrict__ smax,
                                                                   int* __restrict__ gerr, const int* run) {
   if (run != nullptr && *run == 0) return;
   extern __shared__ unsigned char umma_raw[];
@@ -193,13 +216,11 @@ __global__ void __launch_bounds__(UTHREADS, 1) coarse_umma_kernel(const __grid_c
     }
     if (tid < kMaxRhsU) sm.vmax[tid] = 0u;
     __syncthreads();
-    for (int e = tid; e < nrhs * 9 * N / 2; e += UTHREADS) {   // two complex entries per float4
-      const int r = e / (9 * N / 2), q = 2 * (e - r * (9 * N / 2));
-      const int dir = q / N, j = q - dir * N;
-      const float4 v = *reinterpret_cast<const float4*>(in + (size_t)(s0 + r) * sys_stride +
-                                                         (size_t)sm.nb[dir] * N + j);
-      const float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
-      atomicMax(&sm.vmax[r], __float_as_uint(m));
+    // the largest |Re|, |Im| over the nine neighbours, from the per-site
+    // maxima of the prepass (one load per system and direction)
+    for (int e = tid; e < nrhs * 9; e += UTHREADS) {
+      const int r = e / 9, dir = e - 9 * r;
+      atomicMax(&sm.vmax[r], __float_as_uint(smax[(size_t)(s0 + r) * g.V + sm.nb[dir]]));
     }
     __syncthreads();
     if (tid < kMaxRhsU) {
@@ -379,6 +400,30 @@ bool coarse_umma_err_read_and_clear(cudaStream_t st) {
 }
 
 namespace {
+// Grow-only device buffer of per-site maxima (one per device; sized by the
+// first, uncaptured call of a shape, so that a graph capture never allocates).
+float* site_max_buffer(size_t n, cudaStream_t st) {
+  static float* buf[64] = {};
+  static size_t cap[64] = {};
+  int dev = 0;
+  SMG_CUDA_OK(cudaGetDevice(&dev));
+  SMG_REQUIRE(dev >= 0 && dev < 64, "coarse_apply_umma: device ordinal out of range");
+  if (cap[dev] < n) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SMG_CUDA_OK(cudaStreamIsCapturing(st, &cs));
+    SMG_REQUIRE(cs == cudaStreamCaptureStatusNone,
+                "coarse_apply_umma: a new batch shape met inside a graph capture (run it once uncaptured first)");
+    if (buf[dev] != nullptr) {
+      SMG_CUDA_OK(cudaDeviceSynchronize());
+      SMG_CUDA_OK(cudaFree(buf[dev]));
+      buf[dev] = nullptr;
+    }
+    SMG_CUDA_OK(cudaMalloc(&buf[dev], n * sizeof(float)));
+    cap[dev] = n;
+  }
+  return buf[dev];
+}
+
 template <int STAGES>
 void launch_umma(const CUtensorMap& map, const Vec& out, const Vec& in, const CoarseParams& p, const Stored& S,
                  int* err, cudaStream_t st, const int* run, int grid) {
@@ -389,9 +434,15 @@ void launch_umma(const CUtensorMap& map, const Vec& out, const Vec& in, const Co
                                      (int)smem));
     attr = true;
   }
+  float* smax = site_max_buffer((size_t)in.nsys * p.g.V, st);
+  const long long pairs = (long long)in.nsys * p.g.V;
+  site_max_kernel<<<(unsigned)((pairs + 7) / 8), 256, 0, st>>>((const float2*)in.p, in.nsys, p.g.V, p.N, in.n, smax,
+                                                              run);
+  SMG_LAUNCH_OK();
   for (int s0 = 0; s0 < in.nsys; s0 += kMaxRhsU) {
     coarse_umma_kernel<STAGES><<<grid, UTHREADS, smem, st>>>(map, (float2*)out.p, (const float2*)in.p, S.scale, p.g,
-                                                             in.nsys, s0, in.n, (const float2*)p.sub_from, err, run);
+                                                             in.nsys, s0, in.n, (const float2*)p.sub_from, smax, err,
+                                                             run);
     SMG_LAUNCH_OK();
   }
 }

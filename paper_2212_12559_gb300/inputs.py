@@ -180,7 +180,7 @@ CONFIGS = {
             precision="double", nrhs=1, masses=None, seeds=(1001, 2001, 3001)),
     2: dict(dims=(16, 16, 16, 16), hisq=True, mass=0.01, agg=[(4, 4, 4, 4), (2, 2, 2, 2)],
             nvec=[24, 32], precision="mixed", nrhs=1, masses=None, seeds=(1002, 2002, 3002)),
-    3: dict(dims=(32, 32, 32, 32), hisq=False, mass=0.001, agg=[(4, 4, 4, 4)], nvec=[64],
+    3: dict(dims=(32, 32, 32, 32), hisq=False, mass=0.001, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[64, 32],
             precision="mixed", nrhs=12, masses=None, seeds=(1003, 2003, 3003)),
     4: dict(dims=(24, 24, 24, 48), hisq=True, mass=0.001, agg=[(4, 4, 4, 4), (2, 2, 2, 2)],
             nvec=[24, 32], precision="mixed", nrhs=4, masses="log8", seeds=(1004, 2004, 3004)),
