@@ -487,8 +487,12 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     t_wall0 = time.perf_counter()
+    if args.profile:
+        torch.cuda.profiler.start()
     times, infos = timed_batches(torch, s, b, masses, args.steps, flush)
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.stop()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     launches = binding.kernel_launches() - launches0
@@ -506,7 +510,7 @@ def run_ours(args):
     bh = torch.from_numpy(src).pin_memory()
     xh = torch.empty((len(masses),) + tuple(bh.shape), dtype=torch.complex128).pin_memory()
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(args.e2e_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -541,22 +545,21 @@ def run_ours(args):
                       None if c["naik"] is None else torch.from_numpy(c["naik"]).to(dev), c["c_naik"])
         s64.set_mass(c["mass"])
         fp64 = {}
-        for graph in (0, 1):
+        for graph in ((1, 0) if args.fp64_both else (1,)):
             p64 = solver_params(binding, c, cfg, "double", graph, args, persistent=0)
             s64.load_setup(path, p64)
             b1 = b[:1]
             m1 = masses[:1]
-            s64.multi_solve(b1, m1, 1e-10)           # warm-up (graph capture, tuning)
+            if graph:
+                s64.multi_solve(b1, m1, 1e-10)       # warm-up: the graph capture
             t64, inf64 = timed_batches(torch, s64, b1, m1, args.fp64_steps, flush)
-            fp64["graph" if graph else "no_graph"] = {
-                "s_per_solve": statistics.mean(t64), "outer_iters": inf64[0].iterations,
-                "converged": bool(inf64[0].converged), "true_residual": inf64[0].true_residual}
-        fp64["speedup_mixed_batched_vs_fp64"] = fp64["no_graph"]["s_per_solve"] / value
-        fp64["speedup_mixed_batched_vs_fp64_graph"] = fp64["graph"]["s_per_solve"] / value
+            key = "graph" if graph else "no_graph"
+            fp64[key] = {"s_per_solve": statistics.mean(t64), "outer_iters": inf64[0].iterations,
+                         "converged": bool(inf64[0].converged), "true_residual": inf64[0].true_residual}
+            fp64["speedup_mixed_batched_vs_fp64_" + key] = fp64[key]["s_per_solve"] / value
+            log(f"FP64 ({key}): {fp64[key]['s_per_solve']:.2f} s/solve, outer {inf64[0].iterations}")
         s64.close()
         os.remove(path)
-        log(f"FP64: {fp64['no_graph']['s_per_solve']:.2f} s/solve (no graph), "
-            f"{fp64['graph']['s_per_solve']:.2f} (graph)")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -630,6 +633,11 @@ def main():
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--compare-fp64", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 single-system solves per variant")
+    ap.add_argument("--fp64-both", action="store_true",
+                    help="time the FP64 arm without the CUDA graph too (default: with the graph only)")
+    ap.add_argument("--e2e-steps", type=int, default=1, help="batches timed end to end through host buffers")
+    ap.add_argument("--profile", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="level-1 inner GCR tolerance (0: the workload's recipe)")
     ap.add_argument("--inner-maxiter", type=int, default=16)
