@@ -516,7 +516,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         _, einf = s.multi_solve(bh, masses, 1e-10, x=xh)
         e2e_times.append(time.perf_counter() - t0)
-    e2e = statistics.mean(e2e_times) / nsys
+    e2e = statistics.mean(e2e_times) / nsys if e2e_times else None
 
     hbm, peak_kind = measured_peaks()
     roof, kern = None, {}
@@ -593,8 +593,8 @@ def run_ours(args):
                        "setup_cgne_iters": setup_iters, "outer_iters": infos[0].iterations,
                        "all_converged": conv, "max_true_residual": res, "timed_wall_s": t_wall,
                        "parallelism": f"replicas x{ws}", "tuned_kernels": binding.tune_table()},
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 16),
-                    "d2h_bytes_per_step": int(xh.numel() * 16)},
+            "e2e": None if e2e is None else {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 16),
+                                              "d2h_bytes_per_step": int(xh.numel() * 16)},
             "gpu_launches": launches // max(1, args.steps),
             "clocks": clk,
             "roofline": roof,
