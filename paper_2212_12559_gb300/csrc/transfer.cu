@@ -329,6 +329,126 @@ __global__ void prolong_kernel(typename cplx<R>::T* __restrict__ out, const type
     if (sb < ns) out[(size_t)(s0 + sb) * nf + e] = cscale(acc[sb], pscale);
 }
 
+// Restriction with one CTA per aggregate and SB systems: thread (g, k) owns
+// coarse vector k and every groups-th row of the aggregate, keeps both
+// chirality sums for each system in registers (the row's chirality is the
+// same for the whole warp), and reads each prolongator entry once for all SB
+// systems; the row groups are added at the end in a fixed order.
+template <typename R, typename SL, int SB>
+__global__ void __launch_bounds__(256) restrict_agg_kernel(typename cplx<R>::T* __restrict__ out,
+                                                           const typename cplx<R>::T* __restrict__ in,
+                                                           const SL* __restrict__ P, R pscale, TransferGeom t,
+                                                           int nsys, const int* run) {
+  using C = typename cplx<R>::T;
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ __align__(16) unsigned char ra_smem[];
+  const int nv = t.nvec, nd = t.ndof, half = nd / 2;
+  const int groups = blockDim.x / nv;
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  C* part = reinterpret_cast<C*>(ra_smem);                        // [groups][SB][2][nv]
+  int* xs = reinterpret_cast<int*>(part + (size_t)groups * SB * 2 * nv);
+  int* xpar = xs + npos;
+  const int X = blockIdx.x, s0 = blockIdx.y * SB;
+  const int ns = min(SB, nsys - s0);
+  const long long nf = (long long)t.fine.V * nd;
+  for (int p = threadIdx.x; p < npos; p += blockDim.x) {
+    const int x = agg_site(t, X, p);
+    xs[p] = x;
+    xpar[p] = site_parity(t.fine, x);
+  }
+  __syncthreads();
+  const int k = threadIdx.x % nv, g = threadIdx.x / nv;
+  C acc0[SB], acc1[SB];
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb) { acc0[sb] = C{0, 0}; acc1[sb] = C{0, 0}; }
+  if (g < groups) {
+#pragma unroll 4
+    for (int rr = g; rr < npos * nd; rr += groups) {
+      const int p = rr / nd, d = rr - p * nd;
+      const int chi = t.chi_mode == 0 ? xpar[p] : (d >= half ? 1 : 0);
+      const size_t row = (size_t)xs[p] * nd + d;
+      const C pv = ld<R>(P, row * nv + k);
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) {
+        if (sb >= ns) break;
+        const C v = in[(size_t)(s0 + sb) * nf + row];
+        if (chi == 0) cfmac(acc0[sb], pv, v);
+        else cfmac(acc1[sb], pv, v);
+      }
+    }
+#pragma unroll
+    for (int sb = 0; sb < SB; ++sb) {
+      part[(((size_t)g * SB + sb) * 2 + 0) * nv + k] = acc0[sb];
+      part[(((size_t)g * SB + sb) * 2 + 1) * nv + k] = acc1[sb];
+    }
+  }
+  __syncthreads();
+  const int N = 2 * nv;
+  for (int e = threadIdx.x; e < ns * N; e += blockDim.x) {
+    const int sb = e / N, i = e - sb * N;                     // i = chi * nv + k
+    C sum = C{0, 0};
+    for (int gg = 0; gg < groups; ++gg) sum = cadd(sum, part[((size_t)gg * SB + sb) * N + i]);
+    out[(size_t)(s0 + sb) * t.coarse.V * N + (size_t)X * N + i] = cscale(sum, pscale);
+  }
+}
+
+// Prolongation with one CTA per aggregate and SB systems: the aggregate's
+// coarse components of the SB systems are staged in shared memory, each
+// thread takes rows of the aggregate and reads its prolongator row with
+// 16-byte loads, once for all SB systems.
+template <typename R, typename SL, int SB>
+__global__ void __launch_bounds__(256) prolong_agg_kernel(typename cplx<R>::T* __restrict__ out,
+                                                          const typename cplx<R>::T* __restrict__ in,
+                                                          const SL* __restrict__ P, R pscale, TransferGeom t,
+                                                          int nsys, const int* run) {
+  using C = typename cplx<R>::T;
+  constexpr int VPC = 16 / (int)sizeof(SL);
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ __align__(16) unsigned char pa_smem[];
+  const int nv = t.nvec, nd = t.ndof, half = nd / 2, N = 2 * nv;
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  C* ec = reinterpret_cast<C*>(pa_smem);                          // [SB][2 nv]
+  int* xs = reinterpret_cast<int*>(ec + (size_t)SB * N);
+  int* xpar = xs + npos;
+  const int X = blockIdx.x, s0 = blockIdx.y * SB;
+  const int ns = min(SB, nsys - s0);
+  const long long nf = (long long)t.fine.V * nd;
+  for (int e = threadIdx.x; e < ns * N; e += blockDim.x) {
+    const int sb = e / N, i = e - sb * N;
+    ec[e] = in[(size_t)(s0 + sb) * t.coarse.V * N + (size_t)X * N + i];
+  }
+  for (int p = threadIdx.x; p < npos; p += blockDim.x) {
+    const int x = agg_site(t, X, p);
+    xs[p] = x;
+    xpar[p] = site_parity(t.fine, x);
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < npos * nd; rr += blockDim.x) {
+    const int p = rr / nd, d = rr - p * nd;
+    const int chi = t.chi_mode == 0 ? xpar[p] : (d >= half ? 1 : 0);
+    const size_t row = (size_t)xs[p] * nd + d;
+    const uint4* Pr = reinterpret_cast<const uint4*>(P + row * nv);
+    C acc[SB];
+#pragma unroll
+    for (int sb = 0; sb < SB; ++sb) acc[sb] = C{0, 0};
+    for (int kc = 0; kc < nv / VPC; ++kc) {
+      const uint4 raw = __ldg(Pr + kc);
+      const SL* pe = reinterpret_cast<const SL*>(&raw);
+#pragma unroll
+      for (int u = 0; u < VPC; ++u) {
+        const C pk = ld<R>(pe, u);
+        const int kk = chi * nv + kc * VPC + u;
+#pragma unroll
+        for (int sb = 0; sb < SB; ++sb)
+          if (sb < ns) cfma(acc[sb], pk, ec[(size_t)sb * N + kk]);
+      }
+    }
+#pragma unroll
+    for (int sb = 0; sb < SB; ++sb)
+      if (sb < ns) out[(size_t)(s0 + sb) * nf + row] = cscale(acc[sb], pscale);
+  }
+}
+
 // Raise a kernel's dynamic shared-memory limit once (not a stream operation,
 // so it is never issued while a stream is being captured).
 template <typename K>
@@ -444,14 +564,110 @@ const char* sb_name(int sb) {
   return sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA" : sb == 4 ? "4 systems/CTA" : "8 systems/CTA";
 }
 
+// candidate ids of the aggregate kernels: 16 + systems per CTA
+const char* agg_name(int sb) {
+  return sb == 1 ? "aggregate CTA, 1 system" : sb == 2 ? "aggregate CTA, 2 systems"
+                                            : sb == 4 ? "aggregate CTA, 4 systems" : "aggregate CTA, 8 systems";
+}
+
+template <int SB>
+size_t restrict_agg_smem(const TransferGeom& t, size_t cb) {
+  const int groups = 256 / t.nvec;
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  return cb * (size_t)groups * SB * 2 * t.nvec + sizeof(int) * 2 * npos;
+}
+
+template <int SB>
+void launch_restrict_agg(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                         const int* run) {
+  const size_t smem = restrict_agg_smem<SB>(t, prec_bytes(in.prec));
+  dim3 grid(t.coarse.V, ceil_div(in.nsys, SB));
+  if (in.prec == P64) {
+    SMG_REQUIRE(P.s == S64, "restrict: FP64 vectors need FP64 prolongator");
+    auto k = restrict_agg_kernel<double, double2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(256), smem, st, (double2*)out.p, (const double2*)in.p, (const double2*)P.p,
+             (double)P.gscale, t, in.nsys, run);
+  } else if (P.s == S32) {
+    auto k = restrict_agg_kernel<float, float2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t,
+             in.nsys, run);
+  } else {
+    SMG_REQUIRE(P.s == S16, "restrict: unsupported storage");
+    auto k = restrict_agg_kernel<float, __half2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t,
+             in.nsys, run);
+  }
+  SMG_LAUNCH_OK();
+}
+
+void restrict_agg_sb(int sb, const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                     const int* run) {
+  switch (sb) {
+    case 1: launch_restrict_agg<1>(out, in, t, P, st, run); break;
+    case 2: launch_restrict_agg<2>(out, in, t, P, st, run); break;
+    case 4: launch_restrict_agg<4>(out, in, t, P, st, run); break;
+    default: launch_restrict_agg<8>(out, in, t, P, st, run); break;
+  }
+}
+
+template <int SB>
+void launch_prolong_agg(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                        const int* run) {
+  const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
+  const size_t smem = prec_bytes(in.prec) * (size_t)SB * 2 * t.nvec + sizeof(int) * 2 * npos;
+  dim3 grid(t.coarse.V, ceil_div(in.nsys, SB));
+  if (in.prec == P64) {
+    SMG_REQUIRE(P.s == S64, "prolong: FP64 vectors need FP64 prolongator");
+    auto k = prolong_agg_kernel<double, double2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(256), smem, st, (double2*)out.p, (const double2*)in.p, (const double2*)P.p,
+             (double)P.gscale, t, in.nsys, run);
+  } else if (P.s == S32) {
+    auto k = prolong_agg_kernel<float, float2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const float2*)P.p, P.gscale, t,
+             in.nsys, run);
+  } else {
+    SMG_REQUIRE(P.s == S16, "prolong: unsupported storage");
+    auto k = prolong_agg_kernel<float, __half2, SB>;
+    ensure_smem(k, smem);
+    launch_k(k, grid, dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const __half2*)P.p, P.gscale, t,
+             in.nsys, run);
+  }
+  SMG_LAUNCH_OK();
+}
+
+void prolong_agg_sb(int sb, const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                    const int* run) {
+  switch (sb) {
+    case 1: launch_prolong_agg<1>(out, in, t, P, st, run); break;
+    case 2: launch_prolong_agg<2>(out, in, t, P, st, run); break;
+    case 4: launch_prolong_agg<4>(out, in, t, P, st, run); break;
+    default: launch_prolong_agg<8>(out, in, t, P, st, run); break;
+  }
+}
+
+// whether the aggregate kernels serve a transfer: whole nvec-wide thread rows
+// in a CTA of 256, 16-byte prolongator rows
+bool agg_kernels_ok(const TransferGeom& t, const Stored& P) {
+  const int vpc = (int)(16 / store_bytes(P.s));
+  return t.nvec >= 1 && t.nvec <= 256 && t.nvec % vpc == 0;
+}
+
 // the autotuner's choice of systems per CTA for one transfer launch
 template <class F>
 int pick_sb(const char* family, const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P,
-            cudaStream_t st, F&& launch) {
-  if (in.nsys == 1) return 1;
+            cudaStream_t st, F&& launch, bool with_agg) {
   std::vector<TuneCandidate> cands;
   for (int sb : {1, 2, 4, 8})
     if (sb == 1 || sb < 2 * in.nsys) cands.push_back({sb, sb_name(sb)});
+  if (with_agg)
+    for (int sb : {1, 2, 4, 8})
+      if (sb == 1 || sb < 2 * in.nsys) cands.push_back({16 + sb, agg_name(sb)});
+  if (cands.size() == 1) return cands[0].id;
   char key[192];
   std::snprintf(key, sizeof(key), "%s V=%d nvec=%d ndof=%d nsys=%d vec=%s store=%s", family, t.fine.V, t.nvec,
                 t.ndof, in.nsys, in.prec == P64 ? "f64" : "f32",
@@ -486,11 +702,13 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
                  sizeof(int) * 2 * npos <= 200 * 1024;
     };
     if (fits(1)) {
-      int sb = pick_sb("restrict", out, in, t, P, st, [&](int id, const Vec& o) {
-        if (!fits(id) || !restrict_vec_sb(id, o, in, t, P, st, nullptr)) restrict_vec_sb(1, o, in, t, P, st, nullptr);
-      });
-      if (!fits(sb)) sb = 1;
-      restrict_vec_sb(sb, out, in, t, P, st, run);
+      const bool agg = agg_kernels_ok(t, P);
+      auto go = [&](int id, const Vec& o, const int* rr) {
+        if (id >= 16) restrict_agg_sb(id - 16, o, in, t, P, st, rr);
+        else if (!fits(id) || !restrict_vec_sb(id, o, in, t, P, st, rr)) restrict_vec_sb(1, o, in, t, P, st, rr);
+      };
+      const int id = pick_sb("restrict", out, in, t, P, st, [&](int cid, const Vec& o) { go(cid, o, nullptr); }, agg);
+      go(id, out, run);
       return;
     }
   }
@@ -520,9 +738,13 @@ void prolong_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stor
   SMG_REQUIRE(out.n == (long long)t.fine.V * t.ndof && in.n == (long long)t.coarse.V * 2 * t.nvec,
               "prolong: field sizes do not match the transfer");
   SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec, "prolong: batch/precision mismatch");
-  const int sb = pick_sb("prolong", out, in, t, P, st,
-                         [&](int id, const Vec& o) { prolong_sb(id, o, in, t, P, st, nullptr); });
-  prolong_sb(sb, out, in, t, P, st, run);
+  const bool agg = agg_kernels_ok(t, P);
+  auto go = [&](int id, const Vec& o, const int* rr) {
+    if (id >= 16) prolong_agg_sb(id - 16, o, in, t, P, st, rr);
+    else prolong_sb(id, o, in, t, P, st, rr);
+  };
+  const int id = pick_sb("prolong", out, in, t, P, st, [&](int cid, const Vec& o) { go(cid, o, nullptr); }, agg);
+  go(id, out, run);
 }
 
 }  // namespace smg

@@ -1,7 +1,8 @@
 """The autotuner's candidates all compute the same operator.
 
 For each kernel family with several launch shapes (systems per CTA of the
-dslash, the KD block apply, restriction and prolongation; the coarse apply's
+dslash and the KD block apply; kernel and systems per CTA of restriction
+and prolongation; the coarse apply's
 kernels are checked one by one in test_gpu_coarse_shapes), a first call lets the tuner time the candidates and record its
 choice; then every candidate in turn is forced through the table
 (smg_tune_load of "key<TAB>id") and its output compared with the oracle's
@@ -42,7 +43,9 @@ def forced(binding, tmp_path, family, run, check):
     rows = [r for r in binding.tune_table() if r[0].startswith(family + " ")]
     assert rows, (family, binding.tune_table())
     key, chosen, _, times = rows[0]
-    ids = {"1 system/CTA": 1, "2 systems/CTA": 2, "4 systems/CTA": 4, "8 systems/CTA": 8}
+    ids = {"1 system/CTA": 1, "2 systems/CTA": 2, "4 systems/CTA": 4, "8 systems/CTA": 8,
+           "aggregate CTA, 1 system": 17, "aggregate CTA, 2 systems": 18, "aggregate CTA, 4 systems": 20,
+           "aggregate CTA, 8 systems": 24}
     cands = [ids[n] for n in times]
     assert len(cands) >= 2 and chosen in cands, (key, times)
     f = tmp_path / "t.txt"
