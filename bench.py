@@ -67,7 +67,7 @@ SOLVER = {
 # Outer GCR iterations a solve of the workload takes with this algorithm,
 # measured by the GPU path with the same recipe; scales the oracle's
 # per-iteration time in --impl reference (no GPU runs there).
-REF_OUTER_ITERS = {1: 10, 2: 31, 3: 19, 4: 30}
+REF_OUTER_ITERS = {1: 10, 2: 31, 3: 10, 4: 30}
 
 
 # ------------------------------------------------------------------ helpers
@@ -470,6 +470,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     setup_iters = [s.setup_iterations(l) for l in range(len(c["nvec"]))]
+    setup_phases = [{k: round(v, 3) for k, v in s.setup_times(l).items()} for l in range(len(c["nvec"]))]
     log(f"setup {t_setup:.1f} s, CGNE iterations {setup_iters}")
     b = torch.from_numpy(src).to(dev)
     nsys = b.shape[0] * len(masses)
@@ -590,7 +591,8 @@ def run_ours(args):
                        "coarse_inner": [p.coarse_inner_tol or p.inner_tol, p.coarse_inner_maxiter or p.inner_maxiter],
                        "setup_maxiter": p.setup_maxiter, "cuda_graph": bool(args.graph),
                        "l2": "flushed (512 MB write) before every timed step", "setup_s": t_setup,
-                       "setup_cgne_iters": setup_iters, "outer_iters": infos[0].iterations,
+                       "setup_cgne_iters": setup_iters, "setup_phases_s": setup_phases,
+                       "outer_iters": infos[0].iterations,
                        "all_converged": conv, "max_true_residual": res, "timed_wall_s": t_wall,
                        "parallelism": f"replicas x{ws}", "tuned_kernels": binding.tune_table()},
             "e2e": None if e2e is None else {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 16),

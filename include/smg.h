@@ -127,6 +127,14 @@ typedef struct smg_mg_params {
                                       gives every level 0.25; a tighter level-1 rule with Table 1's
                                       rule below it cuts the coarse work at light masses */
   int coarse_inner_maxiter;        /* iteration cap of those levels, 1..16; 0 = inner_maxiter */
+  int galerkin_tc;                 /* Galerkin product A_hat = R A P (Sec. 2.1) with SMG_PREC_HALF:
+                                      1 (default) = from the FP16 prolongator the K-cycle uses, the
+                                      operator parts applied in FP32 with the level's stored links /
+                                      stencil, and the restriction P^dag (A P) on the tensor cores
+                                      (FP16 operands, FP32 sums) wherever that kernel serves the
+                                      transfer (32 or 64 near-null vectors); entries then carry FP16
+                                      rounding, as the stored stencil does.  0 = always the FP64
+                                      product from the FP64 prolongator */
 } smg_mg_params;
 
 /* Fills *p with the defaults above (two-level, 4^4 aggregates, 24 vectors, FP64). */
@@ -280,6 +288,14 @@ SMG_API int smg_fermion_action(smg_ctx* ctx, const void* phi, void* X, void* Y, 
                                double* dSdm, smg_solve_info* info);
 /* Iterations used by the near-null CGNE of coarsening l (max over vectors). */
 SMG_API int smg_setup_iterations(smg_ctx* ctx, int l, int* iters);
+/* Wall-clock seconds that the last smg_mg_setup spent on coarsening l, by
+ * phase (Sec. 3.2 and Table 2 count setup apart from the solves):
+ * secs[0] near-null CGNE, secs[1] chiral doubling, block orthonormalisation
+ * and prolongator packing, secs[2] the Galerkin stencil R A P, secs[3] the
+ * rest (stencil dagger, block preconditioning, packing to storage precision,
+ * dense inverse or deflation of the coarsest level).  The stream is
+ * synchronised at each phase boundary.  After smg_load_setup, secs[0] is 0. */
+SMG_API int smg_setup_times(smg_ctx* ctx, int l, double secs[4]);
 
 /* Kernels that smg_time_kernel can time. */
 enum {
@@ -314,14 +330,18 @@ SMG_API int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int 
  * stencil, FP32 vectors, N % 16 == 0, N <= 128, nsys >= 2); TC_*: tcgen05 + TMA
  * GEMM over up to 16 systems per launch (FP16 stencil, FP32 vectors, N = 128,
  * nsys >= 2) with 1 or 2 persistent CTAs per SM and a 4- or 6-stage stencil
- * ring.  AUTO: the autotuner's choice (below). */
+ * ring; ROWS: CUDA cores, any precision, the V*N output rows of each system
+ * split evenly over a grid that fills every SM once, a half warp per row
+ * (no partly filled last wave when V is not a multiple of the resident
+ * CTAs).  AUTO: the autotuner's choice (below). */
 enum {
   SMG_COARSE_AUTO = 0,
   SMG_COARSE_CORES = 1,
   SMG_COARSE_MMA = 2,
   SMG_COARSE_TC_1x4 = 3,
   SMG_COARSE_TC_2x4 = 4,
-  SMG_COARSE_TC_1x6 = 5
+  SMG_COARSE_TC_1x6 = 5,
+  SMG_COARSE_ROWS = 6
 };
 /* The coarse apply (Sec. 3.1) of a caller's stencil: stencil is FP64
  * [Vc][N][9][N] complex ([site][row][direction][column]; direction 0 self,

@@ -31,7 +31,7 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators", "smg_persist_plan",
            "smg_get_coarse_xinv", "smg_get_deflation", "smg_coarse_solve", "smg_save_setup", "smg_load_setup",
            "smg_coarse_apply_stencil", "smg_coarse_paths", "smg_tune_mode", "smg_tune_table", "smg_tune_save",
-           "smg_tune_load", "smg_tune_clear", "smg_debug_persist_barrier"]
+           "smg_tune_load", "smg_tune_clear", "smg_debug_persist_barrier", "smg_setup_times"]
 
 
 class MGParams(ctypes.Structure):
@@ -59,6 +59,7 @@ class MGParams(ctypes.Structure):
         ("coarsest_basis", ctypes.c_int),
         ("coarse_inner_tol", ctypes.c_double),
         ("coarse_inner_maxiter", ctypes.c_int),
+        ("galerkin_tc", ctypes.c_int),
     ]
 
 
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
         "smg_coarse_apply": (i, [vp, i, i, i, vp, vp, i]),
         "smg_force": (i, [vp, vp, vp, i, vp, i]),
         "smg_setup_iterations": (i, [vp, i, ip]),
+        "smg_setup_times": (i, [vp, i, ctypes.POINTER(d)]),
         "smg_time_kernel": (i, [vp, i, i, i, i, ctypes.POINTER(d)]),
         "smg_kernel_launches": (ctypes.c_longlong, []),
         "smg_fermion_action": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
@@ -142,7 +144,7 @@ def kernel_launches() -> int:
     return int(load().smg_kernel_launches())
 
 
-COARSE_AUTO, COARSE_CORES, COARSE_MMA, COARSE_TC_1x4, COARSE_TC_2x4, COARSE_TC_1x6 = range(6)
+COARSE_AUTO, COARSE_CORES, COARSE_MMA, COARSE_TC_1x4, COARSE_TC_2x4, COARSE_TC_1x6, COARSE_ROWS = range(7)
 
 
 def coarse_paths(N, nsys, prec):
@@ -563,6 +565,13 @@ class Solver:
         v = ctypes.c_int()
         self._check(self.lib.smg_setup_iterations(self.ctx, l, ctypes.byref(v)))
         return v.value
+
+    def setup_times(self, l):
+        """Seconds the last setup spent on coarsening l: dict of the phases
+        cgne, orthonormalise, galerkin, other."""
+        v = (ctypes.c_double * 4)()
+        self._check(self.lib.smg_setup_times(self.ctx, l, v))
+        return dict(zip(("cgne", "orthonormalise", "galerkin", "other"), [float(x) for x in v]))
 
 
 def check_dot_noalloc_args(x, y, out):

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsmg.so")
 
-SOURCES = ["api.cu", "solver.cu", "blas.cu", "dslash.cu", "hop.cu", "kd.cu", "transfer.cu", "coarse.cu", "misc.cu", "persist.cu", "noalloc.cu", "umma.cu", "defl.cu", "deflation.cu", "setup_io.cu", "tune.cu"]
+SOURCES = ["api.cu", "solver.cu", "blas.cu", "dslash.cu", "hop.cu", "kd.cu", "transfer.cu", "transfer_mma.cu", "coarse.cu", "misc.cu", "persist.cu", "noalloc.cu", "umma.cu", "defl.cu", "deflation.cu", "setup_io.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

@@ -100,6 +100,7 @@ void smg_default_params(smg_mg_params* p) {
   p->coarsest_basis = 0;
   p->coarse_inner_tol = 0.0;
   p->coarse_inner_maxiter = 0;
+  p->galerkin_tc = 1;
 }
 
 int smg_create(const int dims[4], smg_ctx** out) {
@@ -378,6 +379,16 @@ int smg_setup_iterations(smg_ctx* ctx, int l, int* iters) {
     if (!c.setup_done) throw smg::StateError("setup_iterations needs mg_setup");
     SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "setup_iterations: bad level");
     *iters = c.coarse[l].setup_iters;
+    return SMG_OK;
+  });
+}
+
+int smg_setup_times(smg_ctx* ctx, int l, double secs[4]) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(secs != nullptr, "setup_times: null output");
+    if (!c.setup_done) throw smg::StateError("setup_times needs mg_setup");
+    SMG_REQUIRE(l >= 0 && l < (int)c.coarse.size(), "setup_times: bad level");
+    for (int i = 0; i < 4; ++i) secs[i] = c.coarse[l].setup_s[i];
     return SMG_OK;
   });
 }

@@ -84,6 +84,70 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(typename cplx<R>::T* 
   }
 }
 
+// The same operator with the V*N output rows of system blockIdx.y split into
+// gridDim.x contiguous ranges that differ by at most one row.  A CTA walks its
+// range site by site, staging each site's nine neighbour vectors in shared
+// memory once, and gives each half warp one row; the grid is sized to the
+// resident CTAs of the GPU, so every SM streams the same share of the stencil.
+template <typename R, typename SL>
+__global__ void __launch_bounds__(256) coarse_apply_rows_kernel(typename cplx<R>::T* __restrict__ out,
+                                                                const typename cplx<R>::T* __restrict__ in,
+                                                                const SL* __restrict__ S,
+                                                                const float* __restrict__ rs, Geom g, int N,
+                                                                int part, int4 agg4,
+                                                                const typename cplx<R>::T* __restrict__ sub_from,
+                                                                const int* run) {
+  using C = typename cplx<R>::T;
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* vin = (C*)smem_raw;   // [9][N]
+  const int s = blockIdx.y;
+  const int agg[4] = {agg4.x, agg4.y, agg4.z, agg4.w};
+  const long long n = (long long)g.V * N;
+  const long long r0 = n * blockIdx.x / gridDim.x, r1 = n * (blockIdx.x + 1) / gridDim.x;
+  const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15, nhw = blockDim.x >> 4;
+  const unsigned hmask = 0xffffu << (threadIdx.x & 16);
+  for (long long row = r0; row < r1;) {
+    const int X = (int)(row / N);
+    const long long rend = min(r1, (long long)(X + 1) * N);
+    int c[4];
+    g.coords(X, c);
+    __syncthreads();   // the previous site's rows are done with vin
+    for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
+      const int dir = e / N, j = e % N;
+      C v = C{0, 0};
+      if (dir_in_part(dir, part, c, agg)) v = in[(size_t)s * n + (size_t)nbr(g, c, dir) * N + j];
+      vin[e] = v;
+    }
+    __syncthreads();
+    for (long long rr = row + hw; rr < rend; rr += nhw) {
+      const int i = (int)(rr - (long long)X * N);
+      const SL* srow = S + ((size_t)X * N + i) * 9 * N;
+      C acc = C{0, 0};
+      if constexpr (sizeof(R) == 4 && sizeof(SL) <= 8) {
+        if (N % 4 == 0) {
+          acc = stencil_row_dot_lanes<16, SL>(srow, N, hl, [&](int dir, int j) { return vin + dir * N + j; });
+        } else {
+          for (int e = hl; e < 9 * N; e += 16) cfma(acc, ld<R>(srow, e), vin[e]);
+        }
+      } else {
+        for (int e = hl; e < 9 * N; e += 16) cfma(acc, ld<R>(srow, e), vin[e]);
+      }
+      for (int o = 8; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(hmask, acc.x, o);
+        acc.y += __shfl_xor_sync(hmask, acc.y, o);
+      }
+      if (hl == 0) {
+        if (rs != nullptr) acc = cscale(acc, (R)rs[(size_t)X * N + i]);
+        const size_t oi = (size_t)s * n + (size_t)X * N + i;
+        if (sub_from != nullptr) acc = csub(sub_from[oi], acc);
+        out[oi] = acc;
+      }
+    }
+    row = rend;
+  }
+}
+
 template <typename SL>
 __global__ void coarse_pack_kernel(SL* __restrict__ dst, float* __restrict__ rs, const double2* __restrict__ S,
                                    long long rows, int N) {
@@ -590,7 +654,8 @@ void launch_mma(const Vec& out, const Vec& in, const CoarseParams& p, const Stor
 bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op) {
   const bool multi16 = vp == P32 && s == S16 && nsys >= 2 && full_op;
   switch (path) {
-    case CPATH_CORES: return 9 * (size_t)N * prec_bytes(vp) <= 48 * 1024;
+    case CPATH_CORES:
+    case CPATH_ROWS: return 9 * (size_t)N * prec_bytes(vp) <= 48 * 1024;
     case CPATH_MMA: return multi16 && N % 16 == 0 && N <= 128;
     case CPATH_UMMA_1x4:
     case CPATH_UMMA_2x4:
@@ -601,7 +666,7 @@ bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op) {
 
 int coarse_path_list(int N, int nsys, Prec vp, Store s, bool full_op, int* out, int cap) {
   int n = 0;
-  for (int path : {CPATH_UMMA_2x4, CPATH_UMMA_1x4, CPATH_UMMA_1x6, CPATH_MMA, CPATH_CORES})
+  for (int path : {CPATH_UMMA_2x4, CPATH_UMMA_1x4, CPATH_UMMA_1x6, CPATH_MMA, CPATH_CORES, CPATH_ROWS})
     if (coarse_path_ok(path, N, nsys, vp, s, full_op)) {
       if (out != nullptr && n < cap) out[n] = path;
       ++n;
@@ -617,6 +682,7 @@ const char* path_name(int path) {
     case CPATH_UMMA_1x4: return "tcgen05 1 CTA/SM 4 stages";
     case CPATH_UMMA_2x4: return "tcgen05 2 CTA/SM 4 stages";
     case CPATH_UMMA_1x6: return "tcgen05 1 CTA/SM 6 stages";
+    case CPATH_ROWS: return "cuda-cores half-warp/row, balanced grid";
     default: return "?";
   }
 }
@@ -646,6 +712,41 @@ void coarse_launch(int path, const Vec& out, const Vec& in, const CoarseParams& 
         else launch_mma<4>(out, in, p, S, st, run, s0);
       }
       return;
+    case CPATH_ROWS: {
+      const size_t smem = (size_t)9 * p.N * prec_bytes(in.prec);
+      SMG_REQUIRE(smem <= 48 * 1024, "coarse_apply: N too large");
+      int4 agg = make_int4(p.agg[0], p.agg[1], p.agg[2], p.agg[3]);
+      const long long rows = (long long)p.g.V * p.N;
+      auto grid_of = [&](auto kernel) {
+        // resident CTAs of this kernel on the whole GPU (host queries, not stream operations)
+        static int per_gpu = 0;
+        if (per_gpu == 0) {
+          int dev = 0, sms = 0, per_sm = 0;
+          SMG_CUDA_OK(cudaGetDevice(&dev));
+          SMG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+          SMG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 48 * 1024));
+          per_gpu = std::max(1, sms * std::max(1, per_sm));
+        }
+        return dim3((unsigned)std::max(1LL, std::min<long long>(per_gpu, (rows + 15) / 16)), in.nsys);
+      };
+      if (in.prec == P64) {
+        SMG_REQUIRE(S.s == S64, "coarse_apply: FP64 vectors need FP64 stencil");
+        auto k = coarse_apply_rows_kernel<double, double2>;
+        launch_k(k, grid_of(k), dim3(256), smem, st, (double2*)out.p, (const double2*)in.p, (const double2*)S.p,
+                 nullptr, p.g, p.N, p.part, agg, (const double2*)p.sub_from, run);
+      } else if (S.s == S32) {
+        auto k = coarse_apply_rows_kernel<float, float2>;
+        launch_k(k, grid_of(k), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const float2*)S.p,
+                 nullptr, p.g, p.N, p.part, agg, (const float2*)p.sub_from, run);
+      } else {
+        SMG_REQUIRE(S.s == S16, "coarse_apply: unsupported storage");
+        auto k = coarse_apply_rows_kernel<float, __half2>;
+        launch_k(k, grid_of(k), dim3(256), smem, st, (float2*)out.p, (const float2*)in.p, (const __half2*)S.p,
+                 S.scale, p.g, p.N, p.part, agg, (const float2*)p.sub_from, run);
+      }
+      SMG_LAUNCH_OK();
+      return;
+    }
     default: break;
   }
   const size_t smem = (size_t)9 * p.N * prec_bytes(in.prec);

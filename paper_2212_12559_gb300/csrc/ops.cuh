@@ -100,6 +100,14 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
 // out (fine) = P in
 void prolong_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
                 const int* run = nullptr);
+// Tensor-core transfers (FP32 vectors, FP16 prolongator, nvec 32 or 64,
+// 16 systems per CTA): whether a transfer has a supported shape, and the two
+// launches (candidates of restrict_op / prolong_op's autotuner).
+bool transfer_mma_ok(const TransferGeom& t, const Stored& P, Prec vp);
+void restrict_mma(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                  const int* run);
+void prolong_mma(const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P, cudaStream_t st,
+                 const int* run);
 
 // ------------------------------------------------------- coarse 9-point op
 // Stencil layout [Vc][N rows][9 dirs][N cols]; dir 0 = self, 1+2mu = hop to
@@ -114,12 +122,13 @@ struct CoarseParams {
   int path = 0;              // CPATH_*: 0 = the tuned (or default) choice for the shape
 };
 // Kernels of the coarse apply: CUDA cores (one CTA per site and system, a warp
-// per row), mma.sync m16n8k16 (several systems, N % 16 == 0, N <= 128), and
+// per row), mma.sync m16n8k16 (several systems, N % 16 == 0, N <= 128),
 // tcgen05 + TMA (several systems, N = 128) with 1 or 2 CTAs per SM and a 4- or
-// 6-stage stencil ring.
+// 6-stage stencil ring, and CUDA cores with the rows split evenly over a grid
+// that fills the GPU once (a half warp per row).
 enum {
   CPATH_AUTO = 0, CPATH_CORES = 1, CPATH_MMA = 2, CPATH_UMMA_1x4 = 3, CPATH_UMMA_2x4 = 4, CPATH_UMMA_1x6 = 5,
-  CPATH_COUNT = 6
+  CPATH_ROWS = 6, CPATH_COUNT = 7
 };
 // Whether a path serves a shape (host logic only).
 bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op);

@@ -1052,6 +1052,31 @@ void op_part64(Context& c, int l, const Vec& out, const Vec& in, Vec& tmp, int p
   }
 }
 
+// The same part of the level-l operator on FP32 vectors with the stored
+// (preconditioner-precision) links, KD blocks or stencil: the operator side
+// of the mixed-precision Galerkin product.
+void op_part_s(Context& c, int l, const Vec& out, const Vec& in, Vec& tmp, int part, const int agg[4]) {
+  const Store sp = c.sstore();
+  if (l == 1) {
+    DslashParams p;
+    p.g = c.g;
+    c.link_params(sp, p, c.trunc1());
+    p.mass0 = c.mass;
+    p.part = part;
+    for (int mu = 0; mu < 4; ++mu) p.agg[mu] = agg[mu];
+    p.nsys = in.nsys;
+    dslash(tmp, in, p, c.stream);
+    const Stored kd = c.kd_of(sp);
+    kd_apply(out, tmp, c.g, &kd, nullptr, 1, 0, c.stream);
+  } else {
+    const CoarseLevel& C = c.coarse[l - 2];
+    CoarseParams p;
+    p.g = C.g; p.N = C.N; p.part = part;
+    for (int mu = 0; mu < 4; ++mu) p.agg[mu] = agg[mu];
+    coarse_apply(out, in, p, C.Ss.st, c.stream);
+  }
+}
+
 // Level-l operator (and adjoint) in preconditioner precision for the setup CGNE.
 struct SetupOp {
   Context& c;
@@ -1140,6 +1165,12 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
     C.tg.ndof = ndof; C.tg.nvec = nvec; C.tg.chi_mode = (l == 0) ? 0 : 1;
     if (l > 0) SMG_REQUIRE(ndof % 2 == 0, "coarse dof must be even");
     const long long n = (long long)fg.V * ndof;
+    auto clock_phase = [&, t = std::chrono::steady_clock::now()](int ph) mutable {
+      SMG_CUDA_OK(cudaStreamSynchronize(st));
+      const auto now = std::chrono::steady_clock::now();
+      C.setup_s[ph] += std::chrono::duration<double>(now - t).count();
+      t = now;
+    };
     // ---- near-null vectors: CGNE on A_l phi = 0 from phi0 (Table 1)
     DevBuf raw;
     raw.alloc((size_t)n * nvec * sizeof(double2));
@@ -1209,6 +1240,7 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
       SMG_CUDA_OK(cudaStreamSynchronize(st));
       for (int v : hit) C.setup_iters = std::max(C.setup_iters, v);
     }
+    clock_phase(0);
     // ---- chiral doubling + block orthonormalisation (FP64); the vectors as
     // the setup produced them are kept for smg_save_setup
     C.pre64.alloc(raw.bytes);
@@ -1223,12 +1255,45 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
     } else {
       C.Ps.st = C.P64.st;
     }
-    // ---- Galerkin stencil by probing R A_part P e_j, FP64
+    clock_phase(1);
+    // ---- Galerkin stencil by probing R A_part P e_j: column j of P on every
+    // aggregate at once is P e_j; the part of A that stays in the aggregate or
+    // crosses into one neighbour, restricted, gives that block column
     const int N = C.N;
     const long long nc = (long long)cg.V * N;
     C.S64.alloc((size_t)nc * 9 * N * sizeof(double2));
     SMG_CUDA_OK(cudaMemsetAsync(C.S64.p, 0, C.S64.bytes, st));
-    {
+    if (P.galerkin_tc && sp == S16 && transfer_mma_ok(C.tg, C.Ps.st, P32)) {
+      // mixed precision: FP16 prolongator (the K-cycle's), FP32 operator
+      // parts, restriction P^dag (A P) on the tensor cores
+      int chunk = N;
+      const size_t per_col = (size_t)n * 8 * 3 + (size_t)nc * (8 * 2 + 16 * 2);
+      while (chunk > 1 && per_col * chunk > ((size_t)16 << 30)) chunk = (chunk + 1) / 2;
+      DevBuf pb;
+      pb.alloc(per_col * chunk);
+      for (int j0 = 0; j0 < N; j0 += chunk) {
+        const int ncol = std::min(chunk, N - j0);
+        char* base = (char*)pb.p;
+        auto vec = [&](size_t off, long long len, Prec pr) {
+          Vec v; v.p = base + off; v.n = len; v.nsys = ncol; v.prec = pr; return v;
+        };
+        const size_t c64 = (size_t)nc * 16 * chunk, c32 = (size_t)nc * 8 * chunk, f32 = (size_t)n * 8 * chunk;
+        Vec E64 = vec(0, nc, P64), Cm64 = vec(c64, nc, P64);
+        Vec E = vec(2 * c64, nc, P32), Cm = vec(2 * c64 + c32, nc, P32);
+        Vec F = vec(2 * c64 + 2 * c32, n, P32), T = vec(2 * c64 + 2 * c32 + f32, n, P32);
+        Vec T2 = vec(2 * c64 + 2 * c32 + 2 * f32, n, P32);
+        unit_probes((double2*)E64.p, cg.V, N, j0, ncol, st);
+        blas_copy(E, E64, st);
+        prolong_op(F, E, C.tg, C.Ps.st, st);
+        for (int dir = 0; dir < 9; ++dir) {
+          op_part_s(c, l + 1, T, F, T2, dir, C.tg.agg);
+          restrict_op(Cm, T, C.tg, C.Ps.st, st);
+          blas_copy(Cm64, Cm, st);
+          galerkin_scatter(C.S64.as<double2>(), (const double2*)Cm64.p, cg, N, dir, j0, ncol, st);
+        }
+      }
+      SMG_CUDA_OK(cudaStreamSynchronize(st));
+    } else {
       int chunk = N;
       const size_t per_col = (size_t)n * 16 * 3 + (size_t)nc * 16 * 2;
       while (chunk > 1 && per_col * chunk > ((size_t)8 << 30)) chunk = (chunk + 1) / 2;
@@ -1253,6 +1318,7 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
       }
       SMG_CUDA_OK(cudaStreamSynchronize(st));
     }
+    clock_phase(2);
     C.Sdag64.alloc(C.S64.bytes);
     coarse_dagger(C.Sdag64.as<double2>(), C.S64.as<double2>(), cg, N, st);
     // ---- block-preconditioned operator X^{-1} A_hat (Sec. 2.3): the level's GCR,
@@ -1310,7 +1376,7 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
       blas_copy(b, a, st);
       C.dense = true;
     }
-    SMG_CUDA_OK(cudaStreamSynchronize(st));
+    clock_phase(3);
     fg = cg;
     ndof = N;
   }
@@ -1332,8 +1398,11 @@ void ctx_mg_setup(Context& c, const smg_mg_params& P, const void* const* phi0, i
       for (int mu = 0; mu < 4; ++mu)
         SMG_REQUIRE(C.g.L[mu] % 2 == 0, "coarsest_schur needs even coarse extents (every hop changes parity)");
     }
+    const auto t0 = std::chrono::steady_clock::now();
     if (restore != nullptr) restore_deflation(c, C, *restore);
     else build_deflation(c, C, phi0[P.n_coarse], where);
+    SMG_CUDA_OK(cudaStreamSynchronize(st));
+    C.setup_s[3] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   c.setup_done = true;
 }

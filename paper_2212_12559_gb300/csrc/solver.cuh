@@ -68,6 +68,11 @@ struct CoarseLevel {
   DevBuf D64, D32;          // dense inverse
   int nd = 0;
   int setup_iters = 0;
+  // wall-clock seconds of this coarsening's setup phases (stream synchronised
+  // at each boundary): near-null CGNE, chiral doubling + block
+  // orthonormalisation + packing, Galerkin stencil, the rest (dagger, block
+  // preconditioning, packing, dense inverse or deflation)
+  double setup_s[4] = {0, 0, 0, 0};
   DevBuf pre64;             // near-null vectors as the setup produced them (before chiral
                             // doubling and block orthonormalisation), FP64 [nvec][V][ndof]:
                             // what smg_save_setup writes

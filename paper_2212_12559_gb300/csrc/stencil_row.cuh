@@ -26,13 +26,14 @@ __device__ __forceinline__ int pick_site(const int nb[9], int dir) {
 // sum_e S[e] * v(e) over the super-row; `vat(dir, j)` returns a pointer to
 // the FP32 input entry j of the neighbour in direction dir (16-byte aligned
 // for even j).
-template <typename SL, typename VAt>
-__device__ __forceinline__ float2 stencil_row_dot(const SL* __restrict__ sr, int N, int lane, VAt vat) {
+// LANES lanes share the row (lane in [0, LANES)).
+template <int LANES, typename SL, typename VAt>
+__device__ __forceinline__ float2 stencil_row_dot_lanes(const SL* __restrict__ sr, int N, int lane, VAt vat) {
   constexpr int C = Chunk<SL>::C;
   const int nchunk = 9 * N / C;
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll 4
-  for (int q = lane; q < nchunk; q += 32) {
+  for (int q = lane; q < nchunk; q += LANES) {
     const int e = q * C;
     const int dir = e / N, j = e - dir * N;
     const uint4 raw = __ldg(reinterpret_cast<const uint4*>(sr + e));
@@ -52,6 +53,12 @@ __device__ __forceinline__ float2 stencil_row_dot(const SL* __restrict__ sr, int
     }
   }
   return make_float2(a0.x + a1.x, a0.y + a1.y);
+}
+
+// A whole warp on the row.
+template <typename SL, typename VAt>
+__device__ __forceinline__ float2 stencil_row_dot(const SL* __restrict__ sr, int N, int lane, VAt vat) {
+  return stencil_row_dot_lanes<32, SL>(sr, N, lane, vat);
 }
 
 }  // namespace smg

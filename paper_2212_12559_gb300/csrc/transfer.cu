@@ -658,15 +658,19 @@ bool agg_kernels_ok(const TransferGeom& t, const Stored& P) {
 }
 
 // the autotuner's choice of systems per CTA for one transfer launch
+// candidate id of the tensor-core kernels
+constexpr int kMmaId = 32;
+
 template <class F>
 int pick_sb(const char* family, const Vec& out, const Vec& in, const TransferGeom& t, const Stored& P,
-            cudaStream_t st, F&& launch, bool with_agg) {
+            cudaStream_t st, F&& launch, bool with_agg, bool with_mma) {
   std::vector<TuneCandidate> cands;
   for (int sb : {1, 2, 4, 8})
     if (sb == 1 || sb < 2 * in.nsys) cands.push_back({sb, sb_name(sb)});
   if (with_agg)
     for (int sb : {1, 2, 4, 8})
       if (sb == 1 || sb < 2 * in.nsys) cands.push_back({16 + sb, agg_name(sb)});
+  if (with_mma) cands.push_back({kMmaId, "tensor cores, 16 systems/CTA"});
   if (cands.size() == 1) return cands[0].id;
   char key[192];
   std::snprintf(key, sizeof(key), "%s V=%d nvec=%d ndof=%d nsys=%d vec=%s store=%s", family, t.fine.V, t.nvec,
@@ -693,7 +697,8 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
   const int npos = t.agg[0] * t.agg[1] * t.agg[2] * t.agg[3];
   const size_t cb = prec_bytes(in.prec);
   const int vpc = (int)(16 / store_bytes(P.s));
-  if (t.nvec % vpc == 0) {
+  const bool mma = transfer_mma_ok(t, P, in.prec);
+  if (t.nvec % vpc == 0 || mma) {
     // vectorised kernel: 512 threads, nvec / vpc threads per row; systems per
     // CTA by the autotuner among the group sizes whose shared memory fits
     const int groups = 512 / (t.nvec / vpc);
@@ -701,13 +706,17 @@ void restrict_op(const Vec& out, const Vec& in, const TransferGeom& t, const Sto
       return cb * ((size_t)groups * 2 * t.nvec + 8 * 2 * t.nvec + (size_t)sb * npos * t.ndof) +
                  sizeof(int) * 2 * npos <= 200 * 1024;
     };
-    if (fits(1)) {
+    if (fits(1) || mma) {
       const bool agg = agg_kernels_ok(t, P);
+      const bool vec = t.nvec % vpc == 0 && fits(1);
       auto go = [&](int id, const Vec& o, const int* rr) {
-        if (id >= 16) restrict_agg_sb(id - 16, o, in, t, P, st, rr);
+        if (id == kMmaId) restrict_mma(o, in, t, P, st, rr);
+        else if (id >= 16) restrict_agg_sb(id - 16, o, in, t, P, st, rr);
+        else if (!vec) restrict_agg_sb(id, o, in, t, P, st, rr);
         else if (!fits(id) || !restrict_vec_sb(id, o, in, t, P, st, rr)) restrict_vec_sb(1, o, in, t, P, st, rr);
       };
-      const int id = pick_sb("restrict", out, in, t, P, st, [&](int cid, const Vec& o) { go(cid, o, nullptr); }, agg);
+      const int id = pick_sb("restrict", out, in, t, P, st, [&](int cid, const Vec& o) { go(cid, o, nullptr); }, agg,
+                             mma);
       go(id, out, run);
       return;
     }
@@ -739,11 +748,14 @@ void prolong_op(const Vec& out, const Vec& in, const TransferGeom& t, const Stor
               "prolong: field sizes do not match the transfer");
   SMG_REQUIRE(in.nsys == out.nsys && in.prec == out.prec, "prolong: batch/precision mismatch");
   const bool agg = agg_kernels_ok(t, P);
+  const bool mma = transfer_mma_ok(t, P, in.prec);
   auto go = [&](int id, const Vec& o, const int* rr) {
-    if (id >= 16) prolong_agg_sb(id - 16, o, in, t, P, st, rr);
+    if (id == kMmaId) prolong_mma(o, in, t, P, st, rr);
+    else if (id >= 16) prolong_agg_sb(id - 16, o, in, t, P, st, rr);
     else prolong_sb(id, o, in, t, P, st, rr);
   };
-  const int id = pick_sb("prolong", out, in, t, P, st, [&](int cid, const Vec& o) { go(cid, o, nullptr); }, agg);
+  const int id = pick_sb("prolong", out, in, t, P, st, [&](int cid, const Vec& o) { go(cid, o, nullptr); }, agg,
+                         mma);
   go(id, out, run);
 }
 

@@ -49,7 +49,8 @@ def test_params_struct_layout(libpath):
     assert p.persistent == 1 and p.truncate_naik == 0 and p.block_coarse == 0
     assert p.coarsest_deflate == 0 and p.coarsest_cheb_s == 8 and p.coarsest_schur == 0
     assert p.schur_coarse == 0 and p.coarsest_basis == 0
-    assert p.coarse_inner_tol == 0.0 and p.coarse_inner_maxiter == 0
+    assert p.coarse_inner_tol == 0.0 and p.coarse_inner_maxiter == 0 and p.galerkin_tc == 1
+    assert ctypes.sizeof(p) == ctypes.sizeof(binding.MGParams)
 
 
 def test_create_rejects_bad_extents(libpath):

@@ -157,6 +157,38 @@ def test_setup_cross_fed(binding, dims, hisq):
 
 
 @pytest.mark.parametrize("hisq", [False, True])
+def test_galerkin_tensor_cores(binding, hisq):
+    """Mixed precision with 32 near-null vectors on both coarsenings: the
+    Galerkin stencils built from the FP16 prolongator, FP32 operator parts and
+    the tensor-core restriction agree with the oracle's FP64 R A P at the FP16
+    bar, per element; with galerkin_tc = 0 the FP64 product agrees to 1e-11.
+    The level-2 product starts from the level-1 stencil each path built."""
+    dims, mass, nv = (8, 8, 8, 8), 0.1, 32
+    fat, naik, c, op = make(dims, hisq, mass, seed=21)
+    lat = op.lat
+    phi1 = inputs.gaussian_fields(nv, lat.V, 3, 71)
+    phi2 = inputs.gaussian_fields(nv, 16, 2 * nv, 72)
+    lop = FineLevelOp(KahlerDirac(op))
+    T1 = Transfer(lat, 3, lop.chirality(), (4, 4, 4, 4), phi1)
+    S1 = galerkin(lop, T1)
+    T2 = Transfer(S1.lat, S1.n, S1.chirality(), (2, 2, 2, 2), phi2)
+    S2 = galerkin(S1, T2)
+    s = binding.Solver(dims)
+    s.set_gauge(fat, naik, c)
+    s.set_mass(mass)
+    kw = dict(n_coarse=2, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[nv, nv], setup_maxiter=0,
+              precision=binding.PREC_HALF)
+    s.mg_setup(binding.default_params(galerkin_tc=1, **kw), [phi1, phi2])
+    got1, got2 = s.coarse_op(0), s.coarse_op(1)
+    assert rel(got1, oracle_stencil_layout(S1)) <= TOL[2]
+    assert rel(got2, oracle_stencil_layout(S2)) <= TOL[2]
+    assert rel(got1, oracle_stencil_layout(S1)) > 1e-9      # the FP16 path really ran
+    s.mg_setup(binding.default_params(galerkin_tc=0, **kw), [phi1, phi2])
+    assert rel(s.coarse_op(0), oracle_stencil_layout(S1)) <= 1e-11
+    assert rel(s.coarse_op(1), oracle_stencil_layout(S2)) <= 1e-11
+
+
+@pytest.mark.parametrize("hisq", [False, True])
 def test_force_kernel(binding, hisq):
     dims = (4, 6, 4, 8)
     fat, naik, c, op = make(dims, hisq, 0.1)
