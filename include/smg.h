@@ -333,7 +333,10 @@ SMG_API int smg_bench_coarse_apply(smg_ctx* ctx, const int cdims[4], int N, int 
  * ring; ROWS: CUDA cores, any precision, the V*N output rows of each system
  * split evenly over a grid that fills every SM once, a half warp per row
  * (no partly filled last wave when V is not a multiple of the resident
- * CTAs).  AUTO: the autotuner's choice (below). */
+ * CTAs); ROWS_MULTI: the same for up to 8 systems per CTA (FP32 vectors,
+ * FP16 or FP32 stencil, N % 4 == 0, nsys >= 2), each stencil chunk loaded
+ * once for the group, vectors kept in FP32 (the near-null CGNE's batched
+ * applies).  AUTO: the autotuner's choice (below). */
 enum {
   SMG_COARSE_AUTO = 0,
   SMG_COARSE_CORES = 1,
@@ -341,7 +344,8 @@ enum {
   SMG_COARSE_TC_1x4 = 3,
   SMG_COARSE_TC_2x4 = 4,
   SMG_COARSE_TC_1x6 = 5,
-  SMG_COARSE_ROWS = 6
+  SMG_COARSE_ROWS = 6,
+  SMG_COARSE_ROWS_MULTI = 7
 };
 /* The coarse apply (Sec. 3.1) of a caller's stencil: stencil is FP64
  * [Vc][N][9][N] complex ([site][row][direction][column]; direction 0 self,

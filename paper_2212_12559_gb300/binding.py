@@ -144,7 +144,8 @@ def kernel_launches() -> int:
     return int(load().smg_kernel_launches())
 
 
-COARSE_AUTO, COARSE_CORES, COARSE_MMA, COARSE_TC_1x4, COARSE_TC_2x4, COARSE_TC_1x6, COARSE_ROWS = range(7)
+(COARSE_AUTO, COARSE_CORES, COARSE_MMA, COARSE_TC_1x4, COARSE_TC_2x4, COARSE_TC_1x6, COARSE_ROWS,
+ COARSE_ROWS_MULTI) = range(8)
 
 
 def coarse_paths(N, nsys, prec):

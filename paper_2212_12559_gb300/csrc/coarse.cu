@@ -148,6 +148,88 @@ __global__ void __launch_bounds__(256) coarse_apply_rows_kernel(typename cplx<R>
   }
 }
 
+// The row-balanced apply for up to SB systems per CTA (FP32 vectors, FP16 or
+// FP32 stencil): each stencil chunk is loaded once and multiplied into every
+// system of the group, in FP32 without rounding the vectors (the kernel of
+// batched applies that must keep FP32 inputs, as the near-null CGNE does).
+template <typename SL, int SB>
+__global__ void __launch_bounds__(256) coarse_apply_rows_multi_kernel(float2* __restrict__ out,
+                                                                      const float2* __restrict__ in,
+                                                                      const SL* __restrict__ S,
+                                                                      const float* __restrict__ rs, Geom g, int N,
+                                                                      int part, int4 agg4,
+                                                                      const float2* __restrict__ sub_from, int nsys,
+                                                                      const int* run) {
+  constexpr int C = Chunk<SL>::C;
+  if (run != nullptr && *run == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* vin = (float2*)smem_raw;   // [SB][9][N]
+  const int s0 = blockIdx.y * SB, ns = min(SB, nsys - s0);
+  const int agg[4] = {agg4.x, agg4.y, agg4.z, agg4.w};
+  const long long n = (long long)g.V * N;
+  const long long r0 = n * blockIdx.x / gridDim.x, r1 = n * (blockIdx.x + 1) / gridDim.x;
+  const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15, nhw = blockDim.x >> 4;
+  const unsigned hmask = 0xffffu << (threadIdx.x & 16);
+  const int nine = 9 * N, nchunk = 9 * N / C;
+  for (long long row = r0; row < r1;) {
+    const int X = (int)(row / N);
+    const long long rend = min(r1, (long long)(X + 1) * N);
+    int c[4];
+    g.coords(X, c);
+    __syncthreads();
+    for (int e = threadIdx.x; e < SB * nine; e += blockDim.x) {
+      const int sb = e / nine, q = e - sb * nine;
+      const int dir = q / N, j = q - dir * N;
+      float2 v = make_float2(0.f, 0.f);
+      if (sb < ns && dir_in_part(dir, part, c, agg)) v = in[(size_t)(s0 + sb) * n + (size_t)nbr(g, c, dir) * N + j];
+      vin[e] = v;
+    }
+    __syncthreads();
+    for (long long rr = row + hw; rr < rend; rr += nhw) {
+      const int i = (int)(rr - (long long)X * N);
+      const SL* srow = S + ((size_t)X * N + i) * 9 * N;
+      float2 acc[SB];
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) acc[sb] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int q = hl; q < nchunk; q += 16) {
+        const int e = q * C;
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(srow + e));
+        const SL* m = reinterpret_cast<const SL*>(&raw);
+        float2 mf[C];
+#pragma unroll
+        for (int u = 0; u < C; ++u) mf[u] = ld<float>(m, u);
+#pragma unroll
+        for (int sb = 0; sb < SB; ++sb) {
+          const float4* v = reinterpret_cast<const float4*>(vin + sb * nine + e);
+#pragma unroll
+          for (int u = 0; u < C; u += 2) {
+            const float4 vv = v[u / 2];
+            cfma(acc[sb], mf[u], make_float2(vv.x, vv.y));
+            cfma(acc[sb], mf[u + 1], make_float2(vv.z, vv.w));
+          }
+        }
+      }
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb)
+        for (int o = 8; o > 0; o >>= 1) {
+          acc[sb].x += __shfl_xor_sync(hmask, acc[sb].x, o);
+          acc[sb].y += __shfl_xor_sync(hmask, acc[sb].y, o);
+        }
+      const float sc = rs != nullptr ? rs[(size_t)X * N + i] : 1.f;
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb)
+        if (hl == sb && sb < ns) {
+          float2 a = cscale(acc[sb], sc);
+          const size_t oi = (size_t)(s0 + sb) * n + (size_t)X * N + i;
+          if (sub_from != nullptr) a = csub(sub_from[oi], a);
+          out[oi] = a;
+        }
+    }
+    row = rend;
+  }
+}
+
 template <typename SL>
 __global__ void coarse_pack_kernel(SL* __restrict__ dst, float* __restrict__ rs, const double2* __restrict__ S,
                                    long long rows, int N) {
@@ -651,11 +733,17 @@ void launch_mma(const Vec& out, const Vec& in, const CoarseParams& p, const Stor
   SMG_LAUNCH_OK();
 }
 
+namespace {
+constexpr int kRowsMultiSys = 8;   // systems per CTA of the multi-system row-balanced kernel
+size_t rows_multi_smem(int N) { return (size_t)kRowsMultiSys * 9 * N * sizeof(float2); }
+}  // namespace
+
 bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op) {
   const bool multi16 = vp == P32 && s == S16 && nsys >= 2 && full_op;
   switch (path) {
     case CPATH_CORES:
     case CPATH_ROWS: return 9 * (size_t)N * prec_bytes(vp) <= 48 * 1024;
+    case CPATH_ROWS_MULTI: return vp == P32 && s != S64 && nsys >= 2 && N % 4 == 0 && rows_multi_smem(N) <= 200 * 1024;
     case CPATH_MMA: return multi16 && N % 16 == 0 && N <= 128;
     case CPATH_UMMA_1x4:
     case CPATH_UMMA_2x4:
@@ -666,7 +754,8 @@ bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op) {
 
 int coarse_path_list(int N, int nsys, Prec vp, Store s, bool full_op, int* out, int cap) {
   int n = 0;
-  for (int path : {CPATH_UMMA_2x4, CPATH_UMMA_1x4, CPATH_UMMA_1x6, CPATH_MMA, CPATH_CORES, CPATH_ROWS})
+  for (int path : {CPATH_UMMA_2x4, CPATH_UMMA_1x4, CPATH_UMMA_1x6, CPATH_MMA, CPATH_CORES, CPATH_ROWS,
+                   CPATH_ROWS_MULTI})
     if (coarse_path_ok(path, N, nsys, vp, s, full_op)) {
       if (out != nullptr && n < cap) out[n] = path;
       ++n;
@@ -683,6 +772,7 @@ const char* path_name(int path) {
     case CPATH_UMMA_2x4: return "tcgen05 2 CTA/SM 4 stages";
     case CPATH_UMMA_1x6: return "tcgen05 1 CTA/SM 6 stages";
     case CPATH_ROWS: return "cuda-cores half-warp/row, balanced grid";
+    case CPATH_ROWS_MULTI: return "cuda-cores half-warp/row, balanced grid, 8 systems/CTA";
     default: return "?";
   }
 }
@@ -747,6 +837,37 @@ void coarse_launch(int path, const Vec& out, const Vec& in, const CoarseParams& 
       SMG_LAUNCH_OK();
       return;
     }
+    case CPATH_ROWS_MULTI: {
+      const size_t smem = rows_multi_smem(p.N);
+      int4 agg = make_int4(p.agg[0], p.agg[1], p.agg[2], p.agg[3]);
+      const long long rows = (long long)p.g.V * p.N;
+      const dim3 block(256);
+      auto go = [&](auto kernel, auto* S_p) {
+        static int per_sm = -1;
+        static size_t smem_set = 0;
+        if (smem > 48 * 1024 && smem > smem_set) {
+          SMG_CUDA_OK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          smem_set = smem;
+          per_sm = -1;
+        }
+        static int sms = 0;
+        if (per_sm < 0) {
+          int dev = 0;
+          SMG_CUDA_OK(cudaGetDevice(&dev));
+          SMG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+          SMG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem));
+        }
+        const long long per_gpu = std::max(1, sms * std::max(1, per_sm));
+        const dim3 grid((unsigned)std::max(1LL, std::min<long long>(per_gpu, (rows + 15) / 16)),
+                        ceil_div(in.nsys, kRowsMultiSys));
+        launch_k(kernel, grid, block, smem, st, (float2*)out.p, (const float2*)in.p, S_p,
+                 S.s == S16 ? S.scale : nullptr, p.g, p.N, p.part, agg, (const float2*)p.sub_from, in.nsys, run);
+      };
+      if (S.s == S32) go(coarse_apply_rows_multi_kernel<float2, kRowsMultiSys>, (const float2*)S.p);
+      else go(coarse_apply_rows_multi_kernel<__half2, kRowsMultiSys>, (const __half2*)S.p);
+      SMG_LAUNCH_OK();
+      return;
+    }
     default: break;
   }
   const size_t smem = (size_t)9 * p.N * prec_bytes(in.prec);
@@ -779,17 +900,25 @@ void coarse_apply(const Vec& out, const Vec& in, const CoarseParams& p, const St
   SMG_REQUIRE(in.n == (long long)p.g.V * p.N && out.n == in.n && in.nsys == out.nsys && in.prec == out.prec,
               "coarse_apply: shape mismatch");
   const bool full = p.part < 0;
-  int path = p.allow_tc ? p.path : CPATH_CORES;
+  auto is_tc = [](int id) { return id == CPATH_MMA || id == CPATH_UMMA_1x4 || id == CPATH_UMMA_2x4 || id == CPATH_UMMA_1x6; };
+  int path = p.path;
+  if (!p.allow_tc && is_tc(path)) path = CPATH_AUTO;
   if (path == CPATH_AUTO) {
-    const std::vector<TuneCandidate> cands = coarse_candidates(p.N, in.nsys, in.prec, S.s, full);
+    std::vector<TuneCandidate> cands = coarse_candidates(p.N, in.nsys, in.prec, S.s, full);
+    if (!p.allow_tc) {
+      std::vector<TuneCandidate> keep;
+      for (const auto& cd : cands)
+        if (!is_tc(cd.id)) keep.push_back(cd);
+      cands.swap(keep);
+    }
     SMG_REQUIRE(!cands.empty(), "coarse_apply: no kernel serves this shape");
     if (cands.size() == 1) {
       path = cands[0].id;
     } else {
       char key[160];
-      std::snprintf(key, sizeof(key), "coarse_apply V=%d N=%d nsys=%d vec=%s store=%s sub=%d", p.g.V, p.N, in.nsys,
-                    in.prec == P64 ? "f64" : "f32", S.s == S16 ? "f16" : (S.s == S32 ? "f32" : "f64"),
-                    p.sub_from != nullptr ? 1 : 0);
+      std::snprintf(key, sizeof(key), "coarse_apply V=%d N=%d nsys=%d vec=%s store=%s sub=%d%s%s", p.g.V, p.N,
+                    in.nsys, in.prec == P64 ? "f64" : "f32", S.s == S16 ? "f16" : (S.s == S32 ? "f32" : "f64"),
+                    p.sub_from != nullptr ? 1 : 0, p.allow_tc ? "" : " fp32-inputs", full ? "" : " part");
       // candidates write a scratch output (freed after tuning)
       struct Scratch {
         void* p = nullptr;

@@ -125,10 +125,11 @@ struct CoarseParams {
 // per row), mma.sync m16n8k16 (several systems, N % 16 == 0, N <= 128),
 // tcgen05 + TMA (several systems, N = 128) with 1 or 2 CTAs per SM and a 4- or
 // 6-stage stencil ring, and CUDA cores with the rows split evenly over a grid
-// that fills the GPU once (a half warp per row).
+// that fills the GPU once (a half warp per row; one system, or up to 8
+// systems per CTA with FP32 vectors).
 enum {
   CPATH_AUTO = 0, CPATH_CORES = 1, CPATH_MMA = 2, CPATH_UMMA_1x4 = 3, CPATH_UMMA_2x4 = 4, CPATH_UMMA_1x6 = 5,
-  CPATH_ROWS = 6, CPATH_COUNT = 7
+  CPATH_ROWS = 6, CPATH_ROWS_MULTI = 7, CPATH_COUNT = 8
 };
 // Whether a path serves a shape (host logic only).
 bool coarse_path_ok(int path, int N, int nsys, Prec vp, Store s, bool full_op);

@@ -183,7 +183,7 @@ CONFIGS = {
     3: dict(dims=(32, 32, 32, 32), hisq=False, mass=0.001, agg=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[64, 32],
             precision="mixed", nrhs=12, masses=None, seeds=(1003, 2003, 3003)),
     4: dict(dims=(24, 24, 24, 48), hisq=True, mass=0.001, agg=[(4, 4, 4, 4), (2, 2, 2, 2)],
-            nvec=[24, 32], precision="mixed", nrhs=4, masses="log8", seeds=(1004, 2004, 3004)),
+            nvec=[64, 32], precision="mixed", nrhs=4, masses="log8", seeds=(1004, 2004, 3004)),
     5: dict(dims=(16, 16, 16, 16), hisq=False, mass=0.02, agg=[(4, 4, 4, 4)], nvec=[24],
             precision="double", nrhs=1, masses=None, seeds=(1005, 2005, 3005)),
 }

@@ -16,17 +16,19 @@ def test_coarse_candidates_by_shape(binding):
     b = binding
     tc = [b.COARSE_TC_2x4, b.COARSE_TC_1x4, b.COARSE_TC_1x6]
     cores = [b.COARSE_CORES, b.COARSE_ROWS]
+    multi = cores + [b.COARSE_ROWS_MULTI]    # several FP32-vector systems, N % 4 == 0
     # tcgen05 needs N = 128, FP16 storage and several systems; its default comes first
-    assert b.coarse_paths(128, 12, b.PREC_HALF) == tc + [b.COARSE_MMA] + cores
-    assert b.coarse_paths(128, 2, b.PREC_HALF) == tc + [b.COARSE_MMA] + cores
-    # one system: only the two CUDA-core kernels
+    assert b.coarse_paths(128, 12, b.PREC_HALF) == tc + [b.COARSE_MMA] + multi
+    assert b.coarse_paths(128, 2, b.PREC_HALF) == tc + [b.COARSE_MMA] + multi
+    # one system: only the two one-system CUDA-core kernels
     assert b.coarse_paths(128, 1, b.PREC_HALF) == cores
     # mma.sync: N % 16 == 0 and N <= 128
-    assert b.coarse_paths(48, 12, b.PREC_HALF) == [b.COARSE_MMA] + cores
-    assert b.coarse_paths(40, 12, b.PREC_HALF) == cores
-    assert b.coarse_paths(144, 12, b.PREC_HALF) == cores
+    assert b.coarse_paths(48, 12, b.PREC_HALF) == [b.COARSE_MMA] + multi
+    assert b.coarse_paths(40, 12, b.PREC_HALF) == multi
+    assert b.coarse_paths(144, 12, b.PREC_HALF) == multi
+    assert b.coarse_paths(42, 12, b.PREC_HALF) == cores
     # FP32 / FP64 storage: CUDA cores only, while 9N vector entries fit 48 KB of shared memory
-    assert b.coarse_paths(128, 12, b.PREC_SINGLE) == cores
+    assert b.coarse_paths(128, 12, b.PREC_SINGLE) == multi
     assert b.coarse_paths(256, 4, b.PREC_DOUBLE) == cores
     assert b.coarse_paths(512, 4, b.PREC_DOUBLE) == []
     with pytest.raises(b.SmgError):
