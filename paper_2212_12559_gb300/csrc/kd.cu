@@ -9,6 +9,7 @@
 // kd_apply multiplies every hypercube of a batched field by its inverse.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "ops.cuh"
@@ -147,6 +148,109 @@ struct KdSet {
 // 4 hypercubes per CTA, one thread per output row; SB systems per CTA
 // (blockIdx.y picks the group, which shares one block inverse), so each block
 // entry is read once for the whole group.
+// FP32 vectors, two rows per thread: eight hypercubes per CTA of 192
+// threads, thread (hypercube lb, row pair rp) computes rows 2rp and 2rp + 1
+// for SB systems.  The block entries of a column pair come in two 8-byte
+// (FP16) or 16-byte (FP32) loads and each staged vector pair in one 16-byte
+// shared load, which then feeds eight complex multiply-adds per system.
+template <typename SL, int SB>
+__global__ void __launch_bounds__(192) kd_apply2_kernel(float2* __restrict__ out, const float2* __restrict__ in,
+                                                        KdSet kd, const int* __restrict__ sys_map, int dagger,
+                                                        long long nblk, Geom g, const float2* __restrict__ sub_from,
+                                                        int nsys, const int* run) {
+  constexpr int PB = NB / 2;   // row pairs per hypercube
+  using P2 = typename std::conditional<sizeof(SL) == 4, uint2, uint4>::type;   // two consecutive entries
+  if (run != nullptr && *run == 0) return;
+  __shared__ __align__(16) float2 vin[SB][8][NB];
+  const int s0 = blockIdx.y * SB;
+  const int ns = min(SB, nsys - s0);
+  const int lb = threadIdx.x / PB, rp = threadIdx.x % PB;
+  const int r0 = 2 * rp;
+  const long long blk = (long long)blockIdx.x * 8 + lb;
+  const long long vs = (long long)g.V * 3;
+  const int kidx = sys_map != nullptr ? sys_map[s0] : 0;
+  const SL* K = (const SL*)kd.p[kidx];
+  const float* sc = kd.scale[kidx];
+  int site0 = 0, site1 = 0;
+  if (blk < nblk) {
+    site0 = hypercube_site(g, (int)blk, r0 / 3);
+    site1 = hypercube_site(g, (int)blk, (r0 + 1) / 3);
+#pragma unroll
+    for (int sb = 0; sb < SB; ++sb)
+      if (sb < ns) {
+        vin[sb][lb][r0] = in[(s0 + sb) * vs + (size_t)site0 * 3 + (r0 % 3)];
+        vin[sb][lb][r0 + 1] = in[(s0 + sb) * vs + (size_t)site1 * 3 + ((r0 + 1) % 3)];
+      }
+  }
+  __syncthreads();
+  if (blk >= nblk) return;
+  const SL* Kb = K + (size_t)blk * NB * NB;
+  float2 a0[SB], a1[SB];
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb) { a0[sb] = make_float2(0.f, 0.f); a1[sb] = a0[sb]; }
+  auto pair = [](const SL* p, float2& x, float2& y) {
+    const P2 raw = __ldg(reinterpret_cast<const P2*>(p));
+    const SL* e = reinterpret_cast<const SL*>(&raw);
+    x = ld<float>(e, 0);
+    y = ld<float>(e, 1);
+  };
+  if (!dagger) {
+    // out[r] = sum_c K[c][r] v[c], K stored column by column
+#pragma unroll 4
+    for (int c = 0; c < NB; c += 2) {
+      float2 k00, k01, k10, k11;   // k<column><row>
+      pair(Kb + (size_t)c * NB + r0, k00, k01);
+      pair(Kb + (size_t)(c + 1) * NB + r0, k10, k11);
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) {
+        const float4 v = *reinterpret_cast<const float4*>(&vin[sb][lb][c]);
+        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+        cfma(a0[sb], k00, v0);
+        cfma(a0[sb], k10, v1);
+        cfma(a1[sb], k01, v0);
+        cfma(a1[sb], k11, v1);
+      }
+    }
+    if (sc != nullptr) {
+      const float f0 = sc[blk * NB + r0], f1 = sc[blk * NB + r0 + 1];
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) { a0[sb] = cscale(a0[sb], f0); a1[sb] = cscale(a1[sb], f1); }
+    }
+  } else {
+    // out[r] = sum_c conj(K[r][c]) v[c] (K^dag), the scale of column c on each entry
+#pragma unroll 4
+    for (int c = 0; c < NB; c += 2) {
+      float2 k00, k01, k10, k11;   // k<row><column>
+      pair(Kb + (size_t)r0 * NB + c, k00, k01);
+      pair(Kb + (size_t)(r0 + 1) * NB + c, k10, k11);
+      if (sc != nullptr) {
+        const float f0 = sc[blk * NB + c], f1 = sc[blk * NB + c + 1];
+        k00 = cscale(k00, f0); k10 = cscale(k10, f0);
+        k01 = cscale(k01, f1); k11 = cscale(k11, f1);
+      }
+#pragma unroll
+      for (int sb = 0; sb < SB; ++sb) {
+        const float4 v = *reinterpret_cast<const float4*>(&vin[sb][lb][c]);
+        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+        cfmac(a0[sb], k00, v0);
+        cfmac(a0[sb], k01, v1);
+        cfmac(a1[sb], k10, v0);
+        cfmac(a1[sb], k11, v1);
+      }
+    }
+  }
+#pragma unroll
+  for (int sb = 0; sb < SB; ++sb) {
+    if (sb >= ns) break;
+    const size_t o0 = (s0 + sb) * vs + (size_t)site0 * 3 + (r0 % 3);
+    const size_t o1 = (s0 + sb) * vs + (size_t)site1 * 3 + ((r0 + 1) % 3);
+    float2 v0 = a0[sb], v1 = a1[sb];
+    if (sub_from != nullptr) { v0 = csub(sub_from[o0], v0); v1 = csub(sub_from[o1], v1); }
+    out[o0] = v0;
+    out[o1] = v1;
+  }
+}
+
 template <typename R, typename SL, int SB>
 __global__ void __launch_bounds__(192) kd_apply_kernel(typename cplx<R>::T* __restrict__ out,
                                                        const typename cplx<R>::T* __restrict__ in, KdSet kd,
@@ -217,6 +321,26 @@ void launch_kd(const Vec& out, const Vec& in, const KdSet& set, const int* sys_m
            g, (const C*)sub_from, in.nsys, run);
 }
 
+template <typename SL, int SB>
+void launch_kd2(const Vec& out, const Vec& in, const KdSet& set, const int* sys_map, int dagger, long long nblk,
+                const Geom& g, const void* sub_from, cudaStream_t st, const int* run) {
+  dim3 grid(ceil_div(nblk, 8), ceil_div(in.nsys, SB));
+  launch_k(kd_apply2_kernel<SL, SB>, grid, dim3(192), 0, st, (float2*)out.p, (const float2*)in.p, set, sys_map,
+           dagger, nblk, g, (const float2*)sub_from, in.nsys, run);
+}
+
+template <typename SL>
+void launch_kd2_sb(int sb, const Vec& out, const Vec& in, const KdSet& set, const int* sys_map, int dagger,
+                   long long nblk, const Geom& g, const void* sub_from, cudaStream_t st, const int* run) {
+  switch (sb) {
+    case 1: launch_kd2<SL, 1>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+    case 2: launch_kd2<SL, 2>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+    case 4: launch_kd2<SL, 4>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+    case 8: launch_kd2<SL, 8>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+    default: launch_kd2<SL, 16>(out, in, set, sys_map, dagger, nblk, g, sub_from, st, run); break;
+  }
+}
+
 template <typename R, typename SL>
 void launch_kd_sb(int sb, const Vec& out, const Vec& in, const KdSet& set, const int* sys_map, int dagger,
                   long long nblk, const Geom& g, const void* sub_from, cudaStream_t st, const int* run) {
@@ -265,7 +389,15 @@ void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, co
   // kd_run consecutive systems share one inverse, and the group size must
   // divide it; with one inverse any group size serves
   const int run_len = (sys_map == nullptr) ? 0 : std::max(1, kd_run);
+  // candidate ids: sb = systems per CTA of the one-row kernel, 32 + sb those of the two-row kernel
+  const bool two_row = in.prec == P32 && (kd[0].s == S16 || kd[0].s == S32);
   auto go = [&](int sb, const Vec& o, const int* rr) {
+    if (sb >= 32) {
+      if (kd[0].s == S32) launch_kd2_sb<float2>(sb - 32, o, in, set, sys_map, dagger, nblk, g, sub_from, st, rr);
+      else launch_kd2_sb<__half2>(sb - 32, o, in, set, sys_map, dagger, nblk, g, sub_from, st, rr);
+      SMG_LAUNCH_OK();
+      return;
+    }
     if (in.prec == P64) {
       SMG_REQUIRE(kd[0].s == S64, "kd_apply: FP64 vectors need FP64 blocks");
       launch_kd_sb<double, double2>(sb, o, in, set, sys_map, dagger, nblk, g, sub_from, st, rr);
@@ -283,6 +415,12 @@ void kd_apply(const Vec& out, const Vec& in, const Geom& g, const Stored* kd, co
     if (sb == 1 || (sb < 2 * in.nsys && (run_len == 0 || run_len % sb == 0)))
       cands.push_back({sb, sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA" : sb == 4 ? "4 systems/CTA"
                                                                                       : "8 systems/CTA"});
+  if (two_row)
+    for (int sb : {1, 2, 4, 8, 16})
+      if (sb == 1 || (sb < 2 * in.nsys && (run_len == 0 || run_len % sb == 0)))
+        cands.push_back({32 + sb, sb == 1 ? "2 rows/thread, 1 system/CTA" : sb == 2 ? "2 rows/thread, 2 systems/CTA"
+                                  : sb == 4 ? "2 rows/thread, 4 systems/CTA" : sb == 8 ? "2 rows/thread, 8 systems/CTA"
+                                                                                       : "2 rows/thread, 16 systems/CTA"});
   int sb = 1;
   if (cands.size() > 1) {
     char key[160];

@@ -46,7 +46,10 @@ def forced(binding, tmp_path, family, run, check, want=None):
     key, chosen, _, times = rows[0]
     ids = {"1 system/CTA": 1, "2 systems/CTA": 2, "4 systems/CTA": 4, "8 systems/CTA": 8,
            "aggregate CTA, 1 system": 17, "aggregate CTA, 2 systems": 18, "aggregate CTA, 4 systems": 20,
-           "aggregate CTA, 8 systems": 24, "tensor cores, 16 systems/CTA": 32}
+           "aggregate CTA, 8 systems": 24, "tensor cores, 16 systems/CTA": 32,
+           "2 rows/thread, 1 system/CTA": 33, "2 rows/thread, 2 systems/CTA": 34,
+           "2 rows/thread, 4 systems/CTA": 36, "2 rows/thread, 8 systems/CTA": 40,
+           "2 rows/thread, 16 systems/CTA": 48}
     cands = [ids[n] for n in times]
     assert len(cands) >= 2 and chosen in cands, (key, times)
     assert want is None or want in cands, (key, times)
