@@ -224,7 +224,8 @@ void launch_hop_sb(int sb, const Vec& out, const Vec& in, const DslashParams& p,
     case 1: launch_hop<SL, K, 1>(out, in, p, st, run); break;
     case 2: launch_hop<SL, K, 2>(out, in, p, st, run); break;
     case 4: launch_hop<SL, K, 4>(out, in, p, st, run); break;
-    default: launch_hop<SL, K, 8>(out, in, p, st, run); break;
+    case 8: launch_hop<SL, K, 8>(out, in, p, st, run); break;
+    default: launch_hop<SL, K, 16>(out, in, p, st, run); break;
   }
 }
 
@@ -282,9 +283,10 @@ void hop_dslash(const Vec& out, const Vec& in, const DslashParams& p, cudaStream
     return;
   }
   std::vector<TuneCandidate> cands;
-  for (int sb : {1, 2, 4, 8})
-    if (sb == 1 || sb < 2 * p.nsys) cands.push_back({sb, sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA"
-                                                                   : sb == 4 ? "4 systems/CTA" : "8 systems/CTA"});
+  for (int sb : {1, 2, 4, 8, 16})
+    if (sb == 1 || sb < 2 * p.nsys)
+      cands.push_back({sb, sb == 1 ? "1 system/CTA" : sb == 2 ? "2 systems/CTA" : sb == 4 ? "4 systems/CTA"
+                                                         : sb == 8 ? "8 systems/CTA" : "16 systems/CTA"});
   char key[160];
   std::snprintf(key, sizeof(key), "hop_dslash V=%d nsys=%d store=%s naik=%d sub=%d", p.g.V, p.nsys,
                 p.hop.s == S16 ? "f16" : "f32", p.hop_kinds == 2 ? 1 : 0, p.sub_from != nullptr ? 1 : 0);

@@ -44,7 +44,7 @@ def forced(binding, tmp_path, family, run, check, want=None):
     rows = [r for r in binding.tune_table() if r[0].startswith(family + " ")]
     assert rows, (family, binding.tune_table())
     key, chosen, _, times = rows[0]
-    ids = {"1 system/CTA": 1, "2 systems/CTA": 2, "4 systems/CTA": 4, "8 systems/CTA": 8,
+    ids = {"1 system/CTA": 1, "2 systems/CTA": 2, "4 systems/CTA": 4, "8 systems/CTA": 8, "16 systems/CTA": 16,
            "aggregate CTA, 1 system": 17, "aggregate CTA, 2 systems": 18, "aggregate CTA, 4 systems": 20,
            "aggregate CTA, 8 systems": 24, "tensor cores, 16 systems/CTA": 32,
            "2 rows/thread, 1 system/CTA": 33, "2 rows/thread, 2 systems/CTA": 34,
@@ -63,9 +63,10 @@ def forced(binding, tmp_path, family, run, check, want=None):
     binding.tune_clear()
 
 
-@pytest.mark.parametrize("hisq", [False, True])
-def test_fine_kernels_every_candidate(binding, tmp_path, hisq):
-    dims, mass, nsys = (8, 4, 6, 10), 0.05, 5
+@pytest.mark.parametrize("hisq,nsys", [(False, 5), (True, 5), (False, 12), (True, 12)])
+def test_fine_kernels_every_candidate(binding, tmp_path, hisq, nsys):
+    """12 systems bring the 16-systems-per-CTA candidates in (one group)."""
+    dims, mass = (8, 4, 6, 10), 0.05
     thin = inputs.random_su3_links(dims, 7)
     if hisq:
         fat, naik, c = inputs.fat_links(thin, dims), inputs.naik_links(thin, dims), -1 / 24
