@@ -267,7 +267,7 @@ bool hop_dslash_ok(const Vec& in, const DslashParams& p) {
 void hop_dslash_sb(int sb, const Vec& out, const Vec& in, const DslashParams& p, cudaStream_t st, const int* run) {
   SMG_REQUIRE(in.n == (long long)p.g.V * 3 && out.n == in.n, "dslash: field size does not match the lattice");
   SMG_REQUIRE(in.nsys == p.nsys && out.nsys == p.nsys && in.prec == P32 && out.prec == P32, "dslash: batch mismatch");
-  SMG_REQUIRE(sb == 1 || sb == 2 || sb == 4 || sb == 8, "dslash: 1, 2, 4 or 8 systems per CTA");
+  SMG_REQUIRE(sb == 1 || sb == 2 || sb == 4 || sb == 8 || sb == 16, "dslash: 1, 2, 4, 8 or 16 systems per CTA");
   if (p.hop.s == S16) {
     if (p.hop_kinds == 2) launch_hop_sb<__half2, 2>(sb, out, in, p, st, run);
     else launch_hop_sb<__half2, 1>(sb, out, in, p, st, run);
