@@ -17,6 +17,11 @@ Test infrastructure (oracle).  Definitions followed:
 * (B + m)^{-1} is block local: one dense 48x48 matrix per hypercube
   (16 sites x 3 colours), ordered (position b, colour a) -> 3*b + a (Sec. 3.1).
 * A = (B + m)^{-1} M (Eq. 2 with the mass, Sec. 3.1).
+* Boundary conditions: periodic, or antiperiodic in time (``bc_t = -1``):
+  psi(x + L_t t) = -psi(x), so a hop whose neighbour wraps around the time
+  extent carries a factor -1.  (Thermal / propagator work on staggered
+  fermions uses the antiperiodic time boundary; the paper does not state its
+  boundary conditions.)
 """
 from __future__ import annotations
 
@@ -32,14 +37,25 @@ def _dag(m):
 class Staggered:
     """M = m + D on one lattice, optionally with Naik links."""
 
-    def __init__(self, lat: Lattice, fat, naik=None, c_naik: float = 0.0, mass: float = 0.0):
+    def __init__(self, lat: Lattice, fat, naik=None, c_naik: float = 0.0, mass: float = 0.0, bc_t: int = 1):
         self.lat = lat
         self.fat = np.asarray(fat, dtype=np.complex128)
         self.naik = None if naik is None else np.asarray(naik, dtype=np.complex128)
         self.c_naik = float(c_naik)
         self.mass = float(mass)
+        assert bc_t in (1, -1)
+        self.bc_t = int(bc_t)
         assert self.fat.shape == (4, lat.V, 3, 3)
         self._eta = [lat.eta(mu) for mu in range(4)]
+
+    def boundary_phase(self, mu, k):
+        """Per site: the factor of psi(x + k mu) relative to the periodic
+        value, -1 where an antiperiodic time hop wraps around, else +1."""
+        if mu != 3 or self.bc_t == 1:
+            return np.ones(self.lat.V)
+        t = self.lat.coords[:, 3] + k
+        wraps = (t >= self.lat.dims[3]) | (t < 0)
+        return np.where(wraps, -1.0, 1.0)
 
     # -- individual hops -------------------------------------------------------
     def _hops(self):
@@ -67,7 +83,7 @@ class Staggered:
         else:
             n = lat.neighbor(mu, -k)
             t = -np.einsum("xab,xb->xa", _dag(links[mu][n]), psi[n])
-        return coef * self._eta[mu][:, None] * t
+        return coef * (self._eta[mu] * self.boundary_phase(mu, sign * k))[:, None] * t
 
     def D(self, psi):
         out = np.zeros_like(psi, dtype=np.complex128)

@@ -41,7 +41,8 @@ def link_gradient(op: Staggered, x, y, naik: bool = False):
     g = np.empty((4, op.lat.V, 3, 3), dtype=np.complex128)
     for mu in range(4):
         n = op.lat.neighbor(mu, k)
-        eta = op.lat.eta(mu)[:, None, None]
+        # the hop through U_mu(x) carries the boundary factor of x + k mu
+        eta = (op.lat.eta(mu) * op.boundary_phase(mu, k))[:, None, None]
         outer = np.einsum("xa,xb->xab", y, np.conj(x[n])) - np.einsum("xa,xb->xab", x, np.conj(y[n]))
         g[mu] = -c * eta * outer
     return g

@@ -118,7 +118,7 @@ class MultigridSolver:
         self.p = params
         op1 = op
         if params.truncate_naik and op.naik is not None:
-            op1 = Staggered(op.lat, op.fat, None, 0.0, op.mass)
+            op1 = Staggered(op.lat, op.fat, None, 0.0, op.mass, bc_t=op.bc_t)
         self.kd = KahlerDirac(op1)                # (B+m)^{-1}: distance-one hops only
         self.levels = [FineLevelOp(self.kd)]      # level 1 operator A (or A')
         self.raw = [self.levels[0]]              # operator the near-null CGNE uses, per level

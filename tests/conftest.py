@@ -13,20 +13,22 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
-LATE_MODULES = ("test_gpu_solve_coarse_forms.py",)
+LATE_MODULES = ("test_gpu_solve_coarse_forms.py", "test_gpu_boundary.py")
+LAST_MODULES = ("test_zz_no_alloc.py",)
 
 
 def pytest_collection_modifyitems(config, items):
-    """The coarse-level form tests (the newest GPU paths) run after the rest of
-    the suite, so that under -x a failure there cannot hide the results of the
-    established tests."""
+    """The coarse-level form and boundary-condition tests (the newest GPU
+    paths) run after the rest of the suite, so that under -x a failure there
+    cannot hide the results of the established tests; the no-allocation entry
+    point's test runs after everything else."""
     def module(it):
         path = getattr(it, "path", None)
         return path.name if path is not None else os.path.basename(str(it.fspath))
 
-    late = [it for it in items if module(it) in LATE_MODULES]
-    if late:
-        items[:] = [it for it in items if module(it) not in LATE_MODULES] + late
+    rank = {m: 1 for m in LATE_MODULES}
+    rank.update({m: 2 for m in LAST_MODULES})
+    items[:] = sorted(items, key=lambda it: rank.get(module(it), 0))   # stable: file order within a rank
 
 
 @pytest.fixture(scope="session")
