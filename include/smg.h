@@ -159,8 +159,23 @@ SMG_API int smg_set_stream(smg_ctx* ctx, void* stream);
 /* ------------------------------------------------------------------ problem */
 /* Sec. 2.2 / 3.1: fat links (distance 1) and optional Naik links (distance 3,
  * NULL for the naive operator) with coefficient c_naik.  Copies the links;
- * invalidates the KD blocks and the multigrid setup. */
+ * invalidates the KD blocks and the multigrid setup.  The time boundary set
+ * by smg_set_boundary applies to these links. */
 SMG_API int smg_set_gauge(smg_ctx* ctx, const void* fat, const void* naik, double c_naik, int where);
+/* Boundary conditions of the fermion field: flags 0 = periodic in all four
+ * directions (default), SMG_BC_T_ANTIPERIODIC = psi(x + L_t t) = -psi(x),
+ * the hops that wrap around the time extent carry -1.  The paper does not
+ * state its boundary conditions; the antiperiodic time boundary is the usual
+ * one for propagators.  Implemented on the stored links: smg_set_gauge
+ * negates the time links whose hop wraps (fat links on the last time slice,
+ * Naik links on the last three), which leaves the KD blocks (no block holds a
+ * wrapping hop) and every kernel unchanged; smg_force returns the gradient
+ * with respect to the links the caller passed.  Takes effect at the next
+ * smg_set_gauge (the current gauge field, KD blocks and setup are dropped:
+ * smg_set_gauge and smg_mg_setup must follow).  SMG_ERR_ARG on unknown
+ * flags. */
+enum { SMG_BC_T_ANTIPERIODIC = 1 };
+SMG_API int smg_set_boundary(smg_ctx* ctx, int flags);
 /* M = m + D with the given real mass.  Rebuilds the KD blocks (B+m)^{-1}
  * (Sec. 3.1); keeps the near-null vectors and the coarse operators, which
  * stay those of the mass they were built with (Sec. 3.2: operators from the

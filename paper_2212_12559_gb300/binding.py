@@ -19,6 +19,7 @@ SMG_HOST, SMG_DEVICE = 0, 1
 PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 OP_M, OP_MDAG, OP_KD, OP_KDDAG, OP_A, OP_ADAG = range(6)
 K_DSLASH, K_KD, K_RESTRICT, K_PROLONG, K_COARSE, K_A, K_COARSE_SOLVE = range(7)
+BC_T_ANTIPERIODIC = 1
 MAX_COARSE = 3
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_STATE",
           -5: "ERR_NOT_CONVERGED", -6: "ERR_BREAKDOWN", -7: "ERR_TIMEOUT"}
@@ -31,7 +32,8 @@ EXPORTS = ["smg_default_params", "smg_create", "smg_destroy", "smg_last_error", 
            "smg_bench_coarse_apply", "smg_multishift_cg", "smg_propagators", "smg_persist_plan",
            "smg_get_coarse_xinv", "smg_get_deflation", "smg_coarse_solve", "smg_save_setup", "smg_load_setup",
            "smg_coarse_apply_stencil", "smg_coarse_paths", "smg_tune_mode", "smg_tune_table", "smg_tune_save",
-           "smg_tune_load", "smg_tune_clear", "smg_debug_persist_barrier", "smg_setup_times"]
+           "smg_tune_load", "smg_tune_clear", "smg_debug_persist_barrier", "smg_setup_times",
+           "smg_set_boundary"]
 
 
 class MGParams(ctypes.Structure):
@@ -125,6 +127,7 @@ def load(path: str = LIB_PATH):
         "smg_force": (i, [vp, vp, vp, i, vp, i]),
         "smg_setup_iterations": (i, [vp, i, ip]),
         "smg_setup_times": (i, [vp, i, ctypes.POINTER(d)]),
+        "smg_set_boundary": (i, [vp, i]),
         "smg_time_kernel": (i, [vp, i, i, i, i, ctypes.POINTER(d)]),
         "smg_kernel_launches": (ctypes.c_longlong, []),
         "smg_fermion_action": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
@@ -303,6 +306,11 @@ class Solver:
 
     def set_mass(self, m):
         self._check(self.lib.smg_set_mass(self.ctx, float(m)))
+
+    def set_boundary(self, antiperiodic_t=False):
+        """Time boundary of the fermion field (periodic or antiperiodic); call
+        set_gauge (and mg_setup) again afterwards."""
+        self._check(self.lib.smg_set_boundary(self.ctx, BC_T_ANTIPERIODIC if antiperiodic_t else 0))
 
     def set_stream(self, stream_handle):
         self._check(self.lib.smg_set_stream(self.ctx, ctypes.c_void_p(stream_handle)))

@@ -156,6 +156,19 @@ int smg_set_gauge(smg_ctx* ctx, const void* fat, const void* naik, double c_naik
   });
 }
 
+int smg_set_boundary(smg_ctx* ctx, int flags) {
+  return guarded(ctx, [&](smg::Context& c) {
+    SMG_REQUIRE(flags == 0 || flags == SMG_BC_T_ANTIPERIODIC, "set_boundary: unknown flags");
+    c.bc_t = (flags & SMG_BC_T_ANTIPERIODIC) ? -1 : 1;
+    c.engine.reset();
+    c.gauge_set = false;
+    c.kd_valid = false;
+    c.setup_done = false;
+    c.coarse.clear();
+    return SMG_OK;
+  });
+}
+
 int smg_set_mass(smg_ctx* ctx, double mass) {
   return guarded(ctx, [&](smg::Context& c) {
     smg::ctx_set_mass(c, mass);
@@ -366,7 +379,7 @@ int smg_force(smg_ctx* ctx, const void* X, const void* Y, int which, void* F, in
     smg::upload(b, X, nv, where, c.stream);
     smg::upload(b + nv, Y, nv, where, c.stream);
     smg::force_outer((double2*)(b + 2 * nv), (const double2*)b, (const double2*)(b + nv), c.g, which ? 3 : 1,
-                     which ? c.c_naik : 1.0, c.stream);
+                     which ? c.c_naik : 1.0, c.bc_t, c.stream);
     smg::download(F, b + 2 * nv, nf, where, c.stream);
     SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
     return SMG_OK;

@@ -23,7 +23,7 @@ __global__ void site_maps_kernel(int* parity, int* kd_block, int* kd_pos, int* a
 
 // F_mu(x)[a][b] = -c eta_mu(x) ( Y_a(x) conj(X_b(x+k mu)) - X_a(x) conj(Y_b(x+k mu)) )
 __global__ void force_kernel(double2* __restrict__ F, const double2* __restrict__ X, const double2* __restrict__ Y,
-                             Geom g, int k, double coef) {
+                             Geom g, int k, double coef, int bc_t) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= 4LL * g.V * 9) return;
   const int ab = (int)(e % 9);
@@ -34,13 +34,26 @@ __global__ void force_kernel(double2* __restrict__ F, const double2* __restrict_
   g.coords(x, c);
   int es = 0;
   for (int nu = 0; nu < mu; ++nu) es += c[nu];
-  const double eta = (es & 1) ? -1.0 : 1.0;
+  double eta = (es & 1) ? -1.0 : 1.0;
+  if (mu == 3 && bc_t < 0 && c[3] + k >= g.L[3]) eta = -eta;   // the hop wraps around the time boundary
   const int xn = g.shift(c, mu, k);
   const double2 ya = Y[(size_t)x * 3 + a], xb = X[(size_t)xn * 3 + b];
   const double2 xa = X[(size_t)x * 3 + a], yb = Y[(size_t)xn * 3 + b];
   double2 t1 = cmul(ya, make_double2(xb.x, -xb.y));
   double2 t2 = cmul(xa, make_double2(yb.x, -yb.y));
   F[e] = make_double2(-coef * eta * (t1.x - t2.x), -coef * eta * (t1.y - t2.y));
+}
+
+// time links (mu = 3) of the sites with x_t + k >= L_t change sign
+__global__ void boundary_flip_kernel(double2* __restrict__ links, Geom g, int k) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)g.V * 9) return;
+  const int x = (int)(e / 9);
+  int c[4];
+  g.coords(x, c);
+  if (c[3] + k < g.L[3]) return;
+  double2* p = links + (size_t)3 * g.V * 9 + (size_t)e;
+  *p = make_double2(-p->x, -p->y);
 }
 
 __global__ void eps_mul_kernel(double2* out, const double2* in, Geom g) {   // may run in place
@@ -66,8 +79,14 @@ void site_maps(int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_p
   SMG_LAUNCH_OK();
 }
 
-void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, int k, double c, cudaStream_t st) {
-  force_kernel<<<ceil_div(4LL * g.V * 9, 256), 256, 0, st>>>(F, X, Y, g, k, c);
+void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, int k, double c, int bc_t,
+                 cudaStream_t st) {
+  force_kernel<<<ceil_div(4LL * g.V * 9, 256), 256, 0, st>>>(F, X, Y, g, k, c, bc_t);
+  SMG_LAUNCH_OK();
+}
+
+void boundary_flip_time(double2* links, const Geom& g, int k, cudaStream_t st) {
+  boundary_flip_kernel<<<ceil_div((long long)g.V * 9, 256), 256, 0, st>>>(links, g, k);
   SMG_LAUNCH_OK();
 }
 

@@ -191,9 +191,13 @@ void site_maps(int* parity, int* kd_block, int* kd_pos, int* agg_idx, int* agg_p
                const int agg[4], cudaStream_t st);
 
 // ------------------------------------------------------- fermion force
-// F_mu(x) = -c eta_mu(x) [ Y(x) X(x+k mu)^dag - X(x) Y(x+k mu)^dag ]
-void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, int k, double c,
+// F_mu(x) = -c eta_mu(x) b_mu(x) [ Y(x) X(x+k mu)^dag - X(x) Y(x+k mu)^dag ], with b_mu(x) = -1
+// for the time links whose hop wraps around an antiperiodic time boundary (bc_t = -1), else 1
+void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, int k, double c, int bc_t,
                  cudaStream_t st);
+// Antiperiodic time boundary on FP64 links [4][V][3][3]: negates the time
+// links of the sites whose hop of length k wraps around (x_t + k >= L_t).
+void boundary_flip_time(double2* links, const Geom& g, int k, cudaStream_t st);
 // out = eps(x) in, eps(x) = (-1)^(x+y+z+t) (Sec. 2.2), one FP64 colour field
 void eps_mul(double2* out, const double2* in, const Geom& g, cudaStream_t st);
 

@@ -944,6 +944,13 @@ void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik,
   } else {
     c.naik64.release();
   }
+  // antiperiodic time boundary: the hops that wrap around the time extent
+  // carry -1, i.e. the wrapping time links change sign (fat: the last time
+  // slice, Naik: the last three); every operator built from the links follows
+  if (c.bc_t < 0) {
+    boundary_flip_time(c.fat64.as<double2>(), c.g, 1, c.stream);
+    if (c.has_naik) boundary_flip_time(c.naik64.as<double2>(), c.g, 3, c.stream);
+  }
   c.fat64_st = Stored{c.fat64.p, nullptr, 1.0f, S64};
   c.naik64_st = Stored{c.naik64.p, nullptr, 1.0f, S64};
   // lower-precision copies; FP16 links carry one global scale (max |entry|)

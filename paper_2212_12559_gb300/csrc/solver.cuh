@@ -121,6 +121,7 @@ struct Context {
   // gauge field
   bool gauge_set = false, has_naik = false;
   double c_naik = 0.0;
+  int bc_t = 1;               // time boundary: 1 periodic, -1 antiperiodic (smg_set_boundary)
   DevBuf fat64, naik64;
   StoredBuf fat32, naik32, fat16, naik16;
   StoredBuf hop32, hop16;     // phase-folded link copies (hop.cu)
