@@ -1,5 +1,8 @@
 // Lattice maps (exported for bit-exact checks) and the fermion-force
 // outer-product kernel.
+#include <algorithm>
+#include <cstring>
+
 #include "ops.cuh"
 
 namespace smg {
@@ -56,6 +59,26 @@ __global__ void boundary_flip_kernel(double2* __restrict__ links, Geom g, int k)
   *p = make_double2(-p->x, -p->y);
 }
 
+// largest |Re|, |Im| (float bits, non-negative, so the integer maximum is the float maximum)
+__global__ void __launch_bounds__(256) absmax_kernel(const float2* __restrict__ v, long long n, unsigned* mx) {
+  __shared__ float red[8];
+  float m = 0.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf(v[e].x), fabsf(v[e].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    atomicMax(mx, __float_as_uint(m));
+  }
+}
+
+__global__ void pack_h16_kernel(__half2* __restrict__ dst, const float2* __restrict__ src, long long n, float sc) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = __floats2half2_rn(src[e].x / sc, src[e].y / sc);
+}
+
 __global__ void eps_mul_kernel(double2* out, const double2* in, Geom g) {   // may run in place
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.V * 3) return;
@@ -83,6 +106,27 @@ void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, 
                  cudaStream_t st) {
   force_kernel<<<ceil_div(4LL * g.V * 9, 256), 256, 0, st>>>(F, X, Y, g, k, c, bc_t);
   SMG_LAUNCH_OK();
+}
+
+float pack_fp16_global(__half2* dst, const float2* src, long long n, cudaStream_t st) {
+  struct Word {
+    unsigned* p = nullptr;
+    ~Word() { if (p) cudaFree(p); }
+  } mb;
+  SMG_CUDA_OK(cudaMalloc(&mb.p, sizeof(unsigned)));
+  SMG_CUDA_OK(cudaMemsetAsync(mb.p, 0, sizeof(unsigned), st));
+  const unsigned grid = (unsigned)std::min<long long>(1216, std::max<long long>(1, (n + 255) / 256));
+  absmax_kernel<<<grid, 256, 0, st>>>(src, n, mb.p);
+  SMG_LAUNCH_OK();
+  unsigned bits = 0;
+  SMG_CUDA_OK(cudaMemcpyAsync(&bits, mb.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  SMG_CUDA_OK(cudaStreamSynchronize(st));
+  float mx = 0.f;
+  std::memcpy(&mx, &bits, sizeof(float));
+  const float sc = mx > 0 ? mx : 1.f;
+  pack_h16_kernel<<<grid, 256, 0, st>>>(dst, src, n, sc);
+  SMG_LAUNCH_OK();
+  return sc;
 }
 
 void boundary_flip_time(double2* links, const Geom& g, int k, cudaStream_t st) {

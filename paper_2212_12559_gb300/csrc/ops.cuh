@@ -198,6 +198,9 @@ void force_outer(double2* F, const double2* X, const double2* Y, const Geom& g, 
 // Antiperiodic time boundary on FP64 links [4][V][3][3]: negates the time
 // links of the sites whose hop of length k wraps around (x_t + k >= L_t).
 void boundary_flip_time(double2* links, const Geom& g, int k, cudaStream_t st);
+// FP16 copy of n FP32 complex numbers with one global scale: returns
+// sc = max |Re|, |Im| (1 when all are zero) and writes dst = src / sc.
+float pack_fp16_global(__half2* dst, const float2* src, long long n, cudaStream_t st);
 // out = eps(x) in, eps(x) = (-1)^(x+y+z+t) (Sec. 2.2), one FP64 colour field
 void eps_mul(double2* out, const double2* in, const Geom& g, cudaStream_t st);
 

@@ -959,19 +959,9 @@ void ctx_set_gauge(Context& c, const void* fat, const void* naik, double c_naik,
     Vec a; a.p = s64.p; a.n = (long long)nl; a.prec = P64;
     Vec b; b.p = d32.v.p; b.n = (long long)nl; b.prec = P32;
     blas_copy(b, a, c.stream);
-    // FP16 from FP32 with global scale = max |entry|
-    std::vector<float2> h(nl);
-    SMG_CUDA_OK(cudaMemcpyAsync(h.data(), d32.v.p, nl * sizeof(float2), cudaMemcpyDeviceToHost, c.stream));
-    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
-    float mx = 0.f;
-    for (auto& v : h) mx = std::fmax(mx, std::fmax(std::fabs(v.x), std::fabs(v.y)));
-    const float sc = mx > 0 ? mx : 1.f;
-    std::vector<__half2> hh(nl);
-    for (size_t i = 0; i < nl; ++i) hh[i] = __floats2half2_rn(h[i].x / sc, h[i].y / sc);
+    // FP16 from FP32 with global scale = max |entry| (device reduction and pack)
     d16.alloc(S16, nl, 0);
-    d16.st.gscale = sc;
-    SMG_CUDA_OK(cudaMemcpyAsync(d16.v.p, hh.data(), nl * sizeof(__half2), cudaMemcpyHostToDevice, c.stream));
-    SMG_CUDA_OK(cudaStreamSynchronize(c.stream));
+    d16.st.gscale = pack_fp16_global((__half2*)d16.v.p, (const float2*)d32.v.p, (long long)nl, c.stream);
   };
   make_lp(c.fat64, c.fat32, c.fat16);
   if (c.has_naik) make_lp(c.naik64, c.naik32, c.naik16);
