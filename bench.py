@@ -4,7 +4,9 @@ Default workload (N=1): 32^4 lattice, naive staggered operator on seeded
 synthetic links Proj_SU3(exp(0.3 i H)), mass 0.001, twelve Gaussian
 right-hand sides solved together by one smg_multi_solve per step; K-cycle
 multigrid with Table 1's two coarsenings (4^4 then 2^4 aggregates, 64 / 32
-near-null vectors from 1000 CGNE iterations), FP32 arithmetic with FP16
+near-null vectors from 1000 CGNE iterations) and an SVD-deflated Chebyshev
+CA-GCR coarsest level (48 singular vectors), level-1 inner GCR to 0.05 or
+16 iterations and Table 1's 0.25 or 8 below it, FP32 arithmetic with FP16
 storage of links, KD blocks, near-null vectors and coarse stencils (the
 12-system coarse apply on the tensor cores), FP64 outer GCR.  Other
 workloads: --config 1 (8^4, FP64), 2 (16^4 HISQ-shaped), 4 (24^3 x 48
