@@ -587,10 +587,14 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f16 storage, f64 outer" if c["precision"] == "mixed" else "f64", "data": "synthetic",
+            "dtype": "f32" if c["precision"] == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[cfg], "dims": list(c["dims"]), "systems_per_step": nsys,
                        "masses": [float(m) for m in masses], "nvec": c["nvec"], "agg": [list(a) for a in c["agg"]],
-                       "precision": c["precision"], "inner": [p.inner_tol, p.inner_maxiter],
+                       "precision": c["precision"],
+                       "storage": ("FP16 links, KD blocks, near-null vectors and coarse stencils (FP32 scales); "
+                                   "FP32 preconditioner vectors; FP64 outer GCR and true residuals")
+                       if c["precision"] == "mixed" else "FP64 throughout",
+                       "inner": [p.inner_tol, p.inner_maxiter],
                        "coarse_inner": [p.coarse_inner_tol or p.inner_tol, p.coarse_inner_maxiter or p.inner_maxiter],
                        "setup_maxiter": p.setup_maxiter, "cuda_graph": bool(args.graph),
                        "l2": "flushed (512 MB write) before every timed step", "setup_s": t_setup,
